@@ -1,0 +1,186 @@
+/*
+ * rsvd.h -- C ABI of the GB300 randomized low-rank decomposition library.
+ *
+ * Problem statement (arXiv:2307.15572, "Randomized matrix decompositions"
+ * paragraph, Eq. (1) and Fig. 1): given a dense matrix V (N x N) -- here a
+ * symmetric channel block of an interaction -- and either a target rank
+ * R_SVD with oversampling p = l - R_SVD, or a relative tolerance, return
+ * the leading singular triplets  V ~ L_k Sigma_k R_k^T.  The method is the
+ * randomized SVD the paper takes from Halko, Martinsson & Tropp (2011):
+ *   1. Z = V P with a random P (N x l); orthonormal Q with Z = Q X;
+ *      optional subspace iteration (q rounds, re-orthogonalised);
+ *   2. Y = Q^T V and its thin SVD  Y = L_Y Sigma R^T;
+ *   3. L = Q L_Y.
+ * Channels of a block-diagonal matrix ("Low-rank interactions" paragraph:
+ * one block per J^Pi T channel, sizes 7650..40050) are independent and are
+ * decomposed together by rsvd_decompose_batched.
+ *
+ * Conventions shared by every entry point:
+ *   - Plain C types only; every pointer argument says whether it is a host or
+ *     a device pointer.  Dense matrices are FP64.  Because V is symmetric,
+ *     row-major and column-major storage coincide; `ld` is the distance in
+ *     elements between consecutive rows (= columns), ld >= n.
+ *   - Factors are column-major: U[i + j*ldu] is row i of column j.
+ *   - The caller owns all input and output buffers.  The plan owns its
+ *     device workspace (allocated with cudaMalloc when the plan is created
+ *     or first needs more; freed by rsvd_plan_destroy).
+ *   - Errors are returned as rsvd_status; no C++ exception crosses this ABI.
+ *     rsvd_last_error_string() gives a thread-local description of the last
+ *     failure.  Negative = error, 0 = OK, positive = warning (result valid).
+ *   - Input is never modified.  Work runs on the plan's CUDA stream; the
+ *     decomposition calls return after that stream has finished the work
+ *     (they read the chosen rank and status words back), so outputs are
+ *     ready when they return.
+ */
+#ifndef RSVD_H
+#define RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSVD_OK = 0,
+  RSVD_WARN_SHIFTED_CQR = 1,    /* a Cholesky breakdown was repaired by a shift  */
+  RSVD_WARN_RANK_CAPPED = 2,    /* l = k + p was clamped to n                      */
+  RSVD_ERR_INVALID_ARG = -1,    /* bad size, pointer, enum or leading dimension    */
+  RSVD_ERR_CUDA = -2,           /* a CUDA runtime/driver call failed               */
+  RSVD_ERR_OOM = -3,            /* workspace allocation failed                     */
+  RSVD_ERR_NONFINITE = -4,      /* NaN or Inf found in the input                   */
+  RSVD_ERR_NOT_CONVERGED = -5,  /* Jacobi sweep cap reached                        */
+  RSVD_ERR_TOL_NOT_MET = -6,    /* tolerance not reached within l_max columns;
+                                   the best factors found are still returned      */
+  RSVD_ERR_TIMEOUT = -7,        /* a bounded device-side wait gave up              */
+  RSVD_ERR_UNSUPPORTED = -8     /* combination not built (reported, never faked)   */
+} rsvd_status;
+
+/* Arithmetic of the passes over V. */
+typedef enum {
+  RSVD_PREC_FP64 = 0,   /* every step in FP64 (CUDA cores); the accuracy reference path */
+  RSVD_PREC_BF16X = 1   /* V split into `slices` BF16 words, tcgen05 tensor-core passes
+                           with FP32 accumulation; FP64 Gram/Cholesky (compensated)      */
+} rsvd_precision;
+
+/* How the rank is chosen. */
+typedef enum {
+  RSVD_RANK_FIXED = 0,    /* R_SVD = k, l = k + p (paper's setting)                      */
+  RSVD_RANK_TOL = 1,      /* l = k + p columns drawn, R_SVD = smallest rank meeting tol  */
+  RSVD_RANK_ADAPTIVE = 2, /* blocks of block_b columns until tol is met (randQB_EI)      */
+  RSVD_RANK_LEARNED = 3   /* per-channel l from the rank model, checked, adaptive fallback */
+} rsvd_rank_policy;
+
+typedef struct {
+  int64_t n_max;        /* largest channel size the plan will be given (>= 1)            */
+  int32_t k;            /* FIXED: rank R_SVD; TOL/LEARNED: cap on the rank (0 = l)       */
+  int32_t p;            /* oversampling p = l - R_SVD (>= 0; paper uses 5)               */
+  int32_t q;            /* subspace-iteration rounds (>= 0; paper uses 0)                */
+  double tol;           /* relative Frobenius tolerance for TOL/ADAPTIVE/LEARNED (> 0)  */
+  int32_t l_max;        /* cap on columns drawn (ADAPTIVE/LEARNED fallback; 0 = 1024)    */
+  int32_t block_b;      /* ADAPTIVE block size (0 = 32)                                   */
+  int32_t precision;    /* rsvd_precision                                                 */
+  int32_t slices;       /* BF16X: BF16 words per FP64 entry for the passes (1..3; 0 = 2) */
+  int32_t rank_policy;  /* rsvd_rank_policy                                               */
+  int32_t rayleigh_ritz;/* 1: symmetric Rayleigh-Ritz small problem (T = Q^T V Q)         */
+  uint64_t seed;        /* Philox key of the random projection P                          */
+  void* stream;         /* cudaStream_t to run on (NULL = legacy default stream)          */
+  const float* mlp_weights; /* LEARNED: device pointer to the rank-model parameter blob   */
+} rsvd_opts;
+
+typedef struct rsvd_plan_s* rsvd_plan_t;
+
+typedef enum {
+  RSVD_DENSE_F64 = 0,   /* stored matrix                                            */
+  RSVD_TILE_RULE = 1    /* entries from the Gaussian-bump rule, generated on device */
+} rsvd_matrix_kind;
+
+typedef enum { RSVD_MEM_DEVICE = 0, RSVD_MEM_HOST = 1 } rsvd_mem;
+
+/*
+ * A channel matrix.  DENSE_F64: `data` is an n x n symmetric FP64 matrix with
+ * leading dimension ld >= n, in device memory (mem = DEVICE) or host memory
+ * (mem = HOST; page-locked memory gives overlapped copies).  The library
+ * does not check symmetry.
+ * TILE_RULE: entries A_ij = sum_m w_m g_m(x_i) g_m(x_j) + eta_ij with
+ * x_i = 8 i/(n-1), g_m(x) = exp(-(x-c_m)^2/(2 s_m^2)) and eta the symmetric
+ * hash noise of amplitude rule_eta (see rsvd_rule_entry); rule_c, rule_s,
+ * rule_w are HOST arrays of rule_m values.  The matrix is never stored.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t mem;
+  int64_t n;
+  const double* data;
+  int64_t ld;
+  int32_t rule_m;
+  const double* rule_c;
+  const double* rule_s;
+  const double* rule_w;
+  double rule_eta;
+  uint64_t rule_seed;
+} rsvd_matrix;
+
+/*
+ * Output factors of one channel, caller-owned.  U (n x k_cap, ldu >= n),
+ * V (n x k_cap, ldv >= n) and S (k_cap) are FP64, in device memory
+ * (mem = DEVICE) or host memory (mem = HOST).  Any of U, V may be NULL to
+ * skip it.  On return: k_out = rank kept (<= k_cap; singular values in S
+ * are descending and the pair (U_i, V_i) is sign-fixed so that the
+ * largest-magnitude entry of U_i is positive), l_used = columns drawn,
+ * err_est = estimated relative Frobenius error of the rank-k_out factors,
+ * status = this channel's rsvd_status.
+ */
+typedef struct {
+  int32_t mem;
+  double* U;
+  int64_t ldu;
+  double* S;
+  double* V;
+  int64_t ldv;
+  int32_t k_cap;
+  int32_t k_out;
+  int32_t l_used;
+  double err_est;
+  int32_t status;
+} rsvd_factors;
+
+/* Create a plan.  Checks the options (RSVD_ERR_INVALID_ARG on a bad value)
+ * and allocates the fixed part of the device workspace.  *out is NULL on
+ * failure. */
+rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* opts);
+
+/* Free the plan and its workspace.  NULL is ignored. */
+void rsvd_plan_destroy(rsvd_plan_t plan);
+
+/* Decompose one channel: equivalent to rsvd_decompose_batched with C = 1. */
+rsvd_status rsvd_decompose(rsvd_plan_t plan, const rsvd_matrix* A, rsvd_factors* f);
+
+/* Decompose C independent channels (C >= 1) of possibly different sizes in
+ * grouped launches: every kernel of the pipeline covers all channels at once.
+ * per_item (host, C entries, may be NULL) receives each channel's status,
+ * which is also stored in f[c].status.  Returns the worst status (the most
+ * negative error if any, else the largest warning, else RSVD_OK). */
+rsvd_status rsvd_decompose_batched(rsvd_plan_t plan, int32_t C, const rsvd_matrix* A,
+                                   rsvd_factors* f, rsvd_status* per_item);
+
+/* Exact relative residual ||A - U diag(S) V^T||_F / ||A||_F of the rank-f->k_out
+ * factors, accumulated in FP64 over every entry (tile rules are regenerated).
+ * *rel_err is a host pointer. */
+rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
+                                   const rsvd_factors* f, double* rel_err);
+
+/* Device buffer size (bytes) the plan holds now. */
+int64_t rsvd_plan_workspace_bytes(rsvd_plan_t plan);
+
+/* Thread-local text of the last error ("" if none). */
+const char* rsvd_last_error_string(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t rsvd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSVD_H */

@@ -1,0 +1,844 @@
+// C ABI of the library: plan, grouped decomposition of channel blocks,
+// exact residual.  Host-side orchestration only; all arithmetic of the
+// method runs in the kernels (k_*.cu).
+//
+// Pipeline per batch (every launch covers all channels):
+//   FP64 path  (every step in FP64 on CUDA cores)
+//     X = P (Philox, Fig. 1 step 1)          Y = V X
+//     Q = CholeskyQR2(Y)                     [Z = Q X of step 1]
+//     q rounds: Y = V Q, Q = CQR2(Y); Y = V Q, Q = CQR2(Y)
+//     W = V Q  (= Y^T of step 1', V symmetric)
+//     W = Q2 R (CQR2, R accumulated), R^T = X Sigma J^T (one-sided Jacobi)
+//     so Y^T-SVD: L_Y = X, R_paper = Q2 J; rank k; L = Q X_k (step 3), R = Q2 J_k
+//   mixed path (passes over V on tensor cores, V and X as BF16 words)
+//     V -> words (+ ||V||^2);  P -> BF16;  Y = V P (tcgen05)
+//     Q = CQR2(Y) with compensated (Dot2) Grams, FP64 Cholesky, FP32 solve
+//     q rounds as above; [W | V G] = V [Q | G]  (G = 16 probe columns)
+//     W^T W = R^T R (Dot2 Gram, FP64 Cholesky); Jacobi on R^T -> X, Sigma
+//     rank from the probe estimate; L = Q X_k, R_paper = W X_k Sigma_k^{-1}
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "tc_gemm.h"
+
+using namespace rsvd;
+
+namespace {
+
+thread_local char g_err[1024] = "";
+
+rsvd_status seterr(rsvd_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return seterr(e_ == cudaErrorMemoryAllocation ? RSVD_ERR_OOM : RSVD_ERR_CUDA, "%s: %s", \
+                    #call, cudaGetErrorString(e_));                                          \
+  } while (0)
+
+inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+constexpr int NPROBE = 16;
+constexpr int NSM = 152;
+
+}  // namespace
+
+struct rsvd_plan_s {
+  rsvd_opts o;
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  char* hp = nullptr;      // pinned host staging
+  size_t hp_cap = 0;
+  int* d_err = nullptr;    // device error word
+  int slices = 2;
+};
+
+namespace {
+
+// Bump allocator over the workspace; base == nullptr only measures.
+struct Bump {
+  char* base;
+  size_t off = 0;
+  explicit Bump(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+// Descriptor arena: built on the host, uploaded once, referenced by kernels.
+struct Arena {
+  std::vector<char> h;
+  char* dbase = nullptr;
+  template <class T>
+  T* put(const T* src, size_t n, size_t align = 64) {
+    size_t o = (h.size() + align - 1) & ~(align - 1);
+    h.resize(o + n * sizeof(T));
+    memcpy(h.data() + o, src, n * sizeof(T));
+    return (T*)(dbase + o);
+  }
+};
+
+rsvd_status grow_pinned(rsvd_plan_s* P, size_t bytes) {
+  if (bytes <= P->hp_cap) return RSVD_OK;
+  if (P->hp) cudaFreeHost(P->hp);
+  P->hp = nullptr;
+  P->hp_cap = 0;
+  size_t cap = std::max(bytes, (size_t)1 << 20);
+  CK(cudaHostAlloc((void**)&P->hp, cap, cudaHostAllocDefault));
+  P->hp_cap = cap;
+  return RSVD_OK;
+}
+
+rsvd_status grow_ws(rsvd_plan_s* P, size_t bytes) {
+  if (bytes <= P->ws_cap) return RSVD_OK;
+  CK(cudaStreamSynchronize(P->st));
+  if (P->ws) cudaFree(P->ws);
+  P->ws = nullptr;
+  P->ws_cap = 0;
+  size_t cap = rup((int64_t)bytes, (int64_t)1 << 21);
+  CK(cudaMalloc((void**)&P->ws, cap));
+  P->ws_cap = cap;
+  return RSVD_OK;
+}
+
+// Split a tile count over k so that the grid covers the GPU a couple of times.
+int pick_splits(int64_t tiles, int64_t k, int min_chunk) {
+  if (tiles >= 2 * NSM) return 1;
+  int ks = (int)((2 * NSM + tiles - 1) / tiles);
+  int maxk = (int)std::max<int64_t>(1, k / min_chunk);
+  return std::max(1, std::min(ks, maxk));
+}
+
+struct ChanDims {
+  int n, l, lw, s, kcap, gsplit;
+  int64_t ldt, ldb;
+};
+
+// Everything one batched call needs.
+struct Job {
+  rsvd_plan_s* P;
+  int C;
+  const rsvd_matrix* A;
+  rsvd_factors* f;
+  bool mixed;
+  bool measure = true;       // first layout pass: sizes only, no device pointers
+  int q, nsl, policy;
+  double tol;
+  std::vector<ChanDims> d;
+  std::vector<Chan> ch;              // host copies of the descriptors
+  std::vector<std::function<rsvd_status()>> steps;
+  Arena ar;
+  Chan* d_ch = nullptr;
+  ChanResult* d_res = nullptr;
+  int max_l = 0, max_lw = 0, max_kcap = 0;
+};
+
+// Per-batch tile offsets (prefix sums) uploaded through the arena.
+const int* offsets(Job& J, const std::function<int64_t(int)>& per) {
+  std::vector<int> off(J.C + 1, 0);
+  for (int c = 0; c < J.C; ++c) off[c + 1] = off[c] + (int)per(c);
+  return J.ar.put(off.data(), off.size());
+}
+int total_of(Job& J, const std::function<int64_t(int)>& per) {
+  int64_t t = 0;
+  for (int c = 0; c < J.C; ++c) t += per(c);
+  return (int)t;
+}
+
+// ------------------------------------------------------------ step builders
+void add_mm(Job& J, MMKind kind, const std::vector<MMDesc>& md) {
+  std::vector<int> off(J.C + 1, 0);
+  for (int c = 0; c < J.C; ++c) off[c + 1] = off[c] + md[c].mt * md[c].nt * md[c].ks;
+  const int tiles = off[J.C];
+  const MMDesc* dmd = J.ar.put(md.data(), md.size());
+  const int* doff = J.ar.put(off.data(), off.size());
+  cudaStream_t st = J.P->st;
+  const int C = J.C;
+  J.steps.push_back([=]() {
+    launch_tile_mm(kind, dmd, doff, C, tiles, st);
+    return RSVD_OK;
+  });
+}
+
+// Gram-like TN product with split partials and fixed-order reduction:
+// out_c (m x n, ld m) = A_c^T B_c over n_c rows.
+void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::function<const void*(int)> Bp,
+            std::function<double*(int)> outp, std::function<int(int)> mcols, std::function<int(int)> ncols,
+            bool sym) {
+  std::vector<MMDesc> md(J.C);
+  std::vector<double*> outs(J.C);
+  int max_elems = 1;
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc m{};
+    m.A = Ap(c); m.lda = d.ldt;
+    m.B = Bp(c); m.ldb = d.ldt;
+    m.m = mcols(c); m.n = ncols(c); m.k = d.n;
+    m.mt = cdiv(m.m, 64); m.nt = cdiv(m.n, 64);
+    m.ks = d.gsplit;
+    m.kchunk = (int)rup(cdiv(d.n, d.gsplit), 16);
+    m.ks = cdiv(d.n, m.kchunk);
+    m.mode = MM_PARTIAL;
+    m.sym = sym ? 1 : 0;
+    m.Cm = J.ch[c].gpart;
+    m.ldc = m.m;
+    m.pstride = (int64_t)m.m * m.n;
+    md[c] = m;
+    outs[c] = outp(c);
+    max_elems = std::max(max_elems, m.m * m.n);
+  }
+  add_mm(J, kind, md);
+  const MMDesc* dmd = J.ar.put(md.data(), md.size());
+  double* const* douts = J.ar.put(outs.data(), outs.size());
+  cudaStream_t st = J.P->st;
+  const int C = J.C;
+  J.steps.push_back([=]() {
+    launch_reduce_partials(dmd, douts, C, max_elems, st);
+    return RSVD_OK;
+  });
+}
+
+void add_chol(Job& J, int accumulate) {
+  const Chan* dch = J.d_ch;
+  const int C = J.C, maxl = J.max_l;
+  cudaStream_t st = J.P->st;
+  J.steps.push_back([=]() {
+    launch_chol_inv(dch, C, accumulate, maxl, st);
+    return RSVD_OK;
+  });
+}
+
+// ---------------------------------------------------------------- FP64 path
+// CholeskyQR2 of src (n x l, FP64) using tmp; result back in src.
+void cqr2_f64(Job& J, std::function<double*(int)> src, std::function<double*(int)> tmp, bool acc_R) {
+  for (int round = 0; round < 2; ++round) {
+    auto in = round == 0 ? src : tmp;
+    auto out = round == 0 ? tmp : src;
+    add_tn(J, MMK_GRAM_F64, [&](int c) { return (const void*)in(c); }, [&](int c) { return (const void*)in(c); },
+           [&](int c) { return J.ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; },
+           true);
+    add_chol(J, (acc_R && round == 1) ? 1 : 0);
+    std::vector<MMDesc> md(J.C);
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      MMDesc m{};
+      m.A = in(c); m.lda = d.ldt;
+      m.B = J.ch[c].Ri; m.ldb = d.l;
+      m.Cm = out(c); m.ldc = d.ldt;
+      m.m = d.n; m.n = d.l; m.k = d.l;
+      m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64); m.ks = 1; m.kchunk = (int)rup(d.l, 16);
+      m.mode = MM_STORE;
+      md[c] = m;
+    }
+    add_mm(J, MMK_NN_F64, md);
+  }
+}
+
+// Y_c = V_c X_c (dense FP64), split over k with atomic accumulation when small.
+void dense_f64(Job& J, std::function<const double*(int)> X, std::function<double*(int)> Y) {
+  int64_t tiles = 0;
+  for (int c = 0; c < J.C; ++c) tiles += (int64_t)cdiv(J.d[c].n, 64) * cdiv(J.d[c].l, 64);
+  std::vector<MMDesc> md(J.C);
+  std::vector<ZeroDesc> zd(J.C);
+  bool any_split = false;
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc m{};
+    m.A = J.ch[c].A; m.lda = J.ch[c].lda;
+    m.B = X(c); m.ldb = d.ldt;
+    m.Cm = Y(c); m.ldc = d.ldt;
+    m.m = d.n; m.n = d.l; m.k = d.n;
+    m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64);
+    m.ks = pick_splits(tiles, d.n, 128);
+    m.kchunk = (int)rup(cdiv(d.n, m.ks), 16);
+    m.ks = cdiv(d.n, m.kchunk);
+    m.mode = m.ks > 1 ? MM_ATOMIC : MM_STORE;
+    any_split |= m.ks > 1;
+    md[c] = m;
+    zd[c] = ZeroDesc{Y(c), d.ldt, d.n, d.l, 8};
+  }
+  if (any_split) {
+    const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+    const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+    const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
+    cudaStream_t st = J.P->st;
+    const int C = J.C;
+    J.steps.push_back([=]() {
+      launch_zero(dzd, off, C, tiles64, st);
+      return RSVD_OK;
+    });
+  }
+  add_mm(J, MMK_DENSE_F64, md);
+}
+
+void lift(Job& J, MMKind kind, std::function<const void*(int)> basis, std::function<const double*(int)> small,
+          std::function<double*(int)> out, std::function<int64_t(int)> ldo, std::function<const double*(int)> scale) {
+  std::vector<MMDesc> md(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc m{};
+    m.A = basis(c); m.lda = d.ldt;
+    m.B = small(c); m.ldb = d.l;
+    m.Cm = out(c); m.ldc = ldo(c);
+    m.m = d.n; m.n = d.kcap; m.k = d.l;
+    m.mt = cdiv(d.n, 64); m.nt = cdiv(d.kcap, 64); m.ks = 1; m.kchunk = (int)rup(d.l, 16);
+    m.mode = MM_STORE;
+    m.colscale = scale(c);
+    m.ncols_dev = &J.d_res[c].k_out;
+    md[c] = m;
+  }
+  add_mm(J, kind, md);
+}
+
+void build_fp64(Job& J) {
+  auto& ch = J.ch;
+  const int C = J.C;
+  cudaStream_t st = J.P->st;
+  const Chan* dch = J.d_ch;
+  const int* off64 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+  const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+  const uint64_t seed = J.P->o.seed;
+  J.steps.push_back([=]() {
+    launch_fro2(dch, off64, C, t64, st);
+    launch_fro2_reduce(dch, C, st);
+    launch_omega_f64(dch, off64, C, t64, seed, 0, st);
+    return RSVD_OK;
+  });
+  auto X = [&](int c) { return ch[c].X; };
+  auto Y = [&](int c) { return ch[c].Y; };
+  auto Q2 = [&](int c) { return ch[c].Q2; };
+  dense_f64(J, [&](int c) { return (const double*)ch[c].X; }, Y);        // Y = V P
+  cqr2_f64(J, Y, X, false);                                              // Q in Y
+  bool q_in_y = true;
+  for (int r = 0; r < 2 * J.q; ++r) {
+    if (q_in_y) { dense_f64(J, [&](int c) { return (const double*)ch[c].Y; }, X); cqr2_f64(J, X, Q2, false); }
+    else { dense_f64(J, [&](int c) { return (const double*)ch[c].X; }, Y); cqr2_f64(J, Y, Q2, false); }
+    q_in_y = !q_in_y;
+  }
+  auto Qb = [&, q_in_y](int c) { return q_in_y ? ch[c].Y : ch[c].X; };
+  auto Wb = [&, q_in_y](int c) { return q_in_y ? ch[c].X : ch[c].Y; };
+  dense_f64(J, [&](int c) { return (const double*)Qb(c); }, Wb);          // W = V Q
+  const bool rr = J.P->o.rayleigh_ritz != 0;
+  if (rr) {
+    // T = Q^T W into R (symmetric); Jacobi SVD of T gives T = X Sigma J^T
+    add_tn(J, MMK_GRAM_F64, [&](int c) { return (const void*)Qb(c); }, [&](int c) { return (const void*)Wb(c); },
+           [&](int c) { return ch[c].R; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; },
+           false);
+  } else {
+    cqr2_f64(J, Wb, Q2, true);                                            // W = Q2 R, Q2 in Wb
+  }
+  const int maxl = J.max_l;
+  const int policy = J.policy;
+  const double tol = J.tol;
+  J.steps.push_back([=]() {
+    launch_jacobi(dch, C, 0, maxl, st);
+    launch_select(dch, C, policy, tol, 0, st);
+    return RSVD_OK;
+  });
+  lift(J, MMK_NN_F64, [&](int c) { return (const void*)Qb(c); }, [&](int c) { return (const double*)ch[c].M; },
+       [&](int c) { return ch[c].U; }, [&](int c) { return ch[c].ldu; }, [&](int c) { return (const double*)nullptr; });
+  lift(J, MMK_NN_F64, [&, rr](int c) { return (const void*)(rr ? Qb(c) : Wb(c)); },
+       [&](int c) { return (const double*)ch[c].J; }, [&](int c) { return ch[c].V; },
+       [&](int c) { return ch[c].ldv; }, [&](int c) { return (const double*)nullptr; });
+  const int maxk = J.max_kcap;
+  J.steps.push_back([=]() {
+    launch_signfix(dch, C, maxk, st);
+    return RSVD_OK;
+  });
+}
+
+// --------------------------------------------------------------- mixed path
+rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
+  // one grouped tcgen05 launch: Y32[:, 0:ncols) = sum words V_a X_b
+  int bn = 16;
+  for (int c = 0; c < J.C; ++c) {
+    const int nc = ncols_of_pass ? J.d[c].lw : J.d[c].l;
+    bn = std::max<int>(bn, (int)std::min<int64_t>(256, rup(nc, 16)));
+  }
+  std::vector<TcChan> tcs(J.C);
+  int64_t items0 = 0;
+  for (int c = 0; c < J.C; ++c) {
+    const int nc = ncols_of_pass ? J.d[c].lw : J.d[c].l;
+    items0 += (int64_t)cdiv(J.d[c].n, 128) * cdiv(nc, bn);
+  }
+  bool any_split = false;
+  std::vector<ZeroDesc> zd(J.C);
+  int item = 0;
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    const int nc = ncols_of_pass ? d.lw : d.l;
+    TcChan& t = tcs[c];
+    memset(&t, 0, sizeof(t));
+    const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
+    const __nv_bfloat16* X[3] = {J.ch[c].Xb[0], J.ch[c].Xb[1], J.ch[c].Xb[2]};
+    if (!J.measure) {
+      const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, nc, bn);
+      if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
+    }
+    t.Y = J.ch[c].Y32;
+    t.ldy = d.ldt;
+    t.n = d.n;
+    t.ncols = nc;
+    t.mt = cdiv(d.n, 128);
+    t.nt = cdiv(nc, bn);
+    const int kt = cdiv(d.n, 64);
+    int ks = pick_splits(items0, kt, 8);
+    t.kt_per_split = cdiv(kt, ks);
+    t.ks = cdiv(kt, t.kt_per_split);
+    t.atomic = t.ks > 1;
+    any_split |= t.atomic != 0;
+    t.item0 = item;
+    item += t.mt * t.nt * t.ks;
+    zd[c] = ZeroDesc{J.ch[c].Y32, d.ldt, d.n, nc, 4};
+  }
+  const int items = item;
+  if (any_split) {
+    const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+    const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+    const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
+    cudaStream_t st = J.P->st;
+    const int C = J.C;
+    J.steps.push_back([=]() {
+      launch_zero(dzd, off, C, tiles64, st);
+      return RSVD_OK;
+    });
+  }
+  const TcChan* dtc = J.ar.put(tcs.data(), tcs.size(), 128);
+  cudaStream_t st = J.P->st;
+  int* derr = J.P->d_err;
+  const int C = J.C;
+  J.steps.push_back([=]() {
+    const int e = tc_launch(dtc, C, items, sa, sx, bn, derr, st);
+    if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    return RSVD_OK;
+  });
+  return RSVD_OK;
+}
+
+// CholeskyQR2 of Y32[:, 0:l) -> Q32 (FP32) and its BF16 words in Xb[:, 0:l).
+void cqr2_mixed(Job& J, int nsl_out) {
+  auto& ch = J.ch;
+  for (int round = 0; round < 2; ++round) {
+    auto in = [&, round](int c) { return round == 0 ? ch[c].Y32 : ch[c].T32; };
+    auto out = [&, round](int c) { return round == 0 ? ch[c].T32 : ch[c].Q32; };
+    add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)in(c); }, [&](int c) { return (const void*)in(c); },
+           [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+    add_chol(J, 0);
+    std::vector<MMDesc> md(J.C);
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      MMDesc m{};
+      m.A = in(c); m.lda = d.ldt;
+      m.B = ch[c].Ri; m.ldb = d.l;
+      m.Cm = out(c); m.ldc = d.ldt;
+      m.m = d.n; m.n = d.l; m.k = d.l;
+      m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64); m.ks = 1; m.kchunk = (int)rup(d.l, 16);
+      m.mode = MM_STORE;
+      if (round == 1) {
+        for (int s = 0; s < nsl_out; ++s) m.sl[s] = ch[c].Xb[s];
+        m.ldsl = d.ldb;
+        m.nsl = nsl_out;
+      }
+      md[c] = m;
+    }
+    add_mm(J, MMK_NN_F32_F64B, md);
+  }
+}
+
+rsvd_status build_mixed(Job& J) {
+  auto& ch = J.ch;
+  const int C = J.C;
+  cudaStream_t st = J.P->st;
+  const Chan* dch = J.d_ch;
+  const int nsl = J.nsl;
+  const int* off8 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 8); });
+  const int t8 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 8); });
+  const int* off64 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+  const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+  const uint64_t seed = J.P->o.seed;
+  const uint64_t pseed = seed ^ 0x5DEECE66DULL;
+  J.steps.push_back([=]() {
+    launch_convert_slices(dch, off8, C, t8, nsl, st);
+    launch_fro2_reduce_rows(dch, C, 8, st);
+    launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
+    return RSVD_OK;
+  });
+  // sketch: only the l sketch columns (X word 0 = P exactly)
+  if (rsvd_status s = tc_pass(J, nsl, 1, 0)) return s;
+  cqr2_mixed(J, nsl);
+  for (int r = 0; r < 2 * J.q; ++r) {
+    if (rsvd_status s = tc_pass(J, nsl, nsl, 0)) return s;
+    cqr2_mixed(J, nsl);
+  }
+  // projection with the probe block: [W | V G] = V [Q | G]
+  if (rsvd_status s = tc_pass(J, nsl, nsl, 1)) return s;
+  // C = Q^T (V G)
+  add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Q32; },
+         [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
+         [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
+  const int maxl = J.max_l;
+  J.steps.push_back([=]() {
+    launch_probe_resid(dch, off64, C, t64, maxl, NPROBE, st);
+    return RSVD_OK;
+  });
+  // W^T W = R^T R
+  add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const void*)ch[c].Y32; },
+         [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+  add_chol(J, 0);
+  const int policy = J.policy;
+  const double tol = J.tol;
+  J.steps.push_back([=]() {
+    launch_jacobi(dch, C, 1, maxl, st);
+    launch_probe_finish(dch, C, st);
+    launch_select(dch, C, policy, tol, 1, st);
+    return RSVD_OK;
+  });
+  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Q32; }, [&](int c) { return (const double*)ch[c].M; },
+       [&](int c) { return ch[c].U; }, [&](int c) { return ch[c].ldu; }, [&](int c) { return (const double*)nullptr; });
+  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const double*)ch[c].M; },
+       [&](int c) { return ch[c].V; }, [&](int c) { return ch[c].ldv; }, [&](int c) { return (const double*)ch[c].scr; });
+  const int maxk = J.max_kcap;
+  J.steps.push_back([=]() {
+    launch_signfix(dch, C, maxk, st);
+    return RSVD_OK;
+  });
+  return RSVD_OK;
+}
+
+// ------------------------------------------------------------ layout
+// Lay out per-channel buffers; with base == nullptr only measures.
+void layout(Job& J, Bump& b) {
+  J.ch.assign(J.C, Chan{});
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    Chan& h = J.ch[c];
+    const rsvd_matrix& A = J.A[c];
+    const rsvd_factors& F = J.f[c];
+    h.n = d.n; h.l = d.l; h.k_cap = d.kcap; h.k_fixed = J.P->o.k;
+    h.ldt = d.ldt; h.ldb = d.ldb; h.lw = d.lw; h.nprobe = d.s;
+    if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
+    else { h.A = A.data; h.lda = A.ld; }
+    const size_t L2 = (size_t)d.l * d.l;
+    h.G = b.take<double>(L2); h.R = b.take<double>(L2); h.Ri = b.take<double>(L2);
+    h.M = b.take<double>(L2); h.J = b.take<double>(L2);
+    h.sig = b.take<double>(d.l); h.scr = b.take<double>(d.l);
+    h.res = nullptr;
+    if (!J.mixed) {
+      const size_t T = (size_t)d.ldt * d.l;
+      h.X = b.take<double>(T); h.Y = b.take<double>(T); h.Q2 = b.take<double>(T);
+      h.gpart = b.take<double>((size_t)d.gsplit * L2);
+      h.fro_part = b.take<double>(cdiv(d.n, 64));
+    } else {
+      for (int s = 0; s < J.nsl; ++s) h.Ab[s] = b.take<__nv_bfloat16>((size_t)d.n * d.ldb);
+      for (int s = 0; s < J.nsl; ++s) h.Xb[s] = b.take<__nv_bfloat16>((size_t)d.lw * d.ldb);
+      h.Y32 = b.take<float>((size_t)d.ldt * d.lw);
+      h.Q32 = b.take<float>((size_t)d.ldt * d.l);
+      h.T32 = b.take<float>((size_t)d.ldt * d.l);
+      h.gpart = b.take<double>((size_t)d.gsplit * d.l * std::max(d.l, d.s));
+      h.fro_part = b.take<double>(cdiv(d.n, 8));
+      h.C64 = b.take<double>((size_t)d.l * d.s);
+      h.est_part = b.take<double>(1 + d.l);
+    }
+    if (F.mem == RSVD_MEM_HOST) {
+      h.U = b.take<double>((size_t)d.n * d.kcap); h.ldu = d.n;
+      h.V = b.take<double>((size_t)d.n * d.kcap); h.ldv = d.n;
+      h.S = b.take<double>(d.kcap);
+    } else {
+      h.U = F.U; h.ldu = F.ldu; h.V = F.V; h.ldv = F.ldv; h.S = F.S;
+      if (!h.U) { h.U = b.take<double>((size_t)d.n * d.kcap); h.ldu = d.n; }
+      if (!h.V) { h.V = b.take<double>((size_t)d.n * d.kcap); h.ldv = d.n; }
+    }
+  }
+  J.d_res = b.take<ChanResult>(J.C);
+  for (int c = 0; c < J.C; ++c) J.ch[c].res = J.d_res ? J.d_res + c : nullptr;
+}
+
+rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f) {
+  if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
+  if (C < 1) return seterr(RSVD_ERR_INVALID_ARG, "channel count %d < 1", C);
+  if (!A || !f) return seterr(RSVD_ERR_INVALID_ARG, "matrix or factor array is NULL");
+  for (int c = 0; c < C; ++c) {
+    const rsvd_matrix& a = A[c];
+    const rsvd_factors& F = f[c];
+    if (a.kind != RSVD_DENSE_F64)
+      return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: matrix kind %d not handled by this entry point", c, a.kind);
+    if (a.n < 1 || a.n > P->o.n_max)
+      return seterr(RSVD_ERR_INVALID_ARG, "channel %d: n = %lld outside [1, n_max = %lld]", c, (long long)a.n,
+                    (long long)P->o.n_max);
+    if (a.n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: n too large", c);
+    if (!a.data) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: data is NULL", c);
+    if (a.ld < a.n) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: ld %lld < n %lld", c, (long long)a.ld, (long long)a.n);
+    if (a.mem != RSVD_MEM_DEVICE && a.mem != RSVD_MEM_HOST) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: bad mem", c);
+    if (F.mem != RSVD_MEM_DEVICE && F.mem != RSVD_MEM_HOST) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: bad factor mem", c);
+    if (F.k_cap < 1) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: k_cap %d < 1", c, F.k_cap);
+    if (!F.S) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: S is NULL", c);
+    if (F.U && F.ldu < a.n) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: ldu < n", c);
+    if (F.V && F.ldv < a.n) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: ldv < n", c);
+    if (F.mem == RSVD_MEM_HOST && (!F.U || !F.V))
+      return seterr(RSVD_ERR_INVALID_ARG, "channel %d: host factors need U and V", c);
+  }
+  return RSVD_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+const char* rsvd_last_error_string(void) { return g_err; }
+int32_t rsvd_version(void) { return 100; }
+
+rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* o) {
+  g_err[0] = 0;
+  if (!out) return seterr(RSVD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!o) return seterr(RSVD_ERR_INVALID_ARG, "opts is NULL");
+  if (o->n_max < 1) return seterr(RSVD_ERR_INVALID_ARG, "n_max %lld < 1", (long long)o->n_max);
+  if (o->p < 0) return seterr(RSVD_ERR_INVALID_ARG, "p %d < 0", o->p);
+  if (o->q < 0 || o->q > 16) return seterr(RSVD_ERR_INVALID_ARG, "q %d outside [0, 16]", o->q);
+  if (o->precision != RSVD_PREC_FP64 && o->precision != RSVD_PREC_BF16X)
+    return seterr(RSVD_ERR_INVALID_ARG, "precision %d unknown", o->precision);
+  if (o->rank_policy < RSVD_RANK_FIXED || o->rank_policy > RSVD_RANK_LEARNED)
+    return seterr(RSVD_ERR_INVALID_ARG, "rank_policy %d unknown", o->rank_policy);
+  if (o->rank_policy == RSVD_RANK_FIXED && o->k < 1) return seterr(RSVD_ERR_INVALID_ARG, "fixed rank needs k >= 1");
+  if (o->rank_policy != RSVD_RANK_FIXED && !(o->tol > 0.0 && o->tol < 1.0))
+    return seterr(RSVD_ERR_INVALID_ARG, "tolerance %g outside (0, 1)", o->tol);
+  if (o->rank_policy == RSVD_RANK_TOL && o->k + o->p < 1)
+    return seterr(RSVD_ERR_INVALID_ARG, "tolerance mode needs k + p >= 1 columns");
+  if (o->slices < 0 || o->slices > 3) return seterr(RSVD_ERR_INVALID_ARG, "slices %d outside [0, 3]", o->slices);
+  if (o->rank_policy == RSVD_RANK_ADAPTIVE || o->rank_policy == RSVD_RANK_LEARNED)
+    return seterr(RSVD_ERR_UNSUPPORTED, "rank policy %d is not available in this build", o->rank_policy);
+  if (o->rayleigh_ritz && (o->precision != RSVD_PREC_FP64 || o->rank_policy != RSVD_RANK_FIXED))
+    return seterr(RSVD_ERR_UNSUPPORTED, "Rayleigh-Ritz is built for the FP64 path with a fixed rank");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return seterr(RSVD_ERR_CUDA, "no CUDA device");
+  if (o->precision == RSVD_PREC_BF16X) {
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return seterr(RSVD_ERR_CUDA, "device query failed");
+    if (pr.major != 10 || pr.minor != 3)
+      return seterr(RSVD_ERR_UNSUPPORTED, "mixed path needs sm_103 (found sm_%d%d)", pr.major, pr.minor);
+  }
+  rsvd_plan_s* P = new rsvd_plan_s();
+  P->o = *o;
+  P->st = (cudaStream_t)o->stream;
+  P->slices = o->slices ? o->slices : 2;
+  if (cudaMalloc((void**)&P->d_err, sizeof(int)) != cudaSuccess) {
+    delete P;
+    return seterr(RSVD_ERR_OOM, "cudaMalloc of the error word failed");
+  }
+  cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st);
+  *out = P;
+  return RSVD_OK;
+}
+
+void rsvd_plan_destroy(rsvd_plan_t P) {
+  if (!P) return;
+  cudaStreamSynchronize(P->st);
+  if (P->ws) cudaFree(P->ws);
+  if (P->hp) cudaFreeHost(P->hp);
+  if (P->d_err) cudaFree(P->d_err);
+  delete P;
+}
+
+int64_t rsvd_plan_workspace_bytes(rsvd_plan_t P) { return P ? (int64_t)P->ws_cap : 0; }
+
+rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, rsvd_factors* f,
+                                   rsvd_status* per_item) {
+  g_err[0] = 0;
+  if (rsvd_status s = validate(P, C, A, f)) return s;
+  Job J;
+  J.P = P;
+  J.C = C;
+  J.A = A;
+  J.f = f;
+  J.mixed = P->o.precision == RSVD_PREC_BF16X;
+  J.q = P->o.q;
+  J.nsl = P->slices;
+  J.policy = P->o.rank_policy;
+  J.tol = P->o.tol;
+  J.d.resize(C);
+  std::vector<int> warn(C, 0);
+  int64_t sum_gram_tiles = 0;
+  for (int c = 0; c < C; ++c) {
+    ChanDims& d = J.d[c];
+    d.n = (int)A[c].n;
+    int64_t l = (int64_t)P->o.k + P->o.p;
+    if (l > d.n) { l = d.n; warn[c] = RSVD_WARN_RANK_CAPPED; }
+    d.l = (int)std::max<int64_t>(1, l);
+    d.s = J.mixed ? NPROBE : 0;
+    d.lw = d.l + d.s;
+    d.kcap = std::min(f[c].k_cap, d.l);
+    d.ldt = rup(d.n, 4);
+    d.ldb = rup(d.n, 64);
+    sum_gram_tiles += (int64_t)cdiv(d.l, 64) * cdiv(d.l, 64);
+    J.max_l = std::max(J.max_l, d.l);
+    J.max_lw = std::max(J.max_lw, d.lw);
+    J.max_kcap = std::max(J.max_kcap, d.kcap);
+  }
+  for (int c = 0; c < C; ++c) {
+    ChanDims& d = J.d[c];
+    int g = (int)((2 * NSM + sum_gram_tiles - 1) / std::max<int64_t>(1, sum_gram_tiles));
+    g = std::max(1, std::min(g, cdiv(d.n, 256)));
+    d.gsplit = g;
+  }
+  // pass 1: measure (buffers + descriptors), grow, pass 2: real pointers
+  for (int pass = 0; pass < 2; ++pass) {
+    Bump b(pass == 0 ? nullptr : P->ws);
+    J.measure = pass == 0;
+    layout(J, b);
+    const size_t buf_bytes = (b.off + 4095) & ~(size_t)4095;
+    J.ar = Arena();
+    J.ar.dbase = pass == 0 ? nullptr : P->ws + buf_bytes;
+    J.steps.clear();
+    J.d_ch = nullptr;
+    // descriptors: the channel array first (its device address is needed by
+    // the step builders), then everything the builders add
+    {
+      std::vector<Chan> tmp(J.ch);
+      J.d_ch = J.ar.put(tmp.data(), tmp.size(), 128);
+    }
+    std::vector<ChanResult> r0(C);
+    memset(r0.data(), 0, sizeof(ChanResult) * C);
+    if (J.mixed) {
+      if (rsvd_status s = build_mixed(J)) return s;
+    } else {
+      build_fp64(J);
+    }
+    const size_t need = buf_bytes + J.ar.h.size() + 4096;
+    if (pass == 0) {
+      if (rsvd_status s = grow_ws(P, need)) return s;
+    } else {
+      if (need > P->ws_cap) return seterr(RSVD_ERR_OOM, "workspace estimate exceeded");
+      if (rsvd_status s = grow_pinned(P, std::max(J.ar.h.size(), sizeof(ChanResult) * C) + 64)) return s;
+      // results start zeroed
+      CK(cudaMemsetAsync(J.d_res, 0, sizeof(ChanResult) * C, P->st));
+      memcpy(P->hp, J.ar.h.data(), J.ar.h.size());
+      CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
+      for (int c = 0; c < C; ++c)
+        if (A[c].mem == RSVD_MEM_HOST)
+          CK(cudaMemcpy2DAsync((void*)J.ch[c].A, (size_t)J.d[c].n * sizeof(double), A[c].data,
+                               (size_t)A[c].ld * sizeof(double), (size_t)J.d[c].n * sizeof(double), J.d[c].n,
+                               cudaMemcpyHostToDevice, P->st));
+    }
+  }
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  for (auto& step : J.steps)
+    if (rsvd_status s = step()) return s;
+  CK(cudaGetLastError());
+  // read back the per-channel results and the device error word
+  ChanResult* hres = (ChanResult*)P->hp;
+  CK(cudaMemcpyAsync(hres, J.d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost, P->st));
+  int* herr = (int*)(P->hp + ((sizeof(ChanResult) * C + 63) & ~(size_t)63));
+  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  std::vector<ChanResult> res(hres, hres + C);
+  const int derr = *herr;
+  if (derr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", derr);
+  rsvd_status worst = RSVD_OK;
+  for (int c = 0; c < C; ++c) {
+    rsvd_status s = (rsvd_status)res[c].status;
+    if (s == RSVD_OK && warn[c]) s = (rsvd_status)warn[c];
+    f[c].k_out = res[c].k_out;
+    f[c].l_used = res[c].l_used;
+    f[c].err_est = res[c].err_est;
+    f[c].status = s;
+    if (per_item) per_item[c] = s;
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (worst >= 0 && s > worst) worst = s;
+    if (f[c].mem == RSVD_MEM_HOST && res[c].k_out > 0) {
+      const int k = res[c].k_out, n = J.d[c].n;
+      CK(cudaMemcpy2DAsync(f[c].U, f[c].ldu * sizeof(double), J.ch[c].U, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpy2DAsync(f[c].V, f[c].ldv * sizeof(double), J.ch[c].V, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpyAsync(f[c].S, J.ch[c].S, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    }
+  }
+  CK(cudaStreamSynchronize(P->st));
+  if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
+  return worst;
+}
+
+rsvd_status rsvd_decompose(rsvd_plan_t P, const rsvd_matrix* A, rsvd_factors* f) {
+  return rsvd_decompose_batched(P, 1, A, f, nullptr);
+}
+
+rsvd_status rsvd_reconstruct_error(rsvd_plan_t P, const rsvd_matrix* A, const rsvd_factors* f,
+                                   double* rel_err) {
+  g_err[0] = 0;
+  if (!P || !A || !f || !rel_err) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  if (A->kind != RSVD_DENSE_F64)
+    return seterr(RSVD_ERR_UNSUPPORTED, "matrix kind %d not handled by this entry point", A->kind);
+  const int64_t n = A->n;
+  const int k = f->k_out;
+  if (n < 1 || n > P->o.n_max || !A->data || A->ld < n) return seterr(RSVD_ERR_INVALID_ARG, "bad matrix");
+  if (k < 0 || k > f->k_cap) return seterr(RSVD_ERR_INVALID_ARG, "k_out %d outside [0, k_cap]", k);
+  if (k > 0 && (!f->U || !f->V || !f->S || f->ldu < n || f->ldv < n))
+    return seterr(RSVD_ERR_INVALID_ARG, "bad factors");
+  const int tiles = resid_tiles((int)n);
+  Bump b(nullptr);
+  const bool hA = A->mem == RSVD_MEM_HOST, hF = f->mem == RSVD_MEM_HOST;
+  for (int pass = 0; pass < 2; ++pass) {
+    Bump bb(pass == 0 ? nullptr : P->ws);
+    double* a = hA ? bb.take<double>((size_t)n * n) : nullptr;
+    double* u = hF ? bb.take<double>((size_t)n * std::max(k, 1)) : nullptr;
+    double* v = hF ? bb.take<double>((size_t)n * std::max(k, 1)) : nullptr;
+    double* s = hF ? bb.take<double>(std::max(k, 1)) : nullptr;
+    double* part = bb.take<double>(2 * (size_t)tiles);
+    if (pass == 0) {
+      if (rsvd_status st = grow_ws(P, bb.off + 4096)) return st;
+      continue;
+    }
+    if (rsvd_status st = grow_pinned(P, 2 * (size_t)tiles * sizeof(double) + 64)) return st;
+    const double* dA = A->data;
+    int64_t lda = A->ld;
+    if (hA) {
+      CK(cudaMemcpy2DAsync(a, n * sizeof(double), A->data, A->ld * sizeof(double), n * sizeof(double), n,
+                           cudaMemcpyHostToDevice, P->st));
+      dA = a; lda = n;
+    }
+    const double *dU = f->U, *dV = f->V, *dS = f->S;
+    int64_t ldu = f->ldu, ldv = f->ldv;
+    if (hF && k > 0) {
+      CK(cudaMemcpy2DAsync(u, n * sizeof(double), f->U, f->ldu * sizeof(double), n * sizeof(double), k,
+                           cudaMemcpyHostToDevice, P->st));
+      CK(cudaMemcpy2DAsync(v, n * sizeof(double), f->V, f->ldv * sizeof(double), n * sizeof(double), k,
+                           cudaMemcpyHostToDevice, P->st));
+      CK(cudaMemcpyAsync(s, f->S, k * sizeof(double), cudaMemcpyHostToDevice, P->st));
+      dU = u; dV = v; dS = s; ldu = n; ldv = n;
+    }
+    launch_resid(dA, lda, dU, ldu, dV, ldv, dS, (int)n, k, part, P->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(P->hp, part, 2 * (size_t)tiles * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    CK(cudaStreamSynchronize(P->st));
+  }
+  (void)b;
+  const double* hp = (const double*)P->hp;
+  double r2 = 0.0, a2 = 0.0;
+  for (int t = 0; t < tiles; ++t) { r2 += hp[2 * t]; a2 += hp[2 * t + 1]; }
+  *rel_err = a2 > 0.0 ? sqrt(r2 / a2) : sqrt(r2);
+  return RSVD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Shared device helpers and per-channel descriptors of the rSVD pipeline.
+//
+// Everything here is device-side arithmetic of the method or plumbing
+// (bounded waits, batched tile lookup).  Nothing is shared with the CPU
+// oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/rsvd.h"
+
+#define RSVD_DEV __device__ __forceinline__
+
+namespace rsvd {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11, Sec. 3): ten rounds of
+// two 32x32->64 multiplies with xor of the other counter words and the key;
+// the key is bumped by the Weyl constants between rounds.  Counter layout
+// (row i, column j, tag, 0), key (seed lo, seed hi).
+// ---------------------------------------------------------------------------
+struct Philox4 { uint32_t x, y, z, w; };
+
+RSVD_DEV Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+
+enum : uint32_t { TAG_OMEGA = 0, TAG_PROBE = 1, TAG_NOISE = 2, TAG_RESID = 3 };
+
+// FP64 Box-Muller entry from two 53-bit uniforms (the all-FP64 path's form).
+RSVD_DEV double gauss_f64(uint64_t seed, uint32_t i, uint32_t j, uint32_t tag) {
+  const Philox4 w = philox4x32_10(i, j, tag, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u1 = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6) + 0.5) * 0x1.0p-53;
+  const double u2 = ((double)(w.z >> 5) * 67108864.0 + (double)(w.w >> 6) + 0.5) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// FP32 Box-Muller entry from the top 24 bits of words 0 and 2 (mixed path).
+RSVD_DEV float gauss_f32(uint64_t seed, uint32_t i, uint32_t j, uint32_t tag) {
+  const Philox4 w = philox4x32_10(i, j, tag, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float u1 = ((float)(w.x >> 8) + 0.5f) * 0x1.0p-24f;
+  const float u2 = ((float)(w.z >> 8) + 0.5f) * 0x1.0p-24f;
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// ---------------------------------------------------------------------------
+// Batched tiling: channel c owns tiles [off[c], off[c+1]).
+// ---------------------------------------------------------------------------
+RSVD_DEV int find_chan(const int* __restrict__ off, int C, int t) {
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Device error word codes (set with atomicCAS so the first error wins).
+enum : int { DERR_NONE = 0, DERR_TIMEOUT_TMA = 1, DERR_TIMEOUT_MMA = 2, DERR_TIMEOUT_EPI = 3,
+             DERR_BAD_ARG = 4 };
+
+RSVD_DEV void set_err(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// Per-channel results written by the device and read once by the host.
+struct ChanResult {
+  int k_out;
+  int l_used;
+  int status;
+  int flags;        // bit0: shifted CholeskyQR used, bit1: jacobi cap hit, bit2: nonfinite
+  double err_est;
+  double fro2;      // ||A||_F^2
+};
+
+enum : int { FLAG_SHIFTED = 1, FLAG_JACOBI_CAP = 2, FLAG_NONFINITE = 4, FLAG_CHOL_FAIL = 8 };
+
+// ---------------------------------------------------------------------------
+// Per-channel pointers of one batched call (device-resident array).
+// Tall-skinny matrices are column-major with leading dimension `ldt`;
+// l x l matrices column-major with leading dimension `l`.
+// ---------------------------------------------------------------------------
+struct Chan {
+  int n, l, k_cap, k_fixed;
+  int64_t lda;
+  const double* A;          // FP64 input (device)
+  int64_t ldt;              // leading dim of n x l buffers
+  // FP64 path
+  double* X;                // n x l   (Omega, then Q)
+  double* Y;                // n x l   (products)
+  double* Q2;               // n x l   (second basis, FP64 path)
+  // small l x l (FP64)
+  double* G;                // Gram
+  double* R;                // Cholesky factor (upper), accumulates R = R2 R1
+  double* Ri;               // inverse of the last Cholesky factor
+  double* M;                // Jacobi working matrix (then left vectors X_svd)
+  double* J;                // Jacobi rotations (right vectors)
+  double* sig;              // singular values (l)
+  double* scr;              // l doubles of scratch (unsorted column norms)
+  double* gpart;            // Gram partials
+  int gsplit;               // number of row splits of the Gram
+  double* fro_part;         // ||A||^2 partials (one per 64-row block)
+  // mixed path
+  __nv_bfloat16* Ab[3];     // V slices, row-major n x ldb
+  __nv_bfloat16* Xb[3];     // X slices, K-major: column j at Xb + j*ldb
+  int64_t ldb;
+  float* Y32;               // n x lw (sketch / projection output)
+  float* Q32;               // n x l
+  float* T32;               // n x s probe residual scratch
+  int lw;                   // columns of the last product (l + probes)
+  int nprobe;
+  double* C64;              // l x s  (Q^T A G)
+  double* est_part;         // probe residual partials
+  // outputs
+  double* U; int64_t ldu;   // device (internal or user)
+  double* V; int64_t ldv;
+  double* S;
+  ChanResult* res;
+  float* feat;              // learned-rank features (19 floats) or null
+};
+
+}  // namespace rsvd

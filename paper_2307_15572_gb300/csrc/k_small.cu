@@ -1,0 +1,479 @@
+// Per-channel kernels of the pipeline: ||V||_F^2, the FP64 random projection
+// matrix, CholeskyQR's l x l factorisation, the one-sided Jacobi SVD of the
+// small factor, rank selection and the sign convention.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace rsvd {
+
+template <typename T>
+RSVD_DEV T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed tree) of one value per thread; blockDim <= 1024.
+RSVD_DEV double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (lane < nw) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------- ||V||_F^2
+__global__ void __launch_bounds__(256) k_fro2(const Chan* __restrict__ ch,
+                                              const int* __restrict__ off, int C) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x;
+  const int c = find_chan(off, C, t);
+  const Chan& h = ch[c];
+  const int b = t - off[c];
+  const int r0 = b * 64, r1 = min(h.n, r0 + 64);
+  double s = 0.0;
+  bool bad = false;
+  for (int r = r0; r < r1; ++r) {
+    const double* row = h.A + (int64_t)r * h.lda;
+    for (int j = threadIdx.x; j < h.n; j += blockDim.x) {
+      const double a = row[j];
+      bad |= !isfinite(a);
+      s = fma(a, a, s);
+    }
+  }
+  s = block_sum(s, sh);
+  if (bad) atomicOr(&h.res->flags, FLAG_NONFINITE);
+  if (threadIdx.x == 0) h.fro_part[b] = s;
+}
+
+__global__ void k_fro2_reduce(const Chan* __restrict__ ch, int nparts_per_row_block) {
+  __shared__ double sh[32];
+  const Chan& h = ch[blockIdx.x];
+  const int nb = (h.n + nparts_per_row_block - 1) / nparts_per_row_block;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += h.fro_part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) h.res->fro2 = s;
+}
+
+void launch_fro2(const Chan* d_ch, const int* d_off, int C, int tiles, cudaStream_t st) {
+  if (tiles > 0) k_fro2<<<tiles, 256, 0, st>>>(d_ch, d_off, C);
+}
+void launch_fro2_reduce(const Chan* d_ch, int C, cudaStream_t st) {
+  k_fro2_reduce<<<C, 256, 0, st>>>(d_ch, 64);
+}
+void launch_fro2_reduce_rows(const Chan* d_ch, int C, int rows_per_part, cudaStream_t st) {
+  k_fro2_reduce<<<C, 256, 0, st>>>(d_ch, rows_per_part);
+}
+
+// ------------------------------------------------------------- Omega (FP64)
+__global__ void __launch_bounds__(256) k_omega_f64(const Chan* __restrict__ ch,
+                                                   const int* __restrict__ off, int C,
+                                                   uint64_t seed, int col0) {
+  const int t = blockIdx.x;
+  const int c = find_chan(off, C, t);
+  const Chan& h = ch[c];
+  const int r0 = (t - off[c]) * 64;
+  const int rows = min(64, h.n - r0);
+  for (int e = threadIdx.x; e < 64 * h.l; e += blockDim.x) {
+    const int rr = e & 63, j = e >> 6;
+    if (rr < rows)
+      h.X[(r0 + rr) + (int64_t)j * h.ldt] = gauss_f64(seed, (uint32_t)(r0 + rr), (uint32_t)(col0 + j), TAG_OMEGA);
+  }
+}
+
+void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
+                      int col0, cudaStream_t st) {
+  if (tiles > 0) k_omega_f64<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0);
+}
+
+// ------------------------------------------------- Cholesky + inverse (FP64)
+// G = R^T R with R upper triangular, computed row by row: for step j,
+// t_i = G_ji - sum_{k<j} R_kj R_ki (i >= j), R_jj = sqrt(t_j), R_ji = t_i / R_jj.
+// A non-positive pivot is a breakdown; the factorisation is then retried on
+// G + s I with the shift of Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa
+// (SIAM J. Sci. Comput. 42, 2020), s = 11 (m l + l (l+1)) u tr(G), which keeps
+// the shifted CholeskyQR well defined for kappa up to ~u^{-1}.
+// Then R^{-1} by back substitution (one thread per column) and, if asked,
+// R_acc <- R R_acc (the triangular factor of a repeated CholeskyQR).
+__global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, int accumulate,
+                                                  int use_smem) {
+  extern __shared__ double smem[];
+  const Chan& h = ch[blockIdx.x];
+  const int l = h.l;
+  double* Ms = use_smem ? smem : h.M;        // working copy of G -> R (column-major)
+  const double* G = h.G;
+  __shared__ int fail;
+  __shared__ double shift;
+  __shared__ double tr;
+  if (threadIdx.x == 0) { fail = 0; shift = 0.0; tr = 0.0; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < l; ++i) s += G[i + (int64_t)i * l];
+    tr = s;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) Ms[e] = G[e];
+    __syncthreads();
+    if (attempt == 1) {
+      for (int i = threadIdx.x; i < l; i += blockDim.x) Ms[i + (int64_t)i * l] += shift;
+      __syncthreads();
+    }
+    for (int j = 0; j < l; ++j) {
+      for (int i = j + threadIdx.x; i < l; i += blockDim.x) {
+        double s = Ms[j + (int64_t)i * l];
+        const double* cj = Ms + (int64_t)j * l;
+        const double* ci = Ms + (int64_t)i * l;
+        for (int k = 0; k < j; ++k) s = fma(-cj[k], ci[k], s);
+        Ms[j + (int64_t)i * l] = s;
+      }
+      __syncthreads();
+      const double d = Ms[j + (int64_t)j * l];
+      const bool bad = !(d > 0.0) || !isfinite(d);
+      if (bad) break;                                  // uniform across the block
+      const double rjj = sqrt(d);
+      for (int i = j + 1 + threadIdx.x; i < l; i += blockDim.x) Ms[j + (int64_t)i * l] /= rjj;
+      __syncthreads();
+      if (threadIdx.x == 0) Ms[j + (int64_t)j * l] = rjj;
+      __syncthreads();
+    }
+    __syncthreads();
+    int ok = 1;
+    for (int j = 0; j < l; ++j) {
+      const double d = Ms[j + (int64_t)j * l];
+      if (!(d > 0.0) || !isfinite(d)) { ok = 0; break; }
+    }
+    if (ok) break;
+    if (threadIdx.x == 0) {
+      if (attempt == 0) {
+        shift = 11.0 * ((double)h.n * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
+        atomicOr(&h.res->flags, FLAG_SHIFTED);
+      } else {
+        fail = 1;
+        atomicOr(&h.res->flags, FLAG_CHOL_FAIL);
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+  }
+  __syncthreads();
+  if (fail) return;
+  // zero the strictly lower part so Ms holds R exactly
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e % l, j = e / l;
+    if (i > j) Ms[e] = 0.0;
+  }
+  __syncthreads();
+  // R^{-1}: column c solves R x = e_c
+  for (int cidx = threadIdx.x; cidx < l; cidx += blockDim.x) {
+    double* x = h.Ri + (int64_t)cidx * l;
+    for (int i = cidx + 1; i < l; ++i) x[i] = 0.0;
+    x[cidx] = 1.0 / Ms[cidx + (int64_t)cidx * l];
+    for (int i = cidx - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= cidx; ++k) s = fma(Ms[i + (int64_t)k * l], x[k], s);
+      x[i] = -s / Ms[i + (int64_t)i * l];
+    }
+  }
+  __syncthreads();
+  if (accumulate) {
+    // R_acc <- R R_acc (both upper); read old R_acc column by column into
+    // registers is not possible for general l, so write the product to G
+    // (free now) and copy back.
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+      const int i = e % l, j = e / l;
+      double s = 0.0;
+      if (i <= j)
+        for (int k = i; k <= j; ++k) s = fma(Ms[i + (int64_t)k * l], h.R[k + (int64_t)j * l], s);
+      h.G[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) h.R[e] = h.G[e];
+  } else {
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) h.R[e] = Ms[e];
+  }
+}
+
+void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, cudaStream_t st) {
+  const size_t bytes = (size_t)max_l * max_l * sizeof(double);
+  const int use_smem = bytes <= 200 * 1024;
+  if (use_smem) {
+    cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_chol_inv<<<C, 256, bytes, st>>>(d_ch, accumulate, 1);
+  } else {
+    k_chol_inv<<<C, 256, 0, st>>>(d_ch, accumulate, 0);
+  }
+}
+
+// ------------------------------------------------ one-sided Jacobi (Hestenes)
+// Orthogonalise the columns of M = R^T by plane rotations on column pairs.
+// For a pair with alpha = |m_i|^2, beta = |m_j|^2, gamma = m_i.m_j the
+// rotation zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| +
+// sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t makes them orthogonal
+// (Golub & Van Loan, 4th ed., Sec. 8.6.3).  Pairs are scheduled in parallel
+// rounds by the round-robin ("circle") ordering of Brent & Luk (1985): in
+// round r of m-1 rounds, index m-1 meets r and (r+i) meets (r-i) mod (m-1);
+// every pair occurs once per sweep and the pairs of a round are disjoint, so
+// one warp per pair runs without synchronisation inside the round.  Sweeps
+// repeat until no pair exceeds |gamma| <= l eps sqrt(alpha beta) (or a cap).
+// Result: M J = X Sigma with X orthonormal, so R^T = X Sigma J^T.
+template <typename T>
+__global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int use_smem,
+                                                int max_sweeps) {
+  extern __shared__ unsigned char sraw[];
+  const Chan& h = ch[blockIdx.x];
+  const int l = h.l;
+  const int m = l + (l & 1);                       // even count; index l (if odd) is a zero column
+  T* Mw;
+  T* Jw;
+  if (use_smem) { Mw = (T*)sraw; Jw = Mw + (int64_t)l * l; }
+  else { Mw = (T*)h.G; Jw = (T*)h.Ri; }            // G and R^{-1} are free at this point
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e % l, j = e / l;
+    Mw[e] = (T)h.R[j + (int64_t)i * l];            // M = R^T
+    Jw[e] = (T)(i == j ? 1.0 : 0.0);
+  }
+  __shared__ int nrot;
+  __shared__ int sweeps_done;
+  __syncthreads();
+  const T eps = (sizeof(T) == 8) ? (T)1.1102230246251565e-16 : (T)5.9604645e-8;
+  const T thr = (T)l * eps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) nrot = 0;
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r) {
+      for (int pi = warp; pi < m / 2; pi += nwarp) {
+        int a, b;
+        if (pi == 0) { a = r; b = m - 1; }
+        else { a = (r + pi) % (m - 1); b = (r - pi + (m - 1)) % (m - 1); }
+        if (a >= l || b >= l) continue;
+        if (a > b) { const int tmp = a; a = b; b = tmp; }
+        T* ca = Mw + (int64_t)a * l;
+        T* cb = Mw + (int64_t)b * l;
+        T al = 0, be = 0, ga = 0;
+        for (int rr = lane; rr < l; rr += 32) {
+          const T x = ca[rr], y = cb[rr];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga == (T)0 || fabs(ga) <= thr * sqrt(al * be)) continue;
+        const T zeta = (be - al) / (2 * ga);
+        T t;
+        if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
+        else t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+        const T cs = (T)1 / sqrt((T)1 + t * t);
+        const T sn = cs * t;
+        for (int rr = lane; rr < l; rr += 32) {
+          const T x = ca[rr], y = cb[rr];
+          ca[rr] = cs * x - sn * y;
+          cb[rr] = sn * x + cs * y;
+        }
+        T* ja = Jw + (int64_t)a * l;
+        T* jb = Jw + (int64_t)b * l;
+        for (int rr = lane; rr < l; rr += 32) {
+          const T x = ja[rr], y = jb[rr];
+          ja[rr] = cs * x - sn * y;
+          jb[rr] = sn * x + cs * y;
+        }
+        if (lane == 0) atomicAdd(&nrot, 1);
+      }
+      __syncthreads();
+    }
+    const int done = (nrot == 0);
+    __syncthreads();
+    if (done) break;
+  }
+  if (threadIdx.x == 0) {
+    sweeps_done = sweep;
+    if (sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
+  }
+  __syncthreads();
+  // column norms (unsorted) into scratch
+  for (int cidx = warp; cidx < l; cidx += nwarp) {
+    const T* cc = Mw + (int64_t)cidx * l;
+    double s = 0.0;
+    for (int rr = lane; rr < l; rr += 32) s += (double)cc[rr] * (double)cc[rr];
+    s = warp_sum(s);
+    if (lane == 0) h.scr[cidx] = sqrt(s);
+  }
+  __syncthreads();
+  // rank sort, descending, ties by index; write sigma, X = M_i / sigma_i, Z = J_i
+  for (int cidx = warp; cidx < l; cidx += nwarp) {
+    const double si = h.scr[cidx];
+    int rank = 0;
+    for (int o = lane; o < l; o += 32) {
+      const double so = h.scr[o];
+      rank += (so > si) || (so == si && o < cidx);
+    }
+    rank = warp_sum(rank);
+    const T* cc = Mw + (int64_t)cidx * l;
+    const T* jc = Jw + (int64_t)cidx * l;
+    const double inv = si > 0.0 ? 1.0 / si : 0.0;
+    for (int rr = lane; rr < l; rr += 32) {
+      h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
+      h.J[rr + (int64_t)rank * l] = (double)jc[rr];
+    }
+    if (lane == 0) h.sig[rank] = si;
+  }
+}
+
+void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st) {
+  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  const size_t bytes = 2 * (size_t)max_l * max_l * esz;
+  const int use_smem = bytes <= 200 * 1024;
+  if (fp32) {
+    if (use_smem) {
+      cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      k_jacobi<float><<<C, 512, bytes, st>>>(d_ch, 1, 60);
+    } else {
+      k_jacobi<float><<<C, 512, 0, st>>>(d_ch, 0, 60);
+    }
+  } else {
+    if (use_smem) {
+      cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      k_jacobi<double><<<C, 512, bytes, st>>>(d_ch, 1, 60);
+    } else {
+      k_jacobi<double><<<C, 512, 0, st>>>(d_ch, 0, 60);
+    }
+  }
+}
+
+// ------------------------------------------------------------ rank selection
+// FP64 identity: for orthonormal U_k = Q X_k and V_k Sigma_k = V^T U_k,
+// ||V - U_k Sigma_k V_k^T||_F^2 = ||V||_F^2 - sum_{i<=k} sigma_i^2.
+// Probe form (mixed path): with G the probe block (s Gaussian columns),
+// C = Q^T V G, D = X^T C, ||(I - U_k U_k^T) V G||^2 = ||V G - Q C||^2 +
+// sum_{i>k} |D_i|^2, and E||(I-P)V G||_F^2 = s ||(I-P) V||_F^2.
+__global__ void k_select(const Chan* __restrict__ ch, int policy, double tol, int use_probe) {
+  const Chan& h = ch[blockIdx.x];
+  const int l = h.l;
+  ChanResult* res = h.res;
+  if (threadIdx.x != 0) return;
+  const double fro2 = res->fro2;
+  int status = RSVD_OK;
+  int k;
+  double est2 = 0.0;
+  const int kcap = min(h.k_cap, l);
+  if (res->flags & FLAG_NONFINITE) status = RSVD_ERR_NONFINITE;
+  else if (res->flags & FLAG_CHOL_FAIL) status = RSVD_ERR_NOT_CONVERGED;
+  if (policy == RSVD_RANK_FIXED) {
+    k = min(h.k_fixed, kcap);
+    double s2 = 0.0;
+    for (int i = 0; i < k; ++i) s2 += h.sig[i] * h.sig[i];
+    est2 = fmax(fro2 - s2, 0.0);
+    if (use_probe) {
+      double t = h.est_part[0];
+      for (int i = k; i < l; ++i) t += h.est_part[1 + i];
+      est2 = t / h.nprobe;
+    }
+  } else {
+    const double thr = tol * tol * fro2;
+    k = -1;
+    if (!use_probe) {
+      double s2 = 0.0;
+      for (int i = 0; i < kcap; ++i) {
+        s2 += h.sig[i] * h.sig[i];
+        if (fro2 - s2 <= thr) { k = i + 1; est2 = fmax(fro2 - s2, 0.0); break; }
+      }
+      if (k < 0) { k = kcap; est2 = fmax(fro2 - s2, 0.0); }
+    } else {
+      // tail sums from the end: t_k = rl2 + sum_{i>k} dn2_i
+      const double margin = 1.0 / (1.1 * 1.1);
+      double t = h.est_part[0];
+      for (int i = l - 1; i >= kcap; --i) t += h.est_part[1 + i];
+      // walk k downward from kcap while the estimate stays under the threshold
+      double tk = t;               // estimate for k = kcap
+      k = kcap;
+      double best = tk;
+      if (tk / h.nprobe > thr * margin) k = -1;
+      else {
+        for (int kk = kcap - 1; kk >= 1; --kk) {
+          const double tn = tk + h.est_part[1 + kk];
+          if (tn / h.nprobe > thr * margin) break;
+          tk = tn; k = kk; best = tk;
+        }
+      }
+      if (k < 0) { k = kcap; best = t; }
+      est2 = best / h.nprobe;
+    }
+    if (fro2 > 0.0 && est2 > thr && status == RSVD_OK) status = RSVD_ERR_TOL_NOT_MET;
+  }
+  if (k < 0) k = 0;
+  for (int i = 0; i < k; ++i) {
+    h.S[i] = h.sig[i];
+    h.scr[i] = h.sig[i] > 0.0 ? 1.0 / h.sig[i] : 0.0;   // column scale of R_k = W X_k Sigma_k^{-1}
+  }
+  res->k_out = k;
+  res->l_used = l;
+  res->err_est = fro2 > 0.0 ? sqrt(est2 / fro2) : 0.0;
+  if (status == RSVD_OK && (res->flags & FLAG_JACOBI_CAP)) status = RSVD_ERR_NOT_CONVERGED;
+  if (status == RSVD_OK && (res->flags & FLAG_SHIFTED)) status = RSVD_WARN_SHIFTED_CQR;
+  res->status = status;
+}
+
+void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
+                   cudaStream_t st) {
+  k_select<<<C, 32, 0, st>>>(d_ch, policy, tol, use_probe);
+}
+
+// ------------------------------------------------------------------ sign fix
+__global__ void __launch_bounds__(256) k_signfix(const Chan* __restrict__ ch) {
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  const Chan& h = ch[blockIdx.x];
+  const int col = blockIdx.y;
+  if (col >= h.res->k_out || h.U == nullptr) return;
+  double* u = h.U + (int64_t)col * h.ldu;
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int r = threadIdx.x; r < h.n; r += blockDim.x) {
+    const double a = fabs(u[r]);
+    if (a > best) { best = a; bi = r; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double ob = sv[threadIdx.x + s];
+      const int oi = si[threadIdx.x + s];
+      if (ob > sv[threadIdx.x] || (ob == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = ob;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const double pivot = u[si[0]];
+  __syncthreads();
+  if (pivot < 0.0) {
+    for (int r = threadIdx.x; r < h.n; r += blockDim.x) u[r] = -u[r];
+    if (h.V) {
+      double* v = h.V + (int64_t)col * h.ldv;
+      for (int r = threadIdx.x; r < h.n; r += blockDim.x) v[r] = -v[r];
+    }
+  }
+}
+
+void launch_signfix(const Chan* d_ch, int C, int max_k, cudaStream_t st) {
+  if (max_k <= 0) return;
+  k_signfix<<<dim3(C, max_k), 256, 0, st>>>(d_ch);
+}
+
+}  // namespace rsvd

@@ -1,0 +1,338 @@
+// Tensor-core passes over V for the mixed path: Y = V X on sm_103a.
+//
+// This is the contraction of Fig. 1 step 1 (Z = V P) and of the projection
+// (Y^T = V Q, V symmetric) when V is held as a sum of BF16 words,
+// V ~ V_0 + V_1 (+ V_2), and X likewise: Y = sum over word pairs (a, b) with
+// a + b < max(SA, SX) of V_a X_b, accumulated in FP32.  Two words carry ~16
+// significant bits of each FP64 entry, three ~24.
+//
+// Structure (one 128-row tile of Y per CTA, all of its columns):
+//   * warp 0, one thread: TMA producer.  For each 64-wide k step it waits for
+//     the stage to be free, arms the stage's mbarrier with the byte count and
+//     issues 2-D tiled bulk copies (128B swizzle) of the V word tiles
+//     (128 x 64) and X word tiles (BN x 64);
+//   * warp 1, one thread: MMA issuer.  Waits for the stage, issues
+//     tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = BN, K = 16) for each
+//     word pair and 16-wide k slice into one TMEM accumulator, then
+//     tcgen05.commit to the stage's "empty" barrier; a final commit signals
+//     the epilogue;
+//   * all four warps: epilogue.  tcgen05.ld (32 lanes x 32 bit, 16 columns at
+//     a time) from the warp's TMEM lane quarter, coalesced column-major
+//     stores (or red.global.add when k is split across CTAs).
+// Every mbarrier wait is bounded (~2 s of clock64); on expiry the thread
+// records an error code, stops issuing work, and the CTA still drains its
+// own copies and frees TMEM before returning.
+#include <cudaTypedefs.h>
+#include <stdio.h>
+
+#include "tc_gemm.h"
+
+namespace rsvd {
+
+static constexpr int BM = 128;
+static constexpr int BK = 64;
+static constexpr int A_TILE_BYTES = BM * BK * 2;   // 16 KiB
+static constexpr int SMEM_BUDGET = 220 * 1024;
+
+int tc_stage_bytes(int sa, int sx, int bn) { return sa * A_TILE_BYTES + sx * bn * BK * 2; }
+
+int tc_stages(int sa, int sx, int bn) {
+  const int sb = tc_stage_bytes(sa, sx, bn);
+  int st = (SMEM_BUDGET - 1024 - 256) / sb;
+  if (st > 8) st = 8;
+  return st;
+}
+
+// ------------------------------------------------------------- PTX helpers
+RSVD_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+RSVD_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+RSVD_DEV void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes) : "memory");
+}
+
+RSVD_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: ~2^32 clocks (about two seconds) before giving up.
+RSVD_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
+}
+
+RSVD_DEV void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+RSVD_DEV void tmap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
+}
+
+RSVD_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+RSVD_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+RSVD_DEV void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+               "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+RSVD_DEV void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// core groups 1024 bytes apart (stride byte offset), descriptor version 1.
+RSVD_DEV uint64_t sdesc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N = bn, M = 128.
+RSVD_DEV uint32_t idesc_bf16(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+RSVD_DEV void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+RSVD_DEV void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+RSVD_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ kernel
+template <int SA, int SX>
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int SB = SA * A_TILE_BYTES + SX * bn * BK * 2;
+  uint64_t* full = (uint64_t*)(base + (size_t)stages * SB);
+  uint64_t* empty = full + stages;
+  uint64_t* done = empty + stages;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // work item -> channel, split, tile
+  const int item = blockIdx.x;
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (chs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+  }
+  const TcChan* ch = chs + lo;
+  int local = item - ch->item0;
+  const int per_split = ch->mt * ch->nt;
+  const int split = local / per_split;
+  local -= split * per_split;
+  const int mi = local / ch->nt, ni = local % ch->nt;
+  const int m0 = mi * BM, n0 = ni * bn;
+  const int kt_total = (ch->n + BK - 1) / BK;
+  const int kb = split * ch->kt_per_split;
+  const int nk = min(kt_total, kb + ch->kt_per_split) - kb;
+  uint32_t ncols_alloc = 32;
+  while ((int)ncols_alloc < bn) ncols_alloc <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, ncols_alloc);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (nk > 0) {
+    if (warp == 0 && lane == 0) {
+      // ---------------- producer
+      for (int a = 0; a < SA; ++a) tmap_acquire(&ch->tmA[a]);
+      for (int x = 0; x < SX; ++x) tmap_acquire(&ch->tmX[x]);
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)(it / stages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) { set_err(err, DERR_TIMEOUT_TMA); break; }
+        mbar_arrive_expect_tx(&full[s], (uint32_t)SB);
+        unsigned char* st = base + (size_t)s * SB;
+        const int kx = (kb + it) * BK;
+        for (int a = 0; a < SA; ++a) tma_load_2d(st + a * A_TILE_BYTES, &ch->tmA[a], &full[s], kx, m0);
+        for (int x = 0; x < SX; ++x)
+          tma_load_2d(st + SA * A_TILE_BYTES + x * bn * BK * 2, &ch->tmX[x], &full[s], kx, n0);
+        issued = it + 1;
+      }
+      // drain: the last copy issued into each stage has landed
+      for (int s = 0; s < stages && s < issued; ++s) {
+        const int last = s + ((issued - 1 - s) / stages) * stages;
+        if (!mbar_wait(&full[s], (uint32_t)(last / stages) & 1u)) set_err(err, DERR_TIMEOUT_TMA);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = idesc_bf16(bn);
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)(it / stages) & 1u;
+        if (!mbar_wait(&full[s], ph)) { set_err(err, DERR_TIMEOUT_MMA); break; }
+        tc_fence_after();
+        const uint32_t sa0 = smem_addr(base + (size_t)s * SB);
+        const uint32_t sx0 = sa0 + SA * A_TILE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+          for (int a = 0; a < SA; ++a) {
+#pragma unroll
+            for (int x = 0; x < SX; ++x) {
+              if (a + x >= (SA > SX ? SA : SX)) continue;
+              const uint64_t ad = sdesc_sw128(sa0 + a * A_TILE_BYTES + kk * 32);
+              const uint64_t bd = sdesc_sw128(sx0 + x * bn * BK * 2 + kk * 32);
+              const uint32_t acc = (it > 0 || kk > 0 || a > 0 || x > 0) ? 1u : 0u;
+              mma_bf16(tmem, ad, bd, idesc, acc);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(done);
+    }
+    __syncwarp();
+
+    // ---------------- epilogue (decisions are made by lane 0 and broadcast,
+    // so the warp-collective tcgen05.ld is executed by all lanes or none)
+    int healthy = 0;
+    if (lane == 0) {
+      const bool ok = mbar_wait(done, 0);
+      if (!ok) set_err(err, DERR_TIMEOUT_EPI);
+      healthy = ok && (*(volatile int*)err == 0);
+    }
+    healthy = __shfl_sync(0xffffffffu, healthy, 0);
+    tc_fence_after();
+    if (healthy) {
+      const int row = m0 + warp * 32 + lane;
+      float* Y = ch->Y;
+      const int64_t ldy = ch->ldy;
+      const int ncols = ch->ncols;
+      const int atomic = ch->atomic;
+      for (int c0 = 0; c0 < bn; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        if (row < ch->n) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < ncols) {
+              float* dst = Y + row + (int64_t)col * ldy;
+              const float v = __uint_as_float(r[j]);
+              if (atomic) atomicAdd(dst, v);
+              else *dst = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, ncols_alloc);
+}
+
+// ------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encode() {
+  if (g_encode) return 0;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return -1;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return 0;
+}
+
+static int encode2d(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer, int64_t ld_elems,
+                    int box_outer) {
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld_elems * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda, const __nv_bfloat16* const* X,
+              int sx, int64_t ldx, int n, int ncols, int bn) {
+  if (get_encode()) return -1;
+  for (int a = 0; a < sa; ++a)
+    if (int e = encode2d(&h->tmA[a], A[a], n, n, lda, BM)) return e;
+  for (int x = 0; x < sx; ++x)
+    if (int e = encode2d(&h->tmX[x], X[x], n, ncols, ldx, bn)) return e;
+  return 0;
+}
+
+template <int SA, int SX>
+static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cudaStream_t st) {
+  const int stages = tc_stages(SA, SX, bn);
+  const int smem = stages * tc_stage_bytes(SA, SX, bn) + 1024 + 256;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  k_tc_gemm<SA, SX><<<items, 128, smem, st>>>(d_ch, C, bn, stages, d_err);
+  return (int)cudaGetLastError();
+}
+
+int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err, cudaStream_t st) {
+  if (items <= 0) return 0;
+  if (bn < 16 || bn > 256 || (bn % 16) != 0) return (int)cudaErrorInvalidValue;
+  if (sa == 1 && sx == 1) return launch_t<1, 1>(d_ch, C, items, bn, d_err, st);
+  if (sa == 2 && sx == 1) return launch_t<2, 1>(d_ch, C, items, bn, d_err, st);
+  if (sa == 2 && sx == 2) return launch_t<2, 2>(d_ch, C, items, bn, d_err, st);
+  if (sa == 3 && sx == 1) return launch_t<3, 1>(d_ch, C, items, bn, d_err, st);
+  if (sa == 3 && sx == 3) return launch_t<3, 3>(d_ch, C, items, bn, d_err, st);
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace rsvd

@@ -1,0 +1,78 @@
+// Internal launcher declarations of the rSVD CUDA kernels (not part of the ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace rsvd {
+
+// ----------------------------------------------------------------- tile GEMMs
+enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2 };
+enum MMKind {
+  MMK_DENSE_F64 = 0,     // C = V B, V dense row-major FP64, FP64 FMA
+  MMK_GRAM_F64 = 1,      // partial C_s = Y_s^T Z_s, FP64
+  MMK_NN_F64 = 2,        // C = A B, A tall column-major FP64
+  MMK_GRAM_DOT2 = 3,     // partial C_s = Y_s^T Z_s, FP32 data, compensated (Dot2) -> FP64
+  MMK_NN_F32_F64B = 4,   // C(FP32) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
+  MMK_NN_F32_OUT64 = 5   // C(FP64) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
+};
+
+struct MMDesc {
+  const void* A; int64_t lda;
+  const void* B; int64_t ldb;
+  void* Cm; int64_t ldc;
+  int m, n, k;
+  int mt, nt, ks, kchunk;   // tiles along m, n; k splits and their length
+  int mode;                 // MMMode
+  int sym;                  // Gram: only upper tiles
+  int64_t pstride;          // MM_PARTIAL: elements between split partials
+  const double* colscale;   // optional per-output-column scale
+  __nv_bfloat16* sl[3];     // optional BF16 slices of the result (column-major, ldsl)
+  int64_t ldsl;
+  int nsl;
+  const int* ncols_dev;     // optional: output columns limited to *ncols_dev (rank chosen on device)
+};
+
+struct ZeroDesc { void* p; int64_t ld; int rows, cols, esz; };
+void launch_zero(const ZeroDesc* d_zd, const int* d_off, int C, int tiles, cudaStream_t st);
+
+void launch_tile_mm(MMKind kind, const MMDesc* d_md, const int* d_off, int C, int tiles,
+                    cudaStream_t st);
+void launch_reduce_partials(const MMDesc* d_md, double* const* d_out, int C, int max_elems,
+                            cudaStream_t st);
+
+// ------------------------------------------------------------ small kernels
+// ||A||_F^2 partials per 64-row block, non-finite detection (dense input).
+void launch_fro2(const Chan* d_ch, const int* d_off_rows64, int C, int tiles, cudaStream_t st);
+void launch_fro2_reduce(const Chan* d_ch, int C, cudaStream_t st);
+void launch_fro2_reduce_rows(const Chan* d_ch, int C, int rows_per_part, cudaStream_t st);
+// Omega (FP64 form) into X[:, 0:l) of each channel, columns col0 + j.
+void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
+                      int col0, cudaStream_t st);
+// Upper Cholesky G = R^T R (l x l), R^{-1}; R_acc <- R R_acc when accumulate.
+// Shifted retry on breakdown (flag FLAG_SHIFTED).
+void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int n_rows_hint, cudaStream_t st);
+// One-sided Jacobi SVD of M = R^T (FP64 or FP32 arithmetic); writes sig, M <- left
+// vectors, J <- right vectors, sorted by descending sigma.
+void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st);
+// Rank selection (fixed or tolerance) from sig and ||A||^2 (FP64 identity),
+// or from the probe residual (mixed path).  Writes S and ChanResult.
+void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
+                   cudaStream_t st);
+// Sign fix: largest-|.| entry of U_i positive, flip V_i with it.
+void launch_signfix(const Chan* d_ch, int C, int max_k, cudaStream_t st);
+
+// --------------------------------------------------------- mixed-path kernels
+void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int tiles, int nsl,
+                           cudaStream_t st);
+void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
+                       int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st);
+void launch_probe_resid(const Chan* d_ch, const int* d_off, int C, int tiles, int max_l, int s,
+                        cudaStream_t st);
+void launch_probe_finish(const Chan* d_ch, int C, cudaStream_t st);
+
+// ------------------------------------------------------------ exact residual
+int resid_tiles(int n);
+void launch_resid(const double* A, int64_t lda, const double* U, int64_t ldu, const double* V, int64_t ldv,
+                  const double* S, int n, int k, double* part, cudaStream_t st);
+
+}  // namespace rsvd

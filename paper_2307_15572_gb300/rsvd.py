@@ -1,0 +1,239 @@
+"""Python binding of the C ABI in include/rsvd.h (argument marshalling only).
+
+Every function here forwards to the compiled library ``_lib/librsvd.so``;
+no step of the decomposition runs in Python.  Loading fails loudly when the
+library is missing or no CUDA device is present -- there is no CPU fallback.
+
+Low-level names mirror the C entry points (``rsvd_plan``, ``rsvd_decompose``,
+``rsvd_decompose_batched``, ``rsvd_reconstruct_error``, ``rsvd_plan_destroy``).
+``Plan`` is a thin convenience wrapper that takes torch CUDA tensors (or host
+numpy arrays) and allocates the caller-owned output buffers with torch.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# ------------------------------------------------------------------ enums
+RSVD_OK = 0
+RSVD_WARN_SHIFTED_CQR = 1
+RSVD_WARN_RANK_CAPPED = 2
+RSVD_ERR_INVALID_ARG = -1
+RSVD_ERR_CUDA = -2
+RSVD_ERR_OOM = -3
+RSVD_ERR_NONFINITE = -4
+RSVD_ERR_NOT_CONVERGED = -5
+RSVD_ERR_TOL_NOT_MET = -6
+RSVD_ERR_TIMEOUT = -7
+RSVD_ERR_UNSUPPORTED = -8
+
+PREC = {"fp64": 0, "bf16x": 1}
+POLICY = {"fixed": 0, "tol": 1, "adaptive": 2, "learned": 3}
+DENSE_F64, TILE_RULE = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+
+
+class Opts(C.Structure):
+    _fields_ = [("n_max", C.c_int64), ("k", C.c_int32), ("p", C.c_int32), ("q", C.c_int32),
+                ("tol", C.c_double), ("l_max", C.c_int32), ("block_b", C.c_int32),
+                ("precision", C.c_int32), ("slices", C.c_int32), ("rank_policy", C.c_int32),
+                ("rayleigh_ritz", C.c_int32), ("seed", C.c_uint64), ("stream", C.c_void_p),
+                ("mlp_weights", C.c_void_p)]
+
+
+class Matrix(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("mem", C.c_int32), ("n", C.c_int64), ("data", C.c_void_p),
+                ("ld", C.c_int64), ("rule_m", C.c_int32), ("rule_c", C.c_void_p),
+                ("rule_s", C.c_void_p), ("rule_w", C.c_void_p), ("rule_eta", C.c_double),
+                ("rule_seed", C.c_uint64)]
+
+
+class Factors(C.Structure):
+    _fields_ = [("mem", C.c_int32), ("U", C.c_void_p), ("ldu", C.c_int64), ("S", C.c_void_p),
+                ("V", C.c_void_p), ("ldv", C.c_int64), ("k_cap", C.c_int32), ("k_out", C.c_int32),
+                ("l_used", C.c_int32), ("err_est", C.c_double), ("status", C.c_int32)]
+
+
+_lib = None
+
+
+def load(build=True):
+    """Load (building first if needed) the C-ABI library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("librsvd.so not found at %s; run paper_2307_15572_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.rsvd_plan.argtypes = [C.POINTER(P), C.POINTER(Opts)]
+    lib.rsvd_plan.restype = C.c_int
+    lib.rsvd_plan_destroy.argtypes = [P]
+    lib.rsvd_plan_destroy.restype = None
+    lib.rsvd_decompose.argtypes = [P, C.POINTER(Matrix), C.POINTER(Factors)]
+    lib.rsvd_decompose.restype = C.c_int
+    lib.rsvd_decompose_batched.argtypes = [P, C.c_int32, C.POINTER(Matrix), C.POINTER(Factors),
+                                           C.POINTER(C.c_int)]
+    lib.rsvd_decompose_batched.restype = C.c_int
+    lib.rsvd_reconstruct_error.argtypes = [P, C.POINTER(Matrix), C.POINTER(Factors), C.POINTER(C.c_double)]
+    lib.rsvd_reconstruct_error.restype = C.c_int
+    lib.rsvd_plan_workspace_bytes.argtypes = [P]
+    lib.rsvd_plan_workspace_bytes.restype = C.c_int64
+    lib.rsvd_last_error_string.argtypes = []
+    lib.rsvd_last_error_string.restype = C.c_char_p
+    lib.rsvd_version.argtypes = []
+    lib.rsvd_version.restype = C.c_int32
+    _lib = lib
+    return lib
+
+
+def last_error():
+    return load().rsvd_last_error_string().decode()
+
+
+class RsvdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("rsvd status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(status):
+    if status < 0:
+        raise RsvdError(status, last_error())
+    return status
+
+
+# -------------------------------------------------------- C-named forwarders
+def rsvd_plan(opts):
+    h = C.c_void_p()
+    _check(load().rsvd_plan(C.byref(h), C.byref(opts)))
+    return h
+
+
+def rsvd_plan_destroy(h):
+    load().rsvd_plan_destroy(h)
+
+
+def rsvd_decompose(h, mat, fac):
+    return load().rsvd_decompose(h, C.byref(mat), C.byref(fac))
+
+
+def rsvd_decompose_batched(h, mats, facs):
+    n = len(mats)
+    MA = (Matrix * n)(*mats)
+    FA = (Factors * n)(*facs)
+    st = (C.c_int * n)()
+    r = load().rsvd_decompose_batched(h, n, MA, FA, st)
+    for i in range(n):
+        facs[i] = FA[i]
+    return r, list(st)
+
+
+def rsvd_reconstruct_error(h, mat, fac):
+    out = C.c_double()
+    _check(load().rsvd_reconstruct_error(h, C.byref(mat), C.byref(fac), C.byref(out)))
+    return out.value
+
+
+# ---------------------------------------------------------------- wrapper
+def make_opts(n_max, k=0, p=10, q=0, tol=0.0, precision="fp64", slices=0, policy="fixed", seed=0,
+              stream=None, rayleigh_ritz=False, l_max=0, block_b=0, mlp_weights=None):
+    o = Opts()
+    o.n_max = int(n_max)
+    o.k = int(k)
+    o.p = int(p)
+    o.q = int(q)
+    o.tol = float(tol)
+    o.l_max = int(l_max)
+    o.block_b = int(block_b)
+    o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.slices = int(slices)
+    o.rank_policy = POLICY[policy] if isinstance(policy, str) else int(policy)
+    o.rayleigh_ritz = 1 if rayleigh_ritz else 0
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    o.stream = stream
+    o.mlp_weights = mlp_weights
+    return o
+
+
+def dense(A):
+    """Matrix descriptor of a torch CUDA tensor (FP64, n x n) or a host numpy array."""
+    m = Matrix()
+    m.kind = DENSE_F64
+    if isinstance(A, np.ndarray):
+        assert A.dtype == np.float64 and A.ndim == 2 and A.shape[0] == A.shape[1]
+        assert A.flags.c_contiguous or A.strides[1] == 8
+        m.mem = MEM_HOST
+        m.n = A.shape[0]
+        m.ld = A.strides[0] // 8
+        m.data = A.ctypes.data
+    else:
+        import torch
+        assert A.dtype == torch.float64 and A.dim() == 2 and A.shape[0] == A.shape[1] and A.is_cuda
+        assert A.stride(1) == 1
+        m.mem = MEM_DEVICE
+        m.n = A.shape[0]
+        m.ld = A.stride(0)
+        m.data = A.data_ptr()
+    return m
+
+
+class Plan:
+    """Plan plus torch-allocated output buffers; see include/rsvd.h for the semantics."""
+
+    def __init__(self, n_max, **kw):
+        load()
+        self.opts = make_opts(n_max, **kw)
+        self.h = rsvd_plan(self.opts)
+
+    def close(self):
+        if self.h is not None:
+            rsvd_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def factors_for(n, k_cap, device="cuda"):
+        import torch
+        U = torch.empty((k_cap, n), dtype=torch.float64, device=device)   # column-major n x k_cap
+        V = torch.empty((k_cap, n), dtype=torch.float64, device=device)
+        S = torch.empty((k_cap,), dtype=torch.float64, device=device)
+        f = Factors()
+        f.mem = MEM_DEVICE
+        f.U, f.ldu = U.data_ptr(), n
+        f.V, f.ldv = V.data_ptr(), n
+        f.S = S.data_ptr()
+        f.k_cap = k_cap
+        return f, (U, S, V)
+
+    def decompose_batched(self, mats, k_cap):
+        """mats: list of torch CUDA FP64 tensors.  Returns (status, [result dicts])."""
+        descs, facs, bufs = [], [], []
+        for A in mats:
+            descs.append(dense(A))
+            f, b = self.factors_for(A.shape[0], min(k_cap, A.shape[0]))
+            facs.append(f)
+            bufs.append(b)
+        r, per = rsvd_decompose_batched(self.h, descs, facs)
+        out = []
+        for f, (U, S, V), s in zip(facs, bufs, per):
+            k = f.k_out
+            out.append(dict(U=U[:k].T, S=S[:k], V=V[:k].T, k=k, l=f.l_used, err_est=f.err_est, status=s,
+                            _fac=f))
+        return r, out
+
+    def decompose(self, A, k_cap):
+        r, out = self.decompose_batched([A], k_cap)
+        return r, out[0]
+
+    def reconstruct_error(self, A, res):
+        return rsvd_reconstruct_error(self.h, dense(A), res["_fac"])

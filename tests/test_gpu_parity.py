@@ -1,0 +1,191 @@
+"""GPU parity of the C-ABI library against the FP64 oracle (same seeded inputs).
+
+Bars (from the method's statement of the problem and the accuracy targets):
+  * all-FP64 path: singular values within 1e-10 relative of the oracle's for
+    sigma_i > 1e-12 sigma_1 (smaller ones within 1e-13 sigma_1 absolute), same
+    rank, and relative Frobenius error within 1.05x the oracle's;
+  * mixed path: relative Frobenius error within 1.05x the oracle's at the same
+    (k, p, q, seed); in tolerance mode error <= tol.
+"""
+import numpy as np
+import pytest
+
+from oracle import rsvd as orsvd
+from paper_2307_15572_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def run(lib, A, **kw):
+    torch = _torch()
+    At = torch.as_tensor(A, device="cuda")
+    k_cap = kw.pop("k_cap", None)
+    n = A.shape[0]
+    plan = lib.Plan(n, **kw)
+    try:
+        st, res = plan.decompose(At, k_cap or max(1, kw.get("k", 0) or n))
+        err = plan.reconstruct_error(At, res) if res["k"] > 0 else 1.0
+    finally:
+        plan.close()
+    return st, res, err
+
+
+def sigma_parity(s_gpu, s_ora, rel=1e-10):
+    s1 = s_ora[0]
+    big = s_ora > 1e-12 * s1
+    d = np.abs(s_gpu - s_ora)
+    assert np.all(d[big] <= rel * s_ora[big]), np.max(d[big] / s_ora[big])
+    assert np.all(d[~big] <= 1e-13 * s1)
+
+
+def test_fp64_dense2048_parity(lib):
+    A = synth.dense_case()
+    o = orsvd.rsvd(A, k=64, p=10, q=2, seed=synth.SEED_DENSE)
+    st, r, err = run(lib, A, k=64, p=10, q=2, seed=synth.SEED_DENSE)
+    assert st == 0, lib.last_error()
+    assert r["k"] == 64 and r["l"] == 74
+    sigma_parity(r["S"].cpu().numpy(), o.S)
+    e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+    assert err <= 1.05 * e_o
+    assert abs(r["err_est"] - o.err_est) <= 1e-10
+    # singular vectors: same sign convention, columns agree where well separated
+    U = r["U"].cpu().numpy()
+    dots = np.abs(np.sum(U[:, :40] * o.U[:, :40], axis=0))
+    assert np.all(dots > 1 - 1e-8)
+    assert np.allclose(U[:, :40], o.U[:, :40], atol=1e-7)
+
+
+@pytest.mark.parametrize("n,k,p,q", [(1, 1, 0, 0), (7, 3, 2, 1), (33, 8, 5, 0), (127, 20, 5, 2),
+                                     (129, 64, 10, 1), (300, 40, 10, 2), (257, 250, 10, 0)])
+def test_fp64_ragged_sizes(lib, n, k, p, q):
+    rng = np.random.default_rng(n)
+    sig = np.exp(-np.arange(1, n + 1) / max(2.0, n / 12))
+    A = synth.planted_haar(n, sig, 100 + n)
+    A += 1e-3 * rng.standard_normal((n, n)) * (A != 0)       # mildly non-symmetric, generic
+    A = 0.5 * (A + A.T)
+    o = orsvd.rsvd(A, k=k, p=p, q=q, seed=77)
+    st, r, err = run(lib, A, k=k, p=p, q=q, seed=77)
+    assert st in (0, 2), lib.last_error()       # 2 = rank capped (k + p > n)
+    kk = min(k, n)
+    assert r["k"] == kk
+    sigma_parity(r["S"].cpu().numpy(), o.S[:kk])
+    assert err <= 1.05 * orsvd.reconstruct_error(A, o.U, o.S, o.V) + 1e-14
+
+
+def test_fp64_tolerance_mode(lib):
+    n = 1500
+    A = synth.batch_channel(3, n)
+    o = orsvd.rsvd(A, tol=1e-4, l=128, q=1, seed=9)
+    st, r, err = run(lib, A, k=118, p=10, q=1, seed=9, tol=1e-4, policy="tol", k_cap=128)
+    assert st == 0, lib.last_error()
+    assert r["k"] == o.k
+    sigma_parity(r["S"].cpu().numpy(), o.S)
+    assert err <= 1e-4 and err <= 1.05 * orsvd.reconstruct_error(A, o.U, o.S, o.V)
+
+
+def test_fp64_rayleigh_ritz(lib):
+    n = 600
+    A = synth.planted_haar(n, synth.spectrum_exp(n, 12.0), 5)
+    o = orsvd.rsvd(A, k=30, p=10, q=1, seed=4, rayleigh_ritz=True)
+    st, r, err = run(lib, A, k=30, p=10, q=1, seed=4, rayleigh_ritz=True)
+    assert st == 0, lib.last_error()
+    sigma_parity(r["S"].cpu().numpy(), o.S)
+    assert err <= 1.05 * orsvd.reconstruct_error(A, o.U, o.S, o.V)
+
+
+def test_mixed_dense2048_error_ratio(lib):
+    A = synth.dense_case()
+    o = orsvd.rsvd(A, k=64, p=10, q=2, seed=synth.SEED_DENSE)
+    e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+    for slices in (2, 3):
+        st, r, err = run(lib, A, k=64, p=10, q=2, seed=synth.SEED_DENSE, precision="bf16x", slices=slices)
+        assert st == 0, lib.last_error()
+        assert r["k"] == 64
+        assert err <= 1.05 * e_o, (slices, err, e_o)
+        # singular values track the oracle to the words' precision
+        s = r["S"].cpu().numpy()
+        assert np.max(np.abs(s - o.S) / o.S) < (1e-3 if slices == 2 else 1e-5)
+
+
+@pytest.mark.parametrize("n", [1000, 2500])
+def test_mixed_tolerance_1e4(lib, n):
+    A = synth.batch_channel(1, n)
+    o = orsvd.rsvd(A, tol=1e-4, l=128, q=0, seed=3)
+    e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+    st, r, err = run(lib, A, k=118, p=10, q=0, seed=3, tol=1e-4, policy="tol", precision="bf16x",
+                     slices=2, k_cap=128)
+    assert st == 0, lib.last_error()
+    assert err <= 1e-4
+    # same draw, same algorithm: the rank may differ by the estimate's margin only
+    assert o.k <= r["k"] <= o.k + 12
+    assert abs(r["err_est"] - err) <= 0.35 * err
+
+
+def test_batched_uneven_channels_fp64_and_mixed(lib):
+    torch = _torch()
+    sizes = [300, 1000, 129, 2100, 64]
+    mats = [synth.batch_channel(c, n) for c, n in enumerate(sizes)]
+    for prec in ("fp64", "bf16x"):
+        plan = lib.Plan(max(sizes), k=40, p=10, q=1, seed=21, precision=prec)
+        try:
+            st, res = plan.decompose_batched([torch.as_tensor(A, device="cuda") for A in mats], 40)
+            assert st == 0, lib.last_error()
+            for A, r in zip(mats, res):
+                o = orsvd.rsvd(A, k=40, p=10, q=1, seed=21)
+                e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+                err = plan.reconstruct_error(torch.as_tensor(A, device="cuda"), r)
+                assert r["k"] == 40
+                assert err <= 1.05 * e_o, (prec, A.shape[0], err, e_o)
+                if prec == "fp64":
+                    sigma_parity(r["S"].cpu().numpy(), o.S)
+        finally:
+            plan.close()
+
+
+def test_host_buffers_match_device_buffers(lib):
+    A = synth.batch_channel(2, 700)
+    rs = lib
+    plan = rs.Plan(700, k=20, p=10, q=1, seed=8)
+    try:
+        torch = _torch()
+        st, rd = plan.decompose(torch.as_tensor(A, device="cuda"), 20)
+        m = rs.dense(np.ascontiguousarray(A))
+        f = rs.Factors()
+        U = np.zeros((20, 700)); V = np.zeros((20, 700)); S = np.zeros(20)
+        f.mem = rs.MEM_HOST; f.U = U.ctypes.data; f.ldu = 700; f.V = V.ctypes.data; f.ldv = 700
+        f.S = S.ctypes.data; f.k_cap = 20
+        st2 = rs.rsvd_decompose(plan.h, m, f)
+        assert st == 0 and st2 == 0
+        assert f.k_out == 20
+        # k-split FP64 accumulation uses atomics, so two runs agree to rounding
+        assert np.allclose(S, rd["S"].cpu().numpy(), rtol=1e-12, atol=0)
+        assert np.allclose(U.T, rd["U"].cpu().numpy(), rtol=0, atol=1e-10)
+        err_h = rs.rsvd_reconstruct_error(plan.h, m, f)
+        assert abs(err_h - plan.reconstruct_error(torch.as_tensor(A, device="cuda"), rd)) < 1e-12
+    finally:
+        plan.close()
+
+
+def test_nonfinite_input_reported(lib):
+    A = synth.batch_channel(0, 200)
+    A[17, 3] = np.nan
+    st, r, _ = run(lib, A, k=10, p=5, q=0, seed=1)
+    assert st == lib.RSVD_ERR_NONFINITE
+
+
+def test_invalid_arguments_rejected(lib):
+    torch = _torch()
+    A = torch.zeros((50, 50), dtype=torch.float64, device="cuda")
+    plan = lib.Plan(40, k=5, p=5)
+    try:
+        with pytest.raises(lib.RsvdError) as e:
+            st, _ = plan.decompose(A, 5)          # n > n_max
+            lib._check(st)
+        assert e.value.status == lib.RSVD_ERR_INVALID_ARG
+    finally:
+        plan.close()
