@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Throughput benchmark: matrix entries decomposed per second at relative
+Frobenius error <= 1e-4, mixed-precision (tensor-core) path vs all-FP64 path.
+
+Workload (one step = one grouped decomposition of the whole channel set):
+forty dense symmetric channel matrices, sizes drawn uniformly from
+[1000, 12000] (seeded), A_c = U_c diag(sigma) U_c^T with sigma_i = i^-2.5 and
+symmetric noise of spectral size 1e-8 sigma_1, decomposed to tolerance 1e-4
+(l = 128 columns, q = 0, rank chosen per channel).  Entries = sum n_c^2.
+Inputs are resident in HBM before timing; they are larger than L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank decomposes its own
+forty-channel set (weak scaling, no data-path collective).
+
+--impl reference times the CPU oracle (oracle/, FP64 numpy) on the machine's host
+cores on the same workload and metric.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matrix entries decomposed/s at rel-Frobenius err ≤1e-4, mixed vs FP64 path, 1 GB300"
+UNIT = "entries/s"
+L_COLS = 128          # columns drawn per channel (k cap 118 + p 10)
+P_OVER = 10
+TOL = 1e-4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--channels", type=int, default=40)
+    ap.add_argument("--nmin", type=int, default=1000)
+    ap.add_argument("--nmax", type=int, default=12000)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- setup
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist_
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist_.init_process_group(backend=backend)
+        dist = dist_
+    return ws, rank, local, dist
+
+
+def workload_sizes(args, rank):
+    from paper_2307_15572_gb300 import synth
+    seed = synth.SEED_BATCH + rank
+    return synth.batch_sizes(args.channels, args.nmin, args.nmax, seed=seed), seed
+
+
+def make_inputs(sizes, seed, device):
+    from paper_2307_15572_gb300 import synth
+    return [synth.batch_channel(c, n, seed=seed, device=device) for c, n in enumerate(sizes)]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def tc_traffic_record():
+    """ncu DRAM bytes of the tensor-core pass, per algorithmic byte, from the
+    committed profile summary -- only if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "tc_gemm_batch40.md")
+    src = os.path.join(ROOT, "paper_2307_15572_gb300", "csrc", "k_tc.cu")
+    if not os.path.exists(p):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    rec = {}
+    for line in open(p):
+        if line.startswith("traffic_per_algorithmic_byte:"):
+            rec["ratio"] = float(line.split(":")[1])
+        if line.startswith("k_tc_source_sha256_16:"):
+            rec["sha"] = line.split(":")[1].strip()
+    if rec.get("sha") != h or "ratio" not in rec:
+        return None
+    return rec["ratio"]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().split("\n") if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- gpu arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2307_15572_gb300 import rsvd
+
+    ws, rank, local, dist = dist_setup(args)
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    sizes, seed = workload_sizes(args, rank)
+    entries = float(sum(n * n for n in sizes))
+    mats = make_inputs(sizes, seed, "cuda")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    kcap = L_COLS - P_OVER
+    lib = rsvd
+
+    def make_plan(prec):
+        return rsvd.Plan(max(sizes), k=kcap, p=P_OVER, q=0, tol=TOL, policy="tol", precision=prec, slices=2,
+                         seed=seed, stream=stream.cuda_stream)
+
+    def alloc_factors(device="cuda", pin=False):
+        facs, bufs = [], []
+        for n in sizes:
+            kk = min(kcap, n)
+            if device == "cuda":
+                f, b = rsvd.Plan.factors_for(n, kk)
+            else:
+                U = torch.empty((kk, n), dtype=torch.float64, pin_memory=pin)
+                V = torch.empty((kk, n), dtype=torch.float64, pin_memory=pin)
+                S = torch.empty((kk,), dtype=torch.float64, pin_memory=pin)
+                f = rsvd.Factors()
+                f.mem = rsvd.MEM_HOST
+                f.U, f.ldu, f.V, f.ldv, f.S, f.k_cap = U.data_ptr(), n, V.data_ptr(), n, S.data_ptr(), kk
+                b = (U, S, V)
+            facs.append(f)
+            bufs.append(b)
+        return facs, bufs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    descs = [rsvd.dense(A) for A in mats]
+
+    def timed_steps(plan, facs, K, W, descs_, clocks=False):
+        for _ in range(W):
+            st, _ = rsvd.rsvd_decompose_batched(plan.h, descs_, facs)
+            if st < 0:
+                raise RuntimeError("decompose failed: %s" % rsvd.last_error())
+        rsvd.rsvd_plan_profile(plan.h, reset=True)
+        barrier()
+        ck = Clocks(dev) if clocks else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(K):
+            st, _ = rsvd.rsvd_decompose_batched(plan.h, descs_, facs)
+            if st < 0:
+                raise RuntimeError("decompose failed: %s" % rsvd.last_error())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk = ck.stop() if ck else None
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = rsvd.rsvd_plan_profile(plan.h, reset=True)
+        return ms, wall, prof, clk
+
+    def verify(plan, facs):
+        errs, ks = [], []
+        for A, f in zip(mats, facs):
+            errs.append(rsvd.rsvd_reconstruct_error(plan.h, rsvd.dense(A), f))
+            ks.append(f.k_out)
+        return max(errs), ks
+
+    # ---- mixed path (headline)
+    plan = make_plan("bf16x")
+    rsvd.rsvd_plan_set_profiling(plan.h, True)
+    facs, bufs = alloc_factors()
+    ms, wall, prof, clk = timed_steps(plan, facs, args.steps, args.warmup, descs, clocks=(rank == 0))
+    max_err, ks = verify(plan, facs)
+    ms_max = max_over_ranks(ms)
+    value = sum_over_ranks(entries * args.steps) / (ms_max / 1e3)
+    hbm_peak, peak_kind = peaks()
+    tc_ms_per = prof["tc_ms"] / max(1, prof["tc_launches"])
+    tc_bytes_per = prof["tc_bytes"] / max(1, prof["tc_launches"])
+    achieved = tc_bytes_per / (tc_ms_per / 1e3) / 1e9 if tc_ms_per > 0 else 0.0
+    ratio = tc_traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": (ratio * tc_bytes_per) if ratio else None,
+                "kernel": "k_tc_gemm (tcgen05 pass over V words)", "peak_source": peak_kind,
+                "launches": prof["tc_launches"], "avg_launch_ms": tc_ms_per,
+                "algorithmic_bytes_per_launch": tc_bytes_per,
+                "share_of_step": prof["tc_ms"] / ms if ms > 0 else None}
+    gpu_launches = int(prof["launches"])
+    plan.close()
+
+    # ---- e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hmats = []
+        for A in mats:
+            h = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
+            h.copy_(A)
+            hmats.append(h)
+        hdescs = [rsvd.dense(h) for h in hmats]
+        plan = make_plan("bf16x")
+        hf, hb = alloc_factors("cpu", pin=True)
+        ms_e, wall_e, prof_e, _ = timed_steps(plan, hf, args.e2e_steps, 1, hdescs)
+        h2d = sum(8 * n * n for n in sizes)
+        d2h = sum(8 * (2 * f.k_out * n + f.k_out) for f, n in zip(hf, sizes))
+        ms_e = max_over_ranks(ms_e)
+        e2e = {"value": sum_over_ranks(entries * args.e2e_steps) / (ms_e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "ms_per_step": ms_e / args.e2e_steps}
+        plan.close()
+        del hmats, hdescs, hb
+
+    # ---- all-FP64 path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        plan = make_plan("fp64")
+        rsvd.rsvd_plan_set_profiling(plan.h, True)
+        ff, fb = alloc_factors()
+        ms_f, wall_f, prof_f, _ = timed_steps(plan, ff, args.fp64_steps, 1, descs)
+        err_f, ks_f = verify(plan, ff)
+        ms_f = max_over_ranks(ms_f)
+        f64_ms = prof_f["f64_ms"] / max(1, prof_f["f64_launches"])
+        f64_tf = prof_f["f64_flops"] / max(1, prof_f["f64_launches"]) / (f64_ms / 1e3) / 1e12 if f64_ms else 0
+        fp64 = {"value": sum_over_ranks(entries * args.fp64_steps) / (ms_f / 1e3), "unit": UNIT,
+                "ms_per_step": ms_f / args.fp64_steps, "steps": args.fp64_steps, "max_rel_err": err_f,
+                "ranks": [min(ks_f), max(ks_f)],
+                "roofline": {"bound": "alu", "kernel": "k_tile_mm<double> (FP64 pass over V)",
+                             "achieved": f64_tf, "peak": 1.25, "unit": "TFLOP/s", "frac": f64_tf / 1.25,
+                             "peak_source": "nominal FP64 rate of GB300"}}
+        plan.close()
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_oracle(mats, sizes, seed, args.cpu_seconds)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+               "config": {"workload": "batch40: %d dense symmetric channels, n ~ U[%d, %d], "
+                                      "sigma_i = i^-2.5 + noise 1e-8 sigma_1, tol 1e-4"
+                                      % (args.channels, args.nmin, args.nmax),
+                          "channels": args.channels, "sum_n2_per_gpu": entries, "tol": TOL, "l": L_COLS,
+                          "q": 0, "words": 2, "policy": "tol",
+                          "precision": "V and X as 2 BF16 words, FP32 accumulate; compensated-FP64 Gram, "
+                                       "FP64 Cholesky",
+                          "l2": "inputs larger than L2 (no flush)", "max_rel_err": max_err,
+                          "verified_tol": bool(max_err <= TOL), "ranks": [min(ks), max(ks)],
+                          "parallelism": "channels per GPU" if ws > 1 else "single GPU"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+               "clocks": clk, "fp64_path": fp64,
+               "mixed_over_fp64": (value / fp64["value"]) if fp64 else None}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ oracle timing
+def cpu_oracle(mats, sizes, seed, budget_s):
+    """The oracle as it stands, on the host cores, over channels until the budget."""
+    import numpy as np
+
+    from oracle import rsvd as orsvd
+    done_entries, t_total, used = 0.0, 0.0, 0
+    host = []
+    for A in mats:
+        host.append(A.cpu().numpy() if hasattr(A, "cpu") else A)
+    for c, A in enumerate(host):
+        t0 = time.perf_counter()
+        r = orsvd.rsvd(A, tol=TOL, l=L_COLS, q=0, seed=seed)
+        t_total += time.perf_counter() - t0
+        done_entries += float(A.shape[0]) ** 2
+        used += 1
+        if t_total > budget_s:
+            break
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done_entries / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d channels (sum n^2 = %.3g), tol 1e-4, l = %d, q = 0, numpy FP64"
+                      % (used, len(host), done_entries, L_COLS),
+            "seconds": t_total}
+
+
+def run_reference(args):
+    ws, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    import numpy as np
+
+    from oracle import rsvd as orsvd
+    sizes, seed = workload_sizes(args, 0)
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else None
+    except Exception:
+        dev = None
+    # each step: a bounded sample of channels (rotating through the set)
+    order = list(range(len(sizes)))
+    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    cache = {}
+
+    def get(c):
+        if c not in cache:
+            from paper_2307_15572_gb300 import synth
+            A = synth.batch_channel(c, sizes[c], seed=seed, device=dev)
+            cache[c] = A.cpu().numpy() if dev else A
+        return cache[c]
+
+    pos = 0
+    times, ents = [], []
+    total_steps = args.warmup + args.steps
+    for s in range(total_steps):
+        t_step, e_step = 0.0, 0.0
+        while t_step < per_step_budget or e_step == 0:
+            c = order[pos % len(order)]
+            pos += 1
+            A = get(c)
+            t0 = time.perf_counter()
+            orsvd.rsvd(A, tol=TOL, l=L_COLS, q=0, seed=seed)
+            t_step += time.perf_counter() - t0
+            e_step += float(sizes[c]) ** 2
+            if len(cache) > 8:
+                cache.pop(next(iter(cache)))
+        if s >= args.warmup:
+            times.append(t_step)
+            ents.append(e_step)
+    value = sum(ents) / sum(times)
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    sample = "per step: channels of the 40-channel set in rotation for ~%.1f s of oracle time" % per_step_budget
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "batch40 (see gb300 arm)", "tol": TOL, "l": L_COLS, "q": 0},
+           "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -171,6 +171,28 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t plan, int32_t C, const rsvd_matri
 rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
                                    const rsvd_factors* f, double* rel_err);
 
+/* Launch accounting of the plan's own kernels, for benchmarks.  When enabled
+ * (rsvd_plan_set_profiling(plan, 1)), each decomposition records CUDA events
+ * on the plan's stream around every tensor-core pass and every FP64 dense
+ * pass over V and adds their device time and algorithmic traffic (bytes of V
+ * words, X words and Y read or written once, as the roofline counts them) to
+ * the counters below.  Kernel launches are counted whether or not timing is
+ * enabled.  rsvd_plan_profile copies the counters (host struct) and, if
+ * `reset` is non-zero, zeroes them. */
+typedef struct {
+  int64_t launches;        /* kernels launched by this plan                     */
+  int64_t tc_launches;     /* tensor-core passes over V                          */
+  double tc_ms;            /* their summed device time (CUDA events)             */
+  double tc_bytes;         /* their summed algorithmic bytes                     */
+  double tc_flops;         /* their summed MMA flops (2 m n k per word pair)     */
+  int64_t f64_launches;    /* FP64 dense passes over V                           */
+  double f64_ms;
+  double f64_flops;        /* 2 n^2 l per pass                                   */
+} rsvd_profile;
+
+rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
+rsvd_status rsvd_plan_profile(rsvd_plan_t plan, rsvd_profile* out, int32_t reset);
+
 /* Device buffer size (bytes) the plan holds now. */
 int64_t rsvd_plan_workspace_bytes(rsvd_plan_t plan);
 

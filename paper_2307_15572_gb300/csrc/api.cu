@@ -31,6 +31,13 @@
 
 using namespace rsvd;
 
+#include <atomic>
+namespace rsvd {
+static std::atomic<long long> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace rsvd
+
 namespace {
 
 thread_local char g_err[1024] = "";
@@ -68,6 +75,14 @@ struct rsvd_plan_s {
   size_t hp_cap = 0;
   int* d_err = nullptr;    // device error word
   int slices = 2;
+  // profiling
+  int profiling = 0;
+  rsvd_profile prof{};
+  std::vector<cudaEvent_t> ev_pool;
+  struct Timed { cudaEvent_t a, b; int kind; double bytes, flops; };
+  std::vector<Timed> pending;
+  size_t ev_next = 0;
+  long long launch_base = 0;
 };
 
 namespace {
@@ -122,6 +137,18 @@ rsvd_status grow_ws(rsvd_plan_s* P, size_t bytes) {
   return RSVD_OK;
 }
 
+// Event pair for a timed launch (pool grows, events are reused across calls).
+void timed_begin(rsvd_plan_s* P, cudaEvent_t* a, cudaEvent_t* b) {
+  while (P->ev_pool.size() < P->ev_next + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    P->ev_pool.push_back(e);
+  }
+  *a = P->ev_pool[P->ev_next++];
+  *b = P->ev_pool[P->ev_next++];
+  cudaEventRecord(*a, P->st);
+}
+
 // Split a tile count over k so that the grid covers the GPU a couple of times.
 int pick_splits(int64_t tiles, int64_t k, int min_chunk) {
   if (tiles >= 2 * NSM) return 1;
@@ -169,14 +196,26 @@ int total_of(Job& J, const std::function<int64_t(int)>& per) {
 // ------------------------------------------------------------ step builders
 void add_mm(Job& J, MMKind kind, const std::vector<MMDesc>& md) {
   std::vector<int> off(J.C + 1, 0);
-  for (int c = 0; c < J.C; ++c) off[c + 1] = off[c] + md[c].mt * md[c].nt * md[c].ks;
+  double flops = 0.0;
+  for (int c = 0; c < J.C; ++c) {
+    off[c + 1] = off[c] + md[c].mt * md[c].nt * md[c].ks;
+    flops += 2.0 * md[c].m * md[c].n * (double)md[c].k;
+  }
   const int tiles = off[J.C];
   const MMDesc* dmd = J.ar.put(md.data(), md.size());
   const int* doff = J.ar.put(off.data(), off.size());
   cudaStream_t st = J.P->st;
   const int C = J.C;
+  rsvd_plan_s* P = J.P;
   J.steps.push_back([=]() {
+    const bool timed = P->profiling && kind == MMK_DENSE_F64;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) timed_begin(P, &a, &b);
     launch_tile_mm(kind, dmd, doff, C, tiles, st);
+    if (timed) {
+      cudaEventRecord(b, st);
+      P->pending.push_back({a, b, 1, 0.0, flops});
+    }
     return RSVD_OK;
   });
 }
@@ -222,9 +261,10 @@ void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::functi
 void add_chol(Job& J, int accumulate) {
   const Chan* dch = J.d_ch;
   const int C = J.C, maxl = J.max_l;
+  const int f32inv = J.mixed ? 1 : 0;
   cudaStream_t st = J.P->st;
   J.steps.push_back([=]() {
-    launch_chol_inv(dch, C, accumulate, maxl, st);
+    launch_chol_inv(dch, C, accumulate, maxl, f32inv, st);
     return RSVD_OK;
   });
 }
@@ -371,11 +411,12 @@ void build_fp64(Job& J) {
 // --------------------------------------------------------------- mixed path
 rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
   // one grouped tcgen05 launch: Y32[:, 0:ncols) = sum words V_a X_b
-  int bn = 16;
-  for (int c = 0; c < J.C; ++c) {
-    const int nc = ncols_of_pass ? J.d[c].lw : J.d[c].l;
-    bn = std::max<int>(bn, (int)std::min<int64_t>(256, rup(nc, 16)));
-  }
+  // tile width: all columns in one tile up to the kernel's register
+  // accumulator width (160), else balanced column tiles
+  int maxnc = 16;
+  for (int c = 0; c < J.C; ++c) maxnc = std::max(maxnc, ncols_of_pass ? J.d[c].lw : J.d[c].l);
+  const int ntile = cdiv(maxnc, 160);
+  const int bn = (int)rup(cdiv(maxnc, ntile), 16);
   std::vector<TcChan> tcs(J.C);
   int64_t items0 = 0;
   for (int c = 0; c < J.C; ++c) {
@@ -428,9 +469,26 @@ rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
   cudaStream_t st = J.P->st;
   int* derr = J.P->d_err;
   const int C = J.C;
+  // algorithmic traffic: every V word, X word and Y element once; MMA flops
+  double bytes = 0.0, flops = 0.0;
+  int npairs = 0;
+  for (int a = 0; a < sa; ++a)
+    for (int x = 0; x < sx; ++x) npairs += (a + x < std::max(sa, sx));
+  for (int c = 0; c < J.C; ++c) {
+    const double n = J.d[c].n, nc = ncols_of_pass ? J.d[c].lw : J.d[c].l;
+    bytes += n * n * 2.0 * sa + n * nc * 2.0 * sx + n * nc * 4.0;
+    flops += 2.0 * n * n * nc * npairs;
+  }
+  rsvd_plan_s* P = J.P;
   J.steps.push_back([=]() {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (P->profiling) timed_begin(P, &ea, &eb);
     const int e = tc_launch(dtc, C, items, sa, sx, bn, derr, st);
     if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    if (P->profiling) {
+      cudaEventRecord(eb, st);
+      P->pending.push_back({ea, eb, 0, bytes, flops});
+    }
     return RSVD_OK;
   });
   return RSVD_OK;
@@ -442,8 +500,12 @@ void cqr2_mixed(Job& J, int nsl_out) {
   for (int round = 0; round < 2; ++round) {
     auto in = [&, round](int c) { return round == 0 ? ch[c].Y32 : ch[c].T32; };
     auto out = [&, round](int c) { return round == 0 ? ch[c].T32 : ch[c].Q32; };
-    add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)in(c); }, [&](int c) { return (const void*)in(c); },
-           [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+    // round 0: Y has kappa up to ~1e5, so the Gram needs FP64-grade accuracy
+    // (compensated Dot2); round 1: Q1 is orthonormal to ~1e-2, a plain FP32
+    // Gram is accurate enough
+    add_tn(J, round == 0 ? MMK_GRAM_DOT2 : MMK_GRAM_F32, [&](int c) { return (const void*)in(c); },
+           [&](int c) { return (const void*)in(c); }, [&](int c) { return ch[c].G; },
+           [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
     add_chol(J, 0);
     std::vector<MMDesc> md(J.C);
     for (int c = 0; c < J.C; ++c) {
@@ -493,8 +555,8 @@ rsvd_status build_mixed(Job& J) {
   }
   // projection with the probe block: [W | V G] = V [Q | G]
   if (rsvd_status s = tc_pass(J, nsl, nsl, 1)) return s;
-  // C = Q^T (V G)
-  add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Q32; },
+  // C = Q^T (V G) (FP32 accumulate is ample for the error estimate)
+  add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
          [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
          [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
   const int maxl = J.max_l;
@@ -658,10 +720,28 @@ void rsvd_plan_destroy(rsvd_plan_t P) {
   if (P->ws) cudaFree(P->ws);
   if (P->hp) cudaFreeHost(P->hp);
   if (P->d_err) cudaFree(P->d_err);
+  for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   delete P;
 }
 
 int64_t rsvd_plan_workspace_bytes(rsvd_plan_t P) { return P ? (int64_t)P->ws_cap : 0; }
+
+rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {
+  if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
+  P->profiling = enable ? 1 : 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_profile(rsvd_plan_t P, rsvd_profile* out, int32_t reset) {
+  if (!P || !out) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  *out = P->prof;
+  out->launches = launch_count() - P->launch_base;
+  if (reset) {
+    P->prof = rsvd_profile{};
+    P->launch_base = launch_count();
+  }
+  return RSVD_OK;
+}
 
 rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, rsvd_factors* f,
                                    rsvd_status* per_item) {
@@ -697,10 +777,12 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* 
     J.max_kcap = std::max(J.max_kcap, d.kcap);
   }
   for (int c = 0; c < C; ++c) {
+    // rows per Gram split: ~512, more when the batch is too small to fill the GPU
     ChanDims& d = J.d[c];
-    int g = (int)((2 * NSM + sum_gram_tiles - 1) / std::max<int64_t>(1, sum_gram_tiles));
-    g = std::max(1, std::min(g, cdiv(d.n, 256)));
-    d.gsplit = g;
+    int g = cdiv(d.n, 512);
+    const int want = (int)((2 * NSM + sum_gram_tiles - 1) / std::max<int64_t>(1, sum_gram_tiles));
+    g = std::max(g, std::min(want, cdiv(d.n, 64)));
+    d.gsplit = std::max(1, std::min(g, 64));
   }
   // pass 1: measure (buffers + descriptors), grow, pass 2: real pointers
   for (int pass = 0; pass < 2; ++pass) {
@@ -753,6 +835,14 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* 
   CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
   std::vector<ChanResult> res(hres, hres + C);
+  for (auto& t : P->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
+    else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
+  }
+  P->pending.clear();
+  P->ev_next = 0;
   const int derr = *herr;
   if (derr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", derr);
   rsvd_status worst = RSVD_OK;

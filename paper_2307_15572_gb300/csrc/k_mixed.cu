@@ -37,7 +37,27 @@ RSVD_DEV double bsum(double v, double* sh) {
   return r;
 }
 
-// 8 rows per tile; fro_part gets one partial per tile.
+// FP64 -> FP32 with round-to-nearest-even done on the integer pipe (the FP64
+// units are a small fraction of this part's throughput).  Normal results are
+// assembled from the bit fields; zeros, subnormal or overflowing results and
+// non-finite inputs take the conversion instruction.
+RSVD_DEV float f64_to_f32_rn(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const unsigned int e = (unsigned int)(b >> 52) & 0x7FFu;
+  const int fe = (int)e - 1023 + 127;
+  if (fe <= 0 || fe >= 255) return __double2float_rn(a);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned int keep = (unsigned int)(m >> 29);
+  const unsigned int rest = (unsigned int)(m & 0x1FFFFFFFull);
+  const unsigned int up = (rest > 0x10000000u) || (rest == 0x10000000u && (keep & 1u));
+  const unsigned int r = ((unsigned int)fe << 23) + keep + up;     // carry into the exponent is RN's overflow
+  return __uint_as_float((unsigned int)(b >> 32 & 0x80000000u) | r);
+}
+
+// 8 rows per tile; fro_part gets one partial per tile.  Each thread handles
+// pairs of adjacent columns so the BF16 words go out as 4-byte stores.
+// ||V||^2 is accumulated from the FP32 values (relative error ~1e-7, far
+// below what the relative tolerance needs) and summed in FP64 per tile.
 __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
                                                  const int* __restrict__ off, int C, int nsl) {
   __shared__ double sh[32];
@@ -46,30 +66,35 @@ __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
   const Chan& h = ch[c];
   const int b = t - off[c];
   const int r0 = b * 8, r1 = min(h.n, r0 + 8);
-  double s = 0.0;
+  float s = 0.0f;
   bool bad = false;
+  const int npair = (h.n + 1) >> 1;
   for (int r = r0; r < r1; ++r) {
     const double* row = h.A + (int64_t)r * h.lda;
-    for (int j = threadIdx.x; j < h.n; j += blockDim.x) {
-      const double a = row[j];
-      bad |= !isfinite(a);
-      s = fma(a, a, s);
-      double rem = a;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+      const int j = 2 * p;
+      const double a0 = row[j];
+      const double a1 = (j + 1 < h.n) ? row[j + 1] : 0.0;
+      bad |= !isfinite(a0) || !isfinite(a1);
+      float f0 = f64_to_f32_rn(a0), f1 = f64_to_f32_rn(a1);
+      s = fmaf(f0, f0, s);
+      s = fmaf(f1, f1, s);
       for (int w = 0; w < nsl; ++w) {
-        const __nv_bfloat16 q = __double2bfloat16(rem);
-        h.Ab[w][(int64_t)r * h.ldb + j] = q;
-        rem -= (double)__bfloat162float(q);
+        const __nv_bfloat16 q0 = __float2bfloat16_rn(f0), q1 = __float2bfloat16_rn(f1);
+        *(__nv_bfloat162*)(h.Ab[w] + (int64_t)r * h.ldb + j) = __halves2bfloat162(q0, q1);
+        f0 -= __bfloat162float(q0);     // exact: the remainder fits in FP32
+        f1 -= __bfloat162float(q1);
       }
     }
   }
-  s = bsum(s, sh);
+  const double sd = bsum((double)s, sh);
   if (bad) atomicOr(&h.res->flags, FLAG_NONFINITE);
-  if (threadIdx.x == 0) h.fro_part[b] = s;
+  if (threadIdx.x == 0) h.fro_part[b] = sd;
 }
 
 void launch_convert_slices(const Chan* d_ch, const int* d_off, int C, int tiles, int nsl,
                            cudaStream_t st) {
-  if (tiles > 0) k_convert<<<tiles, 256, 0, st>>>(d_ch, d_off, C, nsl);
+  if (tiles > 0) { k_convert<<<tiles, 256, 0, st>>>(d_ch, d_off, C, nsl); note_launch(); }
 }
 
 // Columns [j0, j1) of the X words: j < l are sketch columns (global column
@@ -100,7 +125,7 @@ __global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
 
 void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
                        int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st) {
-  if (tiles > 0) k_omega_bf16<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, j0, j1, pseed, nsl);
+  if (tiles > 0) { k_omega_bf16<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, j0, j1, pseed, nsl); note_launch(); }
 }
 
 // ||V G - Q C||^2 partial per 64-row tile (V G = Y32[:, l:l+s], C = C64).
@@ -158,10 +183,12 @@ void launch_probe_resid(const Chan* d_ch, const int* d_off, int C, int tiles, in
   if (bytes > 48 * 1024)
     cudaFuncSetAttribute(k_probe_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_probe_resid<<<tiles, 256, bytes, st>>>(d_ch, d_off, C);
+  note_launch();
 }
 
 void launch_probe_finish(const Chan* d_ch, int C, cudaStream_t st) {
   k_probe_finish<<<C, 256, 0, st>>>(d_ch);
+  note_launch();
 }
 
 // Zero column blocks of tall matrices (before k-split accumulation).
@@ -181,7 +208,7 @@ __global__ void k_zero(const ZeroDesc* __restrict__ zd, const int* __restrict__ 
 }
 
 void launch_zero(const ZeroDesc* d_zd, const int* d_off, int C, int tiles, cudaStream_t st) {
-  if (tiles > 0) k_zero<<<tiles, 256, 0, st>>>(d_zd, d_off, C);
+  if (tiles > 0) { k_zero<<<tiles, 256, 0, st>>>(d_zd, d_off, C); note_launch(); }
 }
 
 }  // namespace rsvd

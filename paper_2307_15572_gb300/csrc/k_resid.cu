@@ -84,6 +84,7 @@ void launch_resid(const double* A, int64_t lda, const double* U, int64_t ldu, co
                   const double* S, int n, int k, double* part, cudaStream_t st) {
   ResidDesc d{A, lda, U, ldu, V, ldv, S, n, k, part};
   k_resid<<<resid_tiles(n), 256, 0, st>>>(d);
+  note_launch();
 }
 
 }  // namespace rsvd

@@ -41,20 +41,28 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
   __shared__ T Bs[16][64 + 4];
   const int t = blockIdx.x;
   const int c = find_chan(off, C, t);
-  const MMDesc d = md[c];
+  // descriptor fields into registers (a struct copy would live on the stack)
+  const MMDesc* __restrict__ dp = md + c;
+  const int dm = dp->m, dn = dp->n, dk = dp->k, mt = dp->mt, nt = dp->nt, kchunk = dp->kchunk;
+  const int mode = dp->mode, sym = dp->sym, nsl = dp->nsl;
+  const int64_t lda = dp->lda, ldb = dp->ldb, ldc = dp->ldc, pstride = dp->pstride, ldsl = dp->ldsl;
+  const double* __restrict__ colscale = dp->colscale;
+  __nv_bfloat16* sl0 = dp->sl[0];
+  __nv_bfloat16* sl1 = dp->sl[1];
+  __nv_bfloat16* sl2 = dp->sl[2];
   int local = t - off[c];
-  const int per_split = d.mt * d.nt;
+  const int per_split = mt * nt;
   const int split = local / per_split;
   local -= split * per_split;
-  const int mi = local / d.nt, ni = local % d.nt;
-  if (d.sym && ni < mi) return;                  // Gram: upper tile triangle only
+  const int mi = local / nt, ni = local % nt;
+  if (sym && ni < mi) return;                    // Gram: upper tile triangle only
   const int m0 = mi * 64, n0 = ni * 64;
-  const int ncols = d.ncols_dev ? min(d.n, *d.ncols_dev) : d.n;
+  const int ncols = dp->ncols_dev ? min(dn, *dp->ncols_dev) : dn;
   if (n0 >= ncols) return;
-  const int kb = split * d.kchunk;
-  const int ke = min(d.k, kb + d.kchunk);
-  const TA* __restrict__ A = (const TA*)d.A;
-  const TB* __restrict__ B = (const TB*)d.B;
+  const int kb = split * kchunk;
+  const int ke = min(dk, kb + kchunk);
+  const TA* __restrict__ A = (const TA*)dp->A;
+  const TB* __restrict__ B = (const TB*)dp->B;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
   T acc[4][4], cmp[4][4];
@@ -73,8 +81,8 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
       else { mm = e & 63; kk = e >> 6; }              // contiguous along m
       const int gm = m0 + mm, gk = k0 + kk;
       T v = 0;
-      if (gm < d.m && gk < ke)
-        v = (T)(AL == AROW ? A[(int64_t)gm * d.lda + gk] : A[gm + (int64_t)gk * d.lda]);
+      if (gm < dm && gk < ke)
+        v = (T)(AL == AROW ? A[(int64_t)gm * lda + gk] : A[gm + (int64_t)gk * lda]);
       As[kk][mm] = v;
     }
     // B tile: 16 (k) x 64 (n), column-major source -> Bs[k][n]
@@ -84,7 +92,7 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
       const int kk = e & 15, nn = e >> 4;
       const int gk = k0 + kk, gn = n0 + nn;
       T v = 0;
-      if (gn < ncols && gk < ke) v = (T)B[gk + (int64_t)gn * d.ldb];
+      if (gn < ncols && gk < ke) v = (T)B[gk + (int64_t)gn * ldb];
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -114,26 +122,33 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
     __syncthreads();
   }
 
-  TC* __restrict__ Cp = (TC*)d.Cm + (d.mode == MM_PARTIAL ? (int64_t)split * d.pstride : 0);
+  TC* __restrict__ Cp = (TC*)dp->Cm + (mode == MM_PARTIAL ? (int64_t)split * pstride : 0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int gm = m0 + ty * 4 + i;
-    if (gm >= d.m) continue;
+    if (gm >= dm) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx * 4 + j;
       if (gn >= ncols) continue;
       double v = (double)acc[i][j] + (ACC == ACC_DOT2 ? (double)cmp[i][j] : 0.0);
-      if (d.colscale) v *= d.colscale[gn];
-      TC* dst = Cp + gm + (int64_t)gn * d.ldc;
-      if (d.mode == MM_ATOMIC) atomicAdd(dst, (TC)v);
+      if (colscale) v *= colscale[gn];
+      TC* dst = Cp + gm + (int64_t)gn * ldc;
+      if (mode == MM_ATOMIC) atomicAdd(dst, (TC)v);
       else *dst = (TC)v;
-      if (d.nsl > 0) {                   // BF16 word slices of the FP32 result
+      if (nsl > 0) {                     // BF16 word slices of the FP32 result
+        const int64_t o = gm + (int64_t)gn * ldsl;
         float r = (float)v;
-        for (int s = 0; s < d.nsl; ++s) {
-          const __nv_bfloat16 h = __float2bfloat16_rn(r);
-          d.sl[s][gm + (int64_t)gn * d.ldsl] = h;
+        __nv_bfloat16 h = __float2bfloat16_rn(r);
+        sl0[o] = h;
+        if (nsl > 1) {
           r -= __bfloat162float(h);
+          h = __float2bfloat16_rn(r);
+          sl1[o] = h;
+          if (nsl > 2) {
+            r -= __bfloat162float(h);
+            sl2[o] = __float2bfloat16_rn(r);
+          }
         }
       }
     }
@@ -165,12 +180,13 @@ void launch_tile_mm(MMKind kind, const MMDesc* d_md, const int* d_off, int C, in
                     cudaStream_t st) {
   if (tiles <= 0) return;
   switch (kind) {
-    case MMK_DENSE_F64: k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_GRAM_F64:  k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_NN_F64:    k_tile_mm<double, double, double, ACOL, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_GRAM_DOT2: k_tile_mm<float, float, double, AROW, ACC_DOT2><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_NN_F32_F64B: k_tile_mm<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_NN_F32_OUT64: k_tile_mm<float, double, double, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_DENSE_F64: k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_GRAM_F64:  k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_NN_F64:    k_tile_mm<double, double, double, ACOL, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_GRAM_DOT2: k_tile_mm<float, float, double, AROW, ACC_DOT2><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_NN_F32_F64B: k_tile_mm<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_NN_F32_OUT64: k_tile_mm<float, double, double, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_GRAM_F32: k_tile_mm<float, float, double, AROW, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
   }
 }
 
@@ -180,6 +196,7 @@ void launch_reduce_partials(const MMDesc* d_md, double* const* d_out, int C, int
   dim3 grid((max_elems + 255) / 256 < 64 ? (max_elems + 255) / 256 : 64, C);
   if (grid.x == 0) grid.x = 1;
   k_reduce_partials<<<grid, 256, 0, st>>>(d_md, d_out, C);
+  note_launch();
 }
 
 }  // namespace rsvd

@@ -70,13 +70,15 @@ __global__ void k_fro2_reduce(const Chan* __restrict__ ch, int nparts_per_row_bl
 }
 
 void launch_fro2(const Chan* d_ch, const int* d_off, int C, int tiles, cudaStream_t st) {
-  if (tiles > 0) k_fro2<<<tiles, 256, 0, st>>>(d_ch, d_off, C);
+  if (tiles > 0) { k_fro2<<<tiles, 256, 0, st>>>(d_ch, d_off, C); note_launch(); }
 }
 void launch_fro2_reduce(const Chan* d_ch, int C, cudaStream_t st) {
   k_fro2_reduce<<<C, 256, 0, st>>>(d_ch, 64);
+  note_launch();
 }
 void launch_fro2_reduce_rows(const Chan* d_ch, int C, int rows_per_part, cudaStream_t st) {
   k_fro2_reduce<<<C, 256, 0, st>>>(d_ch, rows_per_part);
+  note_launch();
 }
 
 // ------------------------------------------------------------- Omega (FP64)
@@ -97,68 +99,67 @@ __global__ void __launch_bounds__(256) k_omega_f64(const Chan* __restrict__ ch,
 
 void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
                       int col0, cudaStream_t st) {
-  if (tiles > 0) k_omega_f64<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0);
+  if (tiles > 0) { k_omega_f64<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0); note_launch(); }
 }
 
 // ------------------------------------------------- Cholesky + inverse (FP64)
-// G = R^T R with R upper triangular, computed row by row: for step j,
-// t_i = G_ji - sum_{k<j} R_kj R_ki (i >= j), R_jj = sqrt(t_j), R_ji = t_i / R_jj.
-// A non-positive pivot is a breakdown; the factorisation is then retried on
-// G + s I with the shift of Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa
-// (SIAM J. Sci. Comput. 42, 2020), s = 11 (m l + l (l+1)) u tr(G), which keeps
-// the shifted CholeskyQR well defined for kappa up to ~u^{-1}.
-// Then R^{-1} by back substitution (one thread per column) and, if asked,
-// R_acc <- R R_acc (the triangular factor of a repeated CholeskyQR).
+// G = R^T R with R upper triangular, right-looking: at step j, R_jj =
+// sqrt(G_jj), row j of R = row j of the updated G / R_jj, and the trailing
+// block is updated G_ab -= R_ja R_jb (independent FMAs, no long chains).  A
+// non-positive pivot is a breakdown; the factorisation is then retried on
+// G + s I with the shift of Fukaya, Kannan, Nakatsukasa, Yamamoto &
+// Yanagisawa (SIAM J. Sci. Comput. 42, 2020), s = 11 (m l + l (l+1)) u tr(G),
+// which keeps the shifted CholeskyQR well defined for kappa up to ~u^{-1}.
+// Then R^{-1}: in FP64 (one thread per column, back substitution), or, for
+// the mixed path, in FP32 row by row with all columns in parallel -- any
+// invertible right factor leaves range(Y R^{-1}) = range(Y), and the second
+// CholeskyQR round restores orthogonality.  If asked, R_acc <- R R_acc (the
+// triangular factor of a repeated CholeskyQR).
 __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, int accumulate,
-                                                  int use_smem) {
+                                                  int use_smem, int f32_inverse) {
   extern __shared__ double smem[];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l;
+  const int ld = use_smem ? l + 1 : l;       // odd stride: conflict-free column access
   double* Ms = use_smem ? smem : h.M;        // working copy of G -> R (column-major)
   const double* G = h.G;
   __shared__ int fail;
   __shared__ double shift;
   __shared__ double tr;
-  if (threadIdx.x == 0) { fail = 0; shift = 0.0; tr = 0.0; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    fail = 0;
+    shift = 0.0;
     double s = 0.0;
     for (int i = 0; i < l; ++i) s += G[i + (int64_t)i * l];
     tr = s;
   }
+  __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x) Ms[e] = G[e];
-    __syncthreads();
-    if (attempt == 1) {
-      for (int i = threadIdx.x; i < l; i += blockDim.x) Ms[i + (int64_t)i * l] += shift;
-      __syncthreads();
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e % l, j = e / l;
+      Ms[i + (int64_t)j * ld] = G[e] + ((i == j) ? shift : 0.0);
     }
+    int bad = 0;
     for (int j = 0; j < l; ++j) {
-      for (int i = j + threadIdx.x; i < l; i += blockDim.x) {
-        double s = Ms[j + (int64_t)i * l];
-        const double* cj = Ms + (int64_t)j * l;
-        const double* ci = Ms + (int64_t)i * l;
-        for (int k = 0; k < j; ++k) s = fma(-cj[k], ci[k], s);
-        Ms[j + (int64_t)i * l] = s;
+      __syncthreads();
+      const double d = Ms[j + (int64_t)j * ld];
+      if (!(d > 0.0) || !isfinite(d)) { bad = 1; break; }      // uniform across the block
+      const double rjj = sqrt(d), inv = 1.0 / rjj;
+      __syncthreads();
+      for (int i = j + tid; i < l; i += nt)
+        Ms[j + (int64_t)i * ld] = (i == j) ? rjj : Ms[j + (int64_t)i * ld] * inv;
+      __syncthreads();
+      const int m = l - j - 1;
+      for (int e = tid; e < m * m; e += nt) {
+        const int a = j + 1 + e % m, b = j + 1 + e / m;
+        if (a <= b) Ms[a + (int64_t)b * ld] = fma(-Ms[j + (int64_t)a * ld], Ms[j + (int64_t)b * ld],
+                                                  Ms[a + (int64_t)b * ld]);
       }
-      __syncthreads();
-      const double d = Ms[j + (int64_t)j * l];
-      const bool bad = !(d > 0.0) || !isfinite(d);
-      if (bad) break;                                  // uniform across the block
-      const double rjj = sqrt(d);
-      for (int i = j + 1 + threadIdx.x; i < l; i += blockDim.x) Ms[j + (int64_t)i * l] /= rjj;
-      __syncthreads();
-      if (threadIdx.x == 0) Ms[j + (int64_t)j * l] = rjj;
-      __syncthreads();
     }
     __syncthreads();
-    int ok = 1;
-    for (int j = 0; j < l; ++j) {
-      const double d = Ms[j + (int64_t)j * l];
-      if (!(d > 0.0) || !isfinite(d)) { ok = 0; break; }
-    }
-    if (ok) break;
-    if (threadIdx.x == 0) {
+    if (!bad) break;
+    if (tid == 0) {
       if (attempt == 0) {
         shift = 11.0 * ((double)h.n * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
         atomicOr(&h.res->flags, FLAG_SHIFTED);
@@ -172,50 +173,80 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
   }
   __syncthreads();
   if (fail) return;
-  // zero the strictly lower part so Ms holds R exactly
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e % l, j = e / l;
-    if (i > j) Ms[e] = 0.0;
-  }
-  __syncthreads();
-  // R^{-1}: column c solves R x = e_c
-  for (int cidx = threadIdx.x; cidx < l; cidx += blockDim.x) {
-    double* x = h.Ri + (int64_t)cidx * l;
-    for (int i = cidx + 1; i < l; ++i) x[i] = 0.0;
-    x[cidx] = 1.0 / Ms[cidx + (int64_t)cidx * l];
-    for (int i = cidx - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= cidx; ++k) s = fma(Ms[i + (int64_t)k * l], x[k], s);
-      x[i] = -s / Ms[i + (int64_t)i * l];
-    }
-  }
-  __syncthreads();
+  // R (upper, zero below) -> h.R, or R_acc <- R R_acc
   if (accumulate) {
-    // R_acc <- R R_acc (both upper); read old R_acc column by column into
-    // registers is not possible for general l, so write the product to G
-    // (free now) and copy back.
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    for (int e = tid; e < l * l; e += nt) {
       const int i = e % l, j = e / l;
       double s = 0.0;
       if (i <= j)
-        for (int k = i; k <= j; ++k) s = fma(Ms[i + (int64_t)k * l], h.R[k + (int64_t)j * l], s);
-      h.G[e] = s;
+        for (int k = i; k <= j; ++k) s = fma(Ms[i + (int64_t)k * ld], h.R[k + (int64_t)j * l], s);
+      h.G[e] = s;                               // G is free now
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x) h.R[e] = h.G[e];
-  } else {
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x) h.R[e] = Ms[e];
+    for (int e = tid; e < l * l; e += nt) h.R[e] = h.G[e];
+  }
+  if (!accumulate) {
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e % l, j = e / l;
+      h.R[e] = (i <= j) ? Ms[i + (int64_t)j * ld] : 0.0;
+    }
+  }
+  __syncthreads();
+  if (f32_inverse && use_smem) {
+    // FP32 copy of R (stride l+1) and X = R^{-1} stored row-major, in the same smem
+    float* Rs = (float*)smem;
+    float* Xs = Rs + (int64_t)l * (l + 1);
+    // Ms (double) overlaps Rs/Xs: copy R via registers in two phases through h.Ri
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e % l, j = e / l;
+      h.Ri[e] = (i <= j) ? Ms[i + (int64_t)j * ld] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e % l, j = e / l;
+      Rs[i + (int64_t)j * (l + 1)] = (float)h.Ri[e];
+      Xs[e] = 0.0f;
+    }
+    __syncthreads();
+    for (int i = l - 1; i >= 0; --i) {
+      const float rii = Rs[i + (int64_t)i * (l + 1)];
+      for (int c = i + tid; c < l; c += nt) {
+        float s = (c == i) ? 1.0f : 0.0f;
+        for (int k = i + 1; k <= c; ++k) s = fmaf(-Rs[i + (int64_t)k * (l + 1)], Xs[(int64_t)k * l + c], s);
+        Xs[(int64_t)i * l + c] = s / rii;
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < l * l; e += nt) {
+      const int k = e % l, c = e / l;           // Ri column-major: Ri[k + c l] = X[k][c]
+      h.Ri[e] = (double)Xs[(int64_t)k * l + c];
+    }
+    return;
+  }
+  // FP64 R^{-1}: column c solves R x = e_c
+  for (int cidx = tid; cidx < l; cidx += nt) {
+    double* x = h.Ri + (int64_t)cidx * l;
+    for (int i = cidx + 1; i < l; ++i) x[i] = 0.0;
+    x[cidx] = 1.0 / Ms[cidx + (int64_t)cidx * ld];
+    for (int i = cidx - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= cidx; ++k) s = fma(Ms[i + (int64_t)k * ld], x[k], s);
+      x[i] = -s / Ms[i + (int64_t)i * ld];
+    }
   }
 }
 
-void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, cudaStream_t st) {
-  const size_t bytes = (size_t)max_l * max_l * sizeof(double);
+void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
+                     cudaStream_t st) {
+  const size_t bytes = (size_t)max_l * (max_l + 1) * sizeof(double);
   const int use_smem = bytes <= 200 * 1024;
   if (use_smem) {
     cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_chol_inv<<<C, 256, bytes, st>>>(d_ch, accumulate, 1);
+    k_chol_inv<<<C, 256, bytes, st>>>(d_ch, accumulate, 1, f32_inverse);
+    note_launch();
   } else {
-    k_chol_inv<<<C, 256, 0, st>>>(d_ch, accumulate, 0);
+    k_chol_inv<<<C, 256, 0, st>>>(d_ch, accumulate, 0, f32_inverse);
+    note_launch();
   }
 }
 
@@ -231,67 +262,81 @@ void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, cudaStr
 // one warp per pair runs without synchronisation inside the round.  Sweeps
 // repeat until no pair exceeds |gamma| <= l eps sqrt(alpha beta) (or a cap).
 // Result: M J = X Sigma with X orthonormal, so R^T = X Sigma J^T.
-template <typename T>
+template <typename T, bool WANT_J>
 __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int use_smem,
                                                 int max_sweeps) {
   extern __shared__ unsigned char sraw[];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l;
   const int m = l + (l & 1);                       // even count; index l (if odd) is a zero column
+  const int ld = use_smem ? l + 1 : l;             // odd stride in shared memory
   T* Mw;
   T* Jw;
-  if (use_smem) { Mw = (T*)sraw; Jw = Mw + (int64_t)l * l; }
+  if (use_smem) { Mw = (T*)sraw; Jw = Mw + (int64_t)l * ld; }
   else { Mw = (T*)h.G; Jw = (T*)h.Ri; }            // G and R^{-1} are free at this point
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e % l, j = e / l;
-    Mw[e] = (T)h.R[j + (int64_t)i * l];            // M = R^T
-    Jw[e] = (T)(i == j ? 1.0 : 0.0);
+    Mw[i + (int64_t)j * ld] = (T)h.R[j + (int64_t)i * l];      // M = R^T
+    if (WANT_J) Jw[i + (int64_t)j * ld] = (T)(i == j ? 1.0 : 0.0);
   }
   __shared__ int nrot;
-  __shared__ int sweeps_done;
   __syncthreads();
   const T eps = (sizeof(T) == 8) ? (T)1.1102230246251565e-16 : (T)5.9604645e-8;
   const T thr = (T)l * eps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int grp = lane >> 3, gl = lane & 7;        // four 8-lane groups per warp, one pair each
+  const int npairs = m / 2;
+  const int per_pass = nwarp * 4;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
     for (int r = 0; r < m - 1; ++r) {
-      for (int pi = warp; pi < m / 2; pi += nwarp) {
-        int a, b;
-        if (pi == 0) { a = r; b = m - 1; }
-        else { a = (r + pi) % (m - 1); b = (r - pi + (m - 1)) % (m - 1); }
-        if (a >= l || b >= l) continue;
-        if (a > b) { const int tmp = a; a = b; b = tmp; }
-        T* ca = Mw + (int64_t)a * l;
-        T* cb = Mw + (int64_t)b * l;
-        T al = 0, be = 0, ga = 0;
-        for (int rr = lane; rr < l; rr += 32) {
-          const T x = ca[rr], y = cb[rr];
-          al += x * x; be += y * y; ga += x * y;
+      for (int base = 0; base < npairs; base += per_pass) {
+        const int pi = base + warp * 4 + grp;
+        int a = -1, b = -1;
+        if (pi < npairs) {
+          if (pi == 0) { a = r; b = m - 1; }
+          else { a = (r + pi) % (m - 1); b = (r - pi + (m - 1)) % (m - 1); }
+          if (a > b) { const int t = a; a = b; b = t; }
+          if (b >= l) a = b = -1;
         }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga == (T)0 || fabs(ga) <= thr * sqrt(al * be)) continue;
+        T al = 0, be = 0, ga = 0;
+        T* ca = Mw + (int64_t)(a < 0 ? 0 : a) * ld;
+        T* cb = Mw + (int64_t)(b < 0 ? 0 : b) * ld;
+        if (a >= 0)
+          for (int rr = gl; rr < l; rr += 8) {
+            const T x = ca[rr], y = cb[rr];
+            al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+          }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {          // reduce inside the 8-lane group
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (a < 0 || ga == (T)0 || fabs(ga) <= thr * sqrt(al * be)) continue;
         const T zeta = (be - al) / (2 * ga);
         T t;
         if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
         else t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
         const T cs = (T)1 / sqrt((T)1 + t * t);
         const T sn = cs * t;
-        for (int rr = lane; rr < l; rr += 32) {
+        for (int rr = gl; rr < l; rr += 8) {
           const T x = ca[rr], y = cb[rr];
           ca[rr] = cs * x - sn * y;
           cb[rr] = sn * x + cs * y;
         }
-        T* ja = Jw + (int64_t)a * l;
-        T* jb = Jw + (int64_t)b * l;
-        for (int rr = lane; rr < l; rr += 32) {
-          const T x = ja[rr], y = jb[rr];
-          ja[rr] = cs * x - sn * y;
-          jb[rr] = sn * x + cs * y;
+        if (WANT_J) {
+          T* ja = Jw + (int64_t)a * ld;
+          T* jb = Jw + (int64_t)b * ld;
+          for (int rr = gl; rr < l; rr += 8) {
+            const T x = ja[rr], y = jb[rr];
+            ja[rr] = cs * x - sn * y;
+            jb[rr] = sn * x + cs * y;
+          }
         }
-        if (lane == 0) atomicAdd(&nrot, 1);
+        if (gl == 0) atomicAdd(&nrot, 1);
       }
       __syncthreads();
     }
@@ -299,14 +344,11 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
     __syncthreads();
     if (done) break;
   }
-  if (threadIdx.x == 0) {
-    sweeps_done = sweep;
-    if (sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
-  }
+  if (threadIdx.x == 0 && sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
   __syncthreads();
   // column norms (unsorted) into scratch
   for (int cidx = warp; cidx < l; cidx += nwarp) {
-    const T* cc = Mw + (int64_t)cidx * l;
+    const T* cc = Mw + (int64_t)cidx * ld;
     double s = 0.0;
     for (int rr = lane; rr < l; rr += 32) s += (double)cc[rr] * (double)cc[rr];
     s = warp_sum(s);
@@ -322,36 +364,38 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
       rank += (so > si) || (so == si && o < cidx);
     }
     rank = warp_sum(rank);
-    const T* cc = Mw + (int64_t)cidx * l;
-    const T* jc = Jw + (int64_t)cidx * l;
+    const T* cc = Mw + (int64_t)cidx * ld;
     const double inv = si > 0.0 ? 1.0 / si : 0.0;
-    for (int rr = lane; rr < l; rr += 32) {
-      h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
-      h.J[rr + (int64_t)rank * l] = (double)jc[rr];
+    for (int rr = lane; rr < l; rr += 32) h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
+    if (WANT_J) {
+      const T* jc = Jw + (int64_t)cidx * ld;
+      for (int rr = lane; rr < l; rr += 32) h.J[rr + (int64_t)rank * l] = (double)jc[rr];
     }
     if (lane == 0) h.sig[rank] = si;
   }
 }
 
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st) {
+  // mixed path (fp32): only the left vectors X are used; FP64 path needs J too
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  const size_t bytes = 2 * (size_t)max_l * max_l * esz;
+  const size_t bytes = (fp32 ? 1 : 2) * (size_t)max_l * (max_l + 1) * esz;
   const int use_smem = bytes <= 200 * 1024;
   if (fp32) {
     if (use_smem) {
-      cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      k_jacobi<float><<<C, 512, bytes, st>>>(d_ch, 1, 60);
+      cudaFuncSetAttribute(k_jacobi<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      k_jacobi<float, false><<<C, 512, bytes, st>>>(d_ch, 1, 60);
     } else {
-      k_jacobi<float><<<C, 512, 0, st>>>(d_ch, 0, 60);
+      k_jacobi<float, false><<<C, 512, 0, st>>>(d_ch, 0, 60);
     }
   } else {
     if (use_smem) {
-      cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      k_jacobi<double><<<C, 512, bytes, st>>>(d_ch, 1, 60);
+      cudaFuncSetAttribute(k_jacobi<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      k_jacobi<double, true><<<C, 512, bytes, st>>>(d_ch, 1, 60);
     } else {
-      k_jacobi<double><<<C, 512, 0, st>>>(d_ch, 0, 60);
+      k_jacobi<double, true><<<C, 512, 0, st>>>(d_ch, 0, 60);
     }
   }
+  note_launch();
 }
 
 // ------------------------------------------------------------ rank selection
@@ -430,6 +474,7 @@ __global__ void k_select(const Chan* __restrict__ ch, int policy, double tol, in
 void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
                    cudaStream_t st) {
   k_select<<<C, 32, 0, st>>>(d_ch, policy, tol, use_probe);
+  note_launch();
 }
 
 // ------------------------------------------------------------------ sign fix
@@ -474,6 +519,7 @@ __global__ void __launch_bounds__(256) k_signfix(const Chan* __restrict__ ch) {
 void launch_signfix(const Chan* d_ch, int C, int max_k, cudaStream_t st) {
   if (max_k <= 0) return;
   k_signfix<<<dim3(C, max_k), 256, 0, st>>>(d_ch);
+  note_launch();
 }
 
 }  // namespace rsvd

@@ -55,6 +55,10 @@ RSVD_DEV void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
                "r"(bytes) : "memory");
 }
 
+RSVD_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 RSVD_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -140,16 +144,29 @@ RSVD_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // ------------------------------------------------------------------ kernel
+// The tensor core rounds its FP32 accumulation toward zero, so one TMEM
+// accumulator summed over all n/16 MMA steps would carry a bias growing
+// linearly with n (~n/16 * 2^-24 relative: 5e-5 at n = 12,000).  The k loop
+// is therefore cut into chunks of CHUNK_KT 64-wide steps; each chunk is
+// accumulated from zero in one of two TMEM buffers and the four epilogue
+// warps add it into FP32 registers (round to nearest) while the next chunk
+// runs in the other buffer.  The bias is then bounded by one chunk's worth
+// (4 * CHUNK_KT truncations, ~2e-6), and the register sum is unbiased.
+static constexpr int CHUNK_KT = 8;
+static constexpr int BN_MAX = 160;            // register accumulator width
+static constexpr int NTHREADS = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
+
 template <int SA, int SX>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int SB = SA * A_TILE_BYTES + SX * bn * BK * 2;
   uint64_t* full = (uint64_t*)(base + (size_t)stages * SB);
   uint64_t* empty = full + stages;
-  uint64_t* done = empty + stages;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* acc_full = empty + stages;     // [2] MMA -> epilogue
+  uint64_t* acc_empty = acc_full + 2;      // [2] epilogue -> MMA (128 arrivals)
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -170,12 +187,13 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
   const int kt_total = (ch->n + BK - 1) / BK;
   const int kb = split * ch->kt_per_split;
   const int nk = min(kt_total, kb + ch->kt_per_split) - kb;
+  const int nchunks = (nk + CHUNK_KT - 1) / CHUNK_KT;
   uint32_t ncols_alloc = 32;
-  while ((int)ncols_alloc < bn) ncols_alloc <<= 1;
+  while ((int)ncols_alloc < 2 * bn) ncols_alloc <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tmem_slot, ncols_alloc);
@@ -185,86 +203,121 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
   const uint32_t tmem = *tmem_slot;
 
   if (nk > 0) {
-    if (warp == 0 && lane == 0) {
-      // ---------------- producer
-      for (int a = 0; a < SA; ++a) tmap_acquire(&ch->tmA[a]);
-      for (int x = 0; x < SX; ++x) tmap_acquire(&ch->tmX[x]);
-      int issued = 0;
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % stages;
-        const uint32_t ph = (uint32_t)(it / stages) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u)) { set_err(err, DERR_TIMEOUT_TMA); break; }
-        mbar_arrive_expect_tx(&full[s], (uint32_t)SB);
-        unsigned char* st = base + (size_t)s * SB;
-        const int kx = (kb + it) * BK;
-        for (int a = 0; a < SA; ++a) tma_load_2d(st + a * A_TILE_BYTES, &ch->tmA[a], &full[s], kx, m0);
-        for (int x = 0; x < SX; ++x)
-          tma_load_2d(st + SA * A_TILE_BYTES + x * bn * BK * 2, &ch->tmX[x], &full[s], kx, n0);
-        issued = it + 1;
+    if (warp == 4) {
+      if (lane == 0) {
+        // ---------------- TMA producer
+        for (int a = 0; a < SA; ++a) tmap_acquire(&ch->tmA[a]);
+        for (int x = 0; x < SX; ++x) tmap_acquire(&ch->tmX[x]);
+        int issued = 0;
+        for (int it = 0; it < nk; ++it) {
+          const int s = it % stages;
+          const uint32_t ph = (uint32_t)(it / stages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) { set_err(err, DERR_TIMEOUT_TMA); break; }
+          mbar_arrive_expect_tx(&full[s], (uint32_t)SB);
+          unsigned char* st = base + (size_t)s * SB;
+          const int kx = (kb + it) * BK;
+          for (int a = 0; a < SA; ++a) tma_load_2d(st + a * A_TILE_BYTES, &ch->tmA[a], &full[s], kx, m0);
+          for (int x = 0; x < SX; ++x)
+            tma_load_2d(st + SA * A_TILE_BYTES + x * bn * BK * 2, &ch->tmX[x], &full[s], kx, n0);
+          issued = it + 1;
+        }
+        // drain: the last copy issued into each stage has landed
+        for (int s = 0; s < stages && s < issued; ++s) {
+          const int last = s + ((issued - 1 - s) / stages) * stages;
+          if (!mbar_wait(&full[s], (uint32_t)(last / stages) & 1u)) set_err(err, DERR_TIMEOUT_TMA);
+        }
       }
-      // drain: the last copy issued into each stage has landed
-      for (int s = 0; s < stages && s < issued; ++s) {
-        const int last = s + ((issued - 1 - s) / stages) * stages;
-        if (!mbar_wait(&full[s], (uint32_t)(last / stages) & 1u)) set_err(err, DERR_TIMEOUT_TMA);
-      }
-    } else if (warp == 1 && lane == 0) {
-      // ---------------- MMA issuer
-      const uint32_t idesc = idesc_bf16(bn);
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % stages;
-        const uint32_t ph = (uint32_t)(it / stages) & 1u;
-        if (!mbar_wait(&full[s], ph)) { set_err(err, DERR_TIMEOUT_MMA); break; }
-        tc_fence_after();
-        const uint32_t sa0 = smem_addr(base + (size_t)s * SB);
-        const uint32_t sx0 = sa0 + SA * A_TILE_BYTES;
+      __syncwarp();
+    } else if (warp == 5) {
+      if (lane == 0) {
+        // ---------------- MMA issuer
+        const uint32_t idesc = idesc_bf16(bn);
+        bool ok = true;
+        int it = 0;
+        for (int c = 0; c < nchunks && ok; ++c) {
+          const int b = c & 1;
+          if (c >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((c >> 1) - 1) & 1u)) {
+            set_err(err, DERR_TIMEOUT_MMA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)(b * bn);
+          const int itend = min(nk, it + CHUNK_KT);
+          for (; it < itend; ++it) {
+            const int s = it % stages;
+            const uint32_t ph = (uint32_t)(it / stages) & 1u;
+            if (!mbar_wait(&full[s], ph)) { set_err(err, DERR_TIMEOUT_MMA); ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa0 = smem_addr(base + (size_t)s * SB);
+            const uint32_t sx0 = sa0 + SA * A_TILE_BYTES;
+            const bool first = (it == c * CHUNK_KT);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
+            for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-          for (int a = 0; a < SA; ++a) {
+              for (int a = 0; a < SA; ++a) {
 #pragma unroll
-            for (int x = 0; x < SX; ++x) {
-              if (a + x >= (SA > SX ? SA : SX)) continue;
-              const uint64_t ad = sdesc_sw128(sa0 + a * A_TILE_BYTES + kk * 32);
-              const uint64_t bd = sdesc_sw128(sx0 + x * bn * BK * 2 + kk * 32);
-              const uint32_t acc = (it > 0 || kk > 0 || a > 0 || x > 0) ? 1u : 0u;
-              mma_bf16(tmem, ad, bd, idesc, acc);
+                for (int x = 0; x < SX; ++x) {
+                  if (a + x >= (SA > SX ? SA : SX)) continue;
+                  const uint64_t ad = sdesc_sw128(sa0 + a * A_TILE_BYTES + kk * 32);
+                  const uint64_t bd = sdesc_sw128(sx0 + x * bn * BK * 2 + kk * 32);
+                  const uint32_t acc = (first && kk == 0 && a == 0 && x == 0) ? 0u : 1u;
+                  mma_bf16(dt, ad, bd, idesc, acc);
+                }
+              }
             }
+            mma_commit(&empty[s]);
+          }
+          mma_commit(&acc_full[b]);     // also issued after an error: completes when prior MMAs do
+        }
+      }
+      __syncwarp();
+    } else {
+      // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = rows of the tile
+      float acc[BN_MAX];
+#pragma unroll
+      for (int j = 0; j < BN_MAX; ++j) acc[j] = 0.0f;
+      int healthy = 1;
+      for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        int ok = 0;
+        if (lane == 0) ok = mbar_wait(&acc_full[b], (uint32_t)(c >> 1) & 1u) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) set_err(err, DERR_TIMEOUT_EPI);
+          healthy = 0;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * bn);
+#pragma unroll
+        for (int g = 0; g < BN_MAX / 16; ++g) {
+          if (g * 16 < bn) {
+            uint32_t r[16];
+            tmem_ld16(ta + (uint32_t)(g * 16), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[g * 16 + j] += __uint_as_float(r[j]);
           }
         }
-        mma_commit(&empty[s]);
+        tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
       }
-      mma_commit(done);
-    }
-    __syncwarp();
-
-    // ---------------- epilogue (decisions are made by lane 0 and broadcast,
-    // so the warp-collective tcgen05.ld is executed by all lanes or none)
-    int healthy = 0;
-    if (lane == 0) {
-      const bool ok = mbar_wait(done, 0);
-      if (!ok) set_err(err, DERR_TIMEOUT_EPI);
-      healthy = ok && (*(volatile int*)err == 0);
-    }
-    healthy = __shfl_sync(0xffffffffu, healthy, 0);
-    tc_fence_after();
-    if (healthy) {
-      const int row = m0 + warp * 32 + lane;
-      float* Y = ch->Y;
-      const int64_t ldy = ch->ldy;
-      const int ncols = ch->ncols;
-      const int atomic = ch->atomic;
-      for (int c0 = 0; c0 < bn; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (healthy) healthy = (*(volatile int*)err == 0);
+      healthy = __shfl_sync(0xffffffffu, healthy, 0);
+      if (healthy) {
+        const int row = m0 + warp * 32 + lane;
         if (row < ch->n) {
+          float* Y = ch->Y;
+          const int64_t ldy = ch->ldy;
+          const int ncols = ch->ncols;
+          const int atomic = ch->atomic;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < ncols) {
+          for (int j = 0; j < BN_MAX; ++j) {
+            const int col = n0 + j;
+            if (j < bn && col < ncols) {
               float* dst = Y + row + (int64_t)col * ldy;
-              const float v = __uint_as_float(r[j]);
-              if (atomic) atomicAdd(dst, v);
-              else *dst = v;
+              if (atomic) atomicAdd(dst, acc[j]);
+              else *dst = acc[j];
             }
           }
         }
@@ -320,13 +373,14 @@ static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cu
   const int smem = stages * tc_stage_bytes(SA, SX, bn) + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
-  k_tc_gemm<SA, SX><<<items, 128, smem, st>>>(d_ch, C, bn, stages, d_err);
+  k_tc_gemm<SA, SX><<<items, NTHREADS, smem, st>>>(d_ch, C, bn, stages, d_err);
+  note_launch();
   return (int)cudaGetLastError();
 }
 
 int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err, cudaStream_t st) {
   if (items <= 0) return 0;
-  if (bn < 16 || bn > 256 || (bn % 16) != 0) return (int)cudaErrorInvalidValue;
+  if (bn < 16 || bn > BN_MAX || (bn % 16) != 0) return (int)cudaErrorInvalidValue;
   if (sa == 1 && sx == 1) return launch_t<1, 1>(d_ch, C, items, bn, d_err, st);
   if (sa == 2 && sx == 1) return launch_t<2, 1>(d_ch, C, items, bn, d_err, st);
   if (sa == 2 && sx == 2) return launch_t<2, 2>(d_ch, C, items, bn, d_err, st);

@@ -5,6 +5,10 @@
 
 namespace rsvd {
 
+// Count of kernels launched by the library (benchmark accounting).
+void note_launch(int k = 1);
+long long launch_count();
+
 // ----------------------------------------------------------------- tile GEMMs
 enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2 };
 enum MMKind {
@@ -13,7 +17,8 @@ enum MMKind {
   MMK_NN_F64 = 2,        // C = A B, A tall column-major FP64
   MMK_GRAM_DOT2 = 3,     // partial C_s = Y_s^T Z_s, FP32 data, compensated (Dot2) -> FP64
   MMK_NN_F32_F64B = 4,   // C(FP32) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
-  MMK_NN_F32_OUT64 = 5   // C(FP64) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
+  MMK_NN_F32_OUT64 = 5,  // C(FP64) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
+  MMK_GRAM_F32 = 6       // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
 };
 
 struct MMDesc {
@@ -50,7 +55,8 @@ void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint
                       int col0, cudaStream_t st);
 // Upper Cholesky G = R^T R (l x l), R^{-1}; R_acc <- R R_acc when accumulate.
 // Shifted retry on breakdown (flag FLAG_SHIFTED).
-void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int n_rows_hint, cudaStream_t st);
+void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
+                     cudaStream_t st);
 // One-sided Jacobi SVD of M = R^T (FP64 or FP32 arithmetic); writes sig, M <- left
 // vectors, J <- right vectors, sorted by descending sigma.
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st);

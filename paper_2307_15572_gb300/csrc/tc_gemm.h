@@ -3,7 +3,7 @@
 
 #include <cuda.h>
 
-#include "common.cuh"
+#include "kernels.h"
 
 namespace rsvd {
 

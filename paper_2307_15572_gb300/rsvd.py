@@ -57,6 +57,12 @@ class Factors(C.Structure):
                 ("l_used", C.c_int32), ("err_est", C.c_double), ("status", C.c_int32)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("tc_launches", C.c_int64), ("tc_ms", C.c_double),
+                ("tc_bytes", C.c_double), ("tc_flops", C.c_double), ("f64_launches", C.c_int64),
+                ("f64_ms", C.c_double), ("f64_flops", C.c_double)]
+
+
 _lib = None
 
 
@@ -87,6 +93,10 @@ def load(build=True):
     lib.rsvd_last_error_string.restype = C.c_char_p
     lib.rsvd_version.argtypes = []
     lib.rsvd_version.restype = C.c_int32
+    lib.rsvd_plan_set_profiling.argtypes = [P, C.c_int32]
+    lib.rsvd_plan_set_profiling.restype = C.c_int
+    lib.rsvd_plan_profile.argtypes = [P, C.POINTER(Profile), C.c_int32]
+    lib.rsvd_plan_profile.restype = C.c_int
     _lib = lib
     return lib
 
@@ -133,6 +143,16 @@ def rsvd_decompose_batched(h, mats, facs):
     return r, list(st)
 
 
+def rsvd_plan_set_profiling(h, enable):
+    _check(load().rsvd_plan_set_profiling(h, 1 if enable else 0))
+
+
+def rsvd_plan_profile(h, reset=False):
+    p = Profile()
+    _check(load().rsvd_plan_profile(h, C.byref(p), 1 if reset else 0))
+    return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+
 def rsvd_reconstruct_error(h, mat, fac):
     out = C.c_double()
     _check(load().rsvd_reconstruct_error(h, C.byref(mat), C.byref(fac), C.byref(out)))
@@ -173,9 +193,9 @@ def dense(A):
         m.data = A.ctypes.data
     else:
         import torch
-        assert A.dtype == torch.float64 and A.dim() == 2 and A.shape[0] == A.shape[1] and A.is_cuda
+        assert A.dtype == torch.float64 and A.dim() == 2 and A.shape[0] == A.shape[1]
         assert A.stride(1) == 1
-        m.mem = MEM_DEVICE
+        m.mem = MEM_DEVICE if A.is_cuda else MEM_HOST
         m.n = A.shape[0]
         m.ld = A.stride(0)
         m.data = A.data_ptr()
