@@ -19,6 +19,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -194,7 +195,13 @@ int total_of(Job& J, const std::function<int64_t(int)>& per) {
 }
 
 // ------------------------------------------------------------ step builders
-void add_mm(Job& J, MMKind kind, const std::vector<MMDesc>& md) {
+void add_mm(Job& J, MMKind kind, std::vector<MMDesc> md) {
+  const int tile = tile_of(kind);
+  for (auto& m : md) {
+    m.tile = tile;
+    m.mt = cdiv(m.m, tile);
+    m.nt = cdiv(m.n, tile);
+  }
   std::vector<int> off(J.C + 1, 0);
   double flops = 0.0;
   for (int c = 0; c < J.C; ++c) {
@@ -248,6 +255,7 @@ void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::functi
     max_elems = std::max(max_elems, m.m * m.n);
   }
   add_mm(J, kind, md);
+  for (auto& m : md) m.tile = tile_of(kind);
   const MMDesc* dmd = J.ar.put(md.data(), md.size());
   double* const* douts = J.ar.put(outs.data(), outs.size());
   cudaStream_t st = J.P->st;
@@ -258,13 +266,13 @@ void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::functi
   });
 }
 
-void add_chol(Job& J, int accumulate) {
+void add_chol(Job& J, int accumulate, int f32_chol = 0) {
   const Chan* dch = J.d_ch;
   const int C = J.C, maxl = J.max_l;
   const int f32inv = J.mixed ? 1 : 0;
   cudaStream_t st = J.P->st;
   J.steps.push_back([=]() {
-    launch_chol_inv(dch, C, accumulate, maxl, f32inv, st);
+    launch_chol_inv(dch, C, accumulate, maxl, f32inv, st, f32_chol);
     return RSVD_OK;
   });
 }
@@ -506,7 +514,7 @@ void cqr2_mixed(Job& J, int nsl_out) {
     add_tn(J, round == 0 ? MMK_GRAM_DOT2 : MMK_GRAM_F32, [&](int c) { return (const void*)in(c); },
            [&](int c) { return (const void*)in(c); }, [&](int c) { return ch[c].G; },
            [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
-    add_chol(J, 0);
+    add_chol(J, 0, round == 1 ? 1 : 0);
     std::vector<MMDesc> md(J.C);
     for (int c = 0; c < J.C; ++c) {
       const ChanDims& d = J.d[c];
@@ -559,11 +567,24 @@ rsvd_status build_mixed(Job& J) {
   add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
          [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
          [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
+  // probe residual ||V G - Q C||^2, one partial per 128-row tile
+  {
+    std::vector<MMDesc> md(J.C);
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      MMDesc m{};
+      m.A = ch[c].Q32; m.lda = d.ldt;
+      m.B = ch[c].C64; m.ldb = d.l;
+      m.Cm = ch[c].Y32 + (int64_t)d.l * d.ldt; m.ldc = d.ldt;     // V G block
+      m.m = d.n; m.n = d.s; m.k = d.l;
+      m.ks = 1; m.kchunk = (int)rup(d.l, 16);
+      m.mode = MM_RESID;
+      m.rpart = ch[c].fro_part;
+      md[c] = m;
+    }
+    add_mm(J, MMK_RESID_F32, md);
+  }
   const int maxl = J.max_l;
-  J.steps.push_back([=]() {
-    launch_probe_resid(dch, off64, C, t64, maxl, NPROBE, st);
-    return RSVD_OK;
-  });
   // W^T W = R^T R
   add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const void*)ch[c].Y32; },
          [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
@@ -572,7 +593,7 @@ rsvd_status build_mixed(Job& J) {
   const double tol = J.tol;
   J.steps.push_back([=]() {
     launch_jacobi(dch, C, 1, maxl, st);
-    launch_probe_finish(dch, C, st);
+    launch_probe_finish(dch, C, maxl, st);
     launch_select(dch, C, policy, tol, 1, st);
     return RSVD_OK;
   });
@@ -602,7 +623,8 @@ void layout(Job& J, Bump& b) {
     if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
     else { h.A = A.data; h.lda = A.ld; }
     const size_t L2 = (size_t)d.l * d.l;
-    h.G = b.take<double>(L2); h.R = b.take<double>(L2); h.Ri = b.take<double>(L2);
+    const size_t L2p = (size_t)d.l * (d.l + 32);      // Jacobi's padded working copies when not in smem
+    h.G = b.take<double>(L2p); h.R = b.take<double>(L2); h.Ri = b.take<double>(L2p);
     h.M = b.take<double>(L2); h.J = b.take<double>(L2);
     h.sig = b.take<double>(d.l); h.scr = b.take<double>(d.l);
     h.res = nullptr;
@@ -843,6 +865,10 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* 
   }
   P->pending.clear();
   P->ev_next = 0;
+  if (getenv("RSVD_DEBUG"))
+    for (int c = 0; c < C; ++c)
+      fprintf(stderr, "rsvd: chan %d n %d l %d k %d flags %d sweeps %d err_est %.3e status %d\n", c, J.d[c].n,
+              J.d[c].l, res[c].k_out, res[c].flags, res[c].sweeps, res[c].err_est, res[c].status);
   const int derr = *herr;
   if (derr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", derr);
   rsvd_status worst = RSVD_OK;

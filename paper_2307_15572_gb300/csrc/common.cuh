@@ -54,6 +54,62 @@ RSVD_DEV float gauss_f32(uint64_t seed, uint32_t i, uint32_t j, uint32_t tag) {
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
+// FP64 -> FP32 with round-to-nearest-even done on the integer pipe (the FP64
+// units are a small fraction of this part's throughput).  Normal results are
+// assembled from the bit fields; zeros, subnormal or overflowing results and
+// non-finite inputs take the conversion instruction.
+static __device__ __noinline__ float f64_to_f32_slow(double a) { return __double2float_rn(a); }
+
+RSVD_DEV float f64_to_f32_rn(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const unsigned int e = (unsigned int)(b >> 52) & 0x7FFu;
+  const int fe = (int)e - 1023 + 127;
+  if (fe <= 0 || fe >= 255) return f64_to_f32_slow(a);   // out of line: never if-converted
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned int keep = (unsigned int)(m >> 29);
+  const unsigned int rest = (unsigned int)(m & 0x1FFFFFFFull);
+  const unsigned int up = (rest > 0x10000000u) || (rest == 0x10000000u && (keep & 1u));
+  const unsigned int r = ((unsigned int)fe << 23) + keep + up;     // carry into the exponent is RN's overflow
+  return __uint_as_float((unsigned int)(b >> 32 & 0x80000000u) | r);
+}
+
+// The same rounding from the two 32-bit halves of the FP64 bit pattern (hi
+// holds sign, exponent and the top 20 mantissa bits), 32-bit integer ops only.
+// Sets `bad` for Inf/NaN.
+RSVD_DEV float f64w_to_f32_rn(unsigned int hi, unsigned int lo, bool& bad) {
+  const unsigned int e = (hi >> 20) & 0x7FFu;
+  bad |= (e == 0x7FFu);
+  const int fe = (int)e - 1023 + 127;
+  if (fe <= 0 || fe >= 255)
+    return f64_to_f32_slow(__hiloint2double((int)hi, (int)lo));
+  const unsigned int keep = ((hi & 0xFFFFFu) << 3) | (lo >> 29);     // top 23 mantissa bits
+  const unsigned int rest = lo & 0x1FFFFFFFu;                         // the 29 dropped bits
+  const unsigned int up = (rest > 0x10000000u) | ((rest == 0x10000000u) & keep);
+  return __uint_as_float((hi & 0x80000000u) | (((unsigned int)fe << 23) + keep + (up & 1u)));
+}
+
+// Exact FP32 -> FP64 widening on the integer pipe for normal numbers and
+// zero; subnormal, Inf and NaN inputs take the conversion instruction.
+static __device__ __noinline__ double f32_to_f64_slow(float x) { return (double)x; }
+
+RSVD_DEV double f32_to_f64(float x) {
+  const unsigned int u = __float_as_uint(x);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
+    return f32_to_f64_slow(x);
+  }
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// Exponent all ones: Inf or NaN (integer test, no FP64 instruction).
+RSVD_DEV bool f64_nonfinite(double a) {
+  return (((unsigned long long)__double_as_longlong(a) >> 52) & 0x7FFull) == 0x7FFull;
+}
+
 // ---------------------------------------------------------------------------
 // Batched tiling: channel c owns tiles [off[c], off[c+1]).
 // ---------------------------------------------------------------------------
@@ -82,6 +138,8 @@ struct ChanResult {
   int flags;        // bit0: shifted CholeskyQR used, bit1: jacobi cap hit, bit2: nonfinite
   double err_est;
   double fro2;      // ||A||_F^2
+  int sweeps;       // Jacobi sweeps used (diagnostics)
+  int pad_;
 };
 
 enum : int { FLAG_SHIFTED = 1, FLAG_JACOBI_CAP = 2, FLAG_NONFINITE = 4, FLAG_CHOL_FAIL = 8 };

@@ -37,27 +37,13 @@ RSVD_DEV double bsum(double v, double* sh) {
   return r;
 }
 
-// FP64 -> FP32 with round-to-nearest-even done on the integer pipe (the FP64
-// units are a small fraction of this part's throughput).  Normal results are
-// assembled from the bit fields; zeros, subnormal or overflowing results and
-// non-finite inputs take the conversion instruction.
-RSVD_DEV float f64_to_f32_rn(double a) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
-  const unsigned int e = (unsigned int)(b >> 52) & 0x7FFu;
-  const int fe = (int)e - 1023 + 127;
-  if (fe <= 0 || fe >= 255) return __double2float_rn(a);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  const unsigned int keep = (unsigned int)(m >> 29);
-  const unsigned int rest = (unsigned int)(m & 0x1FFFFFFFull);
-  const unsigned int up = (rest > 0x10000000u) || (rest == 0x10000000u && (keep & 1u));
-  const unsigned int r = ((unsigned int)fe << 23) + keep + up;     // carry into the exponent is RN's overflow
-  return __uint_as_float((unsigned int)(b >> 32 & 0x80000000u) | r);
-}
-
-// 8 rows per tile; fro_part gets one partial per tile.  Each thread handles
-// pairs of adjacent columns so the BF16 words go out as 4-byte stores.
-// ||V||^2 is accumulated from the FP32 values (relative error ~1e-7, far
-// below what the relative tolerance needs) and summed in FP64 per tile.
+// 8 rows per tile; fro_part gets one partial per tile.  Each thread owns
+// pairs of adjacent columns (two 8-byte loads of the raw FP64 bits, four
+// pairs 512 columns apart in flight) and writes each BF16 word pair as one
+// 4-byte store; the FP64 -> FP32 rounding and the word split use 32-bit
+// integer and FP32 instructions only (no FP64 instruction per element: FP64
+// is a small fraction of this part's issue rate).  ||V||^2 is accumulated
+// from the FP32 values (relative error ~1e-7) and summed in FP64 per tile.
 __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
                                                  const int* __restrict__ off, int C, int nsl) {
   __shared__ double sh[32];
@@ -66,28 +52,52 @@ __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
   const Chan& h = ch[c];
   const int b = t - off[c];
   const int r0 = b * 8, r1 = min(h.n, r0 + 8);
+  const int n = h.n;
+  const int npair = (n + 1) >> 1;
   float s = 0.0f;
   bool bad = false;
-  const int npair = (h.n + 1) >> 1;
   for (int r = r0; r < r1; ++r) {
-    const double* row = h.A + (int64_t)r * h.lda;
-    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
-      const int j = 2 * p;
-      const double a0 = row[j];
-      const double a1 = (j + 1 < h.n) ? row[j + 1] : 0.0;
-      bad |= !isfinite(a0) || !isfinite(a1);
-      float f0 = f64_to_f32_rn(a0), f1 = f64_to_f32_rn(a1);
-      s = fmaf(f0, f0, s);
-      s = fmaf(f1, f1, s);
-      for (int w = 0; w < nsl; ++w) {
-        const __nv_bfloat16 q0 = __float2bfloat16_rn(f0), q1 = __float2bfloat16_rn(f1);
-        *(__nv_bfloat162*)(h.Ab[w] + (int64_t)r * h.ldb + j) = __halves2bfloat162(q0, q1);
-        f0 -= __bfloat162float(q0);     // exact: the remainder fits in FP32
-        f1 -= __bfloat162float(q1);
+    const int2* row = (const int2*)(h.A + (int64_t)r * h.lda);
+    __nv_bfloat162* o0 = (__nv_bfloat162*)(h.Ab[0] + (int64_t)r * h.ldb);
+    __nv_bfloat162* o1 = (__nv_bfloat162*)(h.Ab[1] + (int64_t)r * h.ldb);
+    __nv_bfloat162* o2 = (__nv_bfloat162*)(h.Ab[2] + (int64_t)r * h.ldb);
+    for (int p0 = 0; p0 < npair; p0 += 1024) {
+      int2 v[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = p0 + threadIdx.x + 256 * u;
+        const int j = 2 * p;
+        v[u][0] = (p < npair) ? __ldcs(row + j) : make_int2(0, 0);
+        v[u][1] = (p < npair && j + 1 < n) ? __ldcs(row + j + 1) : make_int2(0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = p0 + threadIdx.x + 256 * u;
+        if (p >= npair) continue;
+        float2 f;
+        f.x = f64w_to_f32_rn((unsigned int)v[u][0].y, (unsigned int)v[u][0].x, bad);
+        f.y = f64w_to_f32_rn((unsigned int)v[u][1].y, (unsigned int)v[u][1].x, bad);
+        s = fmaf(f.x, f.x, s);
+        s = fmaf(f.y, f.y, s);
+        __nv_bfloat162 q = __float22bfloat162_rn(f);
+        o0[p] = q;
+        if (nsl > 1) {
+          float2 g = __bfloat1622float2(q);
+          f.x -= g.x;                      // exact: the remainder fits in FP32
+          f.y -= g.y;
+          q = __float22bfloat162_rn(f);
+          o1[p] = q;
+          if (nsl > 2) {
+            g = __bfloat1622float2(q);
+            f.x -= g.x;
+            f.y -= g.y;
+            o2[p] = __float22bfloat162_rn(f);
+          }
+        }
       }
     }
   }
-  const double sd = bsum((double)s, sh);
+  const double sd = bsum(f32_to_f64(s), sh);
   if (bad) atomicOr(&h.res->flags, FLAG_NONFINITE);
   if (threadIdx.x == 0) h.fro_part[b] = sd;
 }
@@ -128,66 +138,33 @@ void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uin
   if (tiles > 0) { k_omega_bf16<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, j0, j1, pseed, nsl); note_launch(); }
 }
 
-// ||V G - Q C||^2 partial per 64-row tile (V G = Y32[:, l:l+s], C = C64).
-__global__ void __launch_bounds__(256) k_probe_resid(const Chan* __restrict__ ch,
-                                                     const int* __restrict__ off, int C) {
-  extern __shared__ float Cs[];   // l x s
-  __shared__ double sh[32];
-  const int t = blockIdx.x;
-  const int c = find_chan(off, C, t);
-  const Chan& h = ch[c];
-  const int l = h.l, s = h.nprobe;
-  for (int e = threadIdx.x; e < l * s; e += blockDim.x) Cs[e] = (float)h.C64[e];
-  __syncthreads();
-  const int r0 = (t - off[c]) * 64;
-  const int r = r0 + (threadIdx.x & 63);
-  const int tg = threadIdx.x >> 6;   // 4 groups of probes
-  double sq = 0.0;
-  if (r < h.n) {
-    for (int p = tg; p < s; p += 4) {
-      float acc = 0.0f;
-      for (int a = 0; a < l; ++a) acc = fmaf(h.Q32[r + (int64_t)a * h.ldt], Cs[a + p * l], acc);
-      const float v = h.Y32[r + (int64_t)(l + p) * h.ldt] - acc;
-      sq += (double)v * (double)v;
-    }
-  }
-  sq = bsum(sq, sh);
-  if (threadIdx.x == 0) h.fro_part[t - off[c]] = sq;
-}
-
-// est_part[0] = sum of the partials; est_part[1+i] = |(X^T C)_i|^2.
+// est_part[0] = sum of the probe-residual tile partials (fro_part, one per
+// 128-row tile); est_part[1+i] = |(X^T C)_i|^2 for the 8 rows i of this block
+// (one warp per row, lane p < s holds column p of D = X^T C).
 __global__ void __launch_bounds__(256) k_probe_finish(const Chan* __restrict__ ch) {
   __shared__ double sh[32];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l, s = h.nprobe;
-  const int nb = (h.n + 63) / 64;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += h.fro_part[i];
-  v = bsum(v, sh);
-  if (threadIdx.x == 0) h.est_part[0] = v;
-  for (int i = threadIdx.x; i < l; i += blockDim.x) {
-    double acc2 = 0.0;
-    for (int p = 0; p < s; ++p) {
-      double d = 0.0;
-      for (int a = 0; a < l; ++a) d = fma(h.M[a + (int64_t)i * l], h.C64[a + (int64_t)p * l], d);
-      acc2 = fma(d, d, acc2);
-    }
-    h.est_part[1 + i] = acc2;
+  if (blockIdx.y == 0) {
+    const int nb = (h.n + 127) / 128;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += h.fro_part[i];
+    v = bsum(v, sh);
+    if (threadIdx.x == 0) h.est_part[0] = v;
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.y * 8 + warp;
+  if (i >= l) return;
+  double d = 0.0;
+  if (lane < s)
+    for (int a = 0; a < l; ++a) d = fma(h.M[a + (int64_t)i * l], h.C64[a + (int64_t)lane * l], d);
+  double d2 = d * d;
+  d2 = wsum(d2);
+  if (lane == 0) h.est_part[1 + i] = d2;
 }
 
-void launch_probe_resid(const Chan* d_ch, const int* d_off, int C, int tiles, int max_l, int s,
-                        cudaStream_t st) {
-  if (tiles <= 0) return;
-  const size_t bytes = (size_t)max_l * s * sizeof(float);
-  if (bytes > 48 * 1024)
-    cudaFuncSetAttribute(k_probe_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_probe_resid<<<tiles, 256, bytes, st>>>(d_ch, d_off, C);
-  note_launch();
-}
-
-void launch_probe_finish(const Chan* d_ch, int C, cudaStream_t st) {
-  k_probe_finish<<<C, 256, 0, st>>>(d_ch);
+void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st) {
+  k_probe_finish<<<dim3(C, (max_l + 7) / 8), 256, 0, st>>>(d_ch);
   note_launch();
 }
 

@@ -27,6 +27,19 @@ enum { ACC_F64 = 0, ACC_F32 = 1, ACC_DOT2 = 2 };
 template <int ACC> struct AccT { typedef float T; };
 template <> struct AccT<ACC_F64> { typedef double T; };
 
+RSVD_DEV void store_out(float* d, float v, bool atomic) { if (atomic) atomicAdd(d, v); else *d = v; }
+RSVD_DEV void store_out(double* d, float v, bool atomic) {
+  const double w = f32_to_f64(v);
+  if (atomic) atomicAdd(d, w); else *d = w;
+}
+
+RSVD_DEV unsigned int pack_bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned int)__bfloat16_as_ushort(lo) | ((unsigned int)__bfloat16_as_ushort(hi) << 16);
+}
+
+RSVD_DEV float to_f32(float x) { return x; }
+RSVD_DEV float to_f32(double x) { return f64_to_f32_rn(x); }   // integer-pipe rounding
+
 RSVD_DEV void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float z = s - a;
@@ -155,6 +168,199 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
   }
 }
 
+// FP32-compute tiles (Grams of FP32 data, triangular solve, lift): 128 x 128
+// output tile, k steps of 8, 256 threads with an 8 x 8 register block each
+// (two 4 x 4 quadrants, so shared-memory reads are float4 and conflict-free),
+// next k step prefetched into registers while the current one is used.
+template <typename TA, typename TB, typename TC, int AL, int ACC>
+__global__ void __launch_bounds__(256)
+k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
+  // rows padded by 4 floats: the staging stores (8 consecutive threads on 8
+  // different k rows) hit 8 distinct banks, and rows stay 16-byte aligned
+  __shared__ __align__(16) float As[2][8][132];
+  __shared__ __align__(16) float Bs[2][8][132];
+  const int t = blockIdx.x;
+  const int c = find_chan(off, C, t);
+  const MMDesc* __restrict__ dp = md + c;
+  const int dm = dp->m, dn = dp->n, dk = dp->k, mt = dp->mt, nt = dp->nt, kchunk = dp->kchunk;
+  const int mode = dp->mode, sym = dp->sym, nsl = dp->nsl;
+  const int64_t lda = dp->lda, ldb = dp->ldb, ldc = dp->ldc, pstride = dp->pstride, ldsl = dp->ldsl;
+  const double* __restrict__ colscale = dp->colscale;
+  int local = t - off[c];
+  const int per_split = mt * nt;
+  const int split = local / per_split;
+  local -= split * per_split;
+  const int mi = local / nt, ni = local % nt;
+  if (sym && ni < mi) return;
+  const int m0 = mi * 128, n0 = ni * 128;
+  const int ncols = dp->ncols_dev ? min(dn, *dp->ncols_dev) : dn;
+  if (n0 >= ncols) return;
+  const int kb = split * kchunk;
+  const int ke = min(dk, kb + kchunk);
+  const TA* __restrict__ A = (const TA*)dp->A;
+  const TB* __restrict__ B = (const TB*)dp->B;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+
+  float acc[8][8], cmp[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { acc[i][j] = 0.0f; cmp[i][j] = 0.0f; }
+
+  // staging: 4 A and 4 B elements per thread per k step
+  float ra[4], rb[4];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int e = tid + p * 256;
+      int mm, kk;
+      if (AL == AROW) { kk = e & 7; mm = e >> 3; } else { mm = e & 127; kk = e >> 7; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      float v = 0.0f;
+      if (gm < dm && gk < ke) v = to_f32(AL == AROW ? A[(int64_t)gm * lda + gk] : A[gm + (int64_t)gk * lda]);
+      ra[p] = v;
+      const int kb2 = e & 7, nn = e >> 3;
+      const int gn = n0 + nn, gk2 = k0 + kb2;
+      float w = 0.0f;
+      if (gn < ncols && gk2 < ke) w = to_f32(B[gk2 + (int64_t)gn * ldb]);
+      rb[p] = w;
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int e = tid + p * 256;
+      int mm, kk;
+      if (AL == AROW) { kk = e & 7; mm = e >> 3; } else { mm = e & 127; kk = e >> 7; }
+      As[buf][kk][mm] = ra[p];
+      Bs[buf][e & 7][e >> 3] = rb[p];
+    }
+  };
+  int buf = 0;
+  if (kb < ke) { gload(kb); sstore(0); }
+  __syncthreads();
+  for (int k0 = kb; k0 < ke; k0 += 8) {
+    const bool more = k0 + 8 < ke;
+    if (more) gload(k0 + 8);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      // rows follow tx (4 consecutive rows per thread -> vector stores of the
+      // column-major result), columns follow ty
+      const float4 a0 = *(const float4*)&As[buf][kk][tx * 4];
+      const float4 a1 = *(const float4*)&As[buf][kk][64 + tx * 4];
+      const float4 b0 = *(const float4*)&Bs[buf][kk][ty * 4];
+      const float4 b1 = *(const float4*)&Bs[buf][kk][64 + ty * 4];
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (ACC == ACC_DOT2) {
+            const float p = a[i] * b[j];
+            const float pe = fmaf(a[i], b[j], -p);
+            float s, se;
+            two_sum(acc[i][j], p, s, se);
+            acc[i][j] = s;
+            cmp[i][j] += se + pe;
+          } else {
+            acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          }
+        }
+    }
+    if (more) {
+      sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+  TC* __restrict__ Cp = (TC*)dp->Cm + (mode == MM_PARTIAL ? (int64_t)split * pstride : 0);
+  __nv_bfloat16* sl0 = dp->sl[0];
+  __nv_bfloat16* sl1 = dp->sl[1];
+  __nv_bfloat16* sl2 = dp->sl[2];
+  if (mode == MM_RESID) {
+    __shared__ double red[8];
+    float sqf = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int gm = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + i - 4);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gn = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + j - 4);
+        if (gm < dm && gn < ncols) {
+          const float v = (float)Cp[gm + (int64_t)gn * ldc] - acc[i][j];
+          sqf = fmaf(v, v, sqf);
+        }
+      }
+    }
+    double sq = f32_to_f64(sqf);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((tid & 31) == 0) red[tid >> 5] = sq;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < 8; ++w) tot += red[w];
+      dp->rpart[t - off[c]] = tot;
+    }
+    return;
+  }
+  // each thread owns rows {r4, r4+1, r4+2, r4+3} (two such groups) of 8
+  // columns: full groups go out as one vector store per column
+  const bool vec_ok = (mode == MM_STORE) && (sizeof(TC) == 4) && ((ldc & 3) == 0) &&
+                      ((((uintptr_t)Cp) & 15) == 0);
+#pragma unroll
+  for (int ig = 0; ig < 2; ++ig) {
+    const int r4 = m0 + ig * 64 + tx * 4;
+    if (r4 >= dm) continue;
+    const bool full = r4 + 3 < dm;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + j - 4);
+      if (gn >= ncols) continue;
+      float v[4];
+      const float cs = colscale ? f64_to_f32_rn(colscale[gn]) : 1.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = acc[ig * 4 + q][j] * cs;
+      TC* dst = Cp + r4 + (int64_t)gn * ldc;
+      if (full && vec_ok) {
+        *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (r4 + q < dm) store_out(dst + q, v[q], mode == MM_ATOMIC);
+      }
+      if (nsl > 0) {
+        const int64_t o = r4 + (int64_t)gn * ldsl;
+        __nv_bfloat16 w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float r = v[q];
+          w0[q] = __float2bfloat16_rn(r);
+          r -= __bfloat162float(w0[q]);
+          w1[q] = __float2bfloat16_rn(r);
+          r -= __bfloat162float(w1[q]);
+          w2[q] = __float2bfloat16_rn(r);
+        }
+        if (full && ((ldsl & 3) == 0)) {
+          *(uint2*)(sl0 + o) = make_uint2(pack_bf2(w0[0], w0[1]), pack_bf2(w0[2], w0[3]));
+          if (nsl > 1) *(uint2*)(sl1 + o) = make_uint2(pack_bf2(w1[0], w1[1]), pack_bf2(w1[2], w1[3]));
+          if (nsl > 2) *(uint2*)(sl2 + o) = make_uint2(pack_bf2(w2[0], w2[1]), pack_bf2(w2[2], w2[3]));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (r4 + q >= dm) continue;
+            sl0[o + q] = w0[q];
+            if (nsl > 1) sl1[o + q] = w1[q];
+            if (nsl > 2) sl2[o + q] = w2[q];
+          }
+        }
+      }
+    }
+  }
+}
+
 // Sum the split partials of a Gram / inner product in a fixed order; for a
 // symmetric Gram only the upper tiles were written, so mirror them.
 __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* __restrict__ outp,
@@ -168,7 +374,7 @@ __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* 
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     int i = e % d.m, j = e / d.m;
     int si = i, sj = j;
-    if (d.sym && (i / 64) > (j / 64)) { si = j; sj = i; }
+    if (d.sym && (i / d.tile) > (j / d.tile)) { si = j; sj = i; }
     double s = 0.0;
     for (int p = 0; p < ks; ++p) s += P[(int64_t)p * d.pstride + si + (int64_t)sj * d.ldc];
     out[i + (int64_t)j * d.m] = s;
@@ -176,18 +382,27 @@ __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* 
   (void)C;
 }
 
+int tile_of(MMKind kind) {
+  switch (kind) {
+    case MMK_NN_F32_F64B: case MMK_NN_F32_OUT64: case MMK_GRAM_F32: case MMK_RESID_F32: return 128;
+    default: return 64;
+  }
+}
+
 void launch_tile_mm(MMKind kind, const MMDesc* d_md, const int* d_off, int C, int tiles,
                     cudaStream_t st) {
   if (tiles <= 0) return;
   switch (kind) {
-    case MMK_DENSE_F64: k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
-    case MMK_GRAM_F64:  k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
-    case MMK_NN_F64:    k_tile_mm<double, double, double, ACOL, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
-    case MMK_GRAM_DOT2: k_tile_mm<float, float, double, AROW, ACC_DOT2><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
-    case MMK_NN_F32_F64B: k_tile_mm<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
-    case MMK_NN_F32_OUT64: k_tile_mm<float, double, double, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
-    case MMK_GRAM_F32: k_tile_mm<float, float, double, AROW, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); note_launch(); break;
+    case MMK_DENSE_F64: k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_GRAM_F64:  k_tile_mm<double, double, double, AROW, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_NN_F64:    k_tile_mm<double, double, double, ACOL, ACC_F64><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_GRAM_DOT2: k_tile_mm<float, float, double, AROW, ACC_DOT2><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_NN_F32_F64B: k_tile_mm128<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_NN_F32_OUT64: k_tile_mm128<float, double, double, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_GRAM_F32: k_tile_mm128<float, float, double, AROW, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_RESID_F32: k_tile_mm128<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
   }
+  note_launch();
 }
 
 void launch_reduce_partials(const MMDesc* d_md, double* const* d_out, int C, int max_elems,

@@ -115,58 +115,59 @@ void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint
 // invertible right factor leaves range(Y R^{-1}) = range(Y), and the second
 // CholeskyQR round restores orthogonality.  If asked, R_acc <- R R_acc (the
 // triangular factor of a repeated CholeskyQR).
+// T = double: the ill-conditioned Grams (first CholeskyQR round, W^T W);
+// T = float: the second CholeskyQR round, whose Gram is within ~1e-2 of I.
+template <typename T>
 __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, int accumulate,
                                                   int use_smem, int f32_inverse) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char craw[];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l;
   const int ld = use_smem ? l + 1 : l;       // odd stride: conflict-free column access
-  double* Ms = use_smem ? smem : h.M;        // working copy of G -> R (column-major)
+  T* Ms = use_smem ? (T*)craw : (T*)h.M;     // working copy of G -> R (column-major)
   const double* G = h.G;
   __shared__ int fail;
   __shared__ double shift;
-  __shared__ double tr;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
     fail = 0;
-    shift = 0.0;
-    double s = 0.0;
-    for (int i = 0; i < l; ++i) s += G[i + (int64_t)i * l];
-    tr = s;
+    double tr = 0.0;
+    for (int i = 0; i < l; ++i) tr += G[i + (int64_t)i * l];
+    shift = 11.0 * ((double)h.n * l + (double)l * (l + 1)) *
+            (sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08) * tr;
   }
   __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
     for (int e = tid; e < l * l; e += nt) {
       const int i = e % l, j = e / l;
-      Ms[i + (int64_t)j * ld] = G[e] + ((i == j) ? shift : 0.0);
+      const double g = G[e] + ((attempt == 1 && i == j) ? shift : 0.0);
+      Ms[i + (int64_t)j * ld] = (sizeof(T) == 8) ? (T)g : (T)f64_to_f32_rn(g);
     }
     int bad = 0;
     for (int j = 0; j < l; ++j) {
       __syncthreads();
-      const double d = Ms[j + (int64_t)j * ld];
-      if (!(d > 0.0) || !isfinite(d)) { bad = 1; break; }      // uniform across the block
-      const double rjj = sqrt(d), inv = 1.0 / rjj;
+      const T d = Ms[j + (int64_t)j * ld];
+      if (!(d > (T)0) || !isfinite(d)) { bad = 1; break; }      // uniform across the block
+      const T rjj = sqrt(d), inv = (T)1 / rjj;
       __syncthreads();
       for (int i = j + tid; i < l; i += nt)
         Ms[j + (int64_t)i * ld] = (i == j) ? rjj : Ms[j + (int64_t)i * ld] * inv;
       __syncthreads();
-      const int m = l - j - 1;
-      for (int e = tid; e < m * m; e += nt) {
-        const int a = j + 1 + e % m, b = j + 1 + e / m;
-        if (a <= b) Ms[a + (int64_t)b * ld] = fma(-Ms[j + (int64_t)a * ld], Ms[j + (int64_t)b * ld],
-                                                  Ms[a + (int64_t)b * ld]);
+      // trailing update, upper triangle: one warp per column b, lanes over a
+      {
+        const int w = tid >> 5, ln = tid & 31, nw = nt >> 5;
+        for (int b = j + 1 + w; b < l; b += nw) {
+          const T rb = Ms[j + (int64_t)b * ld];
+          T* colb = Ms + (int64_t)b * ld;
+          for (int a = j + 1 + ln; a <= b; a += 32) colb[a] = fma(-Ms[j + (int64_t)a * ld], rb, colb[a]);
+        }
       }
     }
     __syncthreads();
     if (!bad) break;
     if (tid == 0) {
-      if (attempt == 0) {
-        shift = 11.0 * ((double)h.n * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
-        atomicOr(&h.res->flags, FLAG_SHIFTED);
-      } else {
-        fail = 1;
-        atomicOr(&h.res->flags, FLAG_CHOL_FAIL);
-      }
+      if (attempt == 0) atomicOr(&h.res->flags, FLAG_SHIFTED);
+      else { fail = 1; atomicOr(&h.res->flags, FLAG_CHOL_FAIL); }
     }
     __syncthreads();
     if (fail) break;
@@ -179,75 +180,98 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
       const int i = e % l, j = e / l;
       double s = 0.0;
       if (i <= j)
-        for (int k = i; k <= j; ++k) s = fma(Ms[i + (int64_t)k * ld], h.R[k + (int64_t)j * l], s);
+        for (int k = i; k <= j; ++k) s = fma((double)Ms[i + (int64_t)k * ld], h.R[k + (int64_t)j * l], s);
       h.G[e] = s;                               // G is free now
     }
     __syncthreads();
     for (int e = tid; e < l * l; e += nt) h.R[e] = h.G[e];
-  }
-  if (!accumulate) {
+  } else {
     for (int e = tid; e < l * l; e += nt) {
       const int i = e % l, j = e / l;
-      h.R[e] = (i <= j) ? Ms[i + (int64_t)j * ld] : 0.0;
+      h.R[e] = (i <= j) ? (double)Ms[i + (int64_t)j * ld] : 0.0;
     }
   }
   __syncthreads();
-  if (f32_inverse && use_smem) {
-    // FP32 copy of R (stride l+1) and X = R^{-1} stored row-major, in the same smem
-    float* Rs = (float*)smem;
-    float* Xs = Rs + (int64_t)l * (l + 1);
-    // Ms (double) overlaps Rs/Xs: copy R via registers in two phases through h.Ri
-    for (int e = tid; e < l * l; e += nt) {
-      const int i = e % l, j = e / l;
-      h.Ri[e] = (i <= j) ? Ms[i + (int64_t)j * ld] : 0.0;
-    }
-    __syncthreads();
-    for (int e = tid; e < l * l; e += nt) {
-      const int i = e % l, j = e / l;
-      Rs[i + (int64_t)j * (l + 1)] = (float)h.Ri[e];
-      Xs[e] = 0.0f;
-    }
-    __syncthreads();
-    for (int i = l - 1; i >= 0; --i) {
-      const float rii = Rs[i + (int64_t)i * (l + 1)];
-      for (int c = i + tid; c < l; c += nt) {
-        float s = (c == i) ? 1.0f : 0.0f;
-        for (int k = i + 1; k <= c; ++k) s = fmaf(-Rs[i + (int64_t)k * (l + 1)], Xs[(int64_t)k * l + c], s);
-        Xs[(int64_t)i * l + c] = s / rii;
+  // R^{-1} column by column, one warp per column, right-looking back
+  // substitution: for i = c .. 0: x_i /= R_ii, then x_k -= R_ki x_i (k < i)
+  // across the lanes.  Columns are dealt round-robin so warps get a mix of
+  // long and short ones.
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  if ((f32_inverse || sizeof(T) == 4) && use_smem) {
+    // FP32 arithmetic on an FP32 copy of R (stride l+1) in shared memory
+    float* Rs;
+    if (sizeof(T) == 4) {
+      Rs = (float*)Ms;
+    } else {
+      // Ms is dead once h.R holds R: rebuild R in FP32 in the same space
+      Rs = (float*)craw;
+      for (int e = tid; e < l * l; e += nt) {
+        const int i = e % l, j = e / l;
+        h.Ri[e] = (i <= j) ? (double)Ms[i + (int64_t)j * ld] : 0.0;   // stage through global
+      }
+      __syncthreads();
+      for (int e = tid; e < l * l; e += nt) {
+        const int i = e % l, j = e / l;
+        Rs[i + (int64_t)j * (l + 1)] = f64_to_f32_rn(h.Ri[e]);
       }
       __syncthreads();
     }
-    for (int e = tid; e < l * l; e += nt) {
-      const int k = e % l, c = e / l;           // Ri column-major: Ri[k + c l] = X[k][c]
-      h.Ri[e] = (double)Xs[(int64_t)k * l + c];
+    float* x = Rs + (int64_t)l * (l + 1) + (int64_t)warp * l;
+    for (int c = warp; c < l; c += nwarp) {
+      for (int k = lane; k < l; k += 32) x[k] = (k == c) ? 1.0f : 0.0f;
+      __syncwarp();
+      for (int i = c; i >= 0; --i) {
+        const float xi = x[i] / Rs[i + (int64_t)i * (l + 1)];
+        __syncwarp();
+        if (lane == 0) x[i] = xi;
+        const float* ri = Rs + (int64_t)i * (l + 1);
+        for (int k = lane; k < i; k += 32) x[k] = fmaf(-ri[k], xi, x[k]);
+        __syncwarp();
+      }
+      for (int k = lane; k < l; k += 32) h.Ri[k + (int64_t)c * l] = f32_to_f64(x[k]);
+      __syncwarp();
     }
     return;
   }
-  // FP64 R^{-1}: column c solves R x = e_c
-  for (int cidx = tid; cidx < l; cidx += nt) {
-    double* x = h.Ri + (int64_t)cidx * l;
-    for (int i = cidx + 1; i < l; ++i) x[i] = 0.0;
-    x[cidx] = 1.0 / Ms[cidx + (int64_t)cidx * ld];
-    for (int i = cidx - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= cidx; ++k) s = fma(Ms[i + (int64_t)k * ld], x[k], s);
-      x[i] = -s / Ms[i + (int64_t)i * ld];
+  // FP64: R from Ms, the column itself (in h.Ri) as the work vector
+  for (int c = warp; c < l; c += nwarp) {
+    double* x = h.Ri + (int64_t)c * l;
+    for (int k = lane; k < l; k += 32) x[k] = (k == c) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int i = c; i >= 0; --i) {
+      const double xi = x[i] / (double)Ms[i + (int64_t)i * ld];
+      __syncwarp();
+      if (lane == 0) x[i] = xi;
+      const T* ri = Ms + (int64_t)i * ld;
+      for (int k = lane; k < i; k += 32) x[k] = fma(-(double)ri[k], xi, x[k]);
+      __syncwarp();
     }
   }
 }
 
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
-                     cudaStream_t st) {
-  const size_t bytes = (size_t)max_l * (max_l + 1) * sizeof(double);
+                     cudaStream_t st, int f32_chol) {
+  const size_t esz = f32_chol ? sizeof(float) : sizeof(double);
+  size_t bytes = (size_t)max_l * (max_l + 1) * esz;
+  const size_t b32 = (size_t)max_l * (max_l + 1) * sizeof(float) + 8 * (size_t)max_l * sizeof(float);
+  if (b32 > bytes) bytes = b32;
   const int use_smem = bytes <= 200 * 1024;
-  if (use_smem) {
-    cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_chol_inv<<<C, 256, bytes, st>>>(d_ch, accumulate, 1, f32_inverse);
-    note_launch();
+  if (f32_chol) {
+    if (use_smem) {
+      cudaFuncSetAttribute(k_chol_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      k_chol_inv<float><<<C, 256, bytes, st>>>(d_ch, accumulate, 1, 1);
+    } else {
+      k_chol_inv<float><<<C, 256, 0, st>>>(d_ch, accumulate, 0, 1);
+    }
   } else {
-    k_chol_inv<<<C, 256, 0, st>>>(d_ch, accumulate, 0, f32_inverse);
-    note_launch();
+    if (use_smem) {
+      cudaFuncSetAttribute(k_chol_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      k_chol_inv<double><<<C, 256, bytes, st>>>(d_ch, accumulate, 1, f32_inverse);
+    } else {
+      k_chol_inv<double><<<C, 256, 0, st>>>(d_ch, accumulate, 0, f32_inverse);
+    }
   }
+  note_launch();
 }
 
 // ------------------------------------------------ one-sided Jacobi (Hestenes)
@@ -262,24 +286,36 @@ void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32
 // one warp per pair runs without synchronisation inside the round.  Sweeps
 // repeat until no pair exceeds |gamma| <= l eps sqrt(alpha beta) (or a cap).
 // Result: M J = X Sigma with X orthonormal, so R^T = X Sigma J^T.
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float4 V; static constexpr int N = 4; };
+template <> struct Vec2<double> { typedef double2 V; static constexpr int N = 2; };
+
+RSVD_DEV float vget(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+RSVD_DEV double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+// Columns are stored with stride lp = round_up(l, 8 vectors), rows l..lp-1
+// zero, so each 8-lane group moves 128 contiguous bytes per access
+// (conflict-free) with 16-byte vector loads.
 template <typename T, bool WANT_J>
 __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int use_smem,
                                                 int max_sweeps) {
-  extern __shared__ unsigned char sraw[];
+  typedef typename Vec2<T>::V V;
+  constexpr int VE = Vec2<T>::N;
+  extern __shared__ __align__(16) unsigned char sraw[];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l;
   const int m = l + (l & 1);                       // even count; index l (if odd) is a zero column
-  const int ld = use_smem ? l + 1 : l;             // odd stride in shared memory
+  const int lp = (l + 8 * VE - 1) / (8 * VE) * (8 * VE);
+  const int nv = lp / VE;                          // vectors per column
   T* Mw;
   T* Jw;
-  if (use_smem) { Mw = (T*)sraw; Jw = Mw + (int64_t)l * ld; }
-  else { Mw = (T*)h.G; Jw = (T*)h.Ri; }            // G and R^{-1} are free at this point
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e % l, j = e / l;
-    Mw[i + (int64_t)j * ld] = (T)h.R[j + (int64_t)i * l];      // M = R^T
-    if (WANT_J) Jw[i + (int64_t)j * ld] = (T)(i == j ? 1.0 : 0.0);
+  if (use_smem) { Mw = (T*)sraw; Jw = Mw + (int64_t)l * lp; }
+  else { Mw = (T*)h.G; Jw = (T*)h.Ri; }            // G and R^{-1} (sized l x (l+32)) are free here
+  for (int e = threadIdx.x; e < lp * l; e += blockDim.x) {
+    const int i = e % lp, j = e / lp;
+    Mw[e] = (i < l) ? (T)h.R[j + (int64_t)i * l] : (T)0;      // M = R^T
+    if (WANT_J) Jw[e] = (T)(i == j ? 1.0 : 0.0);
   }
-  __shared__ int nrot;
   __syncthreads();
   const T eps = (sizeof(T) == 8) ? (T)1.1102230246251565e-16 : (T)5.9604645e-8;
   const T thr = (T)l * eps;
@@ -289,25 +325,31 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
   const int per_pass = nwarp * 4;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) nrot = 0;
-    __syncthreads();
+    int rotated = 0;
     for (int r = 0; r < m - 1; ++r) {
       for (int base = 0; base < npairs; base += per_pass) {
         const int pi = base + warp * 4 + grp;
         int a = -1, b = -1;
         if (pi < npairs) {
           if (pi == 0) { a = r; b = m - 1; }
-          else { a = (r + pi) % (m - 1); b = (r - pi + (m - 1)) % (m - 1); }
+          else {
+            a = r + pi; if (a >= m - 1) a -= m - 1;
+            b = r - pi; if (b < 0) b += m - 1;
+          }
           if (a > b) { const int t = a; a = b; b = t; }
           if (b >= l) a = b = -1;
         }
         T al = 0, be = 0, ga = 0;
-        T* ca = Mw + (int64_t)(a < 0 ? 0 : a) * ld;
-        T* cb = Mw + (int64_t)(b < 0 ? 0 : b) * ld;
+        V* ca = (V*)(Mw + (int64_t)(a < 0 ? 0 : a) * lp);
+        V* cb = (V*)(Mw + (int64_t)(b < 0 ? 0 : b) * lp);
         if (a >= 0)
-          for (int rr = gl; rr < l; rr += 8) {
-            const T x = ca[rr], y = cb[rr];
-            al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+          for (int v = gl; v < nv; v += 8) {
+            const V x = ca[v], y = cb[v];
+#pragma unroll
+            for (int q = 0; q < VE; ++q) {
+              const T xq = vget(x, q), yq = vget(y, q);
+              al = fma(xq, xq, al); be = fma(yq, yq, be); ga = fma(xq, yq, ga);
+            }
           }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {          // reduce inside the 8-lane group
@@ -316,39 +358,67 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
         if (a < 0 || ga == (T)0 || fabs(ga) <= thr * sqrt(al * be)) continue;
-        const T zeta = (be - al) / (2 * ga);
-        T t;
-        if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
-        else t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-        const T cs = (T)1 / sqrt((T)1 + t * t);
+        T t, cs;
+        if (sizeof(T) == 4) {
+          const float zeta = __fdividef((float)(be - al), (float)(2 * ga));
+          const float az = fabsf(zeta);
+          float tf = az > 1e15f ? __fdividef(0.5f, az) : __fdividef(1.0f, az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+          tf = zeta >= 0.0f ? tf : -tf;
+          t = (T)tf;
+          cs = (T)rsqrtf(fmaf(tf, tf, 1.0f));
+        } else {
+          const T zeta = (be - al) / (2 * ga);
+          if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
+          else t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          cs = (T)1 / sqrt((T)1 + t * t);
+        }
         const T sn = cs * t;
-        for (int rr = gl; rr < l; rr += 8) {
-          const T x = ca[rr], y = cb[rr];
-          ca[rr] = cs * x - sn * y;
-          cb[rr] = sn * x + cs * y;
+        for (int v = gl; v < nv; v += 8) {
+          V x = ca[v], y = cb[v];
+          V nx, ny;
+          T* px = (T*)&nx;
+          T* py = (T*)&ny;
+#pragma unroll
+          for (int q = 0; q < VE; ++q) {
+            const T xq = vget(x, q), yq = vget(y, q);
+            px[q] = cs * xq - sn * yq;
+            py[q] = sn * xq + cs * yq;
+          }
+          ca[v] = nx;
+          cb[v] = ny;
         }
         if (WANT_J) {
-          T* ja = Jw + (int64_t)a * ld;
-          T* jb = Jw + (int64_t)b * ld;
-          for (int rr = gl; rr < l; rr += 8) {
-            const T x = ja[rr], y = jb[rr];
-            ja[rr] = cs * x - sn * y;
-            jb[rr] = sn * x + cs * y;
+          V* ja = (V*)(Jw + (int64_t)a * lp);
+          V* jb = (V*)(Jw + (int64_t)b * lp);
+          for (int v = gl; v < nv; v += 8) {
+            V x = ja[v], y = jb[v];
+            V nx, ny;
+            T* px = (T*)&nx;
+            T* py = (T*)&ny;
+#pragma unroll
+            for (int q = 0; q < VE; ++q) {
+              const T xq = vget(x, q), yq = vget(y, q);
+              px[q] = cs * xq - sn * yq;
+              py[q] = sn * xq + cs * yq;
+            }
+            ja[v] = nx;
+            jb[v] = ny;
           }
         }
-        if (gl == 0) atomicAdd(&nrot, 1);
+        rotated = 1;
       }
-      __syncthreads();
+      if (r < m - 2) __syncthreads();
     }
-    const int done = (nrot == 0);
-    __syncthreads();
-    if (done) break;
+    if (!__syncthreads_or(rotated)) break;     // also the barrier after the last round
   }
-  if (threadIdx.x == 0 && sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
+  if (threadIdx.x == 0) {
+    h.res->sweeps = sweep + 1;
+    if (sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
+  }
   __syncthreads();
   // column norms (unsorted) into scratch
   for (int cidx = warp; cidx < l; cidx += nwarp) {
-    const T* cc = Mw + (int64_t)cidx * ld;
+    const T* cc = Mw + (int64_t)cidx * lp;
     double s = 0.0;
     for (int rr = lane; rr < l; rr += 32) s += (double)cc[rr] * (double)cc[rr];
     s = warp_sum(s);
@@ -364,11 +434,11 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
       rank += (so > si) || (so == si && o < cidx);
     }
     rank = warp_sum(rank);
-    const T* cc = Mw + (int64_t)cidx * ld;
+    const T* cc = Mw + (int64_t)cidx * lp;
     const double inv = si > 0.0 ? 1.0 / si : 0.0;
     for (int rr = lane; rr < l; rr += 32) h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
     if (WANT_J) {
-      const T* jc = Jw + (int64_t)cidx * ld;
+      const T* jc = Jw + (int64_t)cidx * lp;
       for (int rr = lane; rr < l; rr += 32) h.J[rr + (int64_t)rank * l] = (double)jc[rr];
     }
     if (lane == 0) h.sig[rank] = si;
@@ -378,7 +448,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st) {
   // mixed path (fp32): only the left vectors X are used; FP64 path needs J too
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  const size_t bytes = (fp32 ? 1 : 2) * (size_t)max_l * (max_l + 1) * esz;
+  const int ve = fp32 ? 4 : 2;
+  const size_t lp = (size_t)((max_l + 8 * ve - 1) / (8 * ve) * (8 * ve));
+  const size_t bytes = (fp32 ? 1 : 2) * (size_t)max_l * lp * esz;
   const int use_smem = bytes <= 200 * 1024;
   if (fp32) {
     if (use_smem) {

@@ -10,7 +10,9 @@ void note_launch(int k = 1);
 long long launch_count();
 
 // ----------------------------------------------------------------- tile GEMMs
-enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2 };
+enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2, MM_RESID = 3 };
+// MM_RESID: Cm holds a reference block R (same layout); the kernel writes
+// sum over its tile of (R - A B)^2 to rpart[tile index within the channel].
 enum MMKind {
   MMK_DENSE_F64 = 0,     // C = V B, V dense row-major FP64, FP64 FMA
   MMK_GRAM_F64 = 1,      // partial C_s = Y_s^T Z_s, FP64
@@ -18,7 +20,8 @@ enum MMKind {
   MMK_GRAM_DOT2 = 3,     // partial C_s = Y_s^T Z_s, FP32 data, compensated (Dot2) -> FP64
   MMK_NN_F32_F64B = 4,   // C(FP32) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
   MMK_NN_F32_OUT64 = 5,  // C(FP64) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
-  MMK_GRAM_F32 = 6       // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
+  MMK_GRAM_F32 = 6,      // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
+  MMK_RESID_F32 = 7      // sum (R - A B)^2 per tile, A FP32 column-major, B FP64 (MM_RESID)
 };
 
 struct MMDesc {
@@ -35,7 +38,11 @@ struct MMDesc {
   int64_t ldsl;
   int nsl;
   const int* ncols_dev;     // optional: output columns limited to *ncols_dev (rank chosen on device)
+  int tile;                 // output tile edge of the kernel kind (64 or 128)
+  double* rpart;            // MM_RESID partials
 };
+
+int tile_of(MMKind kind);
 
 struct ZeroDesc { void* p; int64_t ld; int rows, cols, esz; };
 void launch_zero(const ZeroDesc* d_zd, const int* d_off, int C, int tiles, cudaStream_t st);
@@ -56,7 +63,7 @@ void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint
 // Upper Cholesky G = R^T R (l x l), R^{-1}; R_acc <- R R_acc when accumulate.
 // Shifted retry on breakdown (flag FLAG_SHIFTED).
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
-                     cudaStream_t st);
+                     cudaStream_t st, int f32_chol = 0);
 // One-sided Jacobi SVD of M = R^T (FP64 or FP32 arithmetic); writes sig, M <- left
 // vectors, J <- right vectors, sorted by descending sigma.
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st);
@@ -72,9 +79,7 @@ void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int t
                            cudaStream_t st);
 void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
                        int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st);
-void launch_probe_resid(const Chan* d_ch, const int* d_off, int C, int tiles, int max_l, int s,
-                        cudaStream_t st);
-void launch_probe_finish(const Chan* d_ch, int C, cudaStream_t st);
+void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st);
 
 // ------------------------------------------------------------ exact residual
 int resid_tiles(int n);
