@@ -193,6 +193,35 @@ typedef struct {
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
 rsvd_status rsvd_plan_profile(rsvd_plan_t plan, rsvd_profile* out, int32_t reset);
 
+/* Exact relative residual with no device allocation (no plan needed).
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory when they check a decomposition -- callers whose
+ * device memory is fully reserved up front by their own pool (a further
+ * cudaMalloc would fail or break their budget), and callers that must not let
+ * cudaMalloc/cudaFree synchronise the device in the middle of a pipeline.
+ * It computes the same quantity as rsvd_reconstruct_error,
+ * ||A - U diag(S) V^T||_F / ||A||_F in FP64, but keeps its per-tile partial
+ * sums in a fixed 1 MiB array that the library holds on every GPU that loads
+ * it, until the process exits.
+ *
+ *   A (n x n, leading dim lda >= n), U (n x k, ldu >= n), S (k),
+ *   V (n x k, ldv >= n): DEVICE pointers, column-major as elsewhere;
+ *   rel_err: DEVICE pointer to one double, written asynchronously;
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Returns RSVD_ERR_INVALID_ARG for n < 1, n > RSVD_NOALLOC_MAX_N, k < 0 or a
+ * bad pointer or leading dimension (nothing is launched then), RSVD_ERR_CUDA
+ * if a CUDA call fails.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before capturing any stream on the device.  All calls on one device
+ * share the array, so calls that overlap on the GPU (concurrent streams, or
+ * several host threads) race and must be serialised by the caller. */
+#define RSVD_NOALLOC_MAX_N 16384
+rsvd_status rsvd_reconstruct_error_noalloc(const double* A, int64_t lda, int64_t n, const double* U,
+                                           int64_t ldu, const double* S, const double* V, int64_t ldv,
+                                           int32_t k, double* rel_err, void* stream);
+
 /* Device buffer size (bytes) the plan holds now. */
 int64_t rsvd_plan_workspace_bytes(rsvd_plan_t plan);
 

@@ -97,6 +97,9 @@ def load(build=True):
     lib.rsvd_plan_set_profiling.restype = C.c_int
     lib.rsvd_plan_profile.argtypes = [P, C.POINTER(Profile), C.c_int32]
     lib.rsvd_plan_profile.restype = C.c_int
+    lib.rsvd_reconstruct_error_noalloc.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int64, P, P, C.c_int64,
+                                                   C.c_int32, P, P]
+    lib.rsvd_reconstruct_error_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -151,6 +154,14 @@ def rsvd_plan_profile(h, reset=False):
     p = Profile()
     _check(load().rsvd_plan_profile(h, C.byref(p), 1 if reset else 0))
     return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+
+RSVD_NOALLOC_MAX_N = 16384
+
+
+def rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, stream=None):
+    """Forward to the no-allocation residual entry point (all device pointers)."""
+    return load().rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, stream)
 
 
 def rsvd_reconstruct_error(h, mat, fac):
