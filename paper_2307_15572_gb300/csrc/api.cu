@@ -685,6 +685,373 @@ rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_fac
   return RSVD_OK;
 }
 
+
+// ------------------------------------------------------------ adaptive loop
+// Tolerance-driven blocked range finder, randQB_EI of Yu, Gu & Li (SIAM J.
+// Matrix Anal. Appl. 39, 2018), all channels advancing in lockstep, one host
+// synchronisation per block (to read each channel's error indicator).
+// Per block of b columns (global columns col .. col+b of the Philox matrix):
+//   Y = V P_i, Y <- (I - Q Q^T) Y (twice), Q_i = CQR2(Y)
+//   q rounds: Z = V Q_i, Qh = CQR2(Z); Y = V Qh, Y <- (I - Q Q^T) Y (twice), Q_i = CQR2(Y)
+//   Q_i <- CQR2((I - Q Q^T) Q_i) (twice projected);  W_i = V Q_i  (= B_i^T)
+//   E <- E - ||W_i||_F^2; stop once E <= tol^2 ||V||_F^2 (or l_max columns)
+// then the thin SVD of B = W^T (CQR2 of W with R accumulated, Jacobi on R^T)
+// and the rank by the FP64 identity, exactly as the fixed-l path.
+struct AdaptBufs {
+  double *Q, *W, *Xo, *T2, *Cb, *Q2big, *E;
+  double *Gs, *Rs, *Ris, *Ms, *Js, *sigs, *scrs;     // block (b x b) small buffers
+  double *Gf, *Rf, *Rif, *Mf, *Jf, *sigf, *scrf;     // final (l x l)
+  double *gpart, *fro_part;
+  int lmax;
+};
+
+void lay_adapt(Bump& b, const std::vector<ChanDims>& d, int bsz, std::vector<AdaptBufs>& ab,
+               std::vector<Chan>& base, const rsvd_matrix* A, rsvd_factors* f, int kfixed) {
+  const int C = (int)d.size();
+  ab.assign(C, AdaptBufs{});
+  base.assign(C, Chan{});
+  for (int c = 0; c < C; ++c) {
+    const ChanDims& dd = d[c];
+    AdaptBufs& x = ab[c];
+    Chan& h = base[c];
+    x.lmax = dd.l;                       // l holds the per-channel column cap here
+    const int64_t T = dd.ldt;
+    x.Q = b.take<double>(T * x.lmax);
+    x.W = b.take<double>(T * x.lmax);
+    x.Xo = b.take<double>(T * bsz);
+    x.T2 = b.take<double>(T * bsz);
+    x.Cb = b.take<double>((size_t)x.lmax * bsz);
+    x.Q2big = b.take<double>(T * x.lmax);
+    x.E = b.take<double>(1);
+    const size_t sb = (size_t)bsz * (bsz + 32);
+    x.Gs = b.take<double>(sb); x.Rs = b.take<double>(sb); x.Ris = b.take<double>(sb);
+    x.Ms = b.take<double>(sb); x.Js = b.take<double>(sb);
+    x.sigs = b.take<double>(bsz); x.scrs = b.take<double>(bsz);
+    const size_t sf = (size_t)x.lmax * (x.lmax + 32);
+    x.Gf = b.take<double>(sf); x.Rf = b.take<double>(sf); x.Rif = b.take<double>(sf);
+    x.Mf = b.take<double>(sf); x.Jf = b.take<double>(sf);
+    x.sigf = b.take<double>(x.lmax); x.scrf = b.take<double>(x.lmax);
+    x.gpart = b.take<double>((size_t)dd.gsplit * x.lmax * std::max(x.lmax, bsz));
+    x.fro_part = b.take<double>(cdiv(dd.n, 64));
+    h.n = dd.n; h.k_cap = dd.kcap; h.k_fixed = kfixed; h.ldt = dd.ldt;
+    if (A[c].mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)dd.n * dd.n); h.lda = dd.n; }
+    else { h.A = A[c].data; h.lda = A[c].ld; }
+    h.gpart = x.gpart;
+    h.fro_part = x.fro_part;
+    const rsvd_factors& F = f[c];
+    if (F.mem == RSVD_MEM_HOST) {
+      h.U = b.take<double>((size_t)dd.n * dd.kcap); h.ldu = dd.n;
+      h.V = b.take<double>((size_t)dd.n * dd.kcap); h.ldv = dd.n;
+      h.S = b.take<double>(dd.kcap);
+    } else {
+      h.U = F.U; h.ldu = F.ldu; h.V = F.V; h.ldv = F.ldv; h.S = F.S;
+      if (!h.U) { h.U = b.take<double>((size_t)dd.n * dd.kcap); h.ldu = dd.n; }
+      if (!h.V) { h.V = b.take<double>((size_t)dd.n * dd.kcap); h.ldv = dd.n; }
+    }
+  }
+}
+
+// Upload a job's arena and run its steps (synchronous at the end).
+rsvd_status run_job(Job& J) {
+  rsvd_plan_s* P = J.P;
+  if (rsvd_status s = grow_pinned(P, J.ar.h.size() + 64)) return s;
+  memcpy(P->hp, J.ar.h.data(), J.ar.h.size());
+  CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
+  for (auto& step : J.steps)
+    if (rsvd_status s = step()) return s;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(P->st));
+  return RSVD_OK;
+}
+
+// Y_c -= Q_c (Q_c^T Y_c) for the active channels (m_c = columns of Q so far).
+void project_out(Job& J, std::function<const double*(int)> Q, std::function<int(int)> m,
+                 std::function<double*(int)> Y, std::function<double*(int)> Cb) {
+  add_tn(J, MMK_GRAM_F64, [&](int c) { return (const void*)Q(c); }, [&](int c) { return (const void*)Y(c); },
+         Cb, m, [&](int c) { return J.d[c].l; }, false);
+  std::vector<MMDesc> md(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc mm{};
+    mm.A = Q(c); mm.lda = d.ldt;
+    mm.B = Cb(c); mm.ldb = std::max(1, m(c));
+    mm.Cm = Y(c); mm.ldc = d.ldt;
+    mm.m = d.n; mm.n = d.l; mm.k = m(c);
+    mm.ks = 1; mm.kchunk = (int)rup(std::max(1, m(c)), 16);
+    mm.mode = MM_SUB;
+    md[c] = mm;
+  }
+  add_mm(J, MMK_NN_F64, md);
+}
+
+rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item) {
+  if (P->o.precision != RSVD_PREC_FP64)
+    return seterr(RSVD_ERR_UNSUPPORTED, "the adaptive loop is built for the FP64 path");
+  const int bsz = P->o.block_b > 0 ? P->o.block_b : 32;
+  const int lcap = P->o.l_max > 0 ? P->o.l_max : 1024;
+  const double tol = P->o.tol;
+  const int q = P->o.q;
+  std::vector<ChanDims> d(C);
+  int64_t sum_tiles = 0;
+  for (int c = 0; c < C; ++c) {
+    d[c].n = (int)A[c].n;
+    d[c].l = std::min(d[c].n, lcap);                       // column cap
+    d[c].s = 0; d[c].lw = d[c].l;
+    d[c].kcap = std::min(f[c].k_cap, d[c].l);
+    d[c].ldt = rup(d[c].n, 4);
+    d[c].ldb = rup(d[c].n, 64);
+    sum_tiles += (int64_t)cdiv(d[c].l, 64) * cdiv(d[c].l, 64);
+  }
+  for (int c = 0; c < C; ++c) {
+    int g = cdiv(d[c].n, 512);
+    const int want = (int)((2 * NSM + sum_tiles - 1) / std::max<int64_t>(1, sum_tiles));
+    g = std::max(g, std::min(want, cdiv(d[c].n, 64)));
+    d[c].gsplit = std::max(1, std::min(g, 64));
+  }
+  // workspace: buffers, then a descriptor region reused by every job
+  std::vector<AdaptBufs> ab;
+  std::vector<Chan> base;
+  const size_t arena_reserve = (size_t)1 << 20 | 0;
+  size_t buf_bytes = 0;
+  {
+    Bump b(nullptr);
+    lay_adapt(b, d, bsz, ab, base, A, f, P->o.k);
+    b.take<ChanResult>(C);
+    buf_bytes = (b.off + 4095) & ~(size_t)4095;
+  }
+  const size_t arena_bytes = arena_reserve + (size_t)C * 64 * 1024;
+  if (rsvd_status s = grow_ws(P, buf_bytes + arena_bytes)) return s;
+  Bump b(P->ws);
+  lay_adapt(b, d, bsz, ab, base, A, f, P->o.k);
+  ChanResult* d_res = b.take<ChanResult>(C);
+  char* arena_dev = P->ws + buf_bytes;
+  for (int c = 0; c < C; ++c) base[c].res = d_res + c;
+  CK(cudaMemsetAsync(d_res, 0, sizeof(ChanResult) * C, P->st));
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  for (int c = 0; c < C; ++c)
+    if (A[c].mem == RSVD_MEM_HOST)
+      CK(cudaMemcpy2DAsync((void*)base[c].A, (size_t)d[c].n * sizeof(double), A[c].data,
+                           (size_t)A[c].ld * sizeof(double), (size_t)d[c].n * sizeof(double), d[c].n,
+                           cudaMemcpyHostToDevice, P->st));
+
+  // ||V||^2 per channel
+  std::vector<double> fro2(C, 0.0);
+  {
+    Job J;
+    J.P = P; J.C = C; J.A = A; J.f = f; J.mixed = false; J.measure = false;
+    J.d = d;
+    J.ch = base;
+    J.ar.dbase = arena_dev;
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    const int* off64 = offsets(J, [&](int c) { return (int64_t)cdiv(d[c].n, 64); });
+    const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(d[c].n, 64); });
+    const Chan* dch = J.d_ch;
+    cudaStream_t st = P->st;
+    J.steps.push_back([=]() {
+      launch_fro2(dch, off64, C, t64, st);
+      launch_fro2_reduce(dch, C, st);
+      return RSVD_OK;
+    });
+    if (rsvd_status s = run_job(J)) return s;
+    std::vector<ChanResult> r(C);
+    CK(cudaMemcpy(r.data(), d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < C; ++c) {
+      fro2[c] = r[c].fro2;
+      if (r[c].flags & FLAG_NONFINITE) {
+        f[c].status = RSVD_ERR_NONFINITE;
+      }
+    }
+  }
+  std::vector<int> cols(C, 0);
+  std::vector<double> E(fro2);
+  std::vector<char> active(C, 1);
+  for (int c = 0; c < C; ++c)
+    if (f[c].status == RSVD_ERR_NONFINITE) active[c] = 0;
+  const uint64_t seed = P->o.seed;
+  std::vector<double> Ei(C);
+  while (true) {
+    std::vector<int> idx;
+    for (int c = 0; c < C; ++c)
+      if (active[c]) idx.push_back(c);
+    if (idx.empty()) break;
+    const int Ca = (int)idx.size();
+    Job J;
+    J.P = P; J.C = Ca; J.A = A; J.f = f; J.mixed = false; J.measure = false;
+    J.d.resize(Ca);
+    J.ch.resize(Ca);
+    J.ar.dbase = arena_dev;
+    bool first = true;
+    for (int a = 0; a < Ca; ++a) {
+      const int c = idx[a];
+      ChanDims dd = d[c];
+      dd.l = std::min(bsz, ab[c].lmax - cols[c]);
+      dd.kcap = dd.l;
+      J.d[a] = dd;
+      Chan h = base[c];
+      h.l = dd.l;
+      h.col0 = cols[c];
+      h.X = ab[c].Xo;
+      h.G = ab[c].Gs; h.R = ab[c].Rs; h.Ri = ab[c].Ris; h.M = ab[c].Ms; h.J = ab[c].Js;
+      h.sig = ab[c].sigs; h.scr = ab[c].scrs;
+      J.ch[a] = h;
+      first &= cols[c] == 0;
+    }
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    J.max_l = bsz;
+    auto Yq = [&](int a) { return ab[idx[a]].Q + (int64_t)cols[idx[a]] * J.d[a].ldt; };
+    auto Xw = [&](int a) { return ab[idx[a]].W + (int64_t)cols[idx[a]] * J.d[a].ldt; };
+    auto T2 = [&](int a) { return ab[idx[a]].T2; };
+    auto Qp = [&](int a) { return (const double*)ab[idx[a]].Q; };
+    auto mcols = [&](int a) { return cols[idx[a]]; };
+    auto Cb = [&](int a) { return ab[idx[a]].Cb; };
+    const int* off64 = offsets(J, [&](int a) { return (int64_t)cdiv(J.d[a].n, 64); });
+    const int t64 = total_of(J, [&](int a) { return (int64_t)cdiv(J.d[a].n, 64); });
+    {
+      const Chan* dch = J.d_ch;
+      cudaStream_t st = P->st;
+      J.steps.push_back([=]() {
+        launch_omega_f64(dch, off64, Ca, t64, seed, 0, st);
+        return RSVD_OK;
+      });
+    }
+    dense_f64(J, [&](int a) { return (const double*)ab[idx[a]].Xo; }, Yq);        // Y = V P_i
+    if (!first) { project_out(J, Qp, mcols, Yq, Cb); project_out(J, Qp, mcols, Yq, Cb); }
+    cqr2_f64(J, Yq, T2, false);
+    for (int r = 0; r < q; ++r) {
+      dense_f64(J, [&](int a) { return (const double*)Yq(a); }, Xw);             // V Q_i
+      cqr2_f64(J, Xw, T2, false);
+      dense_f64(J, [&](int a) { return (const double*)Xw(a); }, Yq);             // V Qh
+      if (!first) { project_out(J, Qp, mcols, Yq, Cb); project_out(J, Qp, mcols, Yq, Cb); }
+      cqr2_f64(J, Yq, T2, false);
+    }
+    if (!first) {
+      project_out(J, Qp, mcols, Yq, Cb);
+      project_out(J, Qp, mcols, Yq, Cb);
+      cqr2_f64(J, Yq, T2, false);
+    }
+    dense_f64(J, [&](int a) { return (const double*)Yq(a); }, Xw);               // W_i = V Q_i
+    {
+      std::vector<SumsqDesc> sd(Ca);
+      for (int a = 0; a < Ca; ++a) sd[a] = SumsqDesc{Xw(a), J.d[a].ldt, J.d[a].n, J.d[a].l, 8, ab[idx[a]].E};
+      const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
+      cudaStream_t st = P->st;
+      J.steps.push_back([=]() {
+        launch_sumsq(dsd, Ca, st);
+        return RSVD_OK;
+      });
+    }
+    if (J.ar.h.size() > arena_bytes) return seterr(RSVD_ERR_OOM, "descriptor region too small");
+    if (rsvd_status s = run_job(J)) return s;
+    for (int a = 0; a < Ca; ++a) {
+      const int c = idx[a];
+      CK(cudaMemcpyAsync(&Ei[c], ab[c].E, sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    }
+    CK(cudaStreamSynchronize(P->st));
+    for (int a = 0; a < Ca; ++a) {
+      const int c = idx[a];
+      E[c] -= Ei[c];
+      cols[c] += J.d[a].l;
+      if (E[c] <= tol * tol * fro2[c] || cols[c] >= ab[c].lmax) active[c] = 0;
+    }
+  }
+  // final: SVD of B = W^T on the drawn columns, rank by tolerance, lift
+  std::vector<int> idx;
+  for (int c = 0; c < C; ++c)
+    if (cols[c] > 0) idx.push_back(c);
+  const int Cf = (int)idx.size();
+  if (Cf > 0) {
+    Job J;
+    J.P = P; J.C = Cf; J.A = A; J.f = f; J.mixed = false; J.measure = false;
+    J.d.resize(Cf);
+    J.ch.resize(Cf);
+    J.ar.dbase = arena_dev;
+    J.policy = RSVD_RANK_TOL;
+    J.tol = tol;
+    for (int a = 0; a < Cf; ++a) {
+      const int c = idx[a];
+      ChanDims dd = d[c];
+      dd.l = cols[c];
+      dd.kcap = std::min(f[c].k_cap, dd.l);
+      J.d[a] = dd;
+      Chan h = base[c];
+      h.l = dd.l;
+      h.k_cap = dd.kcap;
+      h.G = ab[c].Gf; h.R = ab[c].Rf; h.Ri = ab[c].Rif; h.M = ab[c].Mf; h.J = ab[c].Jf;
+      h.sig = ab[c].sigf; h.scr = ab[c].scrf;
+      J.ch[a] = h;
+      J.max_l = std::max(J.max_l, dd.l);
+      J.max_kcap = std::max(J.max_kcap, dd.kcap);
+    }
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    J.d_res = nullptr;
+    // fro2 is already in res; results land in res[c]
+    auto Wb = [&](int a) { return ab[idx[a]].W; };
+    auto Q2 = [&](int a) { return ab[idx[a]].Q2big; };
+    cqr2_f64(J, Wb, Q2, true);
+    const Chan* dch = J.d_ch;
+    const int maxl = J.max_l, maxk = J.max_kcap;
+    cudaStream_t st = P->st;
+    J.steps.push_back([=]() {
+      launch_jacobi(dch, Cf, 0, maxl, st);
+      launch_select(dch, Cf, RSVD_RANK_TOL, tol, 0, st);
+      return RSVD_OK;
+    });
+    // lift (k_out from each channel's result)
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<MMDesc> md(Cf);
+      for (int a = 0; a < Cf; ++a) {
+        const int c = idx[a];
+        const ChanDims& dd = J.d[a];
+        MMDesc m{};
+        m.A = pass == 0 ? (const void*)ab[c].Q : (const void*)ab[c].W; m.lda = dd.ldt;
+        m.B = pass == 0 ? ab[c].Mf : ab[c].Jf; m.ldb = dd.l;
+        m.Cm = pass == 0 ? J.ch[a].U : J.ch[a].V; m.ldc = pass == 0 ? J.ch[a].ldu : J.ch[a].ldv;
+        m.m = dd.n; m.n = dd.kcap; m.k = dd.l;
+        m.ks = 1; m.kchunk = (int)rup(dd.l, 16);
+        m.mode = MM_STORE;
+        m.ncols_dev = &d_res[c].k_out;
+        md[a] = m;
+      }
+      add_mm(J, MMK_NN_F64, md);
+    }
+    J.steps.push_back([=]() {
+      launch_signfix(dch, Cf, maxk, st);
+      return RSVD_OK;
+    });
+    if (J.ar.h.size() > arena_bytes) return seterr(RSVD_ERR_OOM, "descriptor region too small");
+    if (rsvd_status s = run_job(J)) return s;
+  }
+  std::vector<ChanResult> res(C);
+  CK(cudaMemcpy(res.data(), d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost));
+  int herr = 0;
+  CK(cudaMemcpy(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", herr);
+  rsvd_status worst = RSVD_OK;
+  for (int c = 0; c < C; ++c) {
+    rsvd_status s = (rsvd_status)res[c].status;
+    if (res[c].flags & FLAG_NONFINITE) s = RSVD_ERR_NONFINITE;
+    else if (E[c] > tol * tol * fro2[c] && s >= 0) s = RSVD_ERR_TOL_NOT_MET;
+    f[c].k_out = cols[c] > 0 ? res[c].k_out : 0;
+    f[c].l_used = cols[c];
+    f[c].err_est = res[c].err_est;
+    f[c].status = s;
+    if (per_item) per_item[c] = s;
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (worst >= 0 && s > worst) worst = s;
+    if (f[c].mem == RSVD_MEM_HOST && f[c].k_out > 0) {
+      const int k = f[c].k_out, n = d[c].n;
+      CK(cudaMemcpy2DAsync(f[c].U, f[c].ldu * sizeof(double), base[c].U, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpy2DAsync(f[c].V, f[c].ldv * sizeof(double), base[c].V, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpyAsync(f[c].S, base[c].S, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    }
+  }
+  CK(cudaStreamSynchronize(P->st));
+  if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
+  return worst;
+}
+
 }  // namespace
 
 // =================================================================== ABI
@@ -711,8 +1078,11 @@ rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* o) {
   if (o->rank_policy == RSVD_RANK_TOL && o->k + o->p < 1)
     return seterr(RSVD_ERR_INVALID_ARG, "tolerance mode needs k + p >= 1 columns");
   if (o->slices < 0 || o->slices > 3) return seterr(RSVD_ERR_INVALID_ARG, "slices %d outside [0, 3]", o->slices);
-  if (o->rank_policy == RSVD_RANK_ADAPTIVE || o->rank_policy == RSVD_RANK_LEARNED)
+  if (o->rank_policy == RSVD_RANK_LEARNED)
     return seterr(RSVD_ERR_UNSUPPORTED, "rank policy %d is not available in this build", o->rank_policy);
+  if (o->rank_policy == RSVD_RANK_ADAPTIVE && o->precision != RSVD_PREC_FP64)
+    return seterr(RSVD_ERR_UNSUPPORTED, "the adaptive loop is built for the FP64 path");
+  if (o->block_b < 0 || o->l_max < 0) return seterr(RSVD_ERR_INVALID_ARG, "negative block_b or l_max");
   if (o->rayleigh_ritz && (o->precision != RSVD_PREC_FP64 || o->rank_policy != RSVD_RANK_FIXED))
     return seterr(RSVD_ERR_UNSUPPORTED, "Rayleigh-Ritz is built for the FP64 path with a fixed rank");
   int dev = 0;
@@ -769,6 +1139,7 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* 
                                    rsvd_status* per_item) {
   g_err[0] = 0;
   if (rsvd_status s = validate(P, C, A, f)) return s;
+  if (P->o.rank_policy == RSVD_RANK_ADAPTIVE) return run_adaptive(P, C, A, f, per_item);
   Job J;
   J.P = P;
   J.C = C;

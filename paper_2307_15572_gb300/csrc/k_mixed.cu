@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
     if (rr >= rows) continue;
     const int i = r0 + rr;
     float g;
-    if (j < h.l) g = gauss_f32(seed, (uint32_t)i, (uint32_t)(col0 + j), TAG_OMEGA);
+    if (j < h.l) g = gauss_f32(seed, (uint32_t)i, (uint32_t)(col0 + h.col0 + j), TAG_OMEGA);
     else g = gauss_f32(pseed, (uint32_t)i, (uint32_t)(j - h.l), TAG_RESID);
     const int64_t o = (int64_t)j * h.ldb + i;
     h.Xb[0][o] = __float2bfloat16_rn(g);

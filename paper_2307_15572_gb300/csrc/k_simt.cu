@@ -148,6 +148,7 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
       if (colscale) v *= colscale[gn];
       TC* dst = Cp + gm + (int64_t)gn * ldc;
       if (mode == MM_ATOMIC) atomicAdd(dst, (TC)v);
+      else if (mode == MM_SUB) *dst = *dst - (TC)v;
       else *dst = (TC)v;
       if (nsl > 0) {                     // BF16 word slices of the FP32 result
         const int64_t o = gm + (int64_t)gn * ldsl;
@@ -324,7 +325,11 @@ k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) 
 #pragma unroll
       for (int q = 0; q < 4; ++q) v[q] = acc[ig * 4 + q][j] * cs;
       TC* dst = Cp + r4 + (int64_t)gn * ldc;
-      if (full && vec_ok) {
+      if (mode == MM_SUB) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (r4 + q < dm) dst[q] = dst[q] - (TC)v[q];
+      } else if (full && vec_ok) {
         *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
       } else {
 #pragma unroll

@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) k_omega_f64(const Chan* __restrict__ ch,
   for (int e = threadIdx.x; e < 64 * h.l; e += blockDim.x) {
     const int rr = e & 63, j = e >> 6;
     if (rr < rows)
-      h.X[(r0 + rr) + (int64_t)j * h.ldt] = gauss_f64(seed, (uint32_t)(r0 + rr), (uint32_t)(col0 + j), TAG_OMEGA);
+      h.X[(r0 + rr) + (int64_t)j * h.ldt] =
+          gauss_f64(seed, (uint32_t)(r0 + rr), (uint32_t)(col0 + h.col0 + j), TAG_OMEGA);
   }
 }
 
@@ -546,6 +547,33 @@ __global__ void k_select(const Chan* __restrict__ ch, int policy, double tol, in
 void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
                    cudaStream_t st) {
   k_select<<<C, 32, 0, st>>>(d_ch, policy, tol, use_probe);
+  note_launch();
+}
+
+// ------------------------------------------------------- block sum of squares
+__global__ void __launch_bounds__(256) k_sumsq(const SumsqDesc* __restrict__ sd) {
+  __shared__ double sh[32];
+  const SumsqDesc* d = sd + blockIdx.x;
+  const int rows = d->rows, cols = d->cols;
+  double s = 0.0;
+  for (int j = 0; j < cols; ++j) {
+    if (d->esz == 8) {
+      const double* col = (const double*)d->p + (int64_t)j * d->ld;
+      for (int r = threadIdx.x; r < rows; r += blockDim.x) s = fma(col[r], col[r], s);
+    } else {
+      const float* col = (const float*)d->p + (int64_t)j * d->ld;
+      float sf = 0.0f;
+      for (int r = threadIdx.x; r < rows; r += blockDim.x) sf = fmaf(col[r], col[r], sf);
+      s += f32_to_f64(sf);
+    }
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *d->out = s;
+}
+
+void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st) {
+  if (C <= 0) return;
+  k_sumsq<<<C, 256, 0, st>>>(d_sd);
   note_launch();
 }
 

@@ -10,7 +10,8 @@ void note_launch(int k = 1);
 long long launch_count();
 
 // ----------------------------------------------------------------- tile GEMMs
-enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2, MM_RESID = 3 };
+enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2, MM_RESID = 3, MM_SUB = 4 };
+// MM_SUB: C <- C - A B (block Gram-Schmidt against earlier blocks).
 // MM_RESID: Cm holds a reference block R (same layout); the kernel writes
 // sum over its tile of (R - A B)^2 to rpart[tile index within the channel].
 enum MMKind {
@@ -73,6 +74,9 @@ void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_prob
                    cudaStream_t st);
 // Sign fix: largest-|.| entry of U_i positive, flip V_i with it.
 void launch_signfix(const Chan* d_ch, int C, int max_k, cudaStream_t st);
+// out[c] = sum of squares of the n x cols block at p[c] (leading dim ld[c]), FP64.
+struct SumsqDesc { const void* p; int64_t ld; int rows, cols, esz; double* out; };
+void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st);
 
 // --------------------------------------------------------- mixed-path kernels
 void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int tiles, int nsl,

@@ -206,3 +206,32 @@ def test_mixed_tolerance_large_channel(lib):
     assert err <= 1e-4, err
     assert o.k <= r["k"] <= o.k + 12
     assert abs(r["err_est"] - err) <= 0.2 * err
+
+
+@pytest.mark.parametrize("n,tol,b,q", [(900, 1e-4, 16, 0), (1500, 1e-5, 32, 1), (300, 1e-3, 8, 0)])
+def test_fp64_adaptive_matches_oracle(lib, n, tol, b, q):
+    A = synth.batch_channel(n % 7, n)
+    o, drawn, met = orsvd.rsvd_adaptive(A, tol=tol, b=b, q=q, seed=13, l_max=600)
+    st, r, err = run(lib, A, k=0, p=0, q=q, seed=13, tol=tol, policy="adaptive", block_b=b,
+                     l_max=600, k_cap=600)
+    assert st == 0, lib.last_error()
+    assert met
+    assert r["l"] == drawn and r["k"] == o.k
+    sigma_parity(r["S"].cpu().numpy(), o.S)
+    assert err <= tol and err <= 1.05 * orsvd.reconstruct_error(A, o.U, o.S, o.V)
+
+
+def test_fp64_adaptive_batched_uneven(lib):
+    torch = _torch()
+    sizes = [400, 1200, 700]
+    mats = [synth.batch_channel(c, n) for c, n in enumerate(sizes)]
+    plan = lib.Plan(max(sizes), k=0, p=0, q=0, seed=2, tol=1e-4, policy="adaptive", block_b=16, l_max=400)
+    try:
+        st, res = plan.decompose_batched([torch.as_tensor(A, device="cuda") for A in mats], 400)
+        assert st == 0, lib.last_error()
+        for A, r in zip(mats, res):
+            o, drawn, met = orsvd.rsvd_adaptive(A, tol=1e-4, b=16, q=0, seed=2, l_max=400)
+            assert r["l"] == drawn and r["k"] == o.k
+            sigma_parity(r["S"].cpu().numpy(), o.S)
+    finally:
+        plan.close()
