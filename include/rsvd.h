@@ -130,7 +130,8 @@ typedef struct {
  * are descending and the pair (U_i, V_i) is sign-fixed so that the
  * largest-magnitude entry of U_i is positive), l_used = columns drawn,
  * err_est = estimated relative Frobenius error of the rank-k_out factors,
- * status = this channel's rsvd_status.
+ * status = this channel's rsvd_status.  `tol` (input) overrides the plan's
+ * tolerance for this channel when > 0.
  */
 typedef struct {
   int32_t mem;
@@ -144,6 +145,7 @@ typedef struct {
   int32_t l_used;
   double err_est;
   int32_t status;
+  double tol;           /* input: this channel's tolerance (0 = the plan's), TOL/ADAPTIVE/LEARNED */
 } rsvd_factors;
 
 /* Create a plan.  Checks the options (RSVD_ERR_INVALID_ARG on a bad value)

@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 A cheap 16-column probe Y16 = V P16 (P16 from the Philox stream with tag
 TAG_PROBE) sees the leading part of the spectrum.  Its singular values
-t_1 >= ... >= t_16 (from the 16 x 16 Gram Y16^T Y16) and the channel's size
-and tolerance form the feature vector (d = 19):
+t_1 >= ... >= t_16 (LAPACK SVD of Y16; going through the Gram would square
+the spread and lose the small ones) and the channel's size and tolerance
+form the feature vector (d = 19):
 
   f = [ log(t_j / t_1) for j = 2..16,        (15 values; t_j floored at 1e-300)
         log t_1,
@@ -34,9 +35,7 @@ def probe_singular_values(V, seed):
     n = V.shape[0]
     P = philox.gaussian_f64(np.arange(n), np.arange(NPROBE), seed, philox.TAG_PROBE)
     Y = V @ P
-    G = Y.T @ Y
-    ev = np.linalg.eigvalsh(0.5 * (G + G.T))
-    t = np.sqrt(np.maximum(ev[::-1], 0.0))
+    t = np.linalg.svd(Y, compute_uv=False)
     return t, float(np.sum(Y * Y))
 
 

@@ -29,6 +29,7 @@
 
 #include "kernels.h"
 #include "tc_gemm.h"
+#include "../../include/rsvd_mlp.h"
 
 using namespace rsvd;
 
@@ -161,6 +162,7 @@ int pick_splits(int64_t tiles, int64_t k, int min_chunk) {
 struct ChanDims {
   int n, l, lw, s, kcap, gsplit;
   int64_t ldt, ldb;
+  double tol;
 };
 
 // Everything one batched call needs.
@@ -536,7 +538,7 @@ void cqr2_mixed(Job& J, int nsl_out) {
   }
 }
 
-rsvd_status build_mixed(Job& J) {
+rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   auto& ch = J.ch;
   const int C = J.C;
   cudaStream_t st = J.P->st;
@@ -549,8 +551,8 @@ rsvd_status build_mixed(Job& J) {
   const uint64_t seed = J.P->o.seed;
   const uint64_t pseed = seed ^ 0x5DEECE66DULL;
   J.steps.push_back([=]() {
-    launch_convert_slices(dch, off8, C, t8, nsl, st);
-    launch_fro2_reduce_rows(dch, C, 8, st);
+    if (!skip_convert) launch_convert_slices(dch, off8, C, t8, nsl, st);
+    launch_fro2_reduce_rows(dch, C, 8, st);         // partials are kept from the convert pass
     launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
     return RSVD_OK;
   });
@@ -609,39 +611,98 @@ rsvd_status build_mixed(Job& J) {
   return RSVD_OK;
 }
 
+// ------------------------------------------------------------ probe job
+// 16-column probe Y16 = V P16 (P16 from the Philox stream tag 1), its
+// singular values, the rank-model features and (with weights) the network's
+// predictions.  Mixed path: V is converted to its words here (the
+// decomposition that follows reuses them) and the probe pass reads one word.
+rsvd_status build_probe(Job& J, float* d_feat, const float* theta, float* d_pred) {
+  auto& ch = J.ch;
+  const int C = J.C;
+  cudaStream_t st = J.P->st;
+  const Chan* dch = J.d_ch;
+  const uint64_t seed = J.P->o.seed;
+  const double tol = J.tol;
+  const int* off64 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+  const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+  if (J.mixed) {
+    const int* off8 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 8); });
+    const int t8 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 8); });
+    const int nsl = J.nsl;
+    J.steps.push_back([=]() {
+      launch_convert_slices(dch, off8, C, t8, nsl, st);
+      launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 16, seed, 1, st, TAG_PROBE);
+      return RSVD_OK;
+    });
+    if (rsvd_status s = tc_pass(J, 1, 1, 0)) return s;
+    add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Y32; },
+           [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return ch[c].G; },
+           [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+  } else {
+    J.steps.push_back([=]() {
+      launch_omega_f64(dch, off64, C, t64, seed, 0, st, TAG_PROBE);
+      return RSVD_OK;
+    });
+    dense_f64(J, [&](int c) { return (const double*)ch[c].X; }, [&](int c) { return ch[c].Y; });
+    add_tn(J, MMK_GRAM_F64, [&](int c) { return (const void*)ch[c].Y; },
+           [&](int c) { return (const void*)ch[c].Y; }, [&](int c) { return ch[c].G; },
+           [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+  }
+  add_chol(J, 0);
+  const int mixed = J.mixed ? 1 : 0;
+  J.steps.push_back([=]() {
+    launch_jacobi(dch, C, mixed, 16, st);
+    launch_features(dch, C, tol, d_feat, st);
+    if (theta && d_pred) {
+      if (rsvd_mlp_forward(theta, 19, d_feat, C, d_pred, st) != RSVD_OK)
+        return seterr(RSVD_ERR_CUDA, "rank model inference failed");
+    }
+    return RSVD_OK;
+  });
+  return RSVD_OK;
+}
+
 // ------------------------------------------------------------ layout
-// Lay out per-channel buffers; with base == nullptr only measures.
+// Lay out per-channel buffers; with base == nullptr only measures.  The
+// rank-independent part (staged input, V words, partials, results) comes
+// first, so a probe job and the decomposition after it (different l) share it.
 void layout(Job& J, Bump& b) {
   J.ch.assign(J.C, Chan{});
   for (int c = 0; c < J.C; ++c) {
     const ChanDims& d = J.d[c];
     Chan& h = J.ch[c];
     const rsvd_matrix& A = J.A[c];
+    if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
+    else { h.A = A.data; h.lda = A.ld; }
+    if (J.mixed)
+      for (int s = 0; s < J.nsl; ++s) h.Ab[s] = b.take<__nv_bfloat16>((size_t)d.n * d.ldb);
+    h.fro_part = b.take<double>(cdiv(d.n, 8));
+  }
+  J.d_res = b.take<ChanResult>(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    Chan& h = J.ch[c];
     const rsvd_factors& F = J.f[c];
     h.n = d.n; h.l = d.l; h.k_cap = d.kcap; h.k_fixed = J.P->o.k;
     h.ldt = d.ldt; h.ldb = d.ldb; h.lw = d.lw; h.nprobe = d.s;
-    if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
-    else { h.A = A.data; h.lda = A.ld; }
+    h.tol = d.tol;
     const size_t L2 = (size_t)d.l * d.l;
     const size_t L2p = (size_t)d.l * (d.l + 32);      // Jacobi's padded working copies when not in smem
     h.G = b.take<double>(L2p); h.R = b.take<double>(L2); h.Ri = b.take<double>(L2p);
     h.M = b.take<double>(L2); h.J = b.take<double>(L2);
     h.sig = b.take<double>(d.l); h.scr = b.take<double>(d.l);
-    h.res = nullptr;
+    h.res = J.d_res ? J.d_res + c : nullptr;
     if (!J.mixed) {
       const size_t T = (size_t)d.ldt * d.l;
       h.X = b.take<double>(T); h.Y = b.take<double>(T); h.Q2 = b.take<double>(T);
       h.gpart = b.take<double>((size_t)d.gsplit * L2);
-      h.fro_part = b.take<double>(cdiv(d.n, 64));
     } else {
-      for (int s = 0; s < J.nsl; ++s) h.Ab[s] = b.take<__nv_bfloat16>((size_t)d.n * d.ldb);
       for (int s = 0; s < J.nsl; ++s) h.Xb[s] = b.take<__nv_bfloat16>((size_t)d.lw * d.ldb);
       h.Y32 = b.take<float>((size_t)d.ldt * d.lw);
       h.Q32 = b.take<float>((size_t)d.ldt * d.l);
       h.T32 = b.take<float>((size_t)d.ldt * d.l);
       h.gpart = b.take<double>((size_t)d.gsplit * d.l * std::max(d.l, d.s));
-      h.fro_part = b.take<double>(cdiv(d.n, 8));
-      h.C64 = b.take<double>((size_t)d.l * d.s);
+      h.C64 = b.take<double>((size_t)d.l * std::max(d.s, 1));
       h.est_part = b.take<double>(1 + d.l);
     }
     if (F.mem == RSVD_MEM_HOST) {
@@ -654,8 +715,6 @@ void layout(Job& J, Bump& b) {
       if (!h.V) { h.V = b.take<double>((size_t)d.n * d.kcap); h.ldv = d.n; }
     }
   }
-  J.d_res = b.take<ChanResult>(J.C);
-  for (int c = 0; c < J.C; ++c) J.ch[c].res = J.d_res ? J.d_res + c : nullptr;
 }
 
 rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f) {
@@ -733,7 +792,7 @@ void lay_adapt(Bump& b, const std::vector<ChanDims>& d, int bsz, std::vector<Ada
     x.sigf = b.take<double>(x.lmax); x.scrf = b.take<double>(x.lmax);
     x.gpart = b.take<double>((size_t)dd.gsplit * x.lmax * std::max(x.lmax, bsz));
     x.fro_part = b.take<double>(cdiv(dd.n, 64));
-    h.n = dd.n; h.k_cap = dd.kcap; h.k_fixed = kfixed; h.ldt = dd.ldt;
+    h.n = dd.n; h.k_cap = dd.kcap; h.k_fixed = kfixed; h.ldt = dd.ldt; h.tol = dd.tol;
     if (A[c].mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)dd.n * dd.n); h.lda = dd.n; }
     else { h.A = A[c].data; h.lda = A[c].ld; }
     h.gpart = x.gpart;
@@ -800,6 +859,7 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
     d[c].kcap = std::min(f[c].k_cap, d[c].l);
     d[c].ldt = rup(d[c].n, 4);
     d[c].ldb = rup(d[c].n, 64);
+    d[c].tol = f[c].tol > 0.0 ? f[c].tol : tol;
     sum_tiles += (int64_t)cdiv(d[c].l, 64) * cdiv(d[c].l, 64);
   }
   for (int c = 0; c < C; ++c) {
@@ -951,7 +1011,7 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
       const int c = idx[a];
       E[c] -= Ei[c];
       cols[c] += J.d[a].l;
-      if (E[c] <= tol * tol * fro2[c] || cols[c] >= ab[c].lmax) active[c] = 0;
+      if (E[c] <= d[c].tol * d[c].tol * fro2[c] || cols[c] >= ab[c].lmax) active[c] = 0;
     }
   }
   // final: SVD of B = W^T on the drawn columns, rank by tolerance, lift
@@ -1030,7 +1090,7 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
   for (int c = 0; c < C; ++c) {
     rsvd_status s = (rsvd_status)res[c].status;
     if (res[c].flags & FLAG_NONFINITE) s = RSVD_ERR_NONFINITE;
-    else if (E[c] > tol * tol * fro2[c] && s >= 0) s = RSVD_ERR_TOL_NOT_MET;
+    else if (E[c] > d[c].tol * d[c].tol * fro2[c] && s >= 0) s = RSVD_ERR_TOL_NOT_MET;
     f[c].k_out = cols[c] > 0 ? res[c].k_out : 0;
     f[c].l_used = cols[c];
     f[c].err_est = res[c].err_est;
@@ -1048,6 +1108,290 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
     }
   }
   CK(cudaStreamSynchronize(P->st));
+  if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
+  return worst;
+}
+
+
+// ------------------------------------------------------------ job plumbing
+void init_job(Job& J, rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f) {
+  J.P = P;
+  J.C = C;
+  J.A = A;
+  J.f = f;
+  J.mixed = P->o.precision == RSVD_PREC_BF16X;
+  J.q = P->o.q;
+  J.nsl = P->slices;
+  J.policy = P->o.rank_policy == RSVD_RANK_LEARNED ? RSVD_RANK_TOL : P->o.rank_policy;
+  J.tol = P->o.tol;
+}
+
+// Per-channel dims: l from lvec (else k + p, capped at n), s probe columns.
+void make_dims(Job& J, const std::vector<int>* lvec, std::vector<int>& warn, int probe_cols) {
+  const int C = J.C;
+  J.d.assign(C, ChanDims{});
+  warn.assign(C, 0);
+  J.max_l = J.max_lw = J.max_kcap = 0;
+  int64_t sum_gram_tiles = 0;
+  for (int c = 0; c < C; ++c) {
+    ChanDims& d = J.d[c];
+    d.n = (int)J.A[c].n;
+    int64_t l = lvec ? (*lvec)[c] : (int64_t)J.P->o.k + J.P->o.p;
+    if (l > d.n) { l = d.n; warn[c] = RSVD_WARN_RANK_CAPPED; }
+    d.l = (int)std::max<int64_t>(1, l);
+    d.s = probe_cols;
+    d.lw = d.l + d.s;
+    d.kcap = std::min(J.f[c].k_cap, d.l);
+    d.ldt = rup(d.n, 4);
+    d.ldb = rup(d.n, 64);
+    d.tol = J.f[c].tol > 0.0 ? J.f[c].tol : J.P->o.tol;
+    sum_gram_tiles += (int64_t)cdiv(d.l, 64) * cdiv(d.l, 64);
+    J.max_l = std::max(J.max_l, d.l);
+    J.max_lw = std::max(J.max_lw, d.lw);
+    J.max_kcap = std::max(J.max_kcap, d.kcap);
+  }
+  for (int c = 0; c < C; ++c) {
+    // rows per Gram split: ~512, more when the batch is too small to fill the GPU
+    ChanDims& d = J.d[c];
+    int g = cdiv(d.n, 512);
+    const int want = (int)((2 * NSM + sum_gram_tiles - 1) / std::max<int64_t>(1, sum_gram_tiles));
+    g = std::max(g, std::min(want, cdiv(d.n, 64)));
+    d.gsplit = std::max(1, std::min(g, 64));
+  }
+}
+
+enum JobKind { JOB_MAIN = 0, JOB_PROBE = 1 };
+
+// One layout pass + step building; base == nullptr only measures.  Returns
+// the bytes the job needs.
+struct ProbeOut { float* feat = nullptr; float* pred = nullptr; };
+rsvd_status build_job(Job& J, char* base, JobKind kind, bool skip_convert, size_t* need, ProbeOut* po) {
+  Bump b(base);
+  J.measure = base == nullptr;
+  layout(J, b);
+  float* d_feat = nullptr;
+  float* d_pred = nullptr;
+  if (kind == JOB_PROBE) {
+    d_feat = b.take<float>((size_t)J.C * 19);
+    d_pred = b.take<float>((size_t)J.C * 2);
+    if (po) { po->feat = d_feat; po->pred = d_pred; }
+  }
+  const size_t buf_bytes = (b.off + 4095) & ~(size_t)4095;
+  J.ar = Arena();
+  J.ar.dbase = base ? base + buf_bytes : nullptr;
+  J.steps.clear();
+  {
+    std::vector<Chan> tmp(J.ch);
+    J.d_ch = J.ar.put(tmp.data(), tmp.size(), 128);
+  }
+  if (kind == JOB_PROBE) {
+    if (rsvd_status s = build_probe(J, d_feat, J.P->o.mlp_weights, J.P->o.mlp_weights ? d_pred : nullptr)) return s;
+  } else if (J.mixed) {
+    if (rsvd_status s = build_mixed(J, skip_convert)) return s;
+  } else {
+    build_fp64(J);
+  }
+  *need = buf_bytes + J.ar.h.size() + 4096;
+  return RSVD_OK;
+}
+
+// Upload descriptors, stage host inputs (unless reused), run, read results.
+rsvd_status execute(Job& J, bool stage_inputs, std::vector<ChanResult>& res) {
+  rsvd_plan_s* P = J.P;
+  const int C = J.C;
+  if (rsvd_status s = grow_pinned(P, std::max(J.ar.h.size(), sizeof(ChanResult) * C) + 64)) return s;
+  CK(cudaMemsetAsync(J.d_res, 0, sizeof(ChanResult) * C, P->st));
+  memcpy(P->hp, J.ar.h.data(), J.ar.h.size());
+  CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
+  if (stage_inputs)
+    for (int c = 0; c < C; ++c)
+      if (J.A[c].mem == RSVD_MEM_HOST) {
+        const size_t row = (size_t)J.d[c].n * sizeof(double);
+        if (J.A[c].ld == J.d[c].n)
+          CK(cudaMemcpyAsync((void*)J.ch[c].A, J.A[c].data, row * J.d[c].n, cudaMemcpyHostToDevice, P->st));
+        else
+          CK(cudaMemcpy2DAsync((void*)J.ch[c].A, row, J.A[c].data, (size_t)J.A[c].ld * sizeof(double), row,
+                               J.d[c].n, cudaMemcpyHostToDevice, P->st));
+      }
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  for (auto& step : J.steps)
+    if (rsvd_status s = step()) return s;
+  CK(cudaGetLastError());
+  ChanResult* hres = (ChanResult*)P->hp;
+  CK(cudaMemcpyAsync(hres, J.d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost, P->st));
+  int* herr = (int*)(P->hp + ((sizeof(ChanResult) * C + 63) & ~(size_t)63));
+  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  res.assign(hres, hres + C);
+  for (auto& t : P->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
+    else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
+  }
+  P->pending.clear();
+  P->ev_next = 0;
+  if (getenv("RSVD_DEBUG"))
+    for (int c = 0; c < C; ++c)
+      fprintf(stderr, "rsvd: chan %d n %d l %d k %d flags %d sweeps %d err_est %.3e status %d\\n", c, J.d[c].n,
+              J.d[c].l, res[c].k_out, res[c].flags, res[c].sweeps, res[c].err_est, res[c].status);
+  if (*herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", *herr);
+  return RSVD_OK;
+}
+
+// Fill the caller's factor records (and host copies of U, S, V).
+rsvd_status collect(Job& J, const std::vector<ChanResult>& res, const std::vector<int>& warn, rsvd_factors* f,
+                    rsvd_status* per_item, rsvd_status* worst_out) {
+  rsvd_plan_s* P = J.P;
+  rsvd_status worst = RSVD_OK;
+  for (int c = 0; c < J.C; ++c) {
+    rsvd_status s = (rsvd_status)res[c].status;
+    if (s == RSVD_OK && warn[c]) s = (rsvd_status)warn[c];
+    f[c].k_out = res[c].k_out;
+    f[c].l_used = res[c].l_used;
+    f[c].err_est = res[c].err_est;
+    f[c].status = s;
+    if (per_item) per_item[c] = s;
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (worst >= 0 && s > worst) worst = s;
+    if (f[c].mem == RSVD_MEM_HOST && res[c].k_out > 0) {
+      const int k = res[c].k_out, n = J.d[c].n;
+      CK(cudaMemcpy2DAsync(f[c].U, f[c].ldu * sizeof(double), J.ch[c].U, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpy2DAsync(f[c].V, f[c].ldv * sizeof(double), J.ch[c].V, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpyAsync(f[c].S, J.ch[c].S, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    }
+  }
+  CK(cudaStreamSynchronize(P->st));
+  *worst_out = worst;
+  return RSVD_OK;
+}
+
+// Fixed l per channel (lvec, else k + p): FIXED and TOL policies.
+rsvd_status run_fixed_l(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item,
+                        const std::vector<int>* lvec, bool reuse_words) {
+  Job J;
+  init_job(J, P, C, A, f);
+  std::vector<int> warn;
+  make_dims(J, lvec, warn, J.mixed ? NPROBE : 0);
+  size_t need = 0;
+  if (rsvd_status s = build_job(J, nullptr, JOB_MAIN, reuse_words, &need, nullptr)) return s;
+  if (!reuse_words) {
+    if (rsvd_status s = grow_ws(P, need)) return s;
+  } else if (need > P->ws_cap) {
+    return seterr(RSVD_ERR_OOM, "workspace sized for the probe is too small");
+  }
+  if (rsvd_status s = build_job(J, P->ws, JOB_MAIN, reuse_words, &need, nullptr)) return s;
+  if (need > P->ws_cap) return seterr(RSVD_ERR_OOM, "workspace estimate exceeded");
+  std::vector<ChanResult> res;
+  if (rsvd_status s = execute(J, !reuse_words, res)) return s;
+  rsvd_status worst = RSVD_OK;
+  if (rsvd_status s = collect(J, res, warn, f, per_item, &worst)) return s;
+  if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
+  return worst;
+}
+
+// Probe features (and rank-model predictions when the plan has weights) of C
+// channels; sizes the workspace for a decomposition with up to lcap columns.
+rsvd_status run_probe(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, int lcap,
+                      std::vector<float>* feat, std::vector<float>* pred) {
+  Job Jp;
+  init_job(Jp, P, C, A, f);
+  std::vector<int> warn;
+  std::vector<int> l16(C, 16);
+  make_dims(Jp, &l16, warn, 0);
+  size_t need_p = 0, need_m = 0;
+  if (rsvd_status s = build_job(Jp, nullptr, JOB_PROBE, false, &need_p, nullptr)) return s;
+  {
+    Job Jm;
+    init_job(Jm, P, C, A, f);
+    std::vector<int> lc(C, lcap);
+    make_dims(Jm, &lc, warn, Jm.mixed ? NPROBE : 0);
+    if (rsvd_status s = build_job(Jm, nullptr, JOB_MAIN, true, &need_m, nullptr)) return s;
+  }
+  if (rsvd_status s = grow_ws(P, std::max(need_p, need_m))) return s;
+  ProbeOut po;
+  if (rsvd_status s = build_job(Jp, P->ws, JOB_PROBE, false, &need_p, &po)) return s;
+  std::vector<ChanResult> res;
+  if (rsvd_status s = execute(Jp, true, res)) return s;
+  if (feat) {
+    feat->resize((size_t)C * 19);
+    CK(cudaMemcpy(feat->data(), po.feat, sizeof(float) * C * 19, cudaMemcpyDeviceToHost));
+  }
+  if (pred) {
+    pred->resize((size_t)C * 2);
+    CK(cudaMemcpy(pred->data(), po.pred, sizeof(float) * C * 2, cudaMemcpyDeviceToHost));
+  }
+  for (int c = 0; c < C; ++c)
+    if (res[c].flags & FLAG_NONFINITE) return seterr(RSVD_ERR_NONFINITE, "channel %d has NaN/Inf entries", c);
+  return RSVD_OK;
+}
+
+// Learned rank: probe -> features -> network -> per-channel l, one fixed-l
+// decomposition (reusing the probe's V words); channels whose estimate misses
+// the tolerance get one retry at twice the columns, then the FP64 adaptive
+// loop -- the plain method stays both the fallback and the judge.
+rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item) {
+  if (!P->o.mlp_weights) return seterr(RSVD_ERR_INVALID_ARG, "learned rank needs mlp_weights");
+  const int lcap_opt = P->o.l_max > 0 ? P->o.l_max : 1024;
+  int lcap = 16;
+  for (int c = 0; c < C; ++c) lcap = std::max(lcap, (int)std::min<int64_t>(A[c].n, lcap_opt));
+  std::vector<float> pred;
+  if (rsvd_status s = run_probe(P, C, A, f, lcap, nullptr, &pred)) return s;
+  std::vector<int> lvec(C);
+  for (int c = 0; c < C; ++c) {
+    const double k = std::exp((double)pred[2 * c]), p = std::exp((double)pred[2 * c + 1]);
+    const int cap = (int)std::min<int64_t>(A[c].n, lcap_opt);
+    int l = (int)rup((int64_t)std::ceil(k + std::max(p, 1.0)), 16);
+    lvec[c] = std::max(16, std::min(l, cap));
+  }
+  std::vector<rsvd_status> st(C, RSVD_OK);
+  rsvd_status r = run_fixed_l(P, C, A, f, st.data(), &lvec, true);
+  if (r < 0 && r != RSVD_ERR_TOL_NOT_MET && r != RSVD_ERR_NOT_CONVERGED) return r;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    std::vector<int> idx;
+    for (int c = 0; c < C; ++c)
+      if (st[c] == RSVD_ERR_TOL_NOT_MET) idx.push_back(c);
+    if (idx.empty()) break;
+    std::vector<rsvd_matrix> As(idx.size());
+    std::vector<rsvd_factors> fs(idx.size());
+    std::vector<int> ls(idx.size());
+    for (size_t i = 0; i < idx.size(); ++i) {
+      As[i] = A[idx[i]];
+      fs[i] = f[idx[i]];
+      ls[i] = std::min<int>((int)std::min<int64_t>(A[idx[i]].n, lcap_opt), 2 * lvec[idx[i]]);
+      lvec[idx[i]] = ls[i];
+    }
+    std::vector<rsvd_status> sts(idx.size());
+    if (attempt == 0) {
+      r = run_fixed_l(P, (int)idx.size(), As.data(), fs.data(), sts.data(), &ls, false);
+    } else {
+      // the plain adaptive loop in FP64 (a temporary plan sharing the stream)
+      rsvd_plan_s Q;
+      Q.o = P->o;
+      Q.o.precision = RSVD_PREC_FP64;
+      Q.o.rank_policy = RSVD_RANK_ADAPTIVE;
+      Q.st = P->st;
+      Q.d_err = P->d_err;
+      r = run_adaptive(&Q, (int)idx.size(), As.data(), fs.data(), sts.data());
+      if (Q.ws) cudaFree(Q.ws);
+      if (Q.hp) cudaFreeHost(Q.hp);
+      for (cudaEvent_t e : Q.ev_pool) cudaEventDestroy(e);
+    }
+    if (r < 0 && r != RSVD_ERR_TOL_NOT_MET && r != RSVD_ERR_NOT_CONVERGED) return r;
+    for (size_t i = 0; i < idx.size(); ++i) {
+      f[idx[i]] = fs[i];
+      st[idx[i]] = sts[i];
+    }
+  }
+  rsvd_status worst = RSVD_OK;
+  for (int c = 0; c < C; ++c) {
+    if (per_item) per_item[c] = st[c];
+    f[c].status = st[c];
+    if (st[c] < 0 && (worst >= 0 || st[c] < worst)) worst = st[c];
+    else if (worst >= 0 && st[c] > worst) worst = st[c];
+  }
   if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
   return worst;
 }
@@ -1078,8 +1422,6 @@ rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* o) {
   if (o->rank_policy == RSVD_RANK_TOL && o->k + o->p < 1)
     return seterr(RSVD_ERR_INVALID_ARG, "tolerance mode needs k + p >= 1 columns");
   if (o->slices < 0 || o->slices > 3) return seterr(RSVD_ERR_INVALID_ARG, "slices %d outside [0, 3]", o->slices);
-  if (o->rank_policy == RSVD_RANK_LEARNED)
-    return seterr(RSVD_ERR_UNSUPPORTED, "rank policy %d is not available in this build", o->rank_policy);
   if (o->rank_policy == RSVD_RANK_ADAPTIVE && o->precision != RSVD_PREC_FP64)
     return seterr(RSVD_ERR_UNSUPPORTED, "the adaptive loop is built for the FP64 path");
   if (o->block_b < 0 || o->l_max < 0) return seterr(RSVD_ERR_INVALID_ARG, "negative block_b or l_max");
@@ -1140,131 +1482,30 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t P, int32_t C, const rsvd_matrix* 
   g_err[0] = 0;
   if (rsvd_status s = validate(P, C, A, f)) return s;
   if (P->o.rank_policy == RSVD_RANK_ADAPTIVE) return run_adaptive(P, C, A, f, per_item);
-  Job J;
-  J.P = P;
-  J.C = C;
-  J.A = A;
-  J.f = f;
-  J.mixed = P->o.precision == RSVD_PREC_BF16X;
-  J.q = P->o.q;
-  J.nsl = P->slices;
-  J.policy = P->o.rank_policy;
-  J.tol = P->o.tol;
-  J.d.resize(C);
-  std::vector<int> warn(C, 0);
-  int64_t sum_gram_tiles = 0;
+  if (P->o.rank_policy == RSVD_RANK_LEARNED) return run_learned(P, C, A, f, per_item);
+  return run_fixed_l(P, C, A, f, per_item, nullptr, false);
+}
+
+rsvd_status rsvd_probe_features(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, const double* tol,
+                                float* features) {
+  g_err[0] = 0;
+  if (!features) return seterr(RSVD_ERR_INVALID_ARG, "features is NULL");
+  std::vector<rsvd_factors> f(C > 0 ? C : 1);
   for (int c = 0; c < C; ++c) {
-    ChanDims& d = J.d[c];
-    d.n = (int)A[c].n;
-    int64_t l = (int64_t)P->o.k + P->o.p;
-    if (l > d.n) { l = d.n; warn[c] = RSVD_WARN_RANK_CAPPED; }
-    d.l = (int)std::max<int64_t>(1, l);
-    d.s = J.mixed ? NPROBE : 0;
-    d.lw = d.l + d.s;
-    d.kcap = std::min(f[c].k_cap, d.l);
-    d.ldt = rup(d.n, 4);
-    d.ldb = rup(d.n, 64);
-    sum_gram_tiles += (int64_t)cdiv(d.l, 64) * cdiv(d.l, 64);
-    J.max_l = std::max(J.max_l, d.l);
-    J.max_lw = std::max(J.max_lw, d.lw);
-    J.max_kcap = std::max(J.max_kcap, d.kcap);
+    memset(&f[c], 0, sizeof(rsvd_factors));
+    f[c].k_cap = 16;
+    f[c].S = (double*)features;           // placeholder: validate() wants a non-null S
+    f[c].tol = tol ? tol[c] : 0.0;
   }
-  for (int c = 0; c < C; ++c) {
-    // rows per Gram split: ~512, more when the batch is too small to fill the GPU
-    ChanDims& d = J.d[c];
-    int g = cdiv(d.n, 512);
-    const int want = (int)((2 * NSM + sum_gram_tiles - 1) / std::max<int64_t>(1, sum_gram_tiles));
-    g = std::max(g, std::min(want, cdiv(d.n, 64)));
-    d.gsplit = std::max(1, std::min(g, 64));
-  }
-  // pass 1: measure (buffers + descriptors), grow, pass 2: real pointers
-  for (int pass = 0; pass < 2; ++pass) {
-    Bump b(pass == 0 ? nullptr : P->ws);
-    J.measure = pass == 0;
-    layout(J, b);
-    const size_t buf_bytes = (b.off + 4095) & ~(size_t)4095;
-    J.ar = Arena();
-    J.ar.dbase = pass == 0 ? nullptr : P->ws + buf_bytes;
-    J.steps.clear();
-    J.d_ch = nullptr;
-    // descriptors: the channel array first (its device address is needed by
-    // the step builders), then everything the builders add
-    {
-      std::vector<Chan> tmp(J.ch);
-      J.d_ch = J.ar.put(tmp.data(), tmp.size(), 128);
-    }
-    std::vector<ChanResult> r0(C);
-    memset(r0.data(), 0, sizeof(ChanResult) * C);
-    if (J.mixed) {
-      if (rsvd_status s = build_mixed(J)) return s;
-    } else {
-      build_fp64(J);
-    }
-    const size_t need = buf_bytes + J.ar.h.size() + 4096;
-    if (pass == 0) {
-      if (rsvd_status s = grow_ws(P, need)) return s;
-    } else {
-      if (need > P->ws_cap) return seterr(RSVD_ERR_OOM, "workspace estimate exceeded");
-      if (rsvd_status s = grow_pinned(P, std::max(J.ar.h.size(), sizeof(ChanResult) * C) + 64)) return s;
-      // results start zeroed
-      CK(cudaMemsetAsync(J.d_res, 0, sizeof(ChanResult) * C, P->st));
-      memcpy(P->hp, J.ar.h.data(), J.ar.h.size());
-      CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
-      for (int c = 0; c < C; ++c)
-        if (A[c].mem == RSVD_MEM_HOST)
-          CK(cudaMemcpy2DAsync((void*)J.ch[c].A, (size_t)J.d[c].n * sizeof(double), A[c].data,
-                               (size_t)A[c].ld * sizeof(double), (size_t)J.d[c].n * sizeof(double), J.d[c].n,
-                               cudaMemcpyHostToDevice, P->st));
-    }
-  }
-  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
-  for (auto& step : J.steps)
-    if (rsvd_status s = step()) return s;
-  CK(cudaGetLastError());
-  // read back the per-channel results and the device error word
-  ChanResult* hres = (ChanResult*)P->hp;
-  CK(cudaMemcpyAsync(hres, J.d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost, P->st));
-  int* herr = (int*)(P->hp + ((sizeof(ChanResult) * C + 63) & ~(size_t)63));
-  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
-  CK(cudaStreamSynchronize(P->st));
-  std::vector<ChanResult> res(hres, hres + C);
-  for (auto& t : P->pending) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, t.a, t.b);
-    if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
-    else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
-  }
-  P->pending.clear();
-  P->ev_next = 0;
-  if (getenv("RSVD_DEBUG"))
-    for (int c = 0; c < C; ++c)
-      fprintf(stderr, "rsvd: chan %d n %d l %d k %d flags %d sweeps %d err_est %.3e status %d\n", c, J.d[c].n,
-              J.d[c].l, res[c].k_out, res[c].flags, res[c].sweeps, res[c].err_est, res[c].status);
-  const int derr = *herr;
-  if (derr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", derr);
-  rsvd_status worst = RSVD_OK;
-  for (int c = 0; c < C; ++c) {
-    rsvd_status s = (rsvd_status)res[c].status;
-    if (s == RSVD_OK && warn[c]) s = (rsvd_status)warn[c];
-    f[c].k_out = res[c].k_out;
-    f[c].l_used = res[c].l_used;
-    f[c].err_est = res[c].err_est;
-    f[c].status = s;
-    if (per_item) per_item[c] = s;
-    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
-    else if (worst >= 0 && s > worst) worst = s;
-    if (f[c].mem == RSVD_MEM_HOST && res[c].k_out > 0) {
-      const int k = res[c].k_out, n = J.d[c].n;
-      CK(cudaMemcpy2DAsync(f[c].U, f[c].ldu * sizeof(double), J.ch[c].U, (size_t)n * sizeof(double),
-                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
-      CK(cudaMemcpy2DAsync(f[c].V, f[c].ldv * sizeof(double), J.ch[c].V, (size_t)n * sizeof(double),
-                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
-      CK(cudaMemcpyAsync(f[c].S, J.ch[c].S, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, P->st));
-    }
-  }
-  CK(cudaStreamSynchronize(P->st));
-  if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
-  return worst;
+  if (rsvd_status s = validate(P, C, A, f.data())) return s;
+  std::vector<float> feat;
+  const float* saved = P->o.mlp_weights;
+  P->o.mlp_weights = nullptr;
+  rsvd_status s = run_probe(P, C, A, f.data(), 16, &feat, nullptr);
+  P->o.mlp_weights = saved;
+  if (s) return s;
+  CK(cudaMemcpy(features, feat.data(), sizeof(float) * C * 19, cudaMemcpyHostToDevice));
+  return RSVD_OK;
 }
 
 rsvd_status rsvd_decompose(rsvd_plan_t P, const rsvd_matrix* A, rsvd_factors* f) {

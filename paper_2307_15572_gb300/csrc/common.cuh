@@ -152,6 +152,7 @@ enum : int { FLAG_SHIFTED = 1, FLAG_JACOBI_CAP = 2, FLAG_NONFINITE = 4, FLAG_CHO
 struct Chan {
   int n, l, k_cap, k_fixed;
   int col0;                 // first global column of the random matrix for this channel
+  double tol;               // this channel's tolerance (0: the plan's)
   int64_t lda;
   const double* A;          // FP64 input (device)
   int64_t ldt;              // leading dim of n x l buffers

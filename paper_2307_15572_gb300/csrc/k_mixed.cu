@@ -113,7 +113,7 @@ void launch_convert_slices(const Chan* d_ch, const int* d_off, int C, int tiles,
 __global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
                                                     const int* __restrict__ off, int C,
                                                     uint64_t seed, int col0, int j0, int j1,
-                                                    uint64_t pseed, int nsl) {
+                                                    uint64_t pseed, int nsl, uint32_t tag) {
   const int t = blockIdx.x;
   const int c = find_chan(off, C, t);
   const Chan& h = ch[c];
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
     if (rr >= rows) continue;
     const int i = r0 + rr;
     float g;
-    if (j < h.l) g = gauss_f32(seed, (uint32_t)i, (uint32_t)(col0 + h.col0 + j), TAG_OMEGA);
+    if (j < h.l) g = gauss_f32(seed, (uint32_t)i, (uint32_t)(col0 + h.col0 + j), tag);
     else g = gauss_f32(pseed, (uint32_t)i, (uint32_t)(j - h.l), TAG_RESID);
     const int64_t o = (int64_t)j * h.ldb + i;
     h.Xb[0][o] = __float2bfloat16_rn(g);
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
 }
 
 void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
-                       int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st) {
-  if (tiles > 0) { k_omega_bf16<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, j0, j1, pseed, nsl); note_launch(); }
+                       int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st, uint32_t tag) {
+  if (tiles > 0) { k_omega_bf16<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, j0, j1, pseed, nsl, tag); note_launch(); }
 }
 
 // est_part[0] = sum of the probe-residual tile partials (fro_part, one per

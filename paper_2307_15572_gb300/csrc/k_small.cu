@@ -84,7 +84,7 @@ void launch_fro2_reduce_rows(const Chan* d_ch, int C, int rows_per_part, cudaStr
 // ------------------------------------------------------------- Omega (FP64)
 __global__ void __launch_bounds__(256) k_omega_f64(const Chan* __restrict__ ch,
                                                    const int* __restrict__ off, int C,
-                                                   uint64_t seed, int col0) {
+                                                   uint64_t seed, int col0, uint32_t tag) {
   const int t = blockIdx.x;
   const int c = find_chan(off, C, t);
   const Chan& h = ch[c];
@@ -94,13 +94,13 @@ __global__ void __launch_bounds__(256) k_omega_f64(const Chan* __restrict__ ch,
     const int rr = e & 63, j = e >> 6;
     if (rr < rows)
       h.X[(r0 + rr) + (int64_t)j * h.ldt] =
-          gauss_f64(seed, (uint32_t)(r0 + rr), (uint32_t)(col0 + h.col0 + j), TAG_OMEGA);
+          gauss_f64(seed, (uint32_t)(r0 + rr), (uint32_t)(col0 + h.col0 + j), tag);
   }
 }
 
 void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
-                      int col0, cudaStream_t st) {
-  if (tiles > 0) { k_omega_f64<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0); note_launch(); }
+                      int col0, cudaStream_t st, uint32_t tag) {
+  if (tiles > 0) { k_omega_f64<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, tag); note_launch(); }
 }
 
 // ------------------------------------------------- Cholesky + inverse (FP64)
@@ -477,8 +477,9 @@ void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st
 // Probe form (mixed path): with G the probe block (s Gaussian columns),
 // C = Q^T V G, D = X^T C, ||(I - U_k U_k^T) V G||^2 = ||V G - Q C||^2 +
 // sum_{i>k} |D_i|^2, and E||(I-P)V G||_F^2 = s ||(I-P) V||_F^2.
-__global__ void k_select(const Chan* __restrict__ ch, int policy, double tol, int use_probe) {
+__global__ void k_select(const Chan* __restrict__ ch, int policy, double tol_plan, int use_probe) {
   const Chan& h = ch[blockIdx.x];
+  const double tol = h.tol > 0.0 ? h.tol : tol_plan;
   const int l = h.l;
   ChanResult* res = h.res;
   if (threadIdx.x != 0) return;
@@ -547,6 +548,32 @@ __global__ void k_select(const Chan* __restrict__ ch, int policy, double tol, in
 void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
                    cudaStream_t st) {
   k_select<<<C, 32, 0, st>>>(d_ch, policy, tol, use_probe);
+  note_launch();
+}
+
+// ------------------------------------------------------------ probe features
+// From the probe's singular values t (descending, h.sig[0..15]):
+// [log(t_j / t_1), j = 2..16 | log t_1 | 0.5 log(sum t^2 / 16) | log n | log tol]
+__global__ void k_features(const Chan* __restrict__ ch, double tol_plan, float* __restrict__ feat) {
+  const Chan& h = ch[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  const double tol = h.tol > 0.0 ? h.tol : tol_plan;
+  double t[16], s2 = 0.0;
+  for (int j = 0; j < 16; ++j) {
+    t[j] = j < h.l ? h.sig[j] : 0.0;
+    s2 += t[j] * t[j];
+    t[j] = fmax(t[j], 1e-300);
+  }
+  float* f = feat + (int64_t)blockIdx.x * 19;
+  for (int j = 1; j < 16; ++j) f[j - 1] = (float)log(t[j] / t[0]);
+  f[15] = (float)log(t[0]);
+  f[16] = (float)(0.5 * log(fmax(s2, 1e-300) / 16.0));
+  f[17] = (float)log((double)h.n);
+  f[18] = (float)log(tol);
+}
+
+void launch_features(const Chan* d_ch, int C, double tol, float* feat, cudaStream_t st) {
+  k_features<<<C, 32, 0, st>>>(d_ch, tol, feat);
   note_launch();
 }
 

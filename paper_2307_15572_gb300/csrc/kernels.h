@@ -60,7 +60,7 @@ void launch_fro2_reduce(const Chan* d_ch, int C, cudaStream_t st);
 void launch_fro2_reduce_rows(const Chan* d_ch, int C, int rows_per_part, cudaStream_t st);
 // Omega (FP64 form) into X[:, 0:l) of each channel, columns col0 + j.
 void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
-                      int col0, cudaStream_t st);
+                      int col0, cudaStream_t st, uint32_t tag = TAG_OMEGA);
 // Upper Cholesky G = R^T R (l x l), R^{-1}; R_acc <- R R_acc when accumulate.
 // Shifted retry on breakdown (flag FLAG_SHIFTED).
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
@@ -82,7 +82,10 @@ void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st);
 void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int tiles, int nsl,
                            cudaStream_t st);
 void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
-                       int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st);
+                       int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st,
+                       uint32_t tag = TAG_OMEGA);
+// 19 rank-model features per channel from its probe singular values (h.sig).
+void launch_features(const Chan* d_ch, int C, double tol, float* feat, cudaStream_t st);
 void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st);
 
 // ------------------------------------------------------------ exact residual

@@ -54,7 +54,8 @@ class Matrix(C.Structure):
 class Factors(C.Structure):
     _fields_ = [("mem", C.c_int32), ("U", C.c_void_p), ("ldu", C.c_int64), ("S", C.c_void_p),
                 ("V", C.c_void_p), ("ldv", C.c_int64), ("k_cap", C.c_int32), ("k_out", C.c_int32),
-                ("l_used", C.c_int32), ("err_est", C.c_double), ("status", C.c_int32)]
+                ("l_used", C.c_int32), ("err_est", C.c_double), ("status", C.c_int32),
+                ("tol", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -97,6 +98,18 @@ def load(build=True):
     lib.rsvd_plan_set_profiling.restype = C.c_int
     lib.rsvd_plan_profile.argtypes = [P, C.POINTER(Profile), C.c_int32]
     lib.rsvd_plan_profile.restype = C.c_int
+    lib.rsvd_mlp_param_count.argtypes = [C.c_int32]
+    lib.rsvd_mlp_param_count.restype = C.c_int64
+    lib.rsvd_mlp_work_floats.argtypes = [C.c_int32, C.c_int32]
+    lib.rsvd_mlp_work_floats.restype = C.c_int64
+    lib.rsvd_mlp_forward.argtypes = [P, C.c_int32, P, C.c_int32, P, P]
+    lib.rsvd_mlp_forward.restype = C.c_int
+    lib.rsvd_mlp_loss_grad.argtypes = [P, C.c_int32, P, P, C.c_int32, P, P, P, P]
+    lib.rsvd_mlp_loss_grad.restype = C.c_int
+    lib.rsvd_mlp_adam.argtypes = [P, P, P, P, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, P]
+    lib.rsvd_mlp_adam.restype = C.c_int
+    lib.rsvd_probe_features.argtypes = [P, C.c_int32, C.POINTER(Matrix), C.POINTER(C.c_double), P]
+    lib.rsvd_probe_features.restype = C.c_int
     lib.rsvd_reconstruct_error_noalloc.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int64, P, P, C.c_int64,
                                                    C.c_int32, P, P]
     lib.rsvd_reconstruct_error_noalloc.restype = C.c_int
@@ -157,6 +170,36 @@ def rsvd_plan_profile(h, reset=False):
 
 
 RSVD_NOALLOC_MAX_N = 16384
+MLP_FEATURES = 19
+MLP_HIDDEN = 128
+
+
+def rsvd_mlp_param_count(d=MLP_FEATURES):
+    return load().rsvd_mlp_param_count(d)
+
+
+def rsvd_mlp_work_floats(d, B):
+    return load().rsvd_mlp_work_floats(d, B)
+
+
+def rsvd_mlp_forward(theta, d, X, B, Y, stream=None):
+    return _check(load().rsvd_mlp_forward(theta, d, X, B, Y, stream))
+
+
+def rsvd_mlp_loss_grad(theta, d, X, T, B, grad, loss, work, stream=None):
+    return _check(load().rsvd_mlp_loss_grad(theta, d, X, T, B, grad, loss, work, stream))
+
+
+def rsvd_mlp_adam(theta, grad, m, v, nparams, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    return _check(load().rsvd_mlp_adam(theta, grad, m, v, nparams, t, lr, beta1, beta2, eps, stream))
+
+
+def rsvd_probe_features(h, mats, tols, features):
+    n = len(mats)
+    MA = (Matrix * n)(*mats)
+    TA = (C.c_double * n)(*tols)
+    return _check(load().rsvd_probe_features(h, n, MA, TA, features))
+
 
 
 def rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, stream=None):

@@ -205,6 +205,35 @@ def learn_channel_params(count=4000, seed=SEED_LEARN, nlo=500, nhi=20000):
     return out
 
 
+def mixed_decay_spectrum(n, a, tau, beta):
+    """sigma_i = a exp(-i / tau) + (1 - a) i^-beta, i = 1..n."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return a * np.exp(-i / tau) + (1.0 - a) * i ** (-beta)
+
+
+def learn_population(count, seed=SEED_LEARN, nlo=500, nhi=20000, tlo=1e-7, thi=1e-3):
+    """Channels for the rank model: sizes uniform in [nlo, nhi], spectra mixing
+    exponential and algebraic decay (a ~ U[0,1], tau ~ logU[5, 200],
+    beta ~ U[1.5, 4]), tolerances log-uniform in [tlo, thi]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(count):
+        out.append(dict(n=int(rng.integers(nlo, nhi + 1)), a=float(rng.uniform()),
+                        tau=math.exp(rng.uniform(math.log(5.0), math.log(200.0))),
+                        beta=float(rng.uniform(1.5, 4.0)),
+                        tol=math.exp(rng.uniform(math.log(tlo), math.log(thi))),
+                        seed=int(rng.integers(0, 2**62))))
+    return out
+
+
+def population_matrix(ch, device=None):
+    """Dense planted matrix of one population channel (Hartley-mixed U)."""
+    sig = mixed_decay_spectrum(ch["n"], ch["a"], ch["tau"], ch["beta"])
+    if device is None:
+        return planted_mixed(ch["n"], sig, ch["seed"])
+    return planted_mixed_torch(ch["n"], sig, ch["seed"], device=device)
+
+
 # paper-quoted facts used to size the synthetic channels ("Low-rank
 # interactions" paragraph): 15 x 15 momentum mesh, channel sizes 7650..40050.
 PAPER_MESH_POINTS = 15 * 15

@@ -67,8 +67,7 @@ def test_probe_sees_dominant_singular_value():
     u = rng.standard_normal(n); u /= np.linalg.norm(u)
     A = 5.0 * np.outer(u, u)
     t, fro2 = features.probe_singular_values(A, seed=1)
-    # Gram eigenvalues carry ~eps t_1^2 absolute error: null values come out ~sqrt(eps) t_1
-    assert t[1] <= 1e-6 * t[0]
+    assert t[1] <= 1e-12 * t[0]
     assert abs(t[0] - 5.0 * np.linalg.norm(u @ features.philox.gaussian_f64(np.arange(n), np.arange(16), 1, features.philox.TAG_PROBE))) < 1e-12 * t[0]
     f = features.features(t, fro2, n, 1e-4)
     assert f.shape == (features.D,)
