@@ -71,6 +71,15 @@ typedef enum {
   RSVD_RANK_ADAPTIVE = 2, /* blocks of block_b columns until tol is met (randQB_EI)      */
   RSVD_RANK_LEARNED = 3   /* per-channel l from the rank model, checked, adaptive fallback */
 } rsvd_rank_policy;
+/* ADAPTIVE stops a channel once its error indicator is under tol (or l_max
+ * columns are drawn).  FP64: the exact indicator ||V||^2 - sum ||B_i||^2.
+ * BF16X: that difference cancels at the passes' precision, so the indicator
+ * comes from 32 Gaussian probe columns g_j: the energies ||(I - Q Q^T) V g_j||^2,
+ * kept up to date block by block, whose mean estimates the squared error.
+ * A channel stops (and a rank is accepted, in TOL mode too) when an upper
+ * confidence bound (mean + 3.5 standard errors), plus the precision floor of
+ * the BF16 words and the FP32 factors, is under tol^2 ||V||_F^2.
+ * LEARNED falls back to ADAPTIVE in the plan's own precision. */
 
 typedef struct {
   int64_t n_max;        /* largest channel size the plan will be given (>= 1)            */

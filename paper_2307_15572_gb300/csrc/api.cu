@@ -18,11 +18,14 @@
 //     rank from the probe estimate; L = Q X_k, R_paper = W X_k Sigma_k^{-1}
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <functional>
 #include <string>
 #include <vector>
@@ -63,7 +66,7 @@ rsvd_status seterr(rsvd_status s, const char* fmt, ...) {
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-constexpr int NPROBE = 16;
+constexpr int NPROBE = 32;
 constexpr int NSM = 152;
 
 }  // namespace
@@ -151,6 +154,18 @@ void timed_begin(rsvd_plan_s* P, cudaEvent_t* a, cudaEvent_t* b) {
   cudaEventRecord(*a, P->st);
 }
 
+// Fold the timed launches of a finished (synchronised) job into the counters.
+void drain_profile(rsvd_plan_s* P) {
+  for (auto& t : P->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
+    else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
+  }
+  P->pending.clear();
+  P->ev_next = 0;
+}
+
 // Split a tile count over k so that the grid covers the GPU a couple of times.
 int pick_splits(int64_t tiles, int64_t k, int min_chunk) {
   if (tiles >= 2 * NSM) return 1;
@@ -230,28 +245,29 @@ void add_mm(Job& J, MMKind kind, std::vector<MMDesc> md) {
 }
 
 // Gram-like TN product with split partials and fixed-order reduction:
-// out_c (m x n, ld m) = A_c^T B_c over n_c rows.
-void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::function<const void*(int)> Bp,
-            std::function<double*(int)> outp, std::function<int(int)> mcols, std::function<int(int)> ncols,
-            bool sym) {
+// out_c (m x n, ld m) = A_c^T B_c over rows_c rows (leading dims ld_c).
+void add_tn_ex(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::function<const void*(int)> Bp,
+               std::function<double*(int)> outp, std::function<int(int)> mcols, std::function<int(int)> ncols,
+               bool sym, std::function<int(int)> rows, std::function<int64_t(int)> ld,
+               std::function<int(int)> splits, std::function<const int*(int)> cond = nullptr) {
   std::vector<MMDesc> md(J.C);
   std::vector<double*> outs(J.C);
   int max_elems = 1;
   for (int c = 0; c < J.C; ++c) {
-    const ChanDims& d = J.d[c];
+    const int nr = rows(c);
     MMDesc m{};
-    m.A = Ap(c); m.lda = d.ldt;
-    m.B = Bp(c); m.ldb = d.ldt;
-    m.m = mcols(c); m.n = ncols(c); m.k = d.n;
+    m.A = Ap(c); m.lda = ld(c);
+    m.B = Bp(c); m.ldb = ld(c);
+    m.m = mcols(c); m.n = ncols(c); m.k = nr;
     m.mt = cdiv(m.m, 64); m.nt = cdiv(m.n, 64);
-    m.ks = d.gsplit;
-    m.kchunk = (int)rup(cdiv(d.n, d.gsplit), 16);
-    m.ks = cdiv(d.n, m.kchunk);
+    m.kchunk = (int)rup(cdiv(nr, splits(c)), 16);
+    m.ks = cdiv(nr, m.kchunk);
     m.mode = MM_PARTIAL;
     m.sym = sym ? 1 : 0;
     m.Cm = J.ch[c].gpart;
     m.ldc = m.m;
     m.pstride = (int64_t)m.m * m.n;
+    m.cond = cond ? cond(c) : nullptr;
     md[c] = m;
     outs[c] = outp(c);
     max_elems = std::max(max_elems, m.m * m.n);
@@ -266,6 +282,15 @@ void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::functi
     launch_reduce_partials(dmd, douts, C, max_elems, st);
     return RSVD_OK;
   });
+}
+
+// The tall case: A_c, B_c are n_c x . panels with leading dim ldt_c, split in
+// gsplit_c row chunks.
+void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::function<const void*(int)> Bp,
+            std::function<double*(int)> outp, std::function<int(int)> mcols, std::function<int(int)> ncols,
+            bool sym) {
+  add_tn_ex(J, kind, Ap, Bp, outp, mcols, ncols, sym, [&](int c) { return J.d[c].n; },
+            [&](int c) { return J.d[c].ldt; }, [&](int c) { return J.d[c].gsplit; });
 }
 
 void add_chol(Job& J, int accumulate, int f32_chol = 0) {
@@ -419,35 +444,33 @@ void build_fp64(Job& J) {
 }
 
 // --------------------------------------------------------------- mixed path
-rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
-  // one grouped tcgen05 launch: Y32[:, 0:ncols) = sum words V_a X_b
+rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
+                       std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout) {
+  // one grouped tcgen05 launch: Y[:, 0:ncols) = sum words V_a X_b
   // tile width: all columns in one tile up to the kernel's register
   // accumulator width (160), else balanced column tiles
   int maxnc = 16;
-  for (int c = 0; c < J.C; ++c) maxnc = std::max(maxnc, ncols_of_pass ? J.d[c].lw : J.d[c].l);
+  for (int c = 0; c < J.C; ++c) maxnc = std::max(maxnc, ncols_of(c));
   const int ntile = cdiv(maxnc, 160);
   const int bn = (int)rup(cdiv(maxnc, ntile), 16);
   std::vector<TcChan> tcs(J.C);
   int64_t items0 = 0;
-  for (int c = 0; c < J.C; ++c) {
-    const int nc = ncols_of_pass ? J.d[c].lw : J.d[c].l;
-    items0 += (int64_t)cdiv(J.d[c].n, 128) * cdiv(nc, bn);
-  }
+  for (int c = 0; c < J.C; ++c) items0 += (int64_t)cdiv(J.d[c].n, 128) * cdiv(ncols_of(c), bn);
   bool any_split = false;
   std::vector<ZeroDesc> zd(J.C);
   int item = 0;
   for (int c = 0; c < J.C; ++c) {
     const ChanDims& d = J.d[c];
-    const int nc = ncols_of_pass ? d.lw : d.l;
+    const int nc = ncols_of(c);
     TcChan& t = tcs[c];
     memset(&t, 0, sizeof(t));
     const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
-    const __nv_bfloat16* X[3] = {J.ch[c].Xb[0], J.ch[c].Xb[1], J.ch[c].Xb[2]};
+    const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
     if (!J.measure) {
       const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, nc, bn);
       if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
     }
-    t.Y = J.ch[c].Y32;
+    t.Y = yout(c);
     t.ldy = d.ldt;
     t.n = d.n;
     t.ncols = nc;
@@ -461,7 +484,7 @@ rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
     any_split |= t.atomic != 0;
     t.item0 = item;
     item += t.mt * t.nt * t.ks;
-    zd[c] = ZeroDesc{J.ch[c].Y32, d.ldt, d.n, nc, 4};
+    zd[c] = ZeroDesc{t.Y, d.ldt, d.n, nc, 4};
   }
   const int items = item;
   if (any_split) {
@@ -485,7 +508,7 @@ rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
   for (int a = 0; a < sa; ++a)
     for (int x = 0; x < sx; ++x) npairs += (a + x < std::max(sa, sx));
   for (int c = 0; c < J.C; ++c) {
-    const double n = J.d[c].n, nc = ncols_of_pass ? J.d[c].lw : J.d[c].l;
+    const double n = J.d[c].n, nc = ncols_of(c);
     bytes += n * n * 2.0 * sa + n * nc * 2.0 * sx + n * nc * 4.0;
     flops += 2.0 * n * n * nc * npairs;
   }
@@ -502,6 +525,12 @@ rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
     return RSVD_OK;
   });
   return RSVD_OK;
+}
+
+rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
+  return tc_pass_ex(
+      J, sa, sx, [&](int c) { return ncols_of_pass ? J.d[c].lw : J.d[c].l; },
+      [&](int c, int w) { return (const __nv_bfloat16*)J.ch[c].Xb[w]; }, [&](int c) { return J.ch[c].Y32; });
 }
 
 // CholeskyQR2 of Y32[:, 0:l) -> Q32 (FP32) and its BF16 words in Xb[:, 0:l).
@@ -536,6 +565,95 @@ void cqr2_mixed(Job& J, int nsl_out) {
     }
     add_mm(J, MMK_NN_F32_F64B, md);
   }
+  // Conditional third round, only for channels whose Cholesky needed the
+  // shift: shifted CholeskyQR leaves Q orthonormal to about kappa(Y)^2 u only,
+  // and one more round restores it (shifted CholeskyQR3; Fukaya, Kannan,
+  // Nakatsukasa, Yamamoto and Yanagisawa, SIAM J. Sci. Comput. 42 (2020)).
+  // Other channels skip every launch of the round at its first instruction.
+  auto flags = [&](int c) {
+    return (const int*)((uintptr_t)ch[c].res + offsetof(ChanResult, flags));
+  };
+  add_tn_ex(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Q32; },
+            [&](int c) { return (const void*)ch[c].Q32; }, [&](int c) { return ch[c].G; },
+            [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true,
+            [&](int c) { return J.d[c].n; }, [&](int c) { return J.d[c].ldt; },
+            [&](int c) { return J.d[c].gsplit; }, flags);
+  {
+    const Chan* dch = J.d_ch;
+    const int C = J.C, maxl = J.max_l;
+    cudaStream_t st = J.P->st;
+    J.steps.push_back([=]() {
+      launch_chol_inv(dch, C, 0, maxl, 1, st, 0, 1);
+      return RSVD_OK;
+    });
+  }
+  std::vector<MMDesc> md(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc m{};
+    m.A = ch[c].Q32; m.lda = d.ldt;
+    m.B = ch[c].Ri; m.ldb = d.l;
+    m.Cm = ch[c].T32; m.ldc = d.ldt;
+    m.m = d.n; m.n = d.l; m.k = d.l;
+    m.ks = 1; m.kchunk = (int)rup(d.l, 16);
+    m.mode = MM_STORE;
+    for (int w = 0; w < nsl_out; ++w) m.sl[w] = ch[c].Xb[w];
+    m.ldsl = d.ldb;
+    m.nsl = nsl_out;
+    m.cond = flags(c);
+    md[c] = m;
+  }
+  add_mm(J, MMK_NN_F32_F64B, md);
+  {
+    const Chan* dch = J.d_ch;
+    const int C = J.C;
+    cudaStream_t st = J.P->st;
+    J.steps.push_back([=]() {
+      launch_copy_t_to_q_if_shifted(dch, C, st);
+      return RSVD_OK;
+    });
+  }
+}
+
+// FP64 CholeskyQR of the small SVD's left vectors X (l x l, in M).  The FP32
+// Jacobi stops once every pair is orthogonal to l eps_32 (relative), so at
+// large l or tight tolerances U = Q X is measurably not orthonormal and U U^T
+// is not a projector.  X = X~ R with R upper triangular keeps
+// span(X~_1..k) = span(X_1..k) for every k: the rank rule and the truncation
+// see the same nested subspaces, now orthonormal to FP64 rounding.  The
+// columns of X are already orthonormal to ~1e-4, so one round suffices and the
+// Cholesky never needs its shift.  X~ lands in J (free on the FP32 path);
+// the chain after it reads the returned table, whose M is that buffer.
+Chan* reorth_x(Job& J) {
+  std::vector<Chan> sw(J.ch);
+  for (auto& h : sw) h.M = h.J;                     // Cholesky works in (and X~ lands in) J
+  Chan* dsw = J.ar.put(sw.data(), sw.size(), 128);
+  auto& ch = J.ch;
+  add_tn_ex(J, MMK_GRAM_F64, [&](int c) { return (const void*)ch[c].M; }, [&](int c) { return (const void*)ch[c].M; },
+            [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true,
+            [&](int c) { return J.d[c].l; }, [&](int c) { return (int64_t)J.d[c].l; }, [&](int) { return 1; });
+  {
+    const int C = J.C, maxl = J.max_l;
+    cudaStream_t st = J.P->st;
+    J.steps.push_back([=]() {
+      launch_chol_inv(dsw, C, 0, maxl, 0, st, 0);
+      return RSVD_OK;
+    });
+  }
+  std::vector<MMDesc> md(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const int l = J.d[c].l;
+    MMDesc m{};
+    m.A = ch[c].M; m.lda = l;
+    m.B = ch[c].Ri; m.ldb = l;
+    m.Cm = ch[c].J; m.ldc = l;
+    m.m = l; m.n = l; m.k = l;
+    m.ks = 1; m.kchunk = (int)rup(l, 16);
+    m.mode = MM_STORE;
+    md[c] = m;
+  }
+  add_mm(J, MMK_NN_F64, md);
+  return dsw;
 }
 
 rsvd_status build_mixed(Job& J, bool skip_convert = false) {
@@ -569,22 +687,30 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
          [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
          [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
-  // probe residual ||V G - Q C||^2, one partial per 128-row tile
+  // probe residual R = V G - Q C in place of V G, then its column energies
   {
     std::vector<MMDesc> md(J.C);
+    std::vector<SumsqDesc> sd(J.C);
     for (int c = 0; c < J.C; ++c) {
       const ChanDims& d = J.d[c];
+      float* VG = ch[c].Y32 + (int64_t)d.l * d.ldt;
       MMDesc m{};
       m.A = ch[c].Q32; m.lda = d.ldt;
       m.B = ch[c].C64; m.ldb = d.l;
-      m.Cm = ch[c].Y32 + (int64_t)d.l * d.ldt; m.ldc = d.ldt;     // V G block
+      m.Cm = VG; m.ldc = d.ldt;
       m.m = d.n; m.n = d.s; m.k = d.l;
       m.ks = 1; m.kchunk = (int)rup(d.l, 16);
-      m.mode = MM_RESID;
-      m.rpart = ch[c].fro_part;
+      m.mode = MM_SUB;
       md[c] = m;
+      sd[c] = SumsqDesc{VG, d.ldt, d.n, d.s, 4, ch[c].est_part};
     }
-    add_mm(J, MMK_RESID_F32, md);
+    add_mm(J, MMK_NN_F32_F64B, md);
+    const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
+    const int s_max = NPROBE;
+    J.steps.push_back([=]() {
+      launch_colsumsq(dsd, C, s_max, st);
+      return RSVD_OK;
+    });
   }
   const int maxl = J.max_l;
   // W^T W = R^T R
@@ -595,13 +721,17 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   const double tol = J.tol;
   J.steps.push_back([=]() {
     launch_jacobi(dch, C, 1, maxl, st);
-    launch_probe_finish(dch, C, maxl, st);
-    launch_select(dch, C, policy, tol, 1, st);
     return RSVD_OK;
   });
-  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Q32; }, [&](int c) { return (const double*)ch[c].M; },
+  const Chan* dsw = reorth_x(J);                 // X~ in J
+  J.steps.push_back([=]() {
+    launch_probe_finish(dsw, C, maxl, st);
+    launch_select(dsw, C, policy, tol, 1, st);
+    return RSVD_OK;
+  });
+  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Q32; }, [&](int c) { return (const double*)ch[c].J; },
        [&](int c) { return ch[c].U; }, [&](int c) { return ch[c].ldu; }, [&](int c) { return (const double*)nullptr; });
-  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const double*)ch[c].M; },
+  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const double*)ch[c].J; },
        [&](int c) { return ch[c].V; }, [&](int c) { return ch[c].ldv; }, [&](int c) { return (const double*)ch[c].scr; });
   const int maxk = J.max_kcap;
   J.steps.push_back([=]() {
@@ -674,8 +804,10 @@ void layout(Job& J, Bump& b) {
     const rsvd_matrix& A = J.A[c];
     if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
     else { h.A = A.data; h.lda = A.ld; }
-    if (J.mixed)
+    if (J.mixed) {
       for (int s = 0; s < J.nsl; ++s) h.Ab[s] = b.take<__nv_bfloat16>((size_t)d.n * d.ldb);
+      h.wres_part = b.take<double>(cdiv(d.n, 8));
+    }
     h.fro_part = b.take<double>(cdiv(d.n, 8));
   }
   J.d_res = b.take<ChanResult>(J.C);
@@ -703,7 +835,7 @@ void layout(Job& J, Bump& b) {
       h.T32 = b.take<float>((size_t)d.ldt * d.l);
       h.gpart = b.take<double>((size_t)d.gsplit * d.l * std::max(d.l, d.s));
       h.C64 = b.take<double>((size_t)d.l * std::max(d.s, 1));
-      h.est_part = b.take<double>(1 + d.l);
+      h.est_part = b.take<double>((size_t)std::max(d.s, 1) * (1 + d.l));
     }
     if (F.mem == RSVD_MEM_HOST) {
       h.U = b.take<double>((size_t)d.n * d.kcap); h.ldu = d.n;
@@ -820,6 +952,7 @@ rsvd_status run_job(Job& J) {
     if (rsvd_status s = step()) return s;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(P->st));
+  drain_profile(P);
   return RSVD_OK;
 }
 
@@ -843,9 +976,11 @@ void project_out(Job& J, std::function<const double*(int)> Q, std::function<int(
   add_mm(J, MMK_NN_F64, md);
 }
 
+rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f,
+                               rsvd_status* per_item);
+
 rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item) {
-  if (P->o.precision != RSVD_PREC_FP64)
-    return seterr(RSVD_ERR_UNSUPPORTED, "the adaptive loop is built for the FP64 path");
+  if (P->o.precision != RSVD_PREC_FP64) return run_adaptive_mixed(P, C, A, f, per_item);
   const int bsz = P->o.block_b > 0 ? P->o.block_b : 32;
   const int lcap = P->o.l_max > 0 ? P->o.l_max : 1024;
   const double tol = P->o.tol;
@@ -1113,6 +1248,471 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
 }
 
 
+// ------------------------------------------------------ adaptive loop (mixed)
+// The same randQB_EI blocks on the tensor-core path: V words converted once;
+// each block's sketch / power / projection is a tcgen05 pass over the words;
+// Gram-Schmidt against earlier blocks by FP32 tile products; orthonormality by
+// the mixed CholeskyQR2.  The error indicator cannot use ||V||^2 - ||B||^2
+// (it cancels at FP32-accurate projections), so 16 probe columns G ride along
+// the first block's sketch and R_G = (I - Q Q^T) V G is updated block by block:
+// E ~ ||R_G||^2 / 16.  Stop once E <= (tol / 1.1)^2 ||V||^2 (the probe rank
+// rule's margin) or l_max columns.
+void project_out_f32(Job& J, std::function<const float*(int)> Q, std::function<int(int)> m,
+                     std::function<float*(int)> Y, std::function<int(int)> ncols,
+                     std::function<double*(int)> Cb) {
+  add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)Q(c); }, [&](int c) { return (const void*)Y(c); },
+         Cb, m, ncols, false);
+  std::vector<MMDesc> md(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc mm{};
+    mm.A = Q(c); mm.lda = d.ldt;
+    mm.B = Cb(c); mm.ldb = std::max(1, m(c));
+    mm.Cm = Y(c); mm.ldc = d.ldt;
+    mm.m = d.n; mm.n = ncols(c); mm.k = m(c);
+    mm.ks = 1; mm.kchunk = (int)rup(std::max(1, m(c)), 16);
+    mm.mode = MM_SUB;
+    md[c] = mm;
+  }
+  add_mm(J, MMK_NN_F32_F64B, md);
+}
+
+struct AdaptBufsM {
+  float *Q32, *W32, *Yb32, *T32, *AG, *RG;
+  __nv_bfloat16 *Qw[3], *Xo;
+  double *Cb, *E;
+  double *Gs, *Rs, *Ris, *Ms, *Js, *sigs, *scrs;
+  double *Gf, *Rf, *Rif, *Mf, *Jf, *sigf, *scrf, *C64f, *est;
+  double *gpart;
+  int lmax;
+};
+
+void lay_adapt_mixed(Bump& b, const std::vector<ChanDims>& d, int bsz, int nsl, std::vector<AdaptBufsM>& ab,
+                     std::vector<Chan>& base, const rsvd_matrix* A, rsvd_factors* f, int kfixed) {
+  const int C = (int)d.size();
+  ab.assign(C, AdaptBufsM{});
+  base.assign(C, Chan{});
+  for (int c = 0; c < C; ++c) {          // rank-independent prefix: staged input, words, partials
+    Chan& h = base[c];
+    if (A[c].mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d[c].n * d[c].n); h.lda = d[c].n; }
+    else { h.A = A[c].data; h.lda = A[c].ld; }
+    for (int w = 0; w < nsl; ++w) h.Ab[w] = b.take<__nv_bfloat16>((size_t)d[c].n * d[c].ldb);
+    h.fro_part = b.take<double>(cdiv(d[c].n, 8));
+    h.wres_part = b.take<double>(cdiv(d[c].n, 8));
+  }
+  for (int c = 0; c < C; ++c) {
+    const ChanDims& dd = d[c];
+    AdaptBufsM& x = ab[c];
+    Chan& h = base[c];
+    x.lmax = dd.l;
+    const int64_t T = dd.ldt;
+    x.Q32 = b.take<float>(T * x.lmax);
+    x.W32 = b.take<float>(T * x.lmax);
+    for (int w = 0; w < nsl; ++w) x.Qw[w] = b.take<__nv_bfloat16>((size_t)x.lmax * dd.ldb);
+    x.Xo = b.take<__nv_bfloat16>((size_t)(bsz + NPROBE) * dd.ldb);
+    x.Yb32 = b.take<float>(T * (bsz + NPROBE));
+    x.T32 = b.take<float>(T * bsz);
+    x.AG = b.take<float>(T * NPROBE);
+    x.RG = b.take<float>(T * NPROBE);
+    x.Cb = b.take<double>((size_t)x.lmax * std::max(bsz, NPROBE));
+    x.E = b.take<double>(NPROBE);
+    const size_t sb = (size_t)bsz * (bsz + 32);
+    x.Gs = b.take<double>(sb); x.Rs = b.take<double>(sb); x.Ris = b.take<double>(sb);
+    x.Ms = b.take<double>(sb); x.Js = b.take<double>(sb);
+    x.sigs = b.take<double>(bsz); x.scrs = b.take<double>(bsz);
+    const size_t sf = (size_t)x.lmax * (x.lmax + 32);
+    x.Gf = b.take<double>(sf); x.Rf = b.take<double>(sf); x.Rif = b.take<double>(sf);
+    x.Mf = b.take<double>(sf); x.Jf = b.take<double>(sf);
+    x.sigf = b.take<double>(x.lmax); x.scrf = b.take<double>(x.lmax);
+    x.C64f = b.take<double>((size_t)x.lmax * NPROBE);
+    x.est = b.take<double>((size_t)NPROBE * (1 + x.lmax));
+    x.gpart = b.take<double>((size_t)dd.gsplit * x.lmax * std::max(x.lmax, std::max(bsz, NPROBE)));
+    h.n = dd.n; h.k_cap = dd.kcap; h.k_fixed = kfixed; h.ldt = dd.ldt; h.ldb = dd.ldb; h.tol = dd.tol;
+    h.nprobe = NPROBE;
+    h.gpart = x.gpart;
+    const rsvd_factors& F = f[c];
+    if (F.mem == RSVD_MEM_HOST) {
+      h.U = b.take<double>((size_t)dd.n * dd.kcap); h.ldu = dd.n;
+      h.V = b.take<double>((size_t)dd.n * dd.kcap); h.ldv = dd.n;
+      h.S = b.take<double>(dd.kcap);
+    } else {
+      h.U = F.U; h.ldu = F.ldu; h.V = F.V; h.ldv = F.ldv; h.S = F.S;
+      if (!h.U) { h.U = b.take<double>((size_t)dd.n * dd.kcap); h.ldu = dd.n; }
+      if (!h.V) { h.V = b.take<double>((size_t)dd.n * dd.kcap); h.ldv = dd.n; }
+    }
+  }
+}
+
+rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f,
+                               rsvd_status* per_item) {
+  const int bsz = P->o.block_b > 0 ? P->o.block_b : 32;
+  const int lcap = P->o.l_max > 0 ? P->o.l_max : 1024;
+  const int q = P->o.q;
+  const int nsl = P->slices;
+  const double stop_margin = 0.98;
+  std::vector<ChanDims> d(C);
+  int64_t sum_tiles = 0;
+  for (int c = 0; c < C; ++c) {
+    d[c].n = (int)A[c].n;
+    d[c].l = std::min(d[c].n, lcap);
+    d[c].s = NPROBE; d[c].lw = d[c].l + NPROBE;
+    d[c].kcap = std::min(f[c].k_cap, d[c].l);
+    d[c].ldt = rup(d[c].n, 4);
+    d[c].ldb = rup(d[c].n, 64);
+    d[c].tol = f[c].tol > 0.0 ? f[c].tol : P->o.tol;
+    sum_tiles += (int64_t)cdiv(d[c].l, 64) * cdiv(d[c].l, 64);
+  }
+  for (int c = 0; c < C; ++c) {
+    int g = cdiv(d[c].n, 512);
+    const int want = (int)((2 * NSM + sum_tiles - 1) / std::max<int64_t>(1, sum_tiles));
+    g = std::max(g, std::min(want, cdiv(d[c].n, 64)));
+    d[c].gsplit = std::max(1, std::min(g, 64));
+  }
+  std::vector<AdaptBufsM> ab;
+  std::vector<Chan> base;
+  size_t buf_bytes = 0;
+  {
+    Bump b(nullptr);
+    lay_adapt_mixed(b, d, bsz, nsl, ab, base, A, f, P->o.k);
+    b.take<ChanResult>(C);
+    buf_bytes = (b.off + 4095) & ~(size_t)4095;
+  }
+  const size_t arena_bytes = ((size_t)1 << 20) + (size_t)C * 96 * 1024;
+  if (rsvd_status s = grow_ws(P, buf_bytes + arena_bytes)) return s;
+  Bump b(P->ws);
+  lay_adapt_mixed(b, d, bsz, nsl, ab, base, A, f, P->o.k);
+  ChanResult* d_res = b.take<ChanResult>(C);
+  char* arena_dev = P->ws + buf_bytes;
+  for (int c = 0; c < C; ++c) base[c].res = d_res + c;
+  CK(cudaMemsetAsync(d_res, 0, sizeof(ChanResult) * C, P->st));
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  for (int c = 0; c < C; ++c)
+    if (A[c].mem == RSVD_MEM_HOST)
+      CK(cudaMemcpy2DAsync((void*)base[c].A, (size_t)d[c].n * sizeof(double), A[c].data,
+                           (size_t)A[c].ld * sizeof(double), (size_t)d[c].n * sizeof(double), d[c].n,
+                           cudaMemcpyHostToDevice, P->st));
+  auto new_job = [&](int Cj) {
+    Job J;
+    J.P = P; J.C = Cj; J.A = A; J.f = f; J.mixed = true; J.measure = false; J.nsl = nsl; J.q = q;
+    J.tol = P->o.tol;
+    J.ar.dbase = arena_dev;
+    J.d.resize(Cj);
+    J.ch.resize(Cj);
+    return J;
+  };
+  // words + ||V||^2
+  std::vector<double> fro2(C, 0.0), wres2(C, 0.0);
+  {
+    Job J = new_job(C);
+    J.d = d;
+    J.ch = base;
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    const int* off8 = offsets(J, [&](int c) { return (int64_t)cdiv(d[c].n, 8); });
+    const int t8 = total_of(J, [&](int c) { return (int64_t)cdiv(d[c].n, 8); });
+    const Chan* dch = J.d_ch;
+    cudaStream_t st = P->st;
+    J.steps.push_back([=]() {
+      launch_convert_slices(dch, off8, C, t8, nsl, st);
+      launch_fro2_reduce_rows(dch, C, 8, st);
+      return RSVD_OK;
+    });
+    if (rsvd_status s = run_job(J)) return s;
+    std::vector<ChanResult> r(C);
+    CK(cudaMemcpy(r.data(), d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < C; ++c) {
+      fro2[c] = r[c].fro2;
+      wres2[c] = r[c].wres2;
+      if (r[c].flags & FLAG_NONFINITE) f[c].status = RSVD_ERR_NONFINITE;
+    }
+  }
+  std::vector<int> cols(C, 0);
+  std::vector<char> active(C, 1);
+  for (int c = 0; c < C; ++c)
+    if (f[c].status == RSVD_ERR_NONFINITE) active[c] = 0;
+  const uint64_t seed = P->o.seed;
+  const uint64_t pseed = seed ^ 0x5DEECE66DULL;
+  std::vector<double> Ei((size_t)C * NPROBE);
+  const bool dbg = getenv("RSVD_DEBUG") != nullptr;
+  while (true) {
+    std::vector<int> idx;
+    for (int c = 0; c < C; ++c)
+      if (active[c]) idx.push_back(c);
+    if (idx.empty()) break;
+    const int Ca = (int)idx.size();
+    Job J = new_job(Ca);
+    bool first = true;
+    for (int a = 0; a < Ca; ++a) {
+      const int c = idx[a];
+      ChanDims dd = d[c];
+      dd.l = std::min(bsz, ab[c].lmax - cols[c]);
+      dd.kcap = dd.l;
+      J.d[a] = dd;
+      first &= cols[c] == 0;
+    }
+    J.max_l = bsz;
+    auto cb = [&](int a) { return ab[idx[a]]; };
+    auto bb = [&](int a) { return J.d[a].l; };
+    // role tables: omega into Xo; CQR2 of the sketch block into Q_i; CQR2 of Q_i in place
+    std::vector<Chan> chO(Ca), chA(Ca), chB(Ca);
+    for (int a = 0; a < Ca; ++a) {
+      const int c = idx[a];
+      const AdaptBufsM& x = ab[c];
+      Chan h = base[c];
+      h.l = J.d[a].l;
+      h.col0 = cols[c];
+      h.G = x.Gs; h.R = x.Rs; h.Ri = x.Ris; h.M = x.Ms; h.J = x.Js; h.sig = x.sigs; h.scr = x.scrs;
+      h.T32 = x.T32;
+      h.Q32 = x.Q32 + (int64_t)cols[c] * d[c].ldt;
+      for (int w = 0; w < nsl; ++w) h.Xb[w] = x.Qw[w] + (int64_t)cols[c] * d[c].ldb;
+      Chan o = h;
+      o.lw = h.l + (first ? NPROBE : 0);
+      o.Xb[0] = x.Xo;
+      chO[a] = o;
+      h.Y32 = x.Yb32;
+      chA[a] = h;
+      h.Y32 = h.Q32;
+      chB[a] = h;
+    }
+    Chan* dO = J.ar.put(chO.data(), chO.size(), 128);
+    Chan* dA = J.ar.put(chA.data(), chA.size(), 128);
+    Chan* dB = J.ar.put(chB.data(), chB.size(), 128);
+    J.ch = chA;
+    J.d_ch = dA;
+    const int* off64 = offsets(J, [&](int a) { return (int64_t)cdiv(J.d[a].n, 64); });
+    const int t64 = total_of(J, [&](int a) { return (int64_t)cdiv(J.d[a].n, 64); });
+    {
+      cudaStream_t st = P->st;
+      J.steps.push_back([=]() {
+        launch_omega_bf16(dO, off64, Ca, t64, seed, 0, 0, 1 << 30, pseed, 1, st);
+        return RSVD_OK;
+      });
+    }
+    auto Qb = [&](int a) { return cb(a).Q32 + (int64_t)cols[idx[a]] * J.d[a].ldt; };
+    auto Qprev = [&](int a) { return (const float*)cb(a).Q32; };
+    auto mprev = [&](int a) { return cols[idx[a]]; };
+    auto Cbuf = [&](int a) { return cb(a).Cb; };
+    auto Yb = [&](int a) { return cb(a).Yb32; };
+    auto qword = [&](int a, int w) { return (const __nv_bfloat16*)(w < nsl ? cb(a).Qw[w] + (int64_t)cols[idx[a]] * J.d[a].ldb : nullptr); };
+    // sketch (+ probe columns in the first block)
+    if (rsvd_status s = tc_pass_ex(J, nsl, 1, [&](int a) { return bb(a) + (first ? NPROBE : 0); },
+                                   [&](int a, int w) { return (const __nv_bfloat16*)(w == 0 ? cb(a).Xo : nullptr); },
+                                   Yb)) return s;
+    if (first) {
+      std::vector<float*> src(Ca), ag(Ca), rg(Ca);
+      std::vector<int64_t> ldt(Ca);
+      std::vector<int> nrow(Ca);
+      for (int a = 0; a < Ca; ++a) {
+        src[a] = cb(a).Yb32 + (int64_t)bb(a) * J.d[a].ldt;
+        ag[a] = cb(a).AG; rg[a] = cb(a).RG; ldt[a] = J.d[a].ldt; nrow[a] = J.d[a].n;
+      }
+      cudaStream_t st = P->st;
+      J.steps.push_back([=]() {
+        for (int a = 0; a < Ca; ++a) {
+          const size_t w = (size_t)nrow[a] * sizeof(float), pitch = (size_t)ldt[a] * sizeof(float);
+          if (cudaMemcpy2DAsync(ag[a], pitch, src[a], pitch, w, NPROBE, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+              cudaMemcpy2DAsync(rg[a], pitch, src[a], pitch, w, NPROBE, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return seterr(RSVD_ERR_CUDA, "probe copy failed");
+        }
+        return RSVD_OK;
+      });
+    } else {
+      project_out_f32(J, Qprev, mprev, Yb, bb, Cbuf);
+      project_out_f32(J, Qprev, mprev, Yb, bb, Cbuf);
+    }
+    cqr2_mixed(J, nsl);                                     // Q_i (FP32 + words)
+    for (int r = 0; r < q; ++r) {
+      if (rsvd_status s = tc_pass_ex(J, nsl, nsl, bb, qword, Yb)) return s;
+      cqr2_mixed(J, nsl);
+      if (rsvd_status s = tc_pass_ex(J, nsl, nsl, bb, qword, Yb)) return s;
+      if (!first) {
+        project_out_f32(J, Qprev, mprev, Yb, bb, Cbuf);
+        project_out_f32(J, Qprev, mprev, Yb, bb, Cbuf);
+      }
+      cqr2_mixed(J, nsl);
+    }
+    if (!first) {
+      project_out_f32(J, Qprev, mprev, Qb, bb, Cbuf);
+      project_out_f32(J, Qprev, mprev, Qb, bb, Cbuf);
+      J.ch = chB;
+      J.d_ch = dB;
+      cqr2_mixed(J, nsl);
+      J.ch = chA;
+      J.d_ch = dA;
+    }
+    // W_i = V Q_i
+    if (rsvd_status s = tc_pass_ex(J, nsl, nsl, bb, qword,
+                                   [&](int a) { return cb(a).W32 + (int64_t)cols[idx[a]] * J.d[a].ldt; })) return s;
+    // R_G <- (I - Q_i Q_i^T) R_G; E_i = ||R_G||^2
+    project_out_f32(J, [&](int a) { return (const float*)Qb(a); }, bb, [&](int a) { return cb(a).RG; },
+                    [&](int) { return NPROBE; }, Cbuf);
+    {
+      std::vector<SumsqDesc> sd(Ca);
+      for (int a = 0; a < Ca; ++a) sd[a] = SumsqDesc{cb(a).RG, J.d[a].ldt, J.d[a].n, NPROBE, 4, cb(a).E};
+      const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
+      cudaStream_t st = P->st;
+      J.steps.push_back([=]() {
+        launch_colsumsq(dsd, Ca, NPROBE, st);
+        return RSVD_OK;
+      });
+    }
+    if (J.ar.h.size() > arena_bytes) return seterr(RSVD_ERR_OOM, "descriptor region too small");
+    if (rsvd_status s = run_job(J)) return s;
+    for (int a = 0; a < Ca; ++a)
+      CK(cudaMemcpyAsync(&Ei[(size_t)idx[a] * NPROBE], ab[idx[a]].E, NPROBE * sizeof(double), cudaMemcpyDeviceToHost,
+                         P->st));
+    CK(cudaStreamSynchronize(P->st));
+    for (int a = 0; a < Ca; ++a) {
+      const int c = idx[a];
+      cols[c] += J.d[a].l;
+      // the rank rule's bound over the probe columns (see k_select), with a
+      // small extra margin so that the final selection agrees with the stop
+      const double* e = &Ei[(size_t)c * NPROBE];
+      double mean = 0.0, var = 0.0;
+      for (int j = 0; j < NPROBE; ++j) mean += e[j];
+      mean /= NPROBE;
+      for (int j = 0; j < NPROBE; ++j) var += (e[j] - mean) * (e[j] - mean);
+      var /= NPROBE - 1;
+      const double floor2 = precision_floor2(wres2[c], cols[c], fro2[c]);
+      mean += floor2;
+      const double ucb = mean + PROBE_Z * std::sqrt(var / NPROBE);
+      if (ucb <= stop_margin * d[c].tol * d[c].tol * fro2[c] || cols[c] >= ab[c].lmax) active[c] = 0;
+      if (dbg) fprintf(stderr, "rsvd adaptive: chan %d cols %d est %.3e bound %.3e tol %.3e\n", c, cols[c],
+                       std::sqrt(mean / std::max(fro2[c], 1e-300)), std::sqrt(ucb / std::max(fro2[c], 1e-300)),
+                       d[c].tol);
+    }
+  }
+  // final: probe estimate per rank, SVD of B = W^T, rank, lift
+  std::vector<int> idx;
+  for (int c = 0; c < C; ++c)
+    if (cols[c] > 0) idx.push_back(c);
+  const int Cf = (int)idx.size();
+  if (Cf > 0) {
+    Job J = new_job(Cf);
+    J.policy = RSVD_RANK_TOL;
+    for (int a = 0; a < Cf; ++a) {
+      const int c = idx[a];
+      const AdaptBufsM& x = ab[c];
+      ChanDims dd = d[c];
+      dd.l = cols[c];
+      dd.lw = dd.l + NPROBE;
+      dd.kcap = std::min(f[c].k_cap, dd.l);
+      J.d[a] = dd;
+      Chan h = base[c];
+      h.l = dd.l; h.lw = dd.lw; h.k_cap = dd.kcap;
+      h.G = x.Gf; h.R = x.Rf; h.Ri = x.Rif; h.M = x.Mf; h.J = x.Jf; h.sig = x.sigf; h.scr = x.scrf;
+      h.Q32 = x.Q32; h.Y32 = x.W32; h.C64 = x.C64f; h.est_part = x.est;
+      J.ch[a] = h;
+      J.max_l = std::max(J.max_l, dd.l);
+      J.max_kcap = std::max(J.max_kcap, dd.kcap);
+    }
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    auto& ch = J.ch;
+    add_tn(J, MMK_GRAM_F32, [&](int a) { return (const void*)ch[a].Q32; },
+           [&](int a) { return (const void*)ab[idx[a]].AG; }, [&](int a) { return ch[a].C64; },
+           [&](int a) { return J.d[a].l; }, [&](int) { return NPROBE; }, false);
+    {
+      std::vector<MMDesc> md(Cf);
+      std::vector<SumsqDesc> sd(Cf);
+      for (int a = 0; a < Cf; ++a) {
+        const ChanDims& dd = J.d[a];
+        MMDesc m{};
+        m.A = ch[a].Q32; m.lda = dd.ldt;
+        m.B = ch[a].C64; m.ldb = dd.l;
+        m.Cm = ab[idx[a]].AG; m.ldc = dd.ldt;
+        m.m = dd.n; m.n = NPROBE; m.k = dd.l;
+        m.ks = 1; m.kchunk = (int)rup(dd.l, 16);
+        m.mode = MM_SUB;                                   // AG <- V G - Q C
+        md[a] = m;
+        sd[a] = SumsqDesc{ab[idx[a]].AG, dd.ldt, dd.n, NPROBE, 4, ch[a].est_part};
+      }
+      add_mm(J, MMK_NN_F32_F64B, md);
+      const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
+      cudaStream_t st = P->st;
+      J.steps.push_back([=]() {
+        launch_colsumsq(dsd, Cf, NPROBE, st);
+        return RSVD_OK;
+      });
+    }
+    add_tn(J, MMK_GRAM_DOT2, [&](int a) { return (const void*)ch[a].Y32; }, [&](int a) { return (const void*)ch[a].Y32; },
+           [&](int a) { return ch[a].G; }, [&](int a) { return J.d[a].l; }, [&](int a) { return J.d[a].l; }, true);
+    add_chol(J, 0);
+    const int maxl = J.max_l, maxk = J.max_kcap;
+    const double tol = P->o.tol;
+    cudaStream_t st = P->st;
+    {
+      const Chan* d0 = J.d_ch;
+      J.steps.push_back([=]() {
+        launch_jacobi(d0, Cf, 1, maxl, st);
+        return RSVD_OK;
+      });
+    }
+    const Chan* dch = reorth_x(J);
+    J.steps.push_back([=]() {
+      launch_probe_finish(dch, Cf, maxl, st);
+      launch_select(dch, Cf, RSVD_RANK_TOL, tol, 1, st);
+      return RSVD_OK;
+    });
+    J.d_res = d_res;
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<MMDesc> md(Cf);
+      for (int a = 0; a < Cf; ++a) {
+        const int c = idx[a];
+        const ChanDims& dd = J.d[a];
+        MMDesc m{};
+        m.A = pass == 0 ? (const void*)ch[a].Q32 : (const void*)ch[a].Y32; m.lda = dd.ldt;
+        m.B = ch[a].J; m.ldb = dd.l;          // X~ (see reorth_x)
+        m.Cm = pass == 0 ? ch[a].U : ch[a].V; m.ldc = pass == 0 ? ch[a].ldu : ch[a].ldv;
+        m.m = dd.n; m.n = dd.kcap; m.k = dd.l;
+        m.ks = 1; m.kchunk = (int)rup(dd.l, 16);
+        m.mode = MM_STORE;
+        m.colscale = pass == 0 ? nullptr : ch[a].scr;
+        m.ncols_dev = &d_res[c].k_out;
+        md[a] = m;
+      }
+      add_mm(J, MMK_NN_F32_OUT64, md);
+    }
+    J.steps.push_back([=]() {
+      launch_signfix(dch, Cf, maxk, st);
+      return RSVD_OK;
+    });
+    if (J.ar.h.size() > arena_bytes) return seterr(RSVD_ERR_OOM, "descriptor region too small");
+    if (rsvd_status s = run_job(J)) return s;
+  }
+  std::vector<ChanResult> res(C);
+  CK(cudaMemcpy(res.data(), d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost));
+  int herr = 0;
+  CK(cudaMemcpy(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", herr);
+  rsvd_status worst = RSVD_OK;
+  for (int c = 0; c < C; ++c) {
+    rsvd_status s = (rsvd_status)res[c].status;
+    if (res[c].flags & FLAG_NONFINITE) s = RSVD_ERR_NONFINITE;
+    if (dbg)
+      fprintf(stderr,
+              "rsvd adaptive: chan %d final l %d k %d flags %d sweeps %d err_est %.3e status %d words %.3e\n", c,
+              cols[c], res[c].k_out, res[c].flags, res[c].sweeps, res[c].err_est, res[c].status,
+              std::sqrt(res[c].wres2 / std::max(res[c].fro2, 1e-300)));
+    f[c].k_out = cols[c] > 0 ? res[c].k_out : 0;
+    f[c].l_used = cols[c];
+    f[c].err_est = res[c].err_est;
+    f[c].status = s;
+    if (per_item) per_item[c] = s;
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (worst >= 0 && s > worst) worst = s;
+    if (f[c].mem == RSVD_MEM_HOST && f[c].k_out > 0) {
+      const int k = f[c].k_out, n = d[c].n;
+      CK(cudaMemcpy2DAsync(f[c].U, f[c].ldu * sizeof(double), base[c].U, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpy2DAsync(f[c].V, f[c].ldv * sizeof(double), base[c].V, (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), k, cudaMemcpyDeviceToHost, P->st));
+      CK(cudaMemcpyAsync(f[c].S, base[c].S, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    }
+  }
+  CK(cudaStreamSynchronize(P->st));
+  if (worst < 0) seterr(worst, "at least one channel failed (see per-item status)");
+  return worst;
+}
+
 // ------------------------------------------------------------ job plumbing
 void init_job(Job& J, rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f) {
   J.P = P;
@@ -1223,17 +1823,10 @@ rsvd_status execute(Job& J, bool stage_inputs, std::vector<ChanResult>& res) {
   CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
   res.assign(hres, hres + C);
-  for (auto& t : P->pending) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, t.a, t.b);
-    if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
-    else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
-  }
-  P->pending.clear();
-  P->ev_next = 0;
+  drain_profile(P);
   if (getenv("RSVD_DEBUG"))
     for (int c = 0; c < C; ++c)
-      fprintf(stderr, "rsvd: chan %d n %d l %d k %d flags %d sweeps %d err_est %.3e status %d\\n", c, J.d[c].n,
+      fprintf(stderr, "rsvd: chan %d n %d l %d k %d flags %d sweeps %d err_est %.3e status %d\n", c, J.d[c].n,
               J.d[c].l, res[c].k_out, res[c].flags, res[c].sweeps, res[c].err_est, res[c].status);
   if (*herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", *herr);
   return RSVD_OK;
@@ -1328,31 +1921,52 @@ rsvd_status run_probe(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors*
   return RSVD_OK;
 }
 
-// Learned rank: probe -> features -> network -> per-channel l, one fixed-l
-// decomposition (reusing the probe's V words); channels whose estimate misses
-// the tolerance get one retry at twice the columns, then the FP64 adaptive
-// loop -- the plain method stays both the fallback and the judge.
+// Learned rank: probe -> features -> network -> per-channel
+// l = 1.2 (k^ + p^), one fixed-l decomposition (reusing the probe's V words);
+// channels whose rank rule misses the tolerance get one retry at 1.5 l, then
+// the adaptive loop in the plan's precision -- the plain method stays both
+// the fallback and the judge.  A channel that already drew all the columns
+// it may (n or l_max) keeps its best factors and TOL_NOT_MET.
 rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item) {
   if (!P->o.mlp_weights) return seterr(RSVD_ERR_INVALID_ARG, "learned rank needs mlp_weights");
   const int lcap_opt = P->o.l_max > 0 ? P->o.l_max : 1024;
   int lcap = 16;
   for (int c = 0; c < C; ++c) lcap = std::max(lcap, (int)std::min<int64_t>(A[c].n, lcap_opt));
+  const bool dbg = getenv("RSVD_DEBUG") != nullptr;
+  auto now = []() { return std::chrono::steady_clock::now(); };
+  auto ms_since = [&](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(now() - t).count();
+  };
+  auto t0 = now();
   std::vector<float> pred;
   if (rsvd_status s = run_probe(P, C, A, f, lcap, nullptr, &pred)) return s;
   std::vector<int> lvec(C);
   for (int c = 0; c < C; ++c) {
     const double k = std::exp((double)pred[2 * c]), p = std::exp((double)pred[2 * c + 1]);
     const int cap = (int)std::min<int64_t>(A[c].n, lcap_opt);
-    int l = (int)rup((int64_t)std::ceil(k + std::max(p, 1.0)), 16);
+    // 20% headroom over the predicted k + p: a miss costs a second run
+    int l = (int)rup((int64_t)std::ceil(1.2 * (k + std::max(p, 1.0))), 16);
     lvec[c] = std::max(16, std::min(l, cap));
   }
+  if (dbg) fprintf(stderr, "rsvd learned: probe %.2f ms\n", ms_since(t0));
+  t0 = now();
   std::vector<rsvd_status> st(C, RSVD_OK);
   rsvd_status r = run_fixed_l(P, C, A, f, st.data(), &lvec, true);
+  if (dbg) {
+    fprintf(stderr, "rsvd learned: first run %.2f ms\n", ms_since(t0));
+    for (int c = 0; c < C; ++c)
+      fprintf(stderr, "rsvd learned: chan %d n %lld pred k %.1f p %.1f l %d k_out %d status %d\n", c,
+              (long long)A[c].n, std::exp((double)pred[2 * c]), std::exp((double)pred[2 * c + 1]), lvec[c],
+              f[c].k_out, (int)st[c]);
+  }
   if (r < 0 && r != RSVD_ERR_TOL_NOT_MET && r != RSVD_ERR_NOT_CONVERGED) return r;
+  // channels that missed the tolerance: once more with 1.5x the columns,
+  // then the adaptive loop; a channel that already drew every column it may
+  // (n or l_max) keeps its best factors and TOL_NOT_MET
   for (int attempt = 0; attempt < 2; ++attempt) {
     std::vector<int> idx;
     for (int c = 0; c < C; ++c)
-      if (st[c] == RSVD_ERR_TOL_NOT_MET) idx.push_back(c);
+      if (st[c] == RSVD_ERR_TOL_NOT_MET && lvec[c] < (int)std::min<int64_t>(A[c].n, lcap_opt)) idx.push_back(c);
     if (idx.empty()) break;
     std::vector<rsvd_matrix> As(idx.size());
     std::vector<rsvd_factors> fs(idx.size());
@@ -1360,26 +1974,35 @@ rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factor
     for (size_t i = 0; i < idx.size(); ++i) {
       As[i] = A[idx[i]];
       fs[i] = f[idx[i]];
-      ls[i] = std::min<int>((int)std::min<int64_t>(A[idx[i]].n, lcap_opt), 2 * lvec[idx[i]]);
+      ls[i] = std::min<int>((int)std::min<int64_t>(A[idx[i]].n, lcap_opt), (int)rup(3 * lvec[idx[i]] / 2, 16));
       lvec[idx[i]] = ls[i];
     }
     std::vector<rsvd_status> sts(idx.size());
+    t0 = now();
     if (attempt == 0) {
       r = run_fixed_l(P, (int)idx.size(), As.data(), fs.data(), sts.data(), &ls, false);
     } else {
-      // the plain adaptive loop in FP64 (a temporary plan sharing the stream)
+      // the plain adaptive loop in the plan's precision (a temporary plan
+      // sharing the stream)
       rsvd_plan_s Q;
       Q.o = P->o;
-      Q.o.precision = RSVD_PREC_FP64;
       Q.o.rank_policy = RSVD_RANK_ADAPTIVE;
+      Q.slices = P->slices;
       Q.st = P->st;
       Q.d_err = P->d_err;
+      Q.profiling = P->profiling;
       r = run_adaptive(&Q, (int)idx.size(), As.data(), fs.data(), sts.data());
+      P->prof.tc_launches += Q.prof.tc_launches; P->prof.tc_ms += Q.prof.tc_ms;
+      P->prof.tc_bytes += Q.prof.tc_bytes; P->prof.tc_flops += Q.prof.tc_flops;
+      P->prof.f64_launches += Q.prof.f64_launches; P->prof.f64_ms += Q.prof.f64_ms;
+      P->prof.f64_flops += Q.prof.f64_flops;
       if (Q.ws) cudaFree(Q.ws);
       if (Q.hp) cudaFreeHost(Q.hp);
       for (cudaEvent_t e : Q.ev_pool) cudaEventDestroy(e);
     }
     if (r < 0 && r != RSVD_ERR_TOL_NOT_MET && r != RSVD_ERR_NOT_CONVERGED) return r;
+    if (dbg) fprintf(stderr, "rsvd learned: %s for %zu channels %.2f ms\n", attempt == 0 ? "retry" : "fallback",
+                     idx.size(), ms_since(t0));
     for (size_t i = 0; i < idx.size(); ++i) {
       f[idx[i]] = fs[i];
       st[idx[i]] = sts[i];
@@ -1422,8 +2045,6 @@ rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* o) {
   if (o->rank_policy == RSVD_RANK_TOL && o->k + o->p < 1)
     return seterr(RSVD_ERR_INVALID_ARG, "tolerance mode needs k + p >= 1 columns");
   if (o->slices < 0 || o->slices > 3) return seterr(RSVD_ERR_INVALID_ARG, "slices %d outside [0, 3]", o->slices);
-  if (o->rank_policy == RSVD_RANK_ADAPTIVE && o->precision != RSVD_PREC_FP64)
-    return seterr(RSVD_ERR_UNSUPPORTED, "the adaptive loop is built for the FP64 path");
   if (o->block_b < 0 || o->l_max < 0) return seterr(RSVD_ERR_INVALID_ARG, "negative block_b or l_max");
   if (o->rayleigh_ritz && (o->precision != RSVD_PREC_FP64 || o->rank_policy != RSVD_RANK_FIXED))
     return seterr(RSVD_ERR_UNSUPPORTED, "Rayleigh-Ritz is built for the FP64 path with a fixed rank");

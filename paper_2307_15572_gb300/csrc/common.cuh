@@ -140,6 +140,7 @@ struct ChanResult {
   double fro2;      // ||A||_F^2
   int sweeps;       // Jacobi sweeps used (diagnostics)
   int pad_;
+  double wres2;     // mixed path: ||A - (sum of its BF16 words)||_F^2 (FP32 remainders)
 };
 
 enum : int { FLAG_SHIFTED = 1, FLAG_JACOBI_CAP = 2, FLAG_NONFINITE = 4, FLAG_CHOL_FAIL = 8 };
@@ -170,8 +171,9 @@ struct Chan {
   double* scr;              // l doubles of scratch (unsorted column norms)
   double* gpart;            // Gram partials
   int gsplit;               // number of row splits of the Gram
-  double* fro_part;         // ||A||^2 partials (one per 64-row block)
+  double* fro_part;         // ||A||^2 partials (one per 64-row block; 8-row on the mixed path)
   // mixed path
+  double* wres_part;        // word-split remainder energy partials (one per 8-row block)
   __nv_bfloat16* Ab[3];     // V slices, row-major n x ldb
   __nv_bfloat16* Xb[3];     // X slices, K-major: column j at Xb + j*ldb
   int64_t ldb;

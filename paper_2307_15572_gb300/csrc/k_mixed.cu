@@ -43,7 +43,9 @@ RSVD_DEV double bsum(double v, double* sh) {
 // 4-byte store; the FP64 -> FP32 rounding and the word split use 32-bit
 // integer and FP32 instructions only (no FP64 instruction per element: FP64
 // is a small fraction of this part's issue rate).  ||V||^2 is accumulated
-// from the FP32 values (relative error ~1e-7) and summed in FP64 per tile.
+// from the FP32 values (relative error ~1e-7) and summed in FP64 per tile;
+// so is the energy of the remainder the words leave out (wres_part), which
+// the probe error estimate cannot see and the rank rule adds back.
 __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
                                                  const int* __restrict__ off, int C, int nsl) {
   __shared__ double sh[32];
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
   const int r0 = b * 8, r1 = min(h.n, r0 + 8);
   const int n = h.n;
   const int npair = (n + 1) >> 1;
-  float s = 0.0f;
+  float s = 0.0f, w = 0.0f;
   bool bad = false;
   for (int r = r0; r < r1; ++r) {
     const int2* row = (const int2*)(h.A + (int64_t)r * h.lda);
@@ -81,25 +83,35 @@ __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
         s = fmaf(f.y, f.y, s);
         __nv_bfloat162 q = __float22bfloat162_rn(f);
         o0[p] = q;
+        float2 g = __bfloat1622float2(q);
+        f.x -= g.x;                        // exact: the remainder fits in FP32
+        f.y -= g.y;
         if (nsl > 1) {
-          float2 g = __bfloat1622float2(q);
-          f.x -= g.x;                      // exact: the remainder fits in FP32
-          f.y -= g.y;
           q = __float22bfloat162_rn(f);
           o1[p] = q;
+          g = __bfloat1622float2(q);
+          f.x -= g.x;
+          f.y -= g.y;
           if (nsl > 2) {
+            q = __float22bfloat162_rn(f);
+            o2[p] = q;
             g = __bfloat1622float2(q);
             f.x -= g.x;
             f.y -= g.y;
-            o2[p] = __float22bfloat162_rn(f);
           }
         }
+        w = fmaf(f.x, f.x, w);             // what the words leave out
+        w = fmaf(f.y, f.y, w);
       }
     }
   }
   const double sd = bsum(f32_to_f64(s), sh);
+  const double wd = bsum(f32_to_f64(w), sh);
   if (bad) atomicOr(&h.res->flags, FLAG_NONFINITE);
-  if (threadIdx.x == 0) h.fro_part[b] = sd;
+  if (threadIdx.x == 0) {
+    h.fro_part[b] = sd;
+    if (h.wres_part) h.wres_part[b] = wd;
+  }
 }
 
 void launch_convert_slices(const Chan* d_ch, const int* d_off, int C, int tiles, int nsl,
@@ -138,29 +150,18 @@ void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uin
   if (tiles > 0) { k_omega_bf16<<<tiles, 256, 0, st>>>(d_ch, d_off, C, seed, col0, j0, j1, pseed, nsl, tag); note_launch(); }
 }
 
-// est_part[0] = sum of the probe-residual tile partials (fro_part, one per
-// 128-row tile); est_part[1+i] = |(X^T C)_i|^2 for the 8 rows i of this block
-// (one warp per row, lane p < s holds column p of D = X^T C).
+// est_part[s + i s + j] = D_ij^2 for D = X^T C (X the small SVD's left
+// vectors in M, C = Q^T V G), one warp per row i, lane j < s; the residual
+// energies est_part[0..s) come from the column sums of V G - Q C.
 __global__ void __launch_bounds__(256) k_probe_finish(const Chan* __restrict__ ch) {
-  __shared__ double sh[32];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l, s = h.nprobe;
-  if (blockIdx.y == 0) {
-    const int nb = (h.n + 127) / 128;
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += h.fro_part[i];
-    v = bsum(v, sh);
-    if (threadIdx.x == 0) h.est_part[0] = v;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.y * 8 + warp;
-  if (i >= l) return;
+  if (i >= l || lane >= s) return;
   double d = 0.0;
-  if (lane < s)
-    for (int a = 0; a < l; ++a) d = fma(h.M[a + (int64_t)i * l], h.C64[a + (int64_t)lane * l], d);
-  double d2 = d * d;
-  d2 = wsum(d2);
-  if (lane == 0) h.est_part[1 + i] = d2;
+  for (int a = 0; a < l; ++a) d = fma(h.M[a + (int64_t)i * l], h.C64[a + (int64_t)lane * l], d);
+  h.est_part[s + (int64_t)i * s + lane] = d * d;
 }
 
 void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st) {

@@ -56,6 +56,7 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
   const int c = find_chan(off, C, t);
   // descriptor fields into registers (a struct copy would live on the stack)
   const MMDesc* __restrict__ dp = md + c;
+  if (dp->cond && !(*dp->cond & FLAG_SHIFTED)) return;
   const int dm = dp->m, dn = dp->n, dk = dp->k, mt = dp->mt, nt = dp->nt, kchunk = dp->kchunk;
   const int mode = dp->mode, sym = dp->sym, nsl = dp->nsl;
   const int64_t lda = dp->lda, ldb = dp->ldb, ldc = dp->ldc, pstride = dp->pstride, ldsl = dp->ldsl;
@@ -183,6 +184,7 @@ k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) 
   const int t = blockIdx.x;
   const int c = find_chan(off, C, t);
   const MMDesc* __restrict__ dp = md + c;
+  if (dp->cond && !(*dp->cond & FLAG_SHIFTED)) return;
   const int dm = dp->m, dn = dp->n, dk = dp->k, mt = dp->mt, nt = dp->nt, kchunk = dp->kchunk;
   const int mode = dp->mode, sym = dp->sym, nsl = dp->nsl;
   const int64_t lda = dp->lda, ldb = dp->ldb, ldc = dp->ldc, pstride = dp->pstride, ldsl = dp->ldsl;
@@ -280,33 +282,6 @@ k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) 
   __nv_bfloat16* sl0 = dp->sl[0];
   __nv_bfloat16* sl1 = dp->sl[1];
   __nv_bfloat16* sl2 = dp->sl[2];
-  if (mode == MM_RESID) {
-    __shared__ double red[8];
-    float sqf = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int gm = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + i - 4);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int gn = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + j - 4);
-        if (gm < dm && gn < ncols) {
-          const float v = (float)Cp[gm + (int64_t)gn * ldc] - acc[i][j];
-          sqf = fmaf(v, v, sqf);
-        }
-      }
-    }
-    double sq = f32_to_f64(sqf);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if ((tid & 31) == 0) red[tid >> 5] = sq;
-    __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < 8; ++w) tot += red[w];
-      dp->rpart[t - off[c]] = tot;
-    }
-    return;
-  }
   // each thread owns rows {r4, r4+1, r4+2, r4+3} (two such groups) of 8
   // columns: full groups go out as one vector store per column
   const bool vec_ok = (mode == MM_STORE) && (sizeof(TC) == 4) && ((ldc & 3) == 0) &&
@@ -372,6 +347,7 @@ __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* 
                                   int C) {
   const int c = blockIdx.y;
   const MMDesc d = md[c];
+  if (d.cond && !(*d.cond & FLAG_SHIFTED)) return;
   double* out = outp[c];
   const int total = d.m * d.n;
   const int ks = d.ks;
@@ -389,7 +365,7 @@ __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* 
 
 int tile_of(MMKind kind) {
   switch (kind) {
-    case MMK_NN_F32_F64B: case MMK_NN_F32_OUT64: case MMK_GRAM_F32: case MMK_RESID_F32: return 128;
+    case MMK_NN_F32_F64B: case MMK_NN_F32_OUT64: case MMK_GRAM_F32: return 128;
     default: return 64;
   }
 }
@@ -405,7 +381,6 @@ void launch_tile_mm(MMKind kind, const MMDesc* d_md, const int* d_off, int C, in
     case MMK_NN_F32_F64B: k_tile_mm128<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
     case MMK_NN_F32_OUT64: k_tile_mm128<float, double, double, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
     case MMK_GRAM_F32: k_tile_mm128<float, float, double, AROW, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_RESID_F32: k_tile_mm128<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
   }
   note_launch();
 }

@@ -63,10 +63,17 @@ __global__ void k_fro2_reduce(const Chan* __restrict__ ch, int nparts_per_row_bl
   __shared__ double sh[32];
   const Chan& h = ch[blockIdx.x];
   const int nb = (h.n + nparts_per_row_block - 1) / nparts_per_row_block;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += h.fro_part[i];
+  double s = 0.0, w = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    s += h.fro_part[i];
+    if (h.wres_part) w += h.wres_part[i];
+  }
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) h.res->fro2 = s;
+  w = block_sum(w, sh);
+  if (threadIdx.x == 0) {
+    h.res->fro2 = s;
+    h.res->wres2 = w;
+  }
 }
 
 void launch_fro2(const Chan* d_ch, const int* d_off, int C, int tiles, cudaStream_t st) {
@@ -120,9 +127,10 @@ void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint
 // T = float: the second CholeskyQR round, whose Gram is within ~1e-2 of I.
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, int accumulate,
-                                                  int use_smem, int f32_inverse) {
+                                                  int use_smem, int f32_inverse, int conditional) {
   extern __shared__ __align__(16) unsigned char craw[];
   const Chan& h = ch[blockIdx.x];
+  if (conditional && !(h.res->flags & FLAG_SHIFTED)) return;
   const int l = h.l;
   const int ld = use_smem ? l + 1 : l;       // odd stride: conflict-free column access
   T* Ms = use_smem ? (T*)craw : (T*)h.M;     // working copy of G -> R (column-major)
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
 }
 
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
-                     cudaStream_t st, int f32_chol) {
+                     cudaStream_t st, int f32_chol, int conditional) {
   const size_t esz = f32_chol ? sizeof(float) : sizeof(double);
   size_t bytes = (size_t)max_l * (max_l + 1) * esz;
   const size_t b32 = (size_t)max_l * (max_l + 1) * sizeof(float) + 8 * (size_t)max_l * sizeof(float);
@@ -260,16 +268,16 @@ void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32
   if (f32_chol) {
     if (use_smem) {
       cudaFuncSetAttribute(k_chol_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      k_chol_inv<float><<<C, 256, bytes, st>>>(d_ch, accumulate, 1, 1);
+      k_chol_inv<float><<<C, 256, bytes, st>>>(d_ch, accumulate, 1, 1, conditional);
     } else {
-      k_chol_inv<float><<<C, 256, 0, st>>>(d_ch, accumulate, 0, 1);
+      k_chol_inv<float><<<C, 256, 0, st>>>(d_ch, accumulate, 0, 1, conditional);
     }
   } else {
     if (use_smem) {
       cudaFuncSetAttribute(k_chol_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      k_chol_inv<double><<<C, 256, bytes, st>>>(d_ch, accumulate, 1, f32_inverse);
+      k_chol_inv<double><<<C, 256, bytes, st>>>(d_ch, accumulate, 1, f32_inverse, conditional);
     } else {
-      k_chol_inv<double><<<C, 256, 0, st>>>(d_ch, accumulate, 0, f32_inverse);
+      k_chol_inv<double><<<C, 256, 0, st>>>(d_ch, accumulate, 0, f32_inverse, conditional);
     }
   }
   note_launch();
@@ -477,61 +485,88 @@ void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st
 // Probe form (mixed path): with G the probe block (s Gaussian columns),
 // C = Q^T V G, D = X^T C, ||(I - U_k U_k^T) V G||^2 = ||V G - Q C||^2 +
 // sum_{i>k} |D_i|^2, and E||(I-P)V G||_F^2 = s ||(I-P) V||_F^2.
+// Probe energies of the s columns for the current k, held one per lane:
+// mean and upper confidence bound over the lanes (all 32 lanes call).
+RSVD_DEV void probe_stats(double e, int s, double& mean, double& ucb) {
+  const int lane = threadIdx.x & 31;
+  double v = lane < s ? e : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  mean = v / s;
+  double d = lane < s ? (e - mean) * (e - mean) : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  const double var = s > 1 ? d / (s - 1) : 0.0;
+  ucb = mean + PROBE_Z * sqrt(var / s);
+}
+
+// One warp per channel.  Probe layout (mixed path): est_part[j] = ||R g_j||^2
+// with R = V G - Q C the probe residual, est_part[s + i s + j] = D_ij^2 for
+// D = X^T C; e_j(k) = est_part[j] + sum_{i >= k} est_part[s + i s + j].
 __global__ void k_select(const Chan* __restrict__ ch, int policy, double tol_plan, int use_probe) {
   const Chan& h = ch[blockIdx.x];
   const double tol = h.tol > 0.0 ? h.tol : tol_plan;
   const int l = h.l;
   ChanResult* res = h.res;
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x;
   const double fro2 = res->fro2;
-  int status = RSVD_OK;
-  int k;
-  double est2 = 0.0;
   const int kcap = min(h.k_cap, l);
+  const double thr = tol * tol * fro2;
+  int k = -1;
+  double est2 = 0.0;
+  bool unmet = false;
+  if (use_probe) {
+    const int s = h.nprobe;
+    const double* ep = h.est_part;
+    const int kfix = min(h.k_fixed, kcap);
+    const int k0 = policy == RSVD_RANK_FIXED ? kfix : kcap;
+    double e = 0.0;
+    if (lane < s) {
+      e = ep[lane];
+      for (int i = l - 1; i >= k0; --i) e += ep[s + (int64_t)i * s + lane];
+    }
+    const double floor2 = precision_floor2(res->wres2, l, fro2);
+    double mean, ucb;
+    probe_stats(e, s, mean, ucb);
+    mean += floor2; ucb += floor2;
+    k = k0;
+    est2 = mean;
+    if (policy != RSVD_RANK_FIXED) {
+      if (ucb > thr) unmet = true;
+      else {
+        // walk k downward while the bound stays under the threshold
+        for (int kk = k0 - 1; kk >= 1; --kk) {
+          if (lane < s) e += ep[s + (int64_t)kk * s + lane];
+          probe_stats(e, s, mean, ucb);
+          mean += floor2; ucb += floor2;
+          if (ucb > thr) break;
+          k = kk;
+          est2 = mean;
+        }
+      }
+    }
+  }
+  if (lane != 0) return;
+  int status = RSVD_OK;
   if (res->flags & FLAG_NONFINITE) status = RSVD_ERR_NONFINITE;
   else if (res->flags & FLAG_CHOL_FAIL) status = RSVD_ERR_NOT_CONVERGED;
-  if (policy == RSVD_RANK_FIXED) {
-    k = min(h.k_fixed, kcap);
-    double s2 = 0.0;
-    for (int i = 0; i < k; ++i) s2 += h.sig[i] * h.sig[i];
-    est2 = fmax(fro2 - s2, 0.0);
-    if (use_probe) {
-      double t = h.est_part[0];
-      for (int i = k; i < l; ++i) t += h.est_part[1 + i];
-      est2 = t / h.nprobe;
-    }
-  } else {
-    const double thr = tol * tol * fro2;
-    k = -1;
-    if (!use_probe) {
+  if (!use_probe) {
+    if (policy == RSVD_RANK_FIXED) {
+      k = min(h.k_fixed, kcap);
+      double s2 = 0.0;
+      for (int i = 0; i < k; ++i) s2 += h.sig[i] * h.sig[i];
+      est2 = fmax(fro2 - s2, 0.0);
+    } else {
       double s2 = 0.0;
       for (int i = 0; i < kcap; ++i) {
         s2 += h.sig[i] * h.sig[i];
         if (fro2 - s2 <= thr) { k = i + 1; est2 = fmax(fro2 - s2, 0.0); break; }
       }
       if (k < 0) { k = kcap; est2 = fmax(fro2 - s2, 0.0); }
-    } else {
-      // tail sums from the end: t_k = rl2 + sum_{i>k} dn2_i
-      const double margin = 1.0 / (1.1 * 1.1);
-      double t = h.est_part[0];
-      for (int i = l - 1; i >= kcap; --i) t += h.est_part[1 + i];
-      // walk k downward from kcap while the estimate stays under the threshold
-      double tk = t;               // estimate for k = kcap
-      k = kcap;
-      double best = tk;
-      if (tk / h.nprobe > thr * margin) k = -1;
-      else {
-        for (int kk = kcap - 1; kk >= 1; --kk) {
-          const double tn = tk + h.est_part[1 + kk];
-          if (tn / h.nprobe > thr * margin) break;
-          tk = tn; k = kk; best = tk;
-        }
-      }
-      if (k < 0) { k = kcap; best = t; }
-      est2 = best / h.nprobe;
+      unmet = est2 > thr;
     }
-    if (fro2 > 0.0 && est2 > thr && status == RSVD_OK) status = RSVD_ERR_TOL_NOT_MET;
   }
+  if (policy != RSVD_RANK_FIXED && fro2 > 0.0 && unmet && status == RSVD_OK) status = RSVD_ERR_TOL_NOT_MET;
   if (k < 0) k = 0;
   for (int i = 0; i < k; ++i) {
     h.S[i] = h.sig[i];
@@ -596,6 +631,48 @@ __global__ void __launch_bounds__(256) k_sumsq(const SumsqDesc* __restrict__ sd)
   }
   s = block_sum(s, sh);
   if (threadIdx.x == 0) *d->out = s;
+}
+
+__global__ void __launch_bounds__(256) k_colsumsq(const SumsqDesc* __restrict__ sd) {
+  __shared__ double sh[32];
+  const SumsqDesc* d = sd + blockIdx.x;
+  const int j = blockIdx.y;
+  if (j >= d->cols) return;
+  double s = 0.0;
+  if (d->esz == 8) {
+    const double* col = (const double*)d->p + (int64_t)j * d->ld;
+    for (int r = threadIdx.x; r < d->rows; r += blockDim.x) s = fma(col[r], col[r], s);
+  } else {
+    const float* col = (const float*)d->p + (int64_t)j * d->ld;
+    for (int r = threadIdx.x; r < d->rows; r += blockDim.x) {
+      const double v = f32_to_f64(col[r]);
+      s = fma(v, v, s);
+    }
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) d->out[j] = s;
+}
+
+// Q32 <- T32 for the channels whose flags carry FLAG_SHIFTED (the output of
+// the conditional third CholeskyQR round lands in T32).
+__global__ void __launch_bounds__(256) k_copy_t_to_q(const Chan* __restrict__ ch) {
+  const Chan& h = ch[blockIdx.y];
+  if (!(h.res->flags & FLAG_SHIFTED)) return;
+  const int64_t total = (int64_t)h.l * h.ldt;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    h.Q32[e] = h.T32[e];
+}
+
+void launch_copy_t_to_q_if_shifted(const Chan* d_ch, int C, cudaStream_t st) {
+  if (C < 1) return;
+  k_copy_t_to_q<<<dim3(64, C), 256, 0, st>>>(d_ch);
+  note_launch();
+}
+
+void launch_colsumsq(const SumsqDesc* d_sd, int C, int max_cols, cudaStream_t st) {
+  if (C < 1 || max_cols < 1) return;
+  k_colsumsq<<<dim3(C, max_cols), 256, 0, st>>>(d_sd);
+  note_launch();
 }
 
 void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st) {

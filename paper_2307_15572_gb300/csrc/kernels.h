@@ -10,10 +10,8 @@ void note_launch(int k = 1);
 long long launch_count();
 
 // ----------------------------------------------------------------- tile GEMMs
-enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2, MM_RESID = 3, MM_SUB = 4 };
+enum MMMode { MM_STORE = 0, MM_ATOMIC = 1, MM_PARTIAL = 2, MM_SUB = 4 };
 // MM_SUB: C <- C - A B (block Gram-Schmidt against earlier blocks).
-// MM_RESID: Cm holds a reference block R (same layout); the kernel writes
-// sum over its tile of (R - A B)^2 to rpart[tile index within the channel].
 enum MMKind {
   MMK_DENSE_F64 = 0,     // C = V B, V dense row-major FP64, FP64 FMA
   MMK_GRAM_F64 = 1,      // partial C_s = Y_s^T Z_s, FP64
@@ -21,8 +19,7 @@ enum MMKind {
   MMK_GRAM_DOT2 = 3,     // partial C_s = Y_s^T Z_s, FP32 data, compensated (Dot2) -> FP64
   MMK_NN_F32_F64B = 4,   // C(FP32) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
   MMK_NN_F32_OUT64 = 5,  // C(FP64) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
-  MMK_GRAM_F32 = 6,      // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
-  MMK_RESID_F32 = 7      // sum (R - A B)^2 per tile, A FP32 column-major, B FP64 (MM_RESID)
+  MMK_GRAM_F32 = 6       // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
 };
 
 struct MMDesc {
@@ -40,7 +37,7 @@ struct MMDesc {
   int nsl;
   const int* ncols_dev;     // optional: output columns limited to *ncols_dev (rank chosen on device)
   int tile;                 // output tile edge of the kernel kind (64 or 128)
-  double* rpart;            // MM_RESID partials
+  const int* cond;          // optional: run only if (*cond & FLAG_SHIFTED) (a conditional CholeskyQR round)
 };
 
 int tile_of(MMKind kind);
@@ -63,13 +60,31 @@ void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint
                       int col0, cudaStream_t st, uint32_t tag = TAG_OMEGA);
 // Upper Cholesky G = R^T R (l x l), R^{-1}; R_acc <- R R_acc when accumulate.
 // Shifted retry on breakdown (flag FLAG_SHIFTED).
+// conditional: only channels whose result flags carry FLAG_SHIFTED.
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
-                     cudaStream_t st, int f32_chol = 0);
+                     cudaStream_t st, int f32_chol = 0, int conditional = 0);
+// Q32 <- T32 (n x l) for channels whose result flags carry FLAG_SHIFTED.
+void launch_copy_t_to_q_if_shifted(const Chan* d_ch, int C, cudaStream_t st);
 // One-sided Jacobi SVD of M = R^T (FP64 or FP32 arithmetic); writes sig, M <- left
 // vectors, J <- right vectors, sorted by descending sigma.
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st);
 // Rank selection (fixed or tolerance) from sig and ||A||^2 (FP64 identity),
 // or from the probe residual (mixed path).  Writes S and ChanResult.
+// Probe rule: with s Gaussian probe columns g_j the energies
+// e_j(k) = ||(I - U_k U_k^T) V g_j||^2 are i.i.d. with mean ||(I - U_k U_k^T) V||_F^2.
+// A rank is accepted when the upper confidence bound  mean + PROBE_Z sd / sqrt(s)
+// (sd the sample deviation of the e_j) is at most tol^2 ||V||_F^2.  With
+// s = 32 probes PROBE_Z is a little above the one-sided 99.9% point of
+// Student's t with 31 degrees of freedom (3.37), leaving room for the skew of
+// the e_j (weighted chi-square sums).  The reported estimate is the mean.
+constexpr double PROBE_Z = 3.5;
+// Energy the probe estimate cannot see on the mixed path: the remainder the
+// BF16 words leave out of V (measured while converting) plus the FP32
+// rounding of the lifted factors, modelled as 2 sqrt(l) eps_32 relative.
+// Both the rank rule and the adaptive stop add it to the estimate.
+__host__ __device__ inline double precision_floor2(double wres2, int l, double fro2) {
+  return wres2 + 4.0 * l * 3.552713678800501e-15 * fro2;     // eps_32^2 = 2^-48
+}
 void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
                    cudaStream_t st);
 // Sign fix: largest-|.| entry of U_i positive, flip V_i with it.
@@ -77,6 +92,8 @@ void launch_signfix(const Chan* d_ch, int C, int max_k, cudaStream_t st);
 // out[c] = sum of squares of the n x cols block at p[c] (leading dim ld[c]), FP64.
 struct SumsqDesc { const void* p; int64_t ld; int rows, cols, esz; double* out; };
 void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st);
+// out[c][j] = sum of squares of column j of the block (one block per column).
+void launch_colsumsq(const SumsqDesc* d_sd, int C, int max_cols, cudaStream_t st);
 
 // --------------------------------------------------------- mixed-path kernels
 void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int tiles, int nsl,

@@ -152,21 +152,34 @@ def predict(theta, X):
     return Y
 
 
-def run_policy(pop, mats, policy, precision, theta=None, block=16, lmax=1024, seed=1, slices=0):
-    """Decompose the channels with one policy; returns (seconds, factors, per-channel status)."""
+def run_policy(pop, mats, policy, precision, theta=None, block=16, lmax=1024, seed=1, slices=0, repeat=1,
+               stats=None):
+    """Decompose the channels with one policy; returns (seconds of the last of
+    ``repeat`` calls, factors, per-channel status, exact relative errors).
+    With ``stats`` (a dict) it also records the passes over V of that call
+    (tensor-core passes on the mixed path, dense FP64 passes otherwise) and
+    the plan's kernel launches."""
     import torch
     nmax = max(ch["n"] for ch in pop)
     plan = rsvd.Plan(nmax, k=0, p=0, q=0, tol=1e-3, policy=policy, precision=precision, block_b=block,
                      l_max=lmax, seed=seed, slices=slices,
                      mlp_weights=theta.data_ptr() if theta is not None else None)
     try:
-        facs, bufs = _factors(pop, lmax)
         descs = [rsvd.dense(A) for A in mats]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, per = rsvd.rsvd_decompose_batched(plan.h, descs, facs)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        if stats is not None:
+            rsvd.rsvd_plan_set_profiling(plan.h, True)
+        for _ in range(repeat):
+            facs, bufs = _factors(pop, lmax)
+            rsvd.rsvd_plan_profile(plan.h, reset=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, per = rsvd.rsvd_decompose_batched(plan.h, descs, facs)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        if stats is not None:
+            prof = rsvd.rsvd_plan_profile(plan.h)
+            stats["passes"] = prof["tc_launches"] + prof["f64_launches"]
+            stats["launches"] = prof["launches"]
         errs = [rsvd.rsvd_reconstruct_error(plan.h, dsc, f) if f.k_out > 0 else 1.0 for dsc, f in zip(descs, facs)]
     finally:
         plan.close()

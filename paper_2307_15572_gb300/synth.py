@@ -211,16 +211,18 @@ def mixed_decay_spectrum(n, a, tau, beta):
     return a * np.exp(-i / tau) + (1.0 - a) * i ** (-beta)
 
 
-def learn_population(count, seed=SEED_LEARN, nlo=500, nhi=20000, tlo=1e-7, thi=1e-3):
+def learn_population(count, seed=SEED_LEARN, nlo=500, nhi=20000, tlo=1e-7, thi=1e-3, tau=(5.0, 200.0),
+                     beta=(1.5, 4.0)):
     """Channels for the rank model: sizes uniform in [nlo, nhi], spectra mixing
-    exponential and algebraic decay (a ~ U[0,1], tau ~ logU[5, 200],
-    beta ~ U[1.5, 4]), tolerances log-uniform in [tlo, thi]."""
+    exponential and algebraic decay (a ~ U[0,1], tau log-uniform in ``tau``,
+    beta uniform in ``beta``; defaults tau ~ logU[5, 200], beta ~ U[1.5, 4]),
+    tolerances log-uniform in [tlo, thi]."""
     rng = np.random.default_rng(seed)
     out = []
     for c in range(count):
         out.append(dict(n=int(rng.integers(nlo, nhi + 1)), a=float(rng.uniform()),
-                        tau=math.exp(rng.uniform(math.log(5.0), math.log(200.0))),
-                        beta=float(rng.uniform(1.5, 4.0)),
+                        tau=math.exp(rng.uniform(math.log(tau[0]), math.log(tau[1]))),
+                        beta=float(rng.uniform(beta[0], beta[1])),
                         tol=math.exp(rng.uniform(math.log(tlo), math.log(thi))),
                         seed=int(rng.integers(0, 2**62))))
     return out

@@ -235,3 +235,46 @@ def test_fp64_adaptive_batched_uneven(lib):
             sigma_parity(r["S"].cpu().numpy(), o.S)
     finally:
         plan.close()
+
+
+# mixed-precision adaptive loop: the probe indicator (an upper confidence
+# bound) replaces the exact one and the sketch columns are the FP32 evaluation
+# of the Gaussian stream, so the draw may stop up to one block earlier or three
+# later than the oracle's and the rank may sit above the oracle's by the
+# bound's margin (more columns drawn can also mean a smaller rank)
+@pytest.mark.parametrize("n,tol,b,q,slices", [(900, 1e-4, 16, 0, 2), (2500, 1e-4, 32, 0, 2),
+                                              (1500, 1e-5, 32, 1, 3)])
+def test_mixed_adaptive_meets_tolerance(lib, n, tol, b, q, slices):
+    A = synth.batch_channel(n % 7, n)
+    o, drawn, met = orsvd.rsvd_adaptive(A, tol=tol, b=b, q=q, seed=13, l_max=600)
+    e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+    st, r, err = run(lib, A, k=0, p=0, q=q, seed=13, tol=tol, policy="adaptive", block_b=b, l_max=600,
+                     k_cap=600, precision="bf16x", slices=slices)
+    assert st == 0, lib.last_error()
+    assert met
+    assert err <= tol, (err, tol)
+    assert drawn - b <= r["l"] <= drawn + 3 * b, (r["l"], drawn)
+    assert -max(8, 0.1 * o.k) <= r["k"] - o.k <= max(12, 0.25 * o.k), (r["k"], o.k)
+    if r["k"] >= o.k and r["l"] >= drawn:
+        assert err <= 1.05 * e_o, (err, e_o)
+    assert abs(r["err_est"] - err) <= 0.35 * err
+
+
+def test_mixed_adaptive_batched_uneven(lib):
+    torch = _torch()
+    sizes = [400, 1200, 700, 2100]
+    mats = [synth.batch_channel(c, n) for c, n in enumerate(sizes)]
+    plan = lib.Plan(max(sizes), k=0, p=0, q=0, seed=2, tol=1e-4, policy="adaptive", block_b=16, l_max=400,
+                    precision="bf16x")
+    try:
+        dev = [torch.as_tensor(A, device="cuda") for A in mats]
+        st, res = plan.decompose_batched(dev, 400)
+        assert st == 0, lib.last_error()
+        for A, At, r in zip(mats, dev, res):
+            o, drawn, met = orsvd.rsvd_adaptive(A, tol=1e-4, b=16, q=0, seed=2, l_max=400)
+            err = plan.reconstruct_error(At, r)
+            assert err <= 1e-4, (A.shape[0], err)
+            assert drawn - 16 <= r["l"] <= drawn + 48
+            assert -max(8, 0.1 * o.k) <= r["k"] - o.k <= max(12, 0.25 * o.k)
+    finally:
+        plan.close()
