@@ -113,9 +113,21 @@ typedef enum { RSVD_MEM_DEVICE = 0, RSVD_MEM_HOST = 1 } rsvd_mem;
  * (mem = HOST; page-locked memory gives overlapped copies).  The library
  * does not check symmetry.
  * TILE_RULE: entries A_ij = sum_m w_m g_m(x_i) g_m(x_j) + eta_ij with
- * x_i = 8 i/(n-1), g_m(x) = exp(-(x-c_m)^2/(2 s_m^2)) and eta the symmetric
- * hash noise of amplitude rule_eta (see rsvd_rule_entry); rule_c, rule_s,
- * rule_w are HOST arrays of rule_m values.  The matrix is never stored.
+ * x_i = 8 i/(n-1), g_m(x) = exp(-(x-c_m)^2/(2 s_m^2)) (1 <= rule_m <= 4096,
+ * s_m > 0, w_m >= 0) and eta the symmetric hash noise of standard deviation
+ * rule_eta keyed by rule_seed:
+ *   h = mix(mix(min(i,j) * 0x9E3779B1 + key) ^ (max(i,j) * 0x85EBCA77)),
+ *   eta_ij = rule_eta sqrt(3) (2 u - 1), u = ((h >> 8) + 1/2) 2^-24,
+ *   key = mix(seed_lo ^ mix(seed_hi)), mix = the 32-bit "lowbias32" hash
+ * (arithmetic modulo 2^32).  rule_c, rule_s, rule_w are HOST arrays of
+ * rule_m values; `data`, `ld` and `mem` are ignored.  The matrix is never
+ * stored: every pass generates the entries it reads, row panel by row panel,
+ * on the tensor core (BF16x3 factor words, FP32 accumulation; entries
+ * accurate to ~1e-6 relative).  Tile rules need precision BF16X and the
+ * FIXED or TOL rank policy, and cannot share a call with stored channels
+ * (RSVD_ERR_UNSUPPORTED otherwise).  Tuning: the environment variable
+ * RSVD_RULE_PANEL sets the rows generated per panel (default: panels of
+ * ~8 GiB of words).
  */
 typedef struct {
   int32_t kind;
@@ -177,8 +189,9 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t plan, int32_t C, const rsvd_matri
                                    rsvd_factors* f, rsvd_status* per_item);
 
 /* Exact relative residual ||A - U diag(S) V^T||_F / ||A||_F of the rank-f->k_out
- * factors, accumulated in FP64 over every entry (tile rules are regenerated).
- * *rel_err is a host pointer. */
+ * factors, accumulated in FP64 over every entry of a stored channel.
+ * *rel_err is a host pointer.  Tile rules: RSVD_ERR_UNSUPPORTED (generate
+ * their rows with rsvd_rule_rows). */
 rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
                                    const rsvd_factors* f, double* rel_err);
 
@@ -232,6 +245,15 @@ rsvd_status rsvd_plan_profile(rsvd_plan_t plan, rsvd_profile* out, int32_t reset
 rsvd_status rsvd_reconstruct_error_noalloc(const double* A, int64_t lda, int64_t n, const double* U,
                                            int64_t ldu, const double* S, const double* V, int64_t ldv,
                                            int32_t k, double* rel_err, void* stream);
+
+/* Rows r0 .. r0+rows-1 of a tile rule as the decomposition's passes generate
+ * them (FP32, noise included, before the split into BF16 words):
+ * out[p * ldo + j] = A_(r0+p, j), out a DEVICE pointer, ldo >= n.  Uses the
+ * plan's stream and workspace (grown if needed); synchronous.  Returns
+ * RSVD_ERR_INVALID_ARG for a matrix that is not a tile rule, bad parameters
+ * or rows outside [0, n). */
+rsvd_status rsvd_rule_rows(rsvd_plan_t plan, const rsvd_matrix* A, int64_t r0, int32_t rows, float* out,
+                           int64_t ldo);
 
 /* Device buffer size (bytes) the plan holds now. */
 int64_t rsvd_plan_workspace_bytes(rsvd_plan_t plan);

@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <functional>
 #include <string>
@@ -197,7 +198,34 @@ struct Job {
   Chan* d_ch = nullptr;
   ChanResult* d_res = nullptr;
   int max_l = 0, max_lw = 0, max_kcap = 0;
+  // tile-rule channels (all channels of the job, or none)
+  bool rule = false;
+  int panel = 0;                        // rows of A generated per panel
+  struct RuleDev {
+    __nv_bfloat16* H[3];
+    int64_t ldh;
+    int M;
+    uint32_t key;
+    float amp3;
+    double* psums;                      // per panel {sum v^2, sum remainder^2}
+  };
+  std::vector<RuleDev> rd;
+  __nv_bfloat16* pw[3] = {nullptr, nullptr, nullptr};   // panel words (panel x ldb each)
+  double* part = nullptr;               // per (item, warp) partials of one generation launch
 };
+
+// Tile rule: H words have M padded to whole 64-wide k steps.
+int64_t rule_ldh(int M) { return rup(M, 64); }
+int rule_panel_rows(int64_t n, int64_t ldb, int nsl) {
+  // panel words within ~8 GiB (tunable through RSVD_RULE_PANEL for tests)
+  int64_t p = ((int64_t)8 << 30) / std::max<int64_t>(1, (int64_t)nsl * ldb * 2);
+  if (const char* e = getenv("RSVD_RULE_PANEL")) p = std::max<int64_t>(128, atoll(e));
+  p = std::max<int64_t>(128, p / 128 * 128);
+  return (int)std::min<int64_t>(p, rup(n, 128));
+}
+uint32_t rule_key(uint64_t seed) {
+  return lowbias32((uint32_t)seed ^ lowbias32((uint32_t)(seed >> 32)));
+}
 
 // Per-batch tile offsets (prefix sums) uploaded through the arena.
 const int* offsets(Job& J, const std::function<int64_t(int)>& per) {
@@ -467,12 +495,14 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
     const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
     const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
     if (!J.measure) {
-      const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, nc, bn);
+      const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, d.n, nc, bn);
       if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
     }
     t.Y = yout(c);
     t.ldy = d.ldt;
     t.n = d.n;
+    t.m = d.n;
+    t.mode = TC_STORE;
     t.ncols = nc;
     t.mt = cdiv(d.n, 128);
     t.nt = cdiv(nc, bn);
@@ -531,6 +561,103 @@ rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/) {
   return tc_pass_ex(
       J, sa, sx, [&](int c) { return ncols_of_pass ? J.d[c].lw : J.d[c].l; },
       [&](int c, int w) { return (const __nv_bfloat16*)J.ch[c].Xb[w]; }, [&](int c) { return J.ch[c].Y32; });
+}
+
+// One pass Y = A X over tile-rule channels.  Per channel and row panel: a
+// generation launch (H H_panel^T on the tensor core, plus the noise, split
+// into the panel's BF16 words) and a product launch (panel words x X words
+// -> the panel's rows of Y).  A is symmetric, so the generated block, stored
+// with the matrix column index fastest, is exactly the row panel the product
+// reads.  `first`: also reduce the entry energies into fro2 and wres2.
+rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
+                      std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout,
+                      bool first) {
+  const int nsl = J.nsl;
+  rsvd_plan_s* P = J.P;
+  cudaStream_t st = P->st;
+  int* derr = P->d_err;
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    const Job::RuleDev r = J.rd[c];
+    const int Pr = std::min<int>(J.panel, (int)rup(d.n, 128));
+    const int np = cdiv(d.n, Pr);
+    const int nc = ncols_of(c);
+    const int ntile = cdiv(std::max(nc, 16), 160);
+    const int bn = (int)rup(cdiv(std::max(nc, 16), ntile), 16);
+    for (int p = 0; p < np; ++p) {
+      const int r0 = p * Pr, rows = std::min(Pr, d.n - r0);
+      const int gbn = std::min(128, (int)rup(rows, 16));
+      TcChan g, t;
+      memset(&g, 0, sizeof(g));
+      memset(&t, 0, sizeof(t));
+      if (!J.measure) {
+        const __nv_bfloat16* HA[3] = {r.H[0], r.H[1], r.H[2]};
+        const __nv_bfloat16* HX[3] = {r.H[0] + (int64_t)r0 * r.ldh, r.H[1] + (int64_t)r0 * r.ldh,
+                                      r.H[2] + (int64_t)r0 * r.ldh};
+        int e = tc_encode(&g, HA, 3, r.ldh, HX, 3, r.ldh, d.n, r.M, rows, gbn);
+        if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
+        const __nv_bfloat16* PA[3] = {J.pw[0], J.pw[1], J.pw[2]};
+        const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
+        e = tc_encode(&t, PA, nsl, d.ldb, X, sx, d.ldb, rows, d.n, nc, bn);
+        if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
+      }
+      g.n = r.M; g.m = d.n; g.ncols = rows;
+      g.mt = cdiv(d.n, 128); g.nt = cdiv(rows, gbn); g.ks = 1; g.kt_per_split = cdiv(r.M, 64);
+      g.mode = TC_RULE;
+      g.chunk_kt = 1;
+      for (int w = 0; w < nsl; ++w) g.W[w] = J.pw[w];
+      g.ldw = d.ldb; g.nw = nsl; g.r0 = r0;
+      g.eta_key = r.key; g.eta_amp3 = r.amp3;
+      g.part = first ? J.part : nullptr;
+      t.Y = yout(c) + r0; t.ldy = d.ldt;
+      t.n = d.n; t.m = rows; t.ncols = nc;
+      t.mt = cdiv(rows, 128); t.nt = cdiv(nc, bn); t.ks = 1; t.kt_per_split = cdiv(d.n, 64);
+      t.mode = TC_STORE;
+      const int gitems = g.mt * g.nt, titems = t.mt * t.nt;
+      const TcChan* dg = J.ar.put(&g, 1, 128);
+      const TcChan* dt = J.ar.put(&t, 1, 128);
+      const double gflops = 2.0 * d.n * (double)rows * r.ldh * 6;
+      double tpairs = 0;
+      for (int a = 0; a < nsl; ++a)
+        for (int x = 0; x < sx; ++x) tpairs += (a + x < std::max(nsl, sx));
+      const double tbytes = (double)rows * d.n * 2.0 * nsl + (double)d.n * nc * 2.0 * sx + (double)rows * nc * 4.0;
+      const double tflops = 2.0 * rows * (double)d.n * nc * tpairs;
+      double* part = J.part;
+      double* psum = r.psums + 2 * p;
+      J.steps.push_back([=]() {
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (P->profiling) timed_begin(P, &ea, &eb);
+        int e = tc_launch(dg, 1, gitems, 3, 3, gbn, derr, st);
+        if (e) return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
+        if (first) launch_rule_part_sum(part, gitems * 4, psum, st);
+        e = tc_launch(dt, 1, titems, nsl, sx, bn, derr, st);
+        if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
+        if (P->profiling) {
+          cudaEventRecord(eb, st);
+          P->pending.push_back({ea, eb, 0, tbytes, tflops + gflops});
+        }
+        return RSVD_OK;
+      });
+    }
+    if (first) {
+      ChanResult* res = J.ch[c].res;
+      const double* ps = r.psums;
+      J.steps.push_back([=]() {
+        launch_rule_finish(ps, np, res, st);
+        return RSVD_OK;
+      });
+    }
+  }
+  return RSVD_OK;
+}
+
+// One pass over V (dense words) or over the generated rule entries.
+rsvd_status pass_over(Job& J, int sa, int sx, int ncols_of_pass, bool first) {
+  auto ncols = [&](int c) { return ncols_of_pass ? J.d[c].lw : J.d[c].l; };
+  auto xw = [&](int c, int w) { return (const __nv_bfloat16*)J.ch[c].Xb[w]; };
+  auto y = [&](int c) { return J.ch[c].Y32; };
+  if (J.rule) return rule_pass(J, sx, ncols, xw, y, first);
+  return tc_pass_ex(J, sa, sx, ncols, xw, y);
 }
 
 // CholeskyQR2 of Y32[:, 0:l) -> Q32 (FP32) and its BF16 words in Xb[:, 0:l).
@@ -668,21 +795,43 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
   const uint64_t seed = J.P->o.seed;
   const uint64_t pseed = seed ^ 0x5DEECE66DULL;
-  J.steps.push_back([=]() {
-    if (!skip_convert) launch_convert_slices(dch, off8, C, t8, nsl, st);
-    launch_fro2_reduce_rows(dch, C, 8, st);         // partials are kept from the convert pass
-    launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
-    return RSVD_OK;
-  });
+  if (J.rule) {
+    // the factor panel H of each rule (its parameters travel in the descriptor region)
+    std::vector<RuleDesc> rds(C);
+    for (int c = 0; c < C; ++c) {
+      const rsvd_matrix& A = J.A[c];
+      const int M = A.rule_m;
+      RuleDesc r{};
+      r.n = J.d[c].n; r.M = M;
+      r.c = J.ar.put(A.rule_c, M);
+      r.s = J.ar.put(A.rule_s, M);
+      r.w = J.ar.put(A.rule_w, M);
+      for (int w = 0; w < 3; ++w) r.H[w] = J.rd[c].H[w];
+      r.ldh = J.rd[c].ldh;
+      rds[c] = r;
+    }
+    J.steps.push_back([=]() {
+      for (const RuleDesc& r : rds) launch_rule_prep(r, st);
+      launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
+      return RSVD_OK;
+    });
+  } else {
+    J.steps.push_back([=]() {
+      if (!skip_convert) launch_convert_slices(dch, off8, C, t8, nsl, st);
+      launch_fro2_reduce_rows(dch, C, 8, st);         // partials are kept from the convert pass
+      launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
+      return RSVD_OK;
+    });
+  }
   // sketch: only the l sketch columns (X word 0 = P exactly)
-  if (rsvd_status s = tc_pass(J, nsl, 1, 0)) return s;
+  if (rsvd_status s = pass_over(J, nsl, 1, 0, true)) return s;
   cqr2_mixed(J, nsl);
   for (int r = 0; r < 2 * J.q; ++r) {
-    if (rsvd_status s = tc_pass(J, nsl, nsl, 0)) return s;
+    if (rsvd_status s = pass_over(J, nsl, nsl, 0, false)) return s;
     cqr2_mixed(J, nsl);
   }
   // projection with the probe block: [W | V G] = V [Q | G]
-  if (rsvd_status s = tc_pass(J, nsl, nsl, 1)) return s;
+  if (rsvd_status s = pass_over(J, nsl, nsl, 1, false)) return s;
   // C = Q^T (V G) (FP32 accumulate is ample for the error estimate)
   add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
          [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
@@ -802,6 +951,10 @@ void layout(Job& J, Bump& b) {
     const ChanDims& d = J.d[c];
     Chan& h = J.ch[c];
     const rsvd_matrix& A = J.A[c];
+    if (J.rule) {
+      h.fro_part = b.take<double>(cdiv(d.n, 8));
+      continue;
+    }
     if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
     else { h.A = A.data; h.lda = A.ld; }
     if (J.mixed) {
@@ -809,6 +962,33 @@ void layout(Job& J, Bump& b) {
       h.wres_part = b.take<double>(cdiv(d.n, 8));
     }
     h.fro_part = b.take<double>(cdiv(d.n, 8));
+  }
+  if (J.rule) {
+    // factor words per channel; one panel buffer and partial area shared by
+    // the channels (they are generated one after another)
+    J.rd.assign(J.C, Job::RuleDev{});
+    int64_t maxldb = 64, maxitems = 1;
+    int maxn = 1;
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      Job::RuleDev& r = J.rd[c];
+      r.M = J.A[c].rule_m;
+      r.ldh = rule_ldh(r.M);
+      for (int w = 0; w < 3; ++w) r.H[w] = b.take<__nv_bfloat16>((size_t)d.n * r.ldh);
+      r.key = rule_key(J.A[c].rule_seed);
+      r.amp3 = (float)(J.A[c].rule_eta * 1.7320508075688772);
+      maxldb = std::max<int64_t>(maxldb, d.ldb);
+      maxn = std::max(maxn, d.n);
+    }
+    J.panel = rule_panel_rows(maxn, maxldb, J.nsl);
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      const int P = std::min<int>(J.panel, (int)rup(d.n, 128));
+      J.rd[c].psums = b.take<double>(2 * (size_t)cdiv(d.n, P));
+      maxitems = std::max<int64_t>(maxitems, (int64_t)cdiv(d.n, 128) * cdiv(P, 128));
+    }
+    for (int w = 0; w < J.nsl; ++w) J.pw[w] = b.take<__nv_bfloat16>((size_t)J.panel * maxldb);
+    J.part = b.take<double>((size_t)maxitems * 8);
   }
   J.d_res = b.take<ChanResult>(J.C);
   for (int c = 0; c < J.C; ++c) {
@@ -856,15 +1036,36 @@ rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_fac
   for (int c = 0; c < C; ++c) {
     const rsvd_matrix& a = A[c];
     const rsvd_factors& F = f[c];
-    if (a.kind != RSVD_DENSE_F64)
-      return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: matrix kind %d not handled by this entry point", c, a.kind);
+    if (a.kind != RSVD_DENSE_F64 && a.kind != RSVD_TILE_RULE)
+      return seterr(RSVD_ERR_INVALID_ARG, "channel %d: matrix kind %d unknown", c, a.kind);
+    if (a.kind != A[0].kind)
+      return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: stored and tile-rule channels in one call", c);
     if (a.n < 1 || a.n > P->o.n_max)
       return seterr(RSVD_ERR_INVALID_ARG, "channel %d: n = %lld outside [1, n_max = %lld]", c, (long long)a.n,
                     (long long)P->o.n_max);
     if (a.n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: n too large", c);
-    if (!a.data) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: data is NULL", c);
-    if (a.ld < a.n) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: ld %lld < n %lld", c, (long long)a.ld, (long long)a.n);
-    if (a.mem != RSVD_MEM_DEVICE && a.mem != RSVD_MEM_HOST) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: bad mem", c);
+    if (a.kind == RSVD_TILE_RULE) {
+      if (P->o.precision != RSVD_PREC_BF16X)
+        return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules are generated on the tensor-core path only", c);
+      if (P->o.rank_policy != RSVD_RANK_FIXED && P->o.rank_policy != RSVD_RANK_TOL)
+        return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules take the fixed or tolerance rank policy", c);
+      if (a.rule_m < 1 || a.rule_m > 4096)
+        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_m %d outside [1, 4096]", c, a.rule_m);
+      if (!a.rule_c || !a.rule_s || !a.rule_w)
+        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule parameter array is NULL", c);
+      for (int m = 0; m < a.rule_m; ++m)
+        if (!std::isfinite(a.rule_c[m]) || !(a.rule_s[m] > 0.0) || !std::isfinite(a.rule_s[m]) ||
+            !(a.rule_w[m] >= 0.0) || !std::isfinite(a.rule_w[m]))
+          return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule term %d needs finite c, s > 0, w >= 0", c, m);
+      if (!(a.rule_eta >= 0.0) || !std::isfinite(a.rule_eta))
+        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_eta must be finite and >= 0", c);
+    } else {
+      if (!a.data) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: data is NULL", c);
+      if (a.ld < a.n)
+        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: ld %lld < n %lld", c, (long long)a.ld, (long long)a.n);
+      if (a.mem != RSVD_MEM_DEVICE && a.mem != RSVD_MEM_HOST)
+        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: bad mem", c);
+    }
     if (F.mem != RSVD_MEM_DEVICE && F.mem != RSVD_MEM_HOST) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: bad factor mem", c);
     if (F.k_cap < 1) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: k_cap %d < 1", c, F.k_cap);
     if (!F.S) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: S is NULL", c);
@@ -1724,6 +1925,7 @@ void init_job(Job& J, rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors*
   J.nsl = P->slices;
   J.policy = P->o.rank_policy == RSVD_RANK_LEARNED ? RSVD_RANK_TOL : P->o.rank_policy;
   J.tol = P->o.tol;
+  J.rule = C > 0 && A[0].kind == RSVD_TILE_RULE;
 }
 
 // Per-channel dims: l from lvec (else k + p, capped at n), s probe columns.
@@ -2119,6 +2321,8 @@ rsvd_status rsvd_probe_features(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, 
     f[c].tol = tol ? tol[c] : 0.0;
   }
   if (rsvd_status s = validate(P, C, A, f.data())) return s;
+  if (A[0].kind == RSVD_TILE_RULE)
+    return seterr(RSVD_ERR_UNSUPPORTED, "probe features are built for stored channels");
   std::vector<float> feat;
   const float* saved = P->o.mlp_weights;
   P->o.mlp_weights = nullptr;
@@ -2126,6 +2330,70 @@ rsvd_status rsvd_probe_features(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, 
   P->o.mlp_weights = saved;
   if (s) return s;
   CK(cudaMemcpy(features, feat.data(), sizeof(float) * C * 19, cudaMemcpyHostToDevice));
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int32_t rows, float* out,
+                           int64_t ldo) {
+  g_err[0] = 0;
+  if (!P || !A || !out) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  if (A->kind != RSVD_TILE_RULE) return seterr(RSVD_ERR_INVALID_ARG, "matrix is not a tile rule");
+  const rsvd_matrix& a = *A;
+  if (a.n < 1 || a.n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "n = %lld out of range", (long long)a.n);
+  if (a.rule_m < 1 || a.rule_m > 4096) return seterr(RSVD_ERR_INVALID_ARG, "rule_m %d outside [1, 4096]", a.rule_m);
+  if (!a.rule_c || !a.rule_s || !a.rule_w) return seterr(RSVD_ERR_INVALID_ARG, "rule parameter array is NULL");
+  for (int m = 0; m < a.rule_m; ++m)
+    if (!std::isfinite(a.rule_c[m]) || !(a.rule_s[m] > 0.0) || !std::isfinite(a.rule_s[m]) || !(a.rule_w[m] >= 0.0) ||
+        !std::isfinite(a.rule_w[m]))
+      return seterr(RSVD_ERR_INVALID_ARG, "rule term %d needs finite c, s > 0, w >= 0", m);
+  if (!(a.rule_eta >= 0.0) || !std::isfinite(a.rule_eta)) return seterr(RSVD_ERR_INVALID_ARG, "bad rule_eta");
+  if (r0 < 0 || rows < 1 || r0 + rows > a.n)
+    return seterr(RSVD_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, n)", (long long)r0, (long long)(r0 + rows));
+  if (ldo < a.n) return seterr(RSVD_ERR_INVALID_ARG, "ldo < n");
+  const int n = (int)a.n, M = a.rule_m;
+  const int64_t ldh = rule_ldh(M);
+  // workspace: H words, parameters, one descriptor
+  const size_t hbytes = ((size_t)n * ldh * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
+  const size_t pbytes = ((3 * (size_t)M * sizeof(double)) + 255) & ~(size_t)255;
+  if (rsvd_status s = grow_ws(P, 3 * hbytes + pbytes + sizeof(TcChan) + 256)) return s;
+  __nv_bfloat16* H[3];
+  for (int w = 0; w < 3; ++w) H[w] = (__nv_bfloat16*)(P->ws + w * hbytes);
+  double* dpar = (double*)(P->ws + 3 * hbytes);
+  TcChan* dtc = (TcChan*)(P->ws + 3 * hbytes + pbytes);
+  if (rsvd_status s = grow_pinned(P, pbytes + sizeof(TcChan) + 64)) return s;
+  double* hpar = (double*)P->hp;
+  memcpy(hpar, a.rule_c, sizeof(double) * M);
+  memcpy(hpar + M, a.rule_s, sizeof(double) * M);
+  memcpy(hpar + 2 * M, a.rule_w, sizeof(double) * M);
+  TcChan* htc = (TcChan*)(P->hp + pbytes);
+  memset(htc, 0, sizeof(TcChan));
+  const int gbn = std::min(128, (int)rup(rows, 16));
+  const __nv_bfloat16* HA[3] = {H[0], H[1], H[2]};
+  const __nv_bfloat16* HX[3] = {H[0] + r0 * ldh, H[1] + r0 * ldh, H[2] + r0 * ldh};
+  if (int e = tc_encode(htc, HA, 3, ldh, HX, 3, ldh, n, M, rows, gbn))
+    return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
+  htc->Y = out; htc->ldy = ldo;
+  htc->n = M; htc->m = n; htc->ncols = rows;
+  htc->mt = cdiv(n, 128); htc->nt = cdiv(rows, gbn); htc->ks = 1; htc->kt_per_split = cdiv(M, 64);
+  htc->mode = TC_RULE;
+  htc->chunk_kt = 1;
+  htc->nw = 0; htc->r0 = (int)r0;
+  htc->eta_key = rule_key(a.rule_seed);
+  htc->eta_amp3 = (float)(a.rule_eta * 1.7320508075688772);
+  CK(cudaMemcpyAsync(dpar, hpar, pbytes, cudaMemcpyHostToDevice, P->st));
+  CK(cudaMemcpyAsync(dtc, htc, sizeof(TcChan), cudaMemcpyHostToDevice, P->st));
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  RuleDesc rdsc{};
+  rdsc.n = n; rdsc.M = M; rdsc.c = dpar; rdsc.s = dpar + M; rdsc.w = dpar + 2 * M;
+  for (int w = 0; w < 3; ++w) rdsc.H[w] = H[w];
+  rdsc.ldh = ldh;
+  launch_rule_prep(rdsc, P->st);
+  if (int e = tc_launch(dtc, 1, htc->mt * htc->nt, 3, 3, gbn, P->d_err, P->st))
+    return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  if (herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", herr);
   return RSVD_OK;
 }
 

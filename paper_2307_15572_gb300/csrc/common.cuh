@@ -12,6 +12,7 @@
 #include "../../include/rsvd.h"
 
 #define RSVD_DEV __device__ __forceinline__
+#define RSVD_HD __host__ __device__ __forceinline__
 
 namespace rsvd {
 
@@ -128,6 +129,31 @@ enum : int { DERR_NONE = 0, DERR_TIMEOUT_TMA = 1, DERR_TIMEOUT_MMA = 2, DERR_TIM
 
 RSVD_DEV void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Tile-rule noise: the 32-bit "lowbias32" integer hash (C. Wellons, "Hash
+// function prospector", 2018) and the symmetric entry noise built from it,
+//   h = mix(mix(min(i,j) * 0x9E3779B1 + key) ^ (max(i,j) * 0x85EBCA77)),
+//   eta_ij = a sqrt(3) (2 u - 1),  u = ((h >> 8) + 1/2) 2^-24,
+// uniform with standard deviation a; key = mix(seed_lo ^ mix(seed_hi)).
+RSVD_HD uint32_t lowbias32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// 2u - 1 = (2 (h >> 8) + 1 - 2^24) 2^-24: the numerator is an odd integer
+// below 2^24 in magnitude, so the FP32 value is exact.
+RSVD_DEV float rule_eta(uint32_t key, float amp3, int i, int j) {
+  const uint32_t lo = (uint32_t)min(i, j), hi = (uint32_t)max(i, j);
+  uint32_t h = lowbias32(lo * 0x9E3779B1u + key);
+  h = lowbias32(h ^ (hi * 0x85EBCA77u));
+  const int num = 2 * (int)(h >> 8) + 1 - (1 << 24);
+  return amp3 * ((float)num * 5.9604644775390625e-8f);
 }
 
 // Per-channel results written by the device and read once by the host.

@@ -1,4 +1,8 @@
-// Tensor-core passes over V for the mixed path: Y = V X on sm_103a.
+// Tensor-core passes over V for the mixed path: Y = V X on sm_103a.  The
+// same kernel also generates the entries of a tile rule (TC_RULE): with H the
+// n x M matrix of sqrt(w_m) g_m(x_j) in BF16 words, a panel of rule rows is
+// H H_panel^T, to which the epilogue adds the hash noise before splitting the
+// entries into the words the next pass reads.
 //
 // This is the contraction of Fig. 1 step 1 (Z = V P) and of the projection
 // (Y^T = V Q, V symmetric) when V is held as a sum of BF16 words,
@@ -152,6 +156,8 @@ RSVD_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 // warps add it into FP32 registers (round to nearest) while the next chunk
 // runs in the other buffer.  The bias is then bounded by one chunk's worth
 // (4 * CHUNK_KT truncations, ~2e-6), and the register sum is unbiased.
+// A channel may ask for shorter chunks (chunk_kt): the tile-rule generator,
+// whose k extent is only M, takes one 64-wide step per chunk.
 static constexpr int CHUNK_KT = 8;
 static constexpr int BN_MAX = 160;            // register accumulator width
 static constexpr int NTHREADS = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
@@ -187,7 +193,8 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
   const int kt_total = (ch->n + BK - 1) / BK;
   const int kb = split * ch->kt_per_split;
   const int nk = min(kt_total, kb + ch->kt_per_split) - kb;
-  const int nchunks = (nk + CHUNK_KT - 1) / CHUNK_KT;
+  const int chunk = ch->chunk_kt > 0 ? ch->chunk_kt : CHUNK_KT;
+  const int nchunks = (nk + chunk - 1) / chunk;
   uint32_t ncols_alloc = 32;
   while ((int)ncols_alloc < 2 * bn) ncols_alloc <<= 1;
 
@@ -243,7 +250,7 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
           }
           tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)(b * bn);
-          const int itend = min(nk, it + CHUNK_KT);
+          const int itend = min(nk, it + chunk);
           for (; it < itend; ++it) {
             const int s = it % stages;
             const uint32_t ph = (uint32_t)(it / stages) & 1u;
@@ -251,18 +258,24 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
             tc_fence_after();
             const uint32_t sa0 = smem_addr(base + (size_t)s * SB);
             const uint32_t sx0 = sa0 + SA * A_TILE_BYTES;
-            const bool first = (it == c * CHUNK_KT);
+            bool zero = (it == c * chunk);          // first MMA of the chunk overwrites
+            // small word products first, the leading pair (0, 0) last: the
+            // round-toward-zero accumulation then loses least while the
+            // running sum is small
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
+            for (int pr = (SA > SX ? SA : SX) - 1; pr >= 0; --pr) {
 #pragma unroll
               for (int a = 0; a < SA; ++a) {
 #pragma unroll
                 for (int x = 0; x < SX; ++x) {
-                  if (a + x >= (SA > SX ? SA : SX)) continue;
-                  const uint64_t ad = sdesc_sw128(sa0 + a * A_TILE_BYTES + kk * 32);
-                  const uint64_t bd = sdesc_sw128(sx0 + x * bn * BK * 2 + kk * 32);
-                  const uint32_t acc = (first && kk == 0 && a == 0 && x == 0) ? 0u : 1u;
-                  mma_bf16(dt, ad, bd, idesc, acc);
+                  if (a + x != pr) continue;
+#pragma unroll
+                  for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint64_t ad = sdesc_sw128(sa0 + a * A_TILE_BYTES + kk * 32);
+                    const uint64_t bd = sdesc_sw128(sx0 + x * bn * BK * 2 + kk * 32);
+                    mma_bf16(dt, ad, bd, idesc, zero ? 0u : 1u);
+                    zero = false;
+                  }
                 }
               }
             }
@@ -306,7 +319,60 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
       healthy = __shfl_sync(0xffffffffu, healthy, 0);
       if (healthy) {
         const int row = m0 + warp * 32 + lane;
-        if (row < ch->n) {
+        if (ch->mode == TC_RULE) {
+          // generated tile-rule entries: add the symmetric noise, split into
+          // BF16 words, and keep the energy and the words' remainder
+          float s2 = 0.0f, r2 = 0.0f;
+          if (row < ch->m) {
+            float* Y = ch->Y;
+            const int64_t ldy = ch->ldy, ldw = ch->ldw;
+            const int ncols = ch->ncols, nw = ch->nw, r0 = ch->r0;
+            const uint32_t key = ch->eta_key;
+            const float amp3 = ch->eta_amp3;
+            __nv_bfloat16* W0 = ch->W[0];
+            __nv_bfloat16* W1 = ch->W[1];
+            __nv_bfloat16* W2 = ch->W[2];
+#pragma unroll
+            for (int j = 0; j < BN_MAX; ++j) {
+              const int col = n0 + j;
+              if (j < bn && col < ncols) {
+                const float v = acc[j] + rule_eta(key, amp3, r0 + col, row);
+                s2 = fmaf(v, v, s2);
+                if (nw > 0) {
+                  const int64_t o = row + (int64_t)col * ldw;
+                  __nv_bfloat16 q = __float2bfloat16_rn(v);
+                  W0[o] = q;
+                  float rem = v - __bfloat162float(q);      // exact
+                  if (nw > 1) {
+                    q = __float2bfloat16_rn(rem);
+                    W1[o] = q;
+                    rem -= __bfloat162float(q);
+                    if (nw > 2) {
+                      q = __float2bfloat16_rn(rem);
+                      W2[o] = q;
+                      rem -= __bfloat162float(q);
+                    }
+                  }
+                  r2 = fmaf(rem, rem, r2);
+                }
+                if (Y) Y[row + (int64_t)col * ldy] = v;
+              }
+            }
+          }
+          if (ch->part) {
+            double ds = (double)s2, dr = (double)r2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              ds += __shfl_xor_sync(0xffffffffu, ds, o);
+              dr += __shfl_xor_sync(0xffffffffu, dr, o);
+            }
+            if (lane == 0) {
+              double* pp = ch->part + ((int64_t)(item - ch->item0) * 4 + warp) * 2;
+              pp[0] = ds;
+              pp[1] = dr;
+            }
+          }
+        } else if (row < ch->m) {
           float* Y = ch->Y;
           const int64_t ldy = ch->ldy;
           const int ncols = ch->ncols;
@@ -358,10 +424,10 @@ static int encode2d(CUtensorMap* m, const void* ptr, int64_t inner, int64_t oute
 }
 
 int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda, const __nv_bfloat16* const* X,
-              int sx, int64_t ldx, int n, int ncols, int bn) {
+              int sx, int64_t ldx, int m, int n, int ncols, int bn) {
   if (get_encode()) return -1;
   for (int a = 0; a < sa; ++a)
-    if (int e = encode2d(&h->tmA[a], A[a], n, n, lda, BM)) return e;
+    if (int e = encode2d(&h->tmA[a], A[a], n, m, lda, BM)) return e;
   for (int x = 0; x < sx; ++x)
     if (int e = encode2d(&h->tmX[x], X[x], n, ncols, ldx, bn)) return e;
   return 0;

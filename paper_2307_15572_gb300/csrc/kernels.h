@@ -95,6 +95,18 @@ void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st);
 // out[c][j] = sum of squares of column j of the block (one block per column).
 void launch_colsumsq(const SumsqDesc* d_sd, int C, int max_cols, cudaStream_t st);
 
+// --------------------------------------------------------------- tile rule
+// H (n x M, ldh) = sqrt(w_m) g_m(x_j) as three BF16 words of its FP32 value.
+struct RuleDesc {
+  int n, M;
+  const double *c, *s, *w;   // device, M each
+  __nv_bfloat16* H[3];
+  int64_t ldh;
+};
+void launch_rule_prep(const RuleDesc& d, cudaStream_t st);
+void launch_rule_part_sum(const double* part, int nparts, double* out, cudaStream_t st);
+void launch_rule_finish(const double* sums, int npanels, ChanResult* res, cudaStream_t st);
+
 // --------------------------------------------------------- mixed-path kernels
 void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int tiles, int nsl,
                            cudaStream_t st);

@@ -9,22 +9,38 @@ namespace rsvd {
 
 // Per-channel operand maps and output of one grouped launch.  Must be 64-byte
 // aligned (CUtensorMap is), lives in device memory.
+enum TcMode { TC_STORE = 0, TC_RULE = 1 };
+
 struct alignas(64) TcChan {
-  CUtensorMap tmA[3];   // V slices: dims {n (k), n (m)}, box {64, 128}, 128B swizzle
-  CUtensorMap tmX[3];   // X slices: dims {n (k), ncols (n)}, box {64, BN}, 128B swizzle
-  float* Y;             // output, column-major n x ncols, leading dim ldy
+  CUtensorMap tmA[3];   // A operand words: dims {n (k), m (rows)}, box {64, 128}, 128B swizzle
+  CUtensorMap tmX[3];   // X words: dims {n (k), ncols}, box {64, BN}, 128B swizzle
+  float* Y;             // output, column-major m x ncols, leading dim ldy (TC_RULE: optional copy)
   int64_t ldy;
-  int n;                // rows of V (= k extent)
+  int n;                // k extent
+  int m;                // rows of the A operand and of Y
   int ncols;            // output columns
   int mt, nt, ks;       // tiles along m (128), n (BN), k splits
   int kt_per_split;     // 64-wide k steps per split
   int item0;            // first work item of this channel
   int atomic;           // 1: accumulate with red.add (k split), 0: store
+  int mode;             // TcMode
+  int chunk_kt;         // 64-wide k steps per TMEM accumulation chunk (0: the default, 8)
+  // TC_RULE (generated entries of a tile rule; ks must be 1): output element
+  // (row, col) is the matrix entry (r0 + col, row); v = acc + eta is split
+  // into nw BF16 words W[w][row + col * ldw], and each (work item, epilogue
+  // warp) writes {sum v^2, sum (v - words)^2} to part (if non-null).
+  __nv_bfloat16* W[3];
+  int64_t ldw;
+  int nw;
+  int r0;
+  uint32_t eta_key;
+  float eta_amp3;       // sqrt(3) * eta amplitude
+  double* part;
 };
 
 // Encode the maps of one channel (host).  Returns 0 on success.
 int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda_elems,
-              const __nv_bfloat16* const* X, int sx, int64_t ldx_elems, int n, int ncols,
+              const __nv_bfloat16* const* X, int sx, int64_t ldx_elems, int m, int n, int ncols,
               int bn);
 
 // Shared memory bytes per stage and stage count for a configuration.

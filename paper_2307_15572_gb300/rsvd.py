@@ -113,6 +113,8 @@ def load(build=True):
     lib.rsvd_reconstruct_error_noalloc.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int64, P, P, C.c_int64,
                                                    C.c_int32, P, P]
     lib.rsvd_reconstruct_error_noalloc.restype = C.c_int
+    lib.rsvd_rule_rows.argtypes = [P, C.POINTER(Matrix), C.c_int64, C.c_int32, P, C.c_int64]
+    lib.rsvd_rule_rows.restype = C.c_int
     _lib = lib
     return lib
 
@@ -207,6 +209,11 @@ def rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, str
     return load().rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, stream)
 
 
+def rsvd_rule_rows(h, mat, r0, rows, out, ldo):
+    """Rows r0..r0+rows-1 of a tile rule into the device FP32 buffer `out` (row-major, ld ldo)."""
+    return _check(load().rsvd_rule_rows(h, C.byref(mat), int(r0), int(rows), out, int(ldo)))
+
+
 def rsvd_reconstruct_error(h, mat, fac):
     out = C.c_double()
     _check(load().rsvd_reconstruct_error(h, C.byref(mat), C.byref(fac), C.byref(out)))
@@ -256,6 +263,25 @@ def dense(A):
     return m
 
 
+def rule(n, c, s, w, eta=0.0, seed=0):
+    """Descriptor of a tile-rule channel; the host parameter arrays are kept
+    alive on the returned object."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (c, s, w)]
+    assert arrs[0].shape == arrs[1].shape == arrs[2].shape and arrs[0].ndim == 1
+    m = Matrix()
+    m.kind = TILE_RULE
+    m.mem = MEM_DEVICE
+    m.n = int(n)
+    m.data = None
+    m.ld = int(n)
+    m.rule_m = arrs[0].shape[0]
+    m.rule_c, m.rule_s, m.rule_w = (a.ctypes.data for a in arrs)
+    m.rule_eta = float(eta)
+    m.rule_seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    m._keep = arrs
+    return m
+
+
 class Plan:
     """Plan plus torch-allocated output buffers; see include/rsvd.h for the semantics."""
 
@@ -293,8 +319,9 @@ class Plan:
         """mats: list of torch CUDA FP64 tensors.  Returns (status, [result dicts])."""
         descs, facs, bufs = [], [], []
         for A in mats:
-            descs.append(dense(A))
-            f, b = self.factors_for(A.shape[0], min(k_cap, A.shape[0]))
+            descs.append(A if isinstance(A, Matrix) else dense(A))
+            n = descs[-1].n
+            f, b = self.factors_for(n, min(k_cap, n))
             facs.append(f)
             bufs.append(b)
         r, per = rsvd_decompose_batched(self.h, descs, facs)
@@ -310,4 +337,4 @@ class Plan:
         return r, out[0]
 
     def reconstruct_error(self, A, res):
-        return rsvd_reconstruct_error(self.h, dense(A), res["_fac"])
+        return rsvd_reconstruct_error(self.h, A if isinstance(A, Matrix) else dense(A), res["_fac"])
