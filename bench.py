@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--rule-steps", type=int, default=2)
+    ap.add_argument("--rule-n", type=int, default=200000)
+    ap.add_argument("--no-rule", action="store_true")
     return ap.parse_args()
 
 
@@ -74,7 +77,8 @@ def dist_setup(args):
 
 def workload_sizes(args, rank):
     from paper_2307_15572_gb300 import synth
-    seed = synth.SEED_BATCH + rank
+    from paper_2307_15572_gb300 import shard
+    seed = shard.rank_seed(synth.SEED_BATCH, rank)
     return synth.batch_sizes(args.channels, args.nmin, args.nmax, seed=seed), seed
 
 
@@ -89,6 +93,15 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured (burst)"
+    return 1900.0, "fallback"
 
 
 def tc_traffic_record():
@@ -202,19 +215,11 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    from paper_2307_15572_gb300 import shard
 
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    def reduce_runs(ent, ms_):
+        """(entries of all ranks, slowest rank's time): timing only, no data."""
+        return shard.reduce_timing(dist, ent, ms_, device="cuda")
 
     descs = [rsvd.dense(A) for A in mats]
 
@@ -256,8 +261,8 @@ def run_gpu(args):
     facs, bufs = alloc_factors()
     ms, wall, prof, clk = timed_steps(plan, facs, args.steps, args.warmup, descs, clocks=(rank == 0))
     max_err, ks = verify(plan, facs)
-    ms_max = max_over_ranks(ms)
-    value = sum_over_ranks(entries * args.steps) / (ms_max / 1e3)
+    tot, ms_max = reduce_runs(entries * args.steps, ms)
+    value = tot / (ms_max / 1e3)
     hbm_peak, peak_kind = peaks()
     tc_ms_per = prof["tc_ms"] / max(1, prof["tc_launches"])
     tc_bytes_per = prof["tc_bytes"] / max(1, prof["tc_launches"])
@@ -286,8 +291,8 @@ def run_gpu(args):
         ms_e, wall_e, prof_e, _ = timed_steps(plan, hf, args.e2e_steps, 1, hdescs)
         h2d = sum(8 * n * n for n in sizes)
         d2h = sum(8 * (2 * f.k_out * n + f.k_out) for f, n in zip(hf, sizes))
-        ms_e = max_over_ranks(ms_e)
-        e2e = {"value": sum_over_ranks(entries * args.e2e_steps) / (ms_e / 1e3), "unit": UNIT,
+        tot_e, ms_e = reduce_runs(entries * args.e2e_steps, ms_e)
+        e2e = {"value": tot_e / (ms_e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "ms_per_step": ms_e / args.e2e_steps}
         plan.close()
@@ -301,16 +306,54 @@ def run_gpu(args):
         ff, fb = alloc_factors()
         ms_f, wall_f, prof_f, _ = timed_steps(plan, ff, args.fp64_steps, 1, descs)
         err_f, ks_f = verify(plan, ff)
-        ms_f = max_over_ranks(ms_f)
+        tot_f, ms_f = reduce_runs(entries * args.fp64_steps, ms_f)
         f64_ms = prof_f["f64_ms"] / max(1, prof_f["f64_launches"])
         f64_tf = prof_f["f64_flops"] / max(1, prof_f["f64_launches"]) / (f64_ms / 1e3) / 1e12 if f64_ms else 0
-        fp64 = {"value": sum_over_ranks(entries * args.fp64_steps) / (ms_f / 1e3), "unit": UNIT,
+        fp64 = {"value": tot_f / (ms_f / 1e3), "unit": UNIT,
                 "ms_per_step": ms_f / args.fp64_steps, "steps": args.fp64_steps, "max_rel_err": err_f,
                 "ranks": [min(ks_f), max(ks_f)],
                 "roofline": {"bound": "alu", "kernel": "k_tile_mm<double> (FP64 pass over V)",
                              "achieved": f64_tf, "peak": 1.25, "unit": "TFLOP/s", "frac": f64_tf / 1.25,
                              "peak_source": "nominal FP64 rate of GB300"}}
         plan.close()
+
+    # ---- matrix-free tile rule: n = 200,000, M = 300 bumps, k = 320, p = 10, q = 1
+    rule = None
+    if not args.no_rule:
+        from paper_2307_15572_gb300 import synth
+        rn, rM, rk, rp, rq = args.rule_n, 300, 320, 10, 1
+        c_, s_, w_ = synth.rule_params(M=rM, seed=synth.SEED_RULE)
+        rm = rsvd.rule(rn, c_, s_, w_, eta=1e-7, seed=synth.SEED_RULE)
+        plan = rsvd.Plan(rn, k=rk, p=rp, q=rq, seed=seed, precision="bf16x", slices=2, policy="fixed",
+                         stream=stream.cuda_stream)
+        rsvd.rsvd_plan_set_profiling(plan.h, True)
+        rf, rb = rsvd.Plan.factors_for(rn, rk)
+        rfl = [rf]
+        ms_r, wall_r, prof_r, _ = timed_steps(plan, rfl, args.rule_steps, 1, [rm])
+        rf = rfl[0]                       # the call returns its results in the list
+        tot_r, ms_r = reduce_runs(float(rn) * rn * args.rule_steps, ms_r)
+        g_ms = prof_r["gen_ms"] / max(1, prof_r["gen_launches"])
+        g_alg = prof_r["gen_flops"] / max(1, prof_r["gen_launches"])
+        g_mma = prof_r["gen_mma_flops"] / max(1, prof_r["gen_launches"])
+        bpk, bsrc = bf16_peak()
+        rule = {"value": tot_r / (ms_r / 1e3), "unit": UNIT,
+                "ms_per_step": ms_r / args.rule_steps, "steps": args.rule_steps,
+                "workload": "rule: Gaussian-bump tile rule, n = %d, M = 300, w_m = e^-m/25, hash noise 1e-7; "
+                            "k = 320, p = 10, q = 1, 2 words; every pass generates its entries" % rn,
+                "err_est": rf.err_est, "status": int(rf.status), "k": rf.k_out,
+                "passes_per_step": 2 * rq + 2,
+                "roofline": {"bound": "tensor", "kernel": "k_tc_gemm<3,3> (TC_RULE generation)",
+                             "achieved": g_mma / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
+                             "peak": bpk, "unit": "TFLOP/s",
+                             "frac": (g_mma / (g_ms / 1e3) / 1e12) / bpk if g_ms else 0.0,
+                             "achieved_algorithmic": g_alg / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
+                             "peak_source": bsrc, "launches": prof_r["gen_launches"], "avg_launch_ms": g_ms,
+                             "share_of_step": prof_r["gen_ms"] / ms_r if ms_r else None,
+                             "note": "achieved counts the issued BF16 word products (6 per entry term, "
+                                     "M padded to 320); achieved_algorithmic counts 2 M flops per entry"},
+                "product_pass_ms": prof_r["tc_ms"] / max(1, prof_r["tc_launches"])}
+        plan.close()
+        del rb
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -332,7 +375,7 @@ def run_gpu(args):
                           "verified_tol": bool(max_err <= TOL), "ranks": [min(ks), max(ks)],
                           "parallelism": "channels per GPU" if ws > 1 else "single GPU"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-               "clocks": clk, "fp64_path": fp64,
+               "clocks": clk, "fp64_path": fp64, "rule_path": rule,
                "mixed_over_fp64": (value / fp64["value"]) if fp64 else None}
         print(json.dumps(out), flush=True)
     if dist is not None:

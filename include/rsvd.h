@@ -212,6 +212,10 @@ typedef struct {
   int64_t f64_launches;    /* FP64 dense passes over V                           */
   double f64_ms;
   double f64_flops;        /* 2 n^2 l per pass                                   */
+  int64_t gen_launches;    /* tile-rule generation launches (one per row panel)  */
+  double gen_ms;
+  double gen_flops;        /* algorithmic: 2 M per generated entry               */
+  double gen_mma_flops;    /* issued: 6 word products x 2 x (M padded to 64)     */
 } rsvd_profile;
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);

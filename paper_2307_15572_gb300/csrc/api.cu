@@ -85,7 +85,7 @@ struct rsvd_plan_s {
   int profiling = 0;
   rsvd_profile prof{};
   std::vector<cudaEvent_t> ev_pool;
-  struct Timed { cudaEvent_t a, b; int kind; double bytes, flops; };
+  struct Timed { cudaEvent_t a, b; int kind; double bytes, flops; };   // kind 0 tc, 1 FP64, 2 rule generation
   std::vector<Timed> pending;
   size_t ev_next = 0;
   long long launch_base = 0;
@@ -161,6 +161,7 @@ void drain_profile(rsvd_plan_s* P) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, t.a, t.b);
     if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
+    else if (t.kind == 2) { P->prof.gen_launches++; P->prof.gen_ms += ms; P->prof.gen_flops += t.flops; P->prof.gen_mma_flops += t.bytes; }
     else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
   }
   P->pending.clear();
@@ -616,7 +617,8 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
       const int gitems = g.mt * g.nt, titems = t.mt * t.nt;
       const TcChan* dg = J.ar.put(&g, 1, 128);
       const TcChan* dt = J.ar.put(&t, 1, 128);
-      const double gflops = 2.0 * d.n * (double)rows * r.ldh * 6;
+      const double gflops = 2.0 * d.n * (double)rows * r.M;                // algorithmic
+      const double gmma = 2.0 * d.n * (double)rows * r.ldh * 6;            // issued word products
       double tpairs = 0;
       for (int a = 0; a < nsl; ++a)
         for (int x = 0; x < sx; ++x) tpairs += (a + x < std::max(nsl, sx));
@@ -629,12 +631,17 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
         if (P->profiling) timed_begin(P, &ea, &eb);
         int e = tc_launch(dg, 1, gitems, 3, 3, gbn, derr, st);
         if (e) return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
+        if (P->profiling) {
+          cudaEventRecord(eb, st);
+          P->pending.push_back({ea, eb, 2, gmma, gflops});
+        }
         if (first) launch_rule_part_sum(part, gitems * 4, psum, st);
+        if (P->profiling) timed_begin(P, &ea, &eb);
         e = tc_launch(dt, 1, titems, nsl, sx, bn, derr, st);
         if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
         if (P->profiling) {
           cudaEventRecord(eb, st);
-          P->pending.push_back({ea, eb, 0, tbytes, tflops + gflops});
+          P->pending.push_back({ea, eb, 0, tbytes, tflops});
         }
         return RSVD_OK;
       });
