@@ -89,7 +89,18 @@ struct rsvd_plan_s {
   std::vector<Timed> pending;
   size_t ev_next = 0;
   long long launch_base = 0;
+  // CUDA graphs of whole decompositions, keyed by everything that shapes the
+  // launch sequence (descriptor contents are re-uploaded by the first node)
+  int graphs = 0;
+  struct GraphEntry { std::string key; cudaGraphExec_t exec; long long launches; uint64_t used; };
+  std::vector<GraphEntry> gcache;
+  uint64_t gclock = 0;
 };
+
+void drop_graphs(rsvd_plan_s* P) {
+  for (auto& g : P->gcache) cudaGraphExecDestroy(g.exec);
+  P->gcache.clear();
+}
 
 namespace {
 
@@ -122,6 +133,8 @@ struct Arena {
 
 rsvd_status grow_pinned(rsvd_plan_s* P, size_t bytes) {
   if (bytes <= P->hp_cap) return RSVD_OK;
+  CK(cudaStreamSynchronize(P->st));
+  drop_graphs(P);                        // their copy nodes name the old buffer
   if (P->hp) cudaFreeHost(P->hp);
   P->hp = nullptr;
   P->hp_cap = 0;
@@ -134,6 +147,7 @@ rsvd_status grow_pinned(rsvd_plan_s* P, size_t bytes) {
 rsvd_status grow_ws(rsvd_plan_s* P, size_t bytes) {
   if (bytes <= P->ws_cap) return RSVD_OK;
   CK(cudaStreamSynchronize(P->st));
+  drop_graphs(P);                        // their launches name the old workspace
   if (P->ws) cudaFree(P->ws);
   P->ws = nullptr;
   P->ws_cap = 0;
@@ -201,6 +215,8 @@ struct Job {
   int max_l = 0, max_lw = 0, max_kcap = 0;
   // tile-rule channels (all channels of the job, or none)
   bool rule = false;
+  bool skip_convert = false;            // V words reused from a probe job
+  bool probe_job = false;
   int panel = 0;                        // rows of A generated per panel
   struct RuleDev {
     __nv_bfloat16* H[3];
@@ -488,10 +504,16 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
   bool any_split = false;
   std::vector<ZeroDesc> zd(J.C);
   int item = 0;
-  for (int c = 0; c < J.C; ++c) {
+  // items numbered longest first: the persistent CTAs take items round-robin,
+  // so this order balances them (longest-processing-time-first)
+  std::vector<int> order(J.C);
+  for (int c = 0; c < J.C; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return J.d[a].n > J.d[b].n; });
+  for (int pos = 0; pos < J.C; ++pos) {
+    const int c = order[pos];
     const ChanDims& d = J.d[c];
     const int nc = ncols_of(c);
-    TcChan& t = tcs[c];
+    TcChan& t = tcs[pos];
     memset(&t, 0, sizeof(t));
     const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
     const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
@@ -605,7 +627,7 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
       g.n = r.M; g.m = d.n; g.ncols = rows;
       g.mt = cdiv(d.n, 128); g.nt = cdiv(rows, gbn); g.ks = 1; g.kt_per_split = cdiv(r.M, 64);
       g.mode = TC_RULE;
-      g.chunk_kt = 1;
+      g.chunk_kt = 1;              // each 64-wide step from zero: round-toward-zero bias ~2e-7
       for (int w = 0; w < nsl; ++w) g.W[w] = J.pw[w];
       g.ldw = d.ldb; g.nw = nsl; g.r0 = r0;
       g.eta_key = r.key; g.eta_amp3 = r.amp3;
@@ -770,7 +792,7 @@ Chan* reorth_x(Job& J) {
     const int C = J.C, maxl = J.max_l;
     cudaStream_t st = J.P->st;
     J.steps.push_back([=]() {
-      launch_chol_inv(dsw, C, 0, maxl, 0, st, 0);
+      launch_chol_inv(dsw, C, 0, maxl, 0, st, 1);   // X^T X ~ I: an FP32 factor is enough
       return RSVD_OK;
     });
   }
@@ -1976,6 +1998,8 @@ enum JobKind { JOB_MAIN = 0, JOB_PROBE = 1 };
 struct ProbeOut { float* feat = nullptr; float* pred = nullptr; };
 rsvd_status build_job(Job& J, char* base, JobKind kind, bool skip_convert, size_t* need, ProbeOut* po) {
   Bump b(base);
+  J.skip_convert = skip_convert;
+  J.probe_job = kind == JOB_PROBE;
   J.measure = base == nullptr;
   layout(J, b);
   float* d_feat = nullptr;
@@ -2005,31 +2029,91 @@ rsvd_status build_job(Job& J, char* base, JobKind kind, bool skip_convert, size_
 }
 
 // Upload descriptors, stage host inputs (unless reused), run, read results.
+// Everything that shapes a job's launch sequence: sizes, options, buffers.
+std::string graph_key(const Job& J, bool stage_inputs) {
+  const rsvd_plan_s* P = J.P;
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  auto put64 = [&](int64_t v) { put(&v, sizeof(v)); };
+  put64(J.C); put64((int64_t)(uintptr_t)P->ws); put64((int64_t)(uintptr_t)P->hp); put64((int64_t)J.ar.h.size());
+  put64(J.mixed); put64(J.skip_convert); put64(J.probe_job); put64(stage_inputs); put64(J.q); put64(J.nsl);
+  put64(J.policy); put(&J.tol, sizeof(J.tol)); put64(P->o.rayleigh_ritz); put64((int64_t)(uintptr_t)P->o.mlp_weights);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    const int64_t v[] = {d.n, d.l, d.lw, d.s, d.kcap, d.gsplit, d.ldt, d.ldb};
+    put(v, sizeof(v));
+    if (stage_inputs && J.A[c].mem == RSVD_MEM_HOST) { put64((int64_t)(uintptr_t)J.A[c].data); put64(J.A[c].ld); }
+  }
+  return k;
+}
+
+// Upload descriptors, stage host inputs (unless reused), run, read results.
+// With graphs on (and a capturable stream), the whole sequence is captured
+// once per key and replayed; the first node re-uploads the descriptors, so a
+// replay sees this call's pointers.
 rsvd_status execute(Job& J, bool stage_inputs, std::vector<ChanResult>& res) {
   rsvd_plan_s* P = J.P;
   const int C = J.C;
   if (rsvd_status s = grow_pinned(P, std::max(J.ar.h.size(), sizeof(ChanResult) * C) + 64)) return s;
-  CK(cudaMemsetAsync(J.d_res, 0, sizeof(ChanResult) * C, P->st));
   memcpy(P->hp, J.ar.h.data(), J.ar.h.size());
-  CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
-  if (stage_inputs)
-    for (int c = 0; c < C; ++c)
-      if (J.A[c].mem == RSVD_MEM_HOST) {
-        const size_t row = (size_t)J.d[c].n * sizeof(double);
-        if (J.A[c].ld == J.d[c].n)
-          CK(cudaMemcpyAsync((void*)J.ch[c].A, J.A[c].data, row * J.d[c].n, cudaMemcpyHostToDevice, P->st));
-        else
-          CK(cudaMemcpy2DAsync((void*)J.ch[c].A, row, J.A[c].data, (size_t)J.A[c].ld * sizeof(double), row,
-                               J.d[c].n, cudaMemcpyHostToDevice, P->st));
-      }
-  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
-  for (auto& step : J.steps)
-    if (rsvd_status s = step()) return s;
-  CK(cudaGetLastError());
   ChanResult* hres = (ChanResult*)P->hp;
-  CK(cudaMemcpyAsync(hres, J.d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost, P->st));
   int* herr = (int*)(P->hp + ((sizeof(ChanResult) * C + 63) & ~(size_t)63));
-  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  auto enqueue = [&]() -> rsvd_status {
+    CK(cudaMemsetAsync(J.d_res, 0, sizeof(ChanResult) * C, P->st));
+    CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
+    if (stage_inputs)
+      for (int c = 0; c < C; ++c)
+        if (J.A[c].mem == RSVD_MEM_HOST && J.A[c].kind == RSVD_DENSE_F64) {
+          const size_t row = (size_t)J.d[c].n * sizeof(double);
+          if (J.A[c].ld == J.d[c].n)
+            CK(cudaMemcpyAsync((void*)J.ch[c].A, J.A[c].data, row * J.d[c].n, cudaMemcpyHostToDevice, P->st));
+          else
+            CK(cudaMemcpy2DAsync((void*)J.ch[c].A, row, J.A[c].data, (size_t)J.A[c].ld * sizeof(double), row,
+                                 J.d[c].n, cudaMemcpyHostToDevice, P->st));
+        }
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+    for (auto& step : J.steps)
+      if (rsvd_status s = step()) return s;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hres, J.d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost, P->st));
+    CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+    return RSVD_OK;
+  };
+  const bool use_graph = P->graphs && !P->profiling && !J.rule && P->st != nullptr;
+  if (!use_graph) {
+    if (rsvd_status s = enqueue()) return s;
+  } else {
+    const std::string key = graph_key(J, stage_inputs);
+    rsvd_plan_s::GraphEntry* ge = nullptr;
+    for (auto& g : P->gcache)
+      if (g.key == key) ge = &g;
+    if (ge) {
+      ge->used = ++P->gclock;
+      CK(cudaGraphLaunch(ge->exec, P->st));
+      note_launch((int)ge->launches);
+    } else {
+      const long long l0 = launch_count();
+      CK(cudaStreamBeginCapture(P->st, cudaStreamCaptureModeRelaxed));
+      const rsvd_status s = enqueue();
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(P->st, &g);
+      if (s) { if (g) cudaGraphDestroy(g); return s; }
+      if (e != cudaSuccess) return seterr(RSVD_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+      cudaGraphExec_t x = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) return seterr(RSVD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+      if (P->gcache.size() >= 8) {                       // evict the least recently used
+        size_t lru = 0;
+        for (size_t i = 1; i < P->gcache.size(); ++i)
+          if (P->gcache[i].used < P->gcache[lru].used) lru = i;
+        cudaGraphExecDestroy(P->gcache[lru].exec);
+        P->gcache.erase(P->gcache.begin() + lru);
+      }
+      P->gcache.push_back({key, x, launch_count() - l0, ++P->gclock});
+      CK(cudaGraphLaunch(x, P->st));
+    }
+  }
   CK(cudaStreamSynchronize(P->st));
   res.assign(hres, hres + C);
   drain_profile(P);
@@ -2281,6 +2365,7 @@ rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* o) {
 void rsvd_plan_destroy(rsvd_plan_t P) {
   if (!P) return;
   cudaStreamSynchronize(P->st);
+  drop_graphs(P);
   if (P->ws) cudaFree(P->ws);
   if (P->hp) cudaFreeHost(P->hp);
   if (P->d_err) cudaFree(P->d_err);
@@ -2293,6 +2378,16 @@ int64_t rsvd_plan_workspace_bytes(rsvd_plan_t P) { return P ? (int64_t)P->ws_cap
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {
   if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
   P->profiling = enable ? 1 : 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_set_graphs(rsvd_plan_t P, int32_t enable) {
+  if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
+  P->graphs = enable ? 1 : 0;
+  if (!enable) {
+    cudaStreamSynchronize(P->st);
+    drop_graphs(P);
+  }
   return RSVD_OK;
 }
 

@@ -10,7 +10,8 @@
 // a + b < max(SA, SX) of V_a X_b, accumulated in FP32.  Two words carry ~16
 // significant bits of each FP64 entry, three ~24.
 //
-// Structure (one 128-row tile of Y per CTA, all of its columns):
+// Structure (persistent CTAs, one per SM, each taking 128-row tiles of Y with
+// all of their columns in turn):
 //   * warp 0, one thread: TMA producer.  For each 64-wide k step it waits for
 //     the stage to be free, arms the stage's mbarrier with the byte count and
 //     issues 2-D tiled bulk copies (128B swizzle) of the V word tiles
@@ -138,14 +139,28 @@ RSVD_DEV void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-RSVD_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 16 columns of the warp's 32 TMEM lanes; the registers are valid only after
+// tmem_wait_ld (several loads may be in flight before one wait).
+RSVD_DEV void tmem_ld16_nw(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+RSVD_DEV void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+RSVD_DEV void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+RSVD_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ kernel
 // The tensor core rounds its FP32 accumulation toward zero, so one TMEM
@@ -162,9 +177,85 @@ static constexpr int CHUNK_KT = 8;
 static constexpr int BN_MAX = 160;            // register accumulator width
 static constexpr int NTHREADS = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
 
+// Work item -> channel, k split, output tile.
+struct TcItem {
+  const TcChan* ch;
+  int m0, n0, kb, nk;
+  int local;                 // item index within its channel
+};
+
+RSVD_DEV void tc_item(const TcChan* __restrict__ chs, int C, int item, int bn, TcItem& I) {
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (chs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+  }
+  const TcChan* ch = chs + lo;
+  int local = item - ch->item0;
+  I.ch = ch;
+  I.local = local;
+  const int per_split = ch->mt * ch->nt;
+  const int split = local / per_split;
+  local -= split * per_split;
+  const int mi = local / ch->nt, ni = local % ch->nt;
+  I.m0 = mi * BM;
+  I.n0 = ni * bn;
+  const int kt_total = (ch->n + BK - 1) / BK;
+  I.kb = split * ch->kt_per_split;
+  I.nk = max(0, min(kt_total, I.kb + ch->kt_per_split) - I.kb);
+}
+
+// Final processing of 16 generated columns of one tile row (one lane = one
+// row j of the generated block = matrix column j; column col = matrix row
+// r0 + col): noise, words, energy, remainder.  The inner hash of the noise is
+// mix(min(i, j) * C1 + key): the row's is computed once per tile (hrow), the
+// 16 columns' by 16 lanes and broadcast.  All lanes take part (shuffles);
+// `live` masks the stores of rows past the end.
+template <int NW, bool WY>
+RSVD_DEV void rule_group(const uint32_t (&r)[16], int row, bool live, int col0, int ncols, int r0, uint32_t hrow,
+                         uint32_t key, float amp3, __nv_bfloat16* W0, __nv_bfloat16* W1, __nv_bfloat16* W2,
+                         int64_t ldw, float* Y, int64_t ldy, float& s2, float& r2, int lane) {
+  const int i0 = r0 + col0;
+  const uint32_t hcol = lowbias32((uint32_t)(i0 + (lane & 15)) * 0x9E3779B1u + key);
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) {
+    const uint32_t hc = __shfl_sync(0xffffffffu, hcol, jj);
+    if (col0 + jj >= ncols) break;                     // uniform across the warp
+    const int i = i0 + jj;
+    const bool rowlo = row <= i;
+    const uint32_t h = lowbias32((rowlo ? hrow : hc) ^ ((uint32_t)(rowlo ? i : row) * 0x85EBCA77u));
+    const float eta = amp3 * ((float)(2 * (int)(h >> 8) + 1 - (1 << 24)) * 5.9604644775390625e-8f);
+    const float v = __uint_as_float(r[jj]) + eta;
+    if (!live) continue;
+    s2 = fmaf(v, v, s2);
+    const int64_t o = row + (int64_t)(col0 + jj) * ldw;
+    if (NW > 0) {
+      __nv_bfloat16 q = __float2bfloat16_rn(v);
+      W0[o] = q;
+      float rem = v - __bfloat162float(q);             // exact
+      if (NW > 1) {
+        q = __float2bfloat16_rn(rem);
+        W1[o] = q;
+        rem -= __bfloat162float(q);
+      }
+      if (NW > 2) {
+        q = __float2bfloat16_rn(rem);
+        W2[o] = q;
+        rem -= __bfloat162float(q);
+      }
+      r2 = fmaf(rem, rem, r2);
+    }
+    if (WY) Y[row + (int64_t)(col0 + jj) * ldy] = v;
+  }
+}
+
+// Persistent: each CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...
+// The k-step counter (stage ring) and the chunk counter (TMEM ping-pong)
+// run on across items, so the producer loads item i+1 and the MMA warp
+// computes it while the epilogue warps still store item i.
 template <int SA, int SX>
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __restrict__ err) {
+k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int SB = SA * A_TILE_BYTES + SX * bn * BK * 2;
@@ -175,28 +266,10 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  // work item -> channel, split, tile
-  const int item = blockIdx.x;
-  int lo = 0, hi = C - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (chs[mid].item0 <= item) lo = mid; else hi = mid - 1;
-  }
-  const TcChan* ch = chs + lo;
-  int local = item - ch->item0;
-  const int per_split = ch->mt * ch->nt;
-  const int split = local / per_split;
-  local -= split * per_split;
-  const int mi = local / ch->nt, ni = local % ch->nt;
-  const int m0 = mi * BM, n0 = ni * bn;
-  const int kt_total = (ch->n + BK - 1) / BK;
-  const int kb = split * ch->kt_per_split;
-  const int nk = min(kt_total, kb + ch->kt_per_split) - kb;
-  const int chunk = ch->chunk_kt > 0 ? ch->chunk_kt : CHUNK_KT;
-  const int nchunks = (nk + chunk - 1) / chunk;
+  // two accumulation buffers, plus a third region where the tile-rule
+  // epilogue keeps its running sums
   uint32_t ncols_alloc = 32;
-  while ((int)ncols_alloc < 2 * bn) ncols_alloc <<= 1;
+  while ((int)ncols_alloc < 3 * bn) ncols_alloc <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -209,56 +282,70 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (nk > 0) {
-    if (warp == 4) {
-      if (lane == 0) {
-        // ---------------- TMA producer
-        for (int a = 0; a < SA; ++a) tmap_acquire(&ch->tmA[a]);
-        for (int x = 0; x < SX; ++x) tmap_acquire(&ch->tmX[x]);
-        int issued = 0;
-        for (int it = 0; it < nk; ++it) {
-          const int s = it % stages;
-          const uint32_t ph = (uint32_t)(it / stages) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) { set_err(err, DERR_TIMEOUT_TMA); break; }
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int g = 0;                                   // k steps issued by this CTA
+      bool ok = true;
+      const TcChan* last = nullptr;
+      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        TcItem I;
+        tc_item(chs, C, item, bn, I);
+        if (I.ch != last) {
+          for (int a = 0; a < SA; ++a) tmap_acquire(&I.ch->tmA[a]);
+          for (int x = 0; x < SX; ++x) tmap_acquire(&I.ch->tmX[x]);
+          last = I.ch;
+        }
+        for (int it = 0; it < I.nk; ++it) {
+          const int s = g % stages;
+          const uint32_t ph = (uint32_t)(g / stages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) { set_err(err, DERR_TIMEOUT_TMA); ok = false; break; }
           mbar_arrive_expect_tx(&full[s], (uint32_t)SB);
           unsigned char* st = base + (size_t)s * SB;
-          const int kx = (kb + it) * BK;
-          for (int a = 0; a < SA; ++a) tma_load_2d(st + a * A_TILE_BYTES, &ch->tmA[a], &full[s], kx, m0);
+          const int kx = (I.kb + it) * BK;
+          for (int a = 0; a < SA; ++a) tma_load_2d(st + a * A_TILE_BYTES, &I.ch->tmA[a], &full[s], kx, I.m0);
           for (int x = 0; x < SX; ++x)
-            tma_load_2d(st + SA * A_TILE_BYTES + x * bn * BK * 2, &ch->tmX[x], &full[s], kx, n0);
-          issued = it + 1;
-        }
-        // drain: the last copy issued into each stage has landed
-        for (int s = 0; s < stages && s < issued; ++s) {
-          const int last = s + ((issued - 1 - s) / stages) * stages;
-          if (!mbar_wait(&full[s], (uint32_t)(last / stages) & 1u)) set_err(err, DERR_TIMEOUT_TMA);
+            tma_load_2d(st + SA * A_TILE_BYTES + x * bn * BK * 2, &I.ch->tmX[x], &full[s], kx, I.n0);
+          ++g;
         }
       }
-      __syncwarp();
-    } else if (warp == 5) {
-      if (lane == 0) {
-        // ---------------- MMA issuer
-        const uint32_t idesc = idesc_bf16(bn);
-        bool ok = true;
+      // drain: the last copy issued into each stage has landed
+      for (int s = 0; s < stages && s < g; ++s) {
+        const int lastg = s + ((g - 1 - s) / stages) * stages;
+        if (!mbar_wait(&full[s], (uint32_t)(lastg / stages) & 1u)) set_err(err, DERR_TIMEOUT_TMA);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = idesc_bf16(bn);
+      bool ok = true;
+      int g = 0, gc = 0;                           // k steps, chunks consumed by this CTA
+      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        TcItem I;
+        tc_item(chs, C, item, bn, I);
+        const int chunk = I.ch->chunk_kt > 0 ? I.ch->chunk_kt : CHUNK_KT;
+        const int nchunks = (I.nk + chunk - 1) / chunk;
         int it = 0;
-        for (int c = 0; c < nchunks && ok; ++c) {
-          const int b = c & 1;
-          if (c >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((c >> 1) - 1) & 1u)) {
+        for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+          const int b = gc & 1;
+          if (gc >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((gc >> 1) - 1) & 1u)) {
             set_err(err, DERR_TIMEOUT_MMA);
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)(b * bn);
-          const int itend = min(nk, it + chunk);
-          for (; it < itend; ++it) {
-            const int s = it % stages;
-            const uint32_t ph = (uint32_t)(it / stages) & 1u;
+          const int itend = min(I.nk, it + chunk);
+          bool zero = true;                          // first MMA of the chunk overwrites
+          for (; it < itend; ++it, ++g) {
+            const int s = g % stages;
+            const uint32_t ph = (uint32_t)(g / stages) & 1u;
             if (!mbar_wait(&full[s], ph)) { set_err(err, DERR_TIMEOUT_MMA); ok = false; break; }
             tc_fence_after();
             const uint32_t sa0 = smem_addr(base + (size_t)s * SB);
             const uint32_t sx0 = sa0 + SA * A_TILE_BYTES;
-            bool zero = (it == c * chunk);          // first MMA of the chunk overwrites
             // small word products first, the leading pair (0, 0) last: the
             // round-toward-zero accumulation then loses least while the
             // running sum is small
@@ -284,17 +371,110 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
           mma_commit(&acc_full[b]);     // also issued after an error: completes when prior MMAs do
         }
       }
-      __syncwarp();
-    } else {
-      // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = rows of the tile
-      float acc[BN_MAX];
+      // every MMA has completed before TMEM is released (bounded)
+      if (gc > 0) {
+        const int b = (gc - 1) & 1;
+        if (!mbar_wait(&acc_full[b], (uint32_t)((gc - 1) >> 1) & 1u)) set_err(err, DERR_TIMEOUT_MMA);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = rows of the tile
+    int healthy = 1;
+    int gc = 0;
+    for (int item = blockIdx.x; item < items && healthy; item += gridDim.x) {
+      TcItem I;
+      tc_item(chs, C, item, bn, I);
+      const TcChan* ch = I.ch;
+      const int chunk = ch->chunk_kt > 0 ? ch->chunk_kt : CHUNK_KT;
+      const int nchunks = (I.nk + chunk - 1) / chunk;
+      if (ch->mode == TC_RULE) {
+        // generated tile-rule entries.  Chunk sums are added (round to
+        // nearest) into a TMEM region of their own, 16 columns at a time in a
+        // rolled loop (the per-entry code is long: unrolled over every column
+        // it would not fit the instruction cache); after the last chunk the
+        // symmetric noise is added, the entries are split into BF16 words,
+        // and the energy and the words' remainder are kept.
+        const int row = I.m0 + warp * 32 + lane;
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        const uint32_t fin = tmem + lanes + (uint32_t)(2 * bn);
+        const int ncols = ch->ncols, nw = ch->nw, r0 = ch->r0;
+        const int64_t ldy = ch->ldy, ldw = ch->ldw;
+        const uint32_t key = ch->eta_key;
+        const float amp3 = ch->eta_amp3;
+        float* Y = ch->Y;
+        __nv_bfloat16* W0 = ch->W[0];
+        __nv_bfloat16* W1 = ch->W[1];
+        __nv_bfloat16* W2 = ch->W[2];
+        const bool live = row < ch->m;
+        const uint32_t hrow = lowbias32((uint32_t)row * 0x9E3779B1u + key);
+        float s2 = 0.0f, r2 = 0.0f;
+        for (int c = 0; c < nchunks; ++c, ++gc) {
+          const int b = gc & 1;
+          int ok = 0;
+          if (lane == 0) ok = mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            if (lane == 0) set_err(err, DERR_TIMEOUT_EPI);
+            healthy = 0;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ta = tmem + lanes + (uint32_t)(b * bn);
+          const bool lastc = c == nchunks - 1;
+#pragma unroll 1
+          for (int g = 0; g < bn; g += 16) {
+            uint32_t r[16], f[16];
+            tmem_ld16_nw(ta + (uint32_t)g, r);
+            if (c > 0) tmem_ld16_nw(fin + (uint32_t)g, f);
+            tmem_wait_ld();
+            if (c > 0) {
 #pragma unroll
-      for (int j = 0; j < BN_MAX; ++j) acc[j] = 0.0f;
-      int healthy = 1;
-      for (int c = 0; c < nchunks; ++c) {
-        const int b = c & 1;
+              for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(f[j]));
+            }
+            if (!lastc) {
+              tmem_st16(fin + (uint32_t)g, r);
+              continue;
+            }
+            const int col0 = I.n0 + g;
+            if (col0 >= ncols) continue;
+            if (Y) {
+              rule_group<0, true>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            } else if (nw == 2) {
+              rule_group<2, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            } else if (nw == 3) {
+              rule_group<3, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            } else {
+              rule_group<1, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            }
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          mbar_arrive(&acc_empty[b]);
+        }
+        if (healthy) healthy = (*(volatile int*)err == 0);
+        healthy = __shfl_sync(0xffffffffu, healthy, 0);
+        if (!healthy) break;
+        if (ch->part) {
+          double ds = (double)s2, dr = (double)r2;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            ds += __shfl_xor_sync(0xffffffffu, ds, o);
+            dr += __shfl_xor_sync(0xffffffffu, dr, o);
+          }
+          if (lane == 0) {
+            double* pp = ch->part + ((int64_t)I.local * 4 + warp) * 2;
+            pp[0] = ds;
+            pp[1] = dr;
+          }
+        }
+        continue;
+      }
+      float acc[BN_MAX];
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        const int b = gc & 1;
         int ok = 0;
-        if (lane == 0) ok = mbar_wait(&acc_full[b], (uint32_t)(c >> 1) & 1u) ? 1 : 0;
+        if (lane == 0) ok = mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) set_err(err, DERR_TIMEOUT_EPI);
@@ -303,88 +483,48 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int bn, int stages, int* __rest
         }
         tc_fence_after();
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * bn);
+        // 32 columns per wait (two 16-column loads in flight)
 #pragma unroll
-        for (int g = 0; g < BN_MAX / 16; ++g) {
-          if (g * 16 < bn) {
-            uint32_t r[16];
-            tmem_ld16(ta + (uint32_t)(g * 16), r);
+        for (int g32 = 0; g32 < (BN_MAX + 31) / 32; ++g32) {
+          if (g32 * 32 < bn) {
+            uint32_t r[32];
+            tmem_ld16_nw(ta + (uint32_t)(g32 * 32), r);
+            const bool two = g32 * 32 + 16 < bn && g32 * 32 + 16 < BN_MAX;
+            if (two) tmem_ld16_nw(ta + (uint32_t)(g32 * 32 + 16), r + 16);
+            tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[g * 16 + j] += __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) {
+              if (g32 * 32 + j < BN_MAX && (j < 16 || two)) {
+                const float v = __uint_as_float(r[j]);
+                acc[g32 * 32 + j] = c == 0 ? v : acc[g32 * 32 + j] + v;
+              }
+            }
           }
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[b]);
       }
+      if (nchunks == 0) {
+#pragma unroll
+        for (int j = 0; j < BN_MAX; ++j) acc[j] = 0.0f;
+      }
       if (healthy) healthy = (*(volatile int*)err == 0);
       healthy = __shfl_sync(0xffffffffu, healthy, 0);
-      if (healthy) {
-        const int row = m0 + warp * 32 + lane;
-        if (ch->mode == TC_RULE) {
-          // generated tile-rule entries: add the symmetric noise, split into
-          // BF16 words, and keep the energy and the words' remainder
-          float s2 = 0.0f, r2 = 0.0f;
-          if (row < ch->m) {
-            float* Y = ch->Y;
-            const int64_t ldy = ch->ldy, ldw = ch->ldw;
-            const int ncols = ch->ncols, nw = ch->nw, r0 = ch->r0;
-            const uint32_t key = ch->eta_key;
-            const float amp3 = ch->eta_amp3;
-            __nv_bfloat16* W0 = ch->W[0];
-            __nv_bfloat16* W1 = ch->W[1];
-            __nv_bfloat16* W2 = ch->W[2];
+      if (!healthy) break;
+      const int row = I.m0 + warp * 32 + lane;
+      const int n0 = I.n0;
+      if (row < ch->m) {
+        float* Y = ch->Y;
+        const int64_t ldy = ch->ldy;
+        const int ncols = ch->ncols;
+        const int atomic = ch->atomic;
 #pragma unroll
-            for (int j = 0; j < BN_MAX; ++j) {
-              const int col = n0 + j;
-              if (j < bn && col < ncols) {
-                const float v = acc[j] + rule_eta(key, amp3, r0 + col, row);
-                s2 = fmaf(v, v, s2);
-                if (nw > 0) {
-                  const int64_t o = row + (int64_t)col * ldw;
-                  __nv_bfloat16 q = __float2bfloat16_rn(v);
-                  W0[o] = q;
-                  float rem = v - __bfloat162float(q);      // exact
-                  if (nw > 1) {
-                    q = __float2bfloat16_rn(rem);
-                    W1[o] = q;
-                    rem -= __bfloat162float(q);
-                    if (nw > 2) {
-                      q = __float2bfloat16_rn(rem);
-                      W2[o] = q;
-                      rem -= __bfloat162float(q);
-                    }
-                  }
-                  r2 = fmaf(rem, rem, r2);
-                }
-                if (Y) Y[row + (int64_t)col * ldy] = v;
-              }
-            }
-          }
-          if (ch->part) {
-            double ds = (double)s2, dr = (double)r2;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              ds += __shfl_xor_sync(0xffffffffu, ds, o);
-              dr += __shfl_xor_sync(0xffffffffu, dr, o);
-            }
-            if (lane == 0) {
-              double* pp = ch->part + ((int64_t)(item - ch->item0) * 4 + warp) * 2;
-              pp[0] = ds;
-              pp[1] = dr;
-            }
-          }
-        } else if (row < ch->m) {
-          float* Y = ch->Y;
-          const int64_t ldy = ch->ldy;
-          const int ncols = ch->ncols;
-          const int atomic = ch->atomic;
-#pragma unroll
-          for (int j = 0; j < BN_MAX; ++j) {
-            const int col = n0 + j;
-            if (j < bn && col < ncols) {
-              float* dst = Y + row + (int64_t)col * ldy;
-              if (atomic) atomicAdd(dst, acc[j]);
-              else *dst = acc[j];
-            }
+        for (int j = 0; j < BN_MAX; ++j) {
+          const int col = n0 + j;
+          if (j < bn && col < ncols) {
+            float* dst = Y + row + (int64_t)col * ldy;
+            if (atomic) atomicAdd(dst, acc[j]);
+            else *dst = acc[j];
           }
         }
       }
@@ -439,7 +579,12 @@ static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cu
   const int smem = stages * tc_stage_bytes(SA, SX, bn) + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
-  k_tc_gemm<SA, SX><<<items, NTHREADS, smem, st>>>(d_ch, C, bn, stages, d_err);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      nsm < 1)
+    nsm = 148;
+  const int grid = items < nsm ? items : nsm;                  // persistent: one CTA per SM
+  k_tc_gemm<SA, SX><<<grid, NTHREADS, smem, st>>>(d_ch, C, items, bn, stages, d_err);
   note_launch();
   return (int)cudaGetLastError();
 }

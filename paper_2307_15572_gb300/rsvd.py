@@ -97,6 +97,8 @@ def load(build=True):
     lib.rsvd_version.restype = C.c_int32
     lib.rsvd_plan_set_profiling.argtypes = [P, C.c_int32]
     lib.rsvd_plan_set_profiling.restype = C.c_int
+    lib.rsvd_plan_set_graphs.argtypes = [P, C.c_int32]
+    lib.rsvd_plan_set_graphs.restype = C.c_int
     lib.rsvd_plan_profile.argtypes = [P, C.POINTER(Profile), C.c_int32]
     lib.rsvd_plan_profile.restype = C.c_int
     lib.rsvd_mlp_param_count.argtypes = [C.c_int32]
@@ -164,6 +166,10 @@ def rsvd_decompose_batched(h, mats, facs):
 
 def rsvd_plan_set_profiling(h, enable):
     _check(load().rsvd_plan_set_profiling(h, 1 if enable else 0))
+
+
+def rsvd_plan_set_graphs(h, enable):
+    _check(load().rsvd_plan_set_graphs(h, 1 if enable else 0))
 
 
 def rsvd_plan_profile(h, reset=False):
