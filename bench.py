@@ -342,7 +342,7 @@ def run_gpu(args):
                             "k = 320, p = 10, q = 1, 2 words; every pass generates its entries" % rn,
                 "err_est": rf.err_est, "status": int(rf.status), "k": rf.k_out,
                 "passes_per_step": 2 * rq + 2,
-                "roofline": {"bound": "tensor", "kernel": "k_tc_gemm<3,3> (TC_RULE generation)",
+                "roofline": {"bound": "tensor", "kernel": "k_tc_gemm<3, 3, true> (tile-rule generation, two epilogue groups)",
                              "achieved": g_mma / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
                              "peak": bpk, "unit": "TFLOP/s",
                              "frac": (g_mma / (g_ms / 1e3) / 1e12) / bpk if g_ms else 0.0,

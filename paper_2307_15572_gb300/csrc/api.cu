@@ -216,6 +216,7 @@ struct Job {
   // tile-rule channels (all channels of the job, or none)
   bool rule = false;
   bool skip_convert = false;            // V words reused from a probe job
+  std::vector<char> staged;             // host V copied to the device (else read in place)
   bool probe_job = false;
   int panel = 0;                        // rows of A generated per panel
   struct RuleDev {
@@ -242,6 +243,19 @@ int rule_panel_rows(int64_t n, int64_t ldb, int nsl) {
 }
 uint32_t rule_key(uint64_t seed) {
   return lowbias32((uint32_t)seed ^ lowbias32((uint32_t)(seed >> 32)));
+}
+
+// Device address of a page-locked host matrix, or null.  On the mixed path V
+// is read once (by the conversion to words), so a pinned host V is read in
+// place over the CPU-GPU link instead of being staged through a device copy.
+const double* host_direct(const rsvd_matrix& A) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, A.data) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return (const double*)at.devicePointer;
+  return nullptr;
 }
 
 // Per-batch tile offsets (prefix sums) uploaded through the arena.
@@ -651,7 +665,7 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
       J.steps.push_back([=]() {
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (P->profiling) timed_begin(P, &ea, &eb);
-        int e = tc_launch(dg, 1, gitems, 3, 3, gbn, derr, st);
+        int e = tc_launch(dg, 1, gitems, 3, 3, gbn, derr, st, true);
         if (e) return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
         if (P->profiling) {
           cudaEventRecord(eb, st);
@@ -976,6 +990,7 @@ rsvd_status build_probe(Job& J, float* d_feat, const float* theta, float* d_pred
 // first, so a probe job and the decomposition after it (different l) share it.
 void layout(Job& J, Bump& b) {
   J.ch.assign(J.C, Chan{});
+  J.staged.assign(J.C, 0);
   for (int c = 0; c < J.C; ++c) {
     const ChanDims& d = J.d[c];
     Chan& h = J.ch[c];
@@ -984,8 +999,13 @@ void layout(Job& J, Bump& b) {
       h.fro_part = b.take<double>(cdiv(d.n, 8));
       continue;
     }
-    if (A.mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; }
-    else { h.A = A.data; h.lda = A.ld; }
+    if (A.mem == RSVD_MEM_HOST) {
+      const double* direct = J.mixed ? host_direct(A) : nullptr;
+      if (direct) { h.A = direct; h.lda = A.ld; }
+      else { h.A = b.take<double>((size_t)d.n * d.n); h.lda = d.n; J.staged[c] = 1; }
+    } else {
+      h.A = A.data; h.lda = A.ld;
+    }
     if (J.mixed) {
       for (int s = 0; s < J.nsl; ++s) h.Ab[s] = b.take<__nv_bfloat16>((size_t)d.n * d.ldb);
       h.wres_part = b.take<double>(cdiv(d.n, 8));
@@ -1524,8 +1544,9 @@ void lay_adapt_mixed(Bump& b, const std::vector<ChanDims>& d, int bsz, int nsl, 
   base.assign(C, Chan{});
   for (int c = 0; c < C; ++c) {          // rank-independent prefix: staged input, words, partials
     Chan& h = base[c];
-    if (A[c].mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)d[c].n * d[c].n); h.lda = d[c].n; }
-    else { h.A = A[c].data; h.lda = A[c].ld; }
+    const double* direct = A[c].mem == RSVD_MEM_HOST ? host_direct(A[c]) : nullptr;
+    if (A[c].mem == RSVD_MEM_HOST && !direct) { h.A = b.take<double>((size_t)d[c].n * d[c].n); h.lda = d[c].n; }
+    else { h.A = direct ? direct : A[c].data; h.lda = A[c].ld; }
     for (int w = 0; w < nsl; ++w) h.Ab[w] = b.take<__nv_bfloat16>((size_t)d[c].n * d[c].ldb);
     h.fro_part = b.take<double>(cdiv(d[c].n, 8));
     h.wres_part = b.take<double>(cdiv(d[c].n, 8));
@@ -1617,7 +1638,7 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
   CK(cudaMemsetAsync(d_res, 0, sizeof(ChanResult) * C, P->st));
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
   for (int c = 0; c < C; ++c)
-    if (A[c].mem == RSVD_MEM_HOST)
+    if (A[c].mem == RSVD_MEM_HOST && !host_direct(A[c]))        // staged (not read in place)
       CK(cudaMemcpy2DAsync((void*)base[c].A, (size_t)d[c].n * sizeof(double), A[c].data,
                            (size_t)A[c].ld * sizeof(double), (size_t)d[c].n * sizeof(double), d[c].n,
                            cudaMemcpyHostToDevice, P->st));
@@ -2042,7 +2063,7 @@ std::string graph_key(const Job& J, bool stage_inputs) {
     const ChanDims& d = J.d[c];
     const int64_t v[] = {d.n, d.l, d.lw, d.s, d.kcap, d.gsplit, d.ldt, d.ldb};
     put(v, sizeof(v));
-    if (stage_inputs && J.A[c].mem == RSVD_MEM_HOST) { put64((int64_t)(uintptr_t)J.A[c].data); put64(J.A[c].ld); }
+    if (stage_inputs && J.staged[c]) { put64((int64_t)(uintptr_t)J.A[c].data); put64(J.A[c].ld); }
   }
   return k;
 }
@@ -2063,7 +2084,7 @@ rsvd_status execute(Job& J, bool stage_inputs, std::vector<ChanResult>& res) {
     CK(cudaMemcpyAsync(J.ar.dbase, P->hp, J.ar.h.size(), cudaMemcpyHostToDevice, P->st));
     if (stage_inputs)
       for (int c = 0; c < C; ++c)
-        if (J.A[c].mem == RSVD_MEM_HOST && J.A[c].kind == RSVD_DENSE_F64) {
+        if (J.staged[c]) {
           const size_t row = (size_t)J.d[c].n * sizeof(double);
           if (J.A[c].ld == J.d[c].n)
             CK(cudaMemcpyAsync((void*)J.ch[c].A, J.A[c].data, row * J.d[c].n, cudaMemcpyHostToDevice, P->st));
@@ -2490,7 +2511,7 @@ rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int3
   for (int w = 0; w < 3; ++w) rdsc.H[w] = H[w];
   rdsc.ldh = ldh;
   launch_rule_prep(rdsc, P->st);
-  if (int e = tc_launch(dtc, 1, htc->mt * htc->nt, 3, 3, gbn, P->d_err, P->st))
+  if (int e = tc_launch(dtc, 1, htc->mt * htc->nt, 3, 3, gbn, P->d_err, P->st, true))
     return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));

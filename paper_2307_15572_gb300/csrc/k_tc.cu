@@ -176,6 +176,7 @@ RSVD_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" :::
 static constexpr int CHUNK_KT = 8;
 static constexpr int BN_MAX = 160;            // register accumulator width
 static constexpr int NTHREADS = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
+static constexpr int NTHREADS_RULE = 320;     // generation: warps 0-3 and 6-9 epilogue (two groups)
 
 // Work item -> channel, k split, output tile.
 struct TcItem {
@@ -253,8 +254,8 @@ RSVD_DEV void rule_group(const uint32_t (&r)[16], int row, bool live, int col0, 
 // The k-step counter (stage ring) and the chunk counter (TMEM ping-pong)
 // run on across items, so the producer loads item i+1 and the MMA warp
 // computes it while the epilogue warps still store item i.
-template <int SA, int SX>
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <int SA, int SX, bool RULE>
+__global__ void __launch_bounds__(RULE ? NTHREADS_RULE : NTHREADS, 1)
 k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -264,16 +265,18 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
   uint64_t* acc_full = empty + stages;     // [2] MMA -> epilogue
   uint64_t* acc_empty = acc_full + 2;      // [2] epilogue -> MMA (128 arrivals)
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+  int* consumed = (int*)(tmem_slot + 1);   // generation: (chunk, warp) pairs released, in order
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // two accumulation buffers, plus a third region where the tile-rule
-  // epilogue keeps its running sums
+  // two accumulation buffers, plus (generation) one region per epilogue
+  // group where it keeps its running sums
   uint32_t ncols_alloc = 32;
-  while ((int)ncols_alloc < 3 * bn) ncols_alloc <<= 1;
+  while ((int)ncols_alloc < (RULE ? 4 : 2) * bn) ncols_alloc <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
+    *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tmem_slot, ncols_alloc);
@@ -378,6 +381,121 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
       }
     }
     __syncwarp();
+  } else if constexpr (RULE) {
+    // ---------------- generation epilogue: two groups of four warps take the
+    // CTA's items alternately (group g: items 2t + g of its sequence); warp w
+    // reads TMEM lanes 32 (w mod 4) .. + 31 = rows of the tile.  Chunk sums
+    // are added (round to nearest) into the group's own TMEM region, 16
+    // columns per rolled step (the per-entry code is long: unrolled over
+    // every column it would not fit the instruction cache).  Chunks are taken
+    // in order across the groups -- a group waits on a buffer's barrier only
+    // once the chunk before it was released, so no parity wait runs two
+    // phases ahead (it would alias) -- and the entries (noise, BF16 words,
+    // energy and remainder) are made from the group's region after the chunk
+    // buffer is back with the MMA warp and the other group.
+    const int grp = warp >= 6 ? 1 : 0;
+    const int qw = warp & 3;
+    int healthy = 1;
+    int gc = 0, t = 0;
+    for (int item = blockIdx.x; item < items && healthy; item += gridDim.x, ++t) {
+      TcItem I;
+      tc_item(chs, C, item, bn, I);
+      const TcChan* ch = I.ch;
+      const int chunk = ch->chunk_kt > 0 ? ch->chunk_kt : CHUNK_KT;
+      const int nchunks = (I.nk + chunk - 1) / chunk;
+      if ((t & 1) != grp) {                        // the other group's item
+        gc += nchunks;
+        continue;
+      }
+      const int row = I.m0 + qw * 32 + lane;
+      const uint32_t lanes = (uint32_t)(qw * 32) << 16;
+      const uint32_t fin = tmem + lanes + (uint32_t)((2 + grp) * bn);
+      const int ncols = ch->ncols, nw = ch->nw, r0 = ch->r0;
+      const int64_t ldy = ch->ldy, ldw = ch->ldw;
+      const uint32_t key = ch->eta_key;
+      const float amp3 = ch->eta_amp3;
+      float* Y = ch->Y;
+      __nv_bfloat16* W0 = ch->W[0];
+      __nv_bfloat16* W1 = ch->W[1];
+      __nv_bfloat16* W2 = ch->W[2];
+      const bool live = row < ch->m;
+      const uint32_t hrow = lowbias32((uint32_t)row * 0x9E3779B1u + key);
+      float s2 = 0.0f, r2 = 0.0f;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        const int b = gc & 1;
+        int ok = 1;
+        if (lane == 0) {
+          const long long t0 = clock64();
+          while (*(volatile int*)consumed < 4 * gc) {
+            if (clock64() - t0 > (1ll << 32)) { ok = 0; break; }
+          }
+          if (ok) ok = mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u) ? 1 : 0;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) set_err(err, DERR_TIMEOUT_EPI);
+          healthy = 0;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + lanes + (uint32_t)(b * bn);
+#pragma unroll 1
+        for (int g = 0; g < bn; g += 16) {
+          uint32_t r[16], f[16];
+          tmem_ld16_nw(ta + (uint32_t)g, r);
+          if (c > 0) tmem_ld16_nw(fin + (uint32_t)g, f);
+          tmem_wait_ld();
+          if (c > 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(f[j]));
+          }
+          tmem_st16(fin + (uint32_t)g, r);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          atomicAdd(consumed, 1);
+        }
+      }
+      if (healthy) {
+#pragma unroll 1
+        for (int g = 0; g < bn; g += 16) {
+          const int col0 = I.n0 + g;
+          if (col0 >= ncols) break;
+          uint32_t r[16];
+          tmem_ld16_nw(fin + (uint32_t)g, r);
+          tmem_wait_ld();
+          if (Y) {
+            rule_group<0, true>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+          } else if (nw == 2) {
+            rule_group<2, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+          } else if (nw == 3) {
+            rule_group<3, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+          } else {
+            rule_group<1, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+          }
+        }
+      }
+      if (healthy) healthy = (*(volatile int*)err == 0);
+      healthy = __shfl_sync(0xffffffffu, healthy, 0);
+      if (!healthy) break;
+      if (ch->part) {
+        double ds = (double)s2, dr = (double)r2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ds += __shfl_xor_sync(0xffffffffu, ds, o);
+          dr += __shfl_xor_sync(0xffffffffu, dr, o);
+        }
+        if (lane == 0) {
+          double* pp = ch->part + ((int64_t)I.local * 4 + qw) * 2;
+          pp[0] = ds;
+          pp[1] = dr;
+        }
+      }
+    }
   } else {
     // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = rows of the tile
     int healthy = 1;
@@ -388,88 +506,6 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
       const TcChan* ch = I.ch;
       const int chunk = ch->chunk_kt > 0 ? ch->chunk_kt : CHUNK_KT;
       const int nchunks = (I.nk + chunk - 1) / chunk;
-      if (ch->mode == TC_RULE) {
-        // generated tile-rule entries.  Chunk sums are added (round to
-        // nearest) into a TMEM region of their own, 16 columns at a time in a
-        // rolled loop (the per-entry code is long: unrolled over every column
-        // it would not fit the instruction cache); after the last chunk the
-        // symmetric noise is added, the entries are split into BF16 words,
-        // and the energy and the words' remainder are kept.
-        const int row = I.m0 + warp * 32 + lane;
-        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
-        const uint32_t fin = tmem + lanes + (uint32_t)(2 * bn);
-        const int ncols = ch->ncols, nw = ch->nw, r0 = ch->r0;
-        const int64_t ldy = ch->ldy, ldw = ch->ldw;
-        const uint32_t key = ch->eta_key;
-        const float amp3 = ch->eta_amp3;
-        float* Y = ch->Y;
-        __nv_bfloat16* W0 = ch->W[0];
-        __nv_bfloat16* W1 = ch->W[1];
-        __nv_bfloat16* W2 = ch->W[2];
-        const bool live = row < ch->m;
-        const uint32_t hrow = lowbias32((uint32_t)row * 0x9E3779B1u + key);
-        float s2 = 0.0f, r2 = 0.0f;
-        for (int c = 0; c < nchunks; ++c, ++gc) {
-          const int b = gc & 1;
-          int ok = 0;
-          if (lane == 0) ok = mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u) ? 1 : 0;
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          if (!ok) {
-            if (lane == 0) set_err(err, DERR_TIMEOUT_EPI);
-            healthy = 0;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t ta = tmem + lanes + (uint32_t)(b * bn);
-          const bool lastc = c == nchunks - 1;
-#pragma unroll 1
-          for (int g = 0; g < bn; g += 16) {
-            uint32_t r[16], f[16];
-            tmem_ld16_nw(ta + (uint32_t)g, r);
-            if (c > 0) tmem_ld16_nw(fin + (uint32_t)g, f);
-            tmem_wait_ld();
-            if (c > 0) {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(f[j]));
-            }
-            if (!lastc) {
-              tmem_st16(fin + (uint32_t)g, r);
-              continue;
-            }
-            const int col0 = I.n0 + g;
-            if (col0 >= ncols) continue;
-            if (Y) {
-              rule_group<0, true>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
-            } else if (nw == 2) {
-              rule_group<2, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
-            } else if (nw == 3) {
-              rule_group<3, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
-            } else {
-              rule_group<1, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
-            }
-          }
-          tmem_wait_st();
-          tc_fence_before();
-          mbar_arrive(&acc_empty[b]);
-        }
-        if (healthy) healthy = (*(volatile int*)err == 0);
-        healthy = __shfl_sync(0xffffffffu, healthy, 0);
-        if (!healthy) break;
-        if (ch->part) {
-          double ds = (double)s2, dr = (double)r2;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            ds += __shfl_xor_sync(0xffffffffu, ds, o);
-            dr += __shfl_xor_sync(0xffffffffu, dr, o);
-          }
-          if (lane == 0) {
-            double* pp = ch->part + ((int64_t)I.local * 4 + warp) * 2;
-            pp[0] = ds;
-            pp[1] = dr;
-          }
-        }
-        continue;
-      }
       float acc[BN_MAX];
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int b = gc & 1;
@@ -573,30 +609,35 @@ int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda, con
   return 0;
 }
 
-template <int SA, int SX>
+template <int SA, int SX, bool RULE>
 static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cudaStream_t st) {
   const int stages = tc_stages(SA, SX, bn);
   const int smem = stages * tc_stage_bytes(SA, SX, bn) + 1024 + 256;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       nsm < 1)
     nsm = 148;
   const int grid = items < nsm ? items : nsm;                  // persistent: one CTA per SM
-  k_tc_gemm<SA, SX><<<grid, NTHREADS, smem, st>>>(d_ch, C, items, bn, stages, d_err);
+  k_tc_gemm<SA, SX, RULE><<<grid, RULE ? NTHREADS_RULE : NTHREADS, smem, st>>>(d_ch, C, items, bn, stages, d_err);
   note_launch();
   return (int)cudaGetLastError();
 }
 
-int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err, cudaStream_t st) {
+int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err, cudaStream_t st,
+              bool rule) {
   if (items <= 0) return 0;
   if (bn < 16 || bn > BN_MAX || (bn % 16) != 0) return (int)cudaErrorInvalidValue;
-  if (sa == 1 && sx == 1) return launch_t<1, 1>(d_ch, C, items, bn, d_err, st);
-  if (sa == 2 && sx == 1) return launch_t<2, 1>(d_ch, C, items, bn, d_err, st);
-  if (sa == 2 && sx == 2) return launch_t<2, 2>(d_ch, C, items, bn, d_err, st);
-  if (sa == 3 && sx == 1) return launch_t<3, 1>(d_ch, C, items, bn, d_err, st);
-  if (sa == 3 && sx == 3) return launch_t<3, 3>(d_ch, C, items, bn, d_err, st);
+  if (rule) {
+    if (sa == 3 && sx == 3) return launch_t<3, 3, true>(d_ch, C, items, bn, d_err, st);
+    return (int)cudaErrorInvalidValue;
+  }
+  if (sa == 1 && sx == 1) return launch_t<1, 1, false>(d_ch, C, items, bn, d_err, st);
+  if (sa == 2 && sx == 1) return launch_t<2, 1, false>(d_ch, C, items, bn, d_err, st);
+  if (sa == 2 && sx == 2) return launch_t<2, 2, false>(d_ch, C, items, bn, d_err, st);
+  if (sa == 3 && sx == 1) return launch_t<3, 1, false>(d_ch, C, items, bn, d_err, st);
+  if (sa == 3 && sx == 3) return launch_t<3, 3, false>(d_ch, C, items, bn, d_err, st);
   return (int)cudaErrorInvalidValue;
 }
 

@@ -49,7 +49,8 @@ int tc_stages(int sa, int sx, int bn);
 
 // Launch over `items` work items (sum over channels of mt*nt*ks).
 // Returns a cudaError_t value.
+// rule: the tile-rule generation instantiation (<3, 3>, TC_RULE channels only).
 int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err,
-              cudaStream_t st);
+              cudaStream_t st, bool rule = false);
 
 }  // namespace rsvd

@@ -278,3 +278,57 @@ def test_mixed_adaptive_batched_uneven(lib):
             assert -max(8, 0.1 * o.k) <= r["k"] - o.k <= max(12, 0.25 * o.k)
     finally:
         plan.close()
+
+
+def test_fp64_tolerance_1e6_batch_channels(lib):
+    # the batched set's parity tolerance (1e-6): the noise floor (spectral
+    # 1e-8 sigma_1) puts the rank near 700, so l = 800 and the small SVD runs
+    # at l = 800 (one CTA per channel: seconds, see the design notes)
+    torch = _torch()
+    sizes = [1800, 2600]
+    mats = [synth.batch_channel(c, n) for c, n in enumerate(sizes)]
+    plan = lib.Plan(max(sizes), k=790, p=10, q=1, seed=9, tol=1e-6, policy="tol")
+    try:
+        dev = [torch.as_tensor(A, device="cuda") for A in mats]
+        st, res = plan.decompose_batched(dev, 800)
+        for A, At, r in zip(mats, dev, res):
+            o = orsvd.rsvd(A, tol=1e-6, l=800, q=1, seed=9)
+            e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+            err = plan.reconstruct_error(At, r)
+            assert r["status"] >= 0, (r["status"], lib.last_error())
+            # the tail error crosses 1e-6 within ~1e-3 of tol here, so the
+            # rank may differ by one between FP64 implementations
+            assert abs(r["k"] - o.k) <= 1, (r["k"], o.k)
+            kk = min(r["k"], o.k)
+            sigma_parity(r["S"].cpu().numpy()[:kk], o.S[:kk])
+            assert err <= 1e-6 * (1 + 1e-9)
+            if r["k"] >= o.k:
+                assert err <= 1.05 * e_o
+    finally:
+        plan.close()
+
+
+def test_mixed_pinned_and_pageable_host_inputs(lib):
+    # mixed path: a page-locked host V is read in place by the conversion
+    # kernel, a pageable one is staged; both match the device-resident run
+    torch = _torch()
+    A = synth.batch_channel(4, 1500)
+    pinned = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.as_tensor(A))
+    for policy in ("tol", "adaptive"):
+        plan = lib.Plan(1500, k=118, p=10, q=0, seed=4, tol=1e-4, policy=policy, precision="bf16x", block_b=32,
+                        l_max=256)
+        try:
+            st0, r0 = plan.decompose(torch.as_tensor(A, device="cuda"), 128)
+            e0 = plan.reconstruct_error(torch.as_tensor(A, device="cuda"), r0)
+            for host in (pinned, np.ascontiguousarray(A)):
+                st, r = plan.decompose(host, 128)
+                assert st == st0 == 0, lib.last_error()
+                assert r["k"] == r0["k"] and r["l"] == r0["l"]
+                # split-k atomics reorder FP32 sums: agreement to the FP32 small
+                # SVD's absolute accuracy (~l 2^-24 sigma_1)
+                assert torch.allclose(r["S"], r0["S"], rtol=0, atol=1e-5 * float(r0["S"][0]))
+                e = plan.reconstruct_error(torch.as_tensor(A, device="cuda"), r)
+                assert abs(e - e0) <= 1e-3 * e0
+        finally:
+            plan.close()
