@@ -80,6 +80,7 @@ struct rsvd_plan_s {
   char* hp = nullptr;      // pinned host staging
   size_t hp_cap = 0;
   int* d_err = nullptr;    // device error word
+  int* d_coop = nullptr;   // scratch of the cooperative Jacobi (after the error word)
   int slices = 2;
   // profiling
   int profiling = 0;
@@ -167,6 +168,39 @@ void timed_begin(rsvd_plan_s* P, cudaEvent_t* a, cudaEvent_t* b) {
   *a = P->ev_pool[P->ev_next++];
   *b = P->ev_pool[P->ev_next++];
   cudaEventRecord(*a, P->st);
+}
+
+// Small SVD of every channel's factor: one CTA per channel while the factor
+// fits its shared memory, else the cooperative kernel (several CTAs per
+// channel; not while the stream is being captured into a graph).
+void run_jacobi(const Chan* dch, const std::vector<int>& ls, int fp32, int maxl, int* coop, cudaStream_t st) {
+  const int C = (int)ls.size();
+  const int ve = fp32 ? 4 : 2;
+  const size_t lp = (size_t)((maxl + 8 * ve - 1) / (8 * ve) * (8 * ve));
+  const size_t bytes = (fp32 ? 1 : 2) * (size_t)maxl * lp * (fp32 ? 4 : 8);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st) cudaStreamIsCapturing(st, &cs);
+  if (bytes > 200 * 1024 && cs == cudaStreamCaptureStatusNone &&
+      launch_jacobi_coop(dch, ls.data(), C, fp32, coop, st) == 0)
+    return;
+  launch_jacobi(dch, C, fp32, maxl, st);
+}
+
+// Cholesky + inverse of every channel's Gram: one CTA per channel while the
+// factor fits its shared memory, else the cooperative kernel.
+void run_chol(const Chan* dch, const std::vector<int>& ls, int accumulate, int maxl, int f32inv, int f32_chol,
+              int conditional, int* coop, cudaStream_t st) {
+  const int C = (int)ls.size();
+  const size_t esz = f32_chol ? sizeof(float) : sizeof(double);
+  size_t bytes = (size_t)maxl * (maxl + 1) * esz;
+  const size_t b32 = (size_t)maxl * (maxl + 1) * sizeof(float) + 8 * (size_t)maxl * sizeof(float);
+  if (b32 > bytes) bytes = b32;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st) cudaStreamIsCapturing(st, &cs);
+  if (bytes > 200 * 1024 && cs == cudaStreamCaptureStatusNone &&
+      launch_chol_coop(dch, ls.data(), C, accumulate, f32_chol, conditional, coop, st) == 0)
+    return;
+  launch_chol_inv(dch, C, accumulate, maxl, f32inv, st, f32_chol, conditional);
 }
 
 // Fold the timed launches of a finished (synchronised) job into the counters.
@@ -352,13 +386,21 @@ void add_tn(Job& J, MMKind kind, std::function<const void*(int)> Ap, std::functi
             [&](int c) { return J.d[c].ldt; }, [&](int c) { return J.d[c].gsplit; });
 }
 
+std::vector<int> chan_ls(const Job& J) {
+  std::vector<int> ls(J.C);
+  for (int c = 0; c < J.C; ++c) ls[c] = J.d[c].l;
+  return ls;
+}
+
 void add_chol(Job& J, int accumulate, int f32_chol = 0) {
   const Chan* dch = J.d_ch;
-  const int C = J.C, maxl = J.max_l;
+  const int maxl = J.max_l;
   const int f32inv = J.mixed ? 1 : 0;
   cudaStream_t st = J.P->st;
+  const std::vector<int> ls = chan_ls(J);
+  int* coop = J.P->d_coop;
   J.steps.push_back([=]() {
-    launch_chol_inv(dch, C, accumulate, maxl, f32inv, st, f32_chol);
+    run_chol(dch, ls, accumulate, maxl, f32inv, f32_chol, 0, coop, st);
     return RSVD_OK;
   });
 }
@@ -485,8 +527,11 @@ void build_fp64(Job& J) {
   const int maxl = J.max_l;
   const int policy = J.policy;
   const double tol = J.tol;
+  std::vector<int> ls(C);
+  for (int c = 0; c < C; ++c) ls[c] = J.d[c].l;
+  int* coop = J.P->d_coop;
   J.steps.push_back([=]() {
-    launch_jacobi(dch, C, 0, maxl, st);
+    run_jacobi(dch, ls, 0, maxl, coop, st);
     launch_select(dch, C, policy, tol, 0, st);
     return RSVD_OK;
   });
@@ -752,8 +797,10 @@ void cqr2_mixed(Job& J, int nsl_out) {
     const Chan* dch = J.d_ch;
     const int C = J.C, maxl = J.max_l;
     cudaStream_t st = J.P->st;
+    const std::vector<int> ls = chan_ls(J);
+    int* coop = J.P->d_coop;
     J.steps.push_back([=]() {
-      launch_chol_inv(dch, C, 0, maxl, 1, st, 0, 1);
+      run_chol(dch, ls, 0, maxl, 1, 0, 1, coop, st);
       return RSVD_OK;
     });
   }
@@ -805,8 +852,10 @@ Chan* reorth_x(Job& J) {
   {
     const int C = J.C, maxl = J.max_l;
     cudaStream_t st = J.P->st;
+    const std::vector<int> ls = chan_ls(J);
+    int* coop = J.P->d_coop;
     J.steps.push_back([=]() {
-      launch_chol_inv(dsw, C, 0, maxl, 0, st, 1);   // X^T X ~ I: an FP32 factor is enough
+      run_chol(dsw, ls, 0, maxl, 0, 1, 0, coop, st);   // X^T X ~ I: an FP32 factor is enough
       return RSVD_OK;
     });
   }
@@ -911,8 +960,11 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   add_chol(J, 0);
   const int policy = J.policy;
   const double tol = J.tol;
+  std::vector<int> ls(C);
+  for (int c = 0; c < C; ++c) ls[c] = J.d[c].l;
+  int* coop = J.P->d_coop;
   J.steps.push_back([=]() {
-    launch_jacobi(dch, C, 1, maxl, st);
+    run_jacobi(dch, ls, 1, maxl, coop, st);
     return RSVD_OK;
   });
   const Chan* dsw = reorth_x(J);                 // X~ in J
@@ -1436,8 +1488,11 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
     const Chan* dch = J.d_ch;
     const int maxl = J.max_l, maxk = J.max_kcap;
     cudaStream_t st = P->st;
+    std::vector<int> ls(Cf);
+    for (int a = 0; a < Cf; ++a) ls[a] = J.d[a].l;
+    int* coop = P->d_coop;
     J.steps.push_back([=]() {
-      launch_jacobi(dch, Cf, 0, maxl, st);
+      run_jacobi(dch, ls, 0, maxl, coop, st);
       launch_select(dch, Cf, RSVD_RANK_TOL, tol, 0, st);
       return RSVD_OK;
     });
@@ -1892,8 +1947,11 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
     cudaStream_t st = P->st;
     {
       const Chan* d0 = J.d_ch;
+      std::vector<int> ls(Cf);
+      for (int a = 0; a < Cf; ++a) ls[a] = J.d[a].l;
+      int* coop = P->d_coop;
       J.steps.push_back([=]() {
-        launch_jacobi(d0, Cf, 1, maxl, st);
+        run_jacobi(d0, ls, 1, maxl, coop, st);
         return RSVD_OK;
       });
     }
@@ -2304,6 +2362,7 @@ rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factor
       Q.slices = P->slices;
       Q.st = P->st;
       Q.d_err = P->d_err;
+      Q.d_coop = P->d_coop;
       Q.profiling = P->profiling;
       r = run_adaptive(&Q, (int)idx.size(), As.data(), fs.data(), sts.data());
       P->prof.tc_launches += Q.prof.tc_launches; P->prof.tc_ms += Q.prof.tc_ms;
@@ -2374,10 +2433,11 @@ rsvd_status rsvd_plan(rsvd_plan_t* out, const rsvd_opts* o) {
   P->o = *o;
   P->st = (cudaStream_t)o->stream;
   P->slices = o->slices ? o->slices : 2;
-  if (cudaMalloc((void**)&P->d_err, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc((void**)&P->d_err, sizeof(int) * (64 + (size_t)kCoopWsInts)) != cudaSuccess) {
     delete P;
     return seterr(RSVD_ERR_OOM, "cudaMalloc of the error word failed");
   }
+  P->d_coop = P->d_err + 64;
   cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st);
   *out = P;
   return RSVD_OK;

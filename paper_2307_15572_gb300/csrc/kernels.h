@@ -68,6 +68,17 @@ void launch_copy_t_to_q_if_shifted(const Chan* d_ch, int C, cudaStream_t st);
 // One-sided Jacobi SVD of M = R^T (FP64 or FP32 arithmetic); writes sig, M <- left
 // vectors, J <- right vectors, sorted by descending sigma.
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st);
+// The same on a cooperative grid, several CTAs per channel (for l past the
+// single CTA's shared memory); h_l: host copy of the channels' l.  coop_ws:
+// kCoopWsInts zero-able ints of device scratch.  Returns 0, or -1 if it did
+// not launch (the caller then runs launch_jacobi).
+constexpr int kCoopMaxChannels = 512;
+constexpr int kCoopWsInts = 4 + 60 * kCoopMaxChannels;
+int launch_jacobi_coop(const Chan* d_ch, const int* h_l, int C, int fp32, int* coop_ws, cudaStream_t st);
+// Cholesky + inverse (launch_chol_inv's contract, FP64 inverse) on a
+// cooperative grid; same return convention.
+int launch_chol_coop(const Chan* d_ch, const int* h_l, int C, int accumulate, int f32_chol, int conditional,
+                     int* coop_ws, cudaStream_t st);
 // Rank selection (fixed or tolerance) from sig and ||A||^2 (FP64 identity),
 // or from the probe residual (mixed path).  Writes S and ChanResult.
 // Probe rule: with s Gaussian probe columns g_j the energies

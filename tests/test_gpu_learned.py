@@ -131,7 +131,7 @@ def test_learned_beats_adaptive_mixed(lib, trained):
         stats = {}
         theta = trained["thetas"]["bf16x"] if policy == "learned" else None
         dt, facs, per, errs = learn.run_policy(pop, mats, policy, "bf16x", theta=theta, lmax=LMAX, block=32,
-                                               slices=3, repeat=2, stats=stats)
+                                               slices=3, repeat=4, stats=stats)
         out[policy] = (dt, stats["passes"], np.array([s >= 0 for s in per]), errs)
     (ta, pa, oka, ea), (tl, pl, okl, el) = out["adaptive"], out["learned"]
     print(f"adaptive: {ta * 1e3:.1f} ms, {pa} passes, {oka.sum()} met; "
