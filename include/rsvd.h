@@ -124,7 +124,9 @@ typedef enum { RSVD_MEM_DEVICE = 0, RSVD_MEM_HOST = 1 } rsvd_mem;
  * stored: every pass generates the entries it reads, row panel by row panel,
  * on the tensor core (BF16x3 factor words, FP32 accumulation; entries
  * accurate to ~1e-6 relative).  Tile rules need precision BF16X and the
- * FIXED or TOL rank policy, and cannot share a call with stored channels
+ * FIXED, TOL or LEARNED rank policy (LEARNED's last resort is then one run at
+ * l_max instead of the adaptive loop, which would regenerate the matrix for
+ * every block), and cannot share a call with stored channels
  * (RSVD_ERR_UNSUPPORTED otherwise).  Tuning: the environment variable
  * RSVD_RULE_PANEL sets the rows generated per panel (default: panels of
  * ~8 GiB of words).

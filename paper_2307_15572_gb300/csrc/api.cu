@@ -875,6 +875,25 @@ Chan* reorth_x(Job& J) {
   return dsw;
 }
 
+// The factor panel H of each tile rule (its parameters travel in the
+// descriptor region).
+std::vector<RuleDesc> rule_descs(Job& J) {
+  std::vector<RuleDesc> rds(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const rsvd_matrix& A = J.A[c];
+    const int M = A.rule_m;
+    RuleDesc r{};
+    r.n = J.d[c].n; r.M = M;
+    r.c = J.ar.put(A.rule_c, M);
+    r.s = J.ar.put(A.rule_s, M);
+    r.w = J.ar.put(A.rule_w, M);
+    for (int w = 0; w < 3; ++w) r.H[w] = J.rd[c].H[w];
+    r.ldh = J.rd[c].ldh;
+    rds[c] = r;
+  }
+  return rds;
+}
+
 rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   auto& ch = J.ch;
   const int C = J.C;
@@ -888,20 +907,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   const uint64_t seed = J.P->o.seed;
   const uint64_t pseed = seed ^ 0x5DEECE66DULL;
   if (J.rule) {
-    // the factor panel H of each rule (its parameters travel in the descriptor region)
-    std::vector<RuleDesc> rds(C);
-    for (int c = 0; c < C; ++c) {
-      const rsvd_matrix& A = J.A[c];
-      const int M = A.rule_m;
-      RuleDesc r{};
-      r.n = J.d[c].n; r.M = M;
-      r.c = J.ar.put(A.rule_c, M);
-      r.s = J.ar.put(A.rule_s, M);
-      r.w = J.ar.put(A.rule_w, M);
-      for (int w = 0; w < 3; ++w) r.H[w] = J.rd[c].H[w];
-      r.ldh = J.rd[c].ldh;
-      rds[c] = r;
-    }
+    const std::vector<RuleDesc> rds = rule_descs(J);
     J.steps.push_back([=]() {
       for (const RuleDesc& r : rds) launch_rule_prep(r, st);
       launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
@@ -999,7 +1005,19 @@ rsvd_status build_probe(Job& J, float* d_feat, const float* theta, float* d_pred
   const double tol = J.tol;
   const int* off64 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
   const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
-  if (J.mixed) {
+  if (J.mixed && J.rule) {
+    // tile rules: the probe is one generated pass with 16 columns
+    const std::vector<RuleDesc> rds = rule_descs(J);
+    J.steps.push_back([=]() {
+      for (const RuleDesc& r : rds) launch_rule_prep(r, st);
+      launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 16, seed, 1, st, TAG_PROBE);
+      return RSVD_OK;
+    });
+    if (rsvd_status s = pass_over(J, J.nsl, 1, 0, true)) return s;
+    add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Y32; },
+           [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return ch[c].G; },
+           [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+  } else if (J.mixed) {
     const int* off8 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 8); });
     const int t8 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 8); });
     const int nsl = J.nsl;
@@ -1148,8 +1166,8 @@ rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_fac
     if (a.kind == RSVD_TILE_RULE) {
       if (P->o.precision != RSVD_PREC_BF16X)
         return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules are generated on the tensor-core path only", c);
-      if (P->o.rank_policy != RSVD_RANK_FIXED && P->o.rank_policy != RSVD_RANK_TOL)
-        return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules take the fixed or tolerance rank policy", c);
+      if (P->o.rank_policy == RSVD_RANK_ADAPTIVE)
+        return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules take the fixed, tolerance or learned policy", c);
       if (a.rule_m < 1 || a.rule_m > 4096)
         return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_m %d outside [1, 4096]", c, a.rule_m);
       if (!a.rule_c || !a.rule_s || !a.rule_w)
@@ -2296,8 +2314,8 @@ rsvd_status run_probe(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors*
 // Learned rank: probe -> features -> network -> per-channel
 // l = 1.2 (k^ + p^), one fixed-l decomposition (reusing the probe's V words);
 // channels whose rank rule misses the tolerance get one retry at 1.5 l, then
-// the adaptive loop in the plan's precision -- the plain method stays both
-// the fallback and the judge.  A channel that already drew all the columns
+// the adaptive loop in the plan's precision (for tile rules: one run at the
+// column cap) -- the plain method stays both the fallback and the judge.  A channel that already drew all the columns
 // it may (n or l_max) keeps its best factors and TOL_NOT_MET.
 rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item) {
   if (!P->o.mlp_weights) return seterr(RSVD_ERR_INVALID_ARG, "learned rank needs mlp_weights");
@@ -2352,6 +2370,14 @@ rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factor
     std::vector<rsvd_status> sts(idx.size());
     t0 = now();
     if (attempt == 0) {
+      r = run_fixed_l(P, (int)idx.size(), As.data(), fs.data(), sts.data(), &ls, false);
+    } else if (A[0].kind == RSVD_TILE_RULE) {
+      // tile rules have no adaptive loop (every block would regenerate the
+      // matrix twice): the last resort is one run at the column cap
+      for (size_t i = 0; i < idx.size(); ++i) {
+        ls[i] = (int)std::min<int64_t>(A[idx[i]].n, lcap_opt);
+        lvec[idx[i]] = ls[i];
+      }
       r = run_fixed_l(P, (int)idx.size(), As.data(), fs.data(), sts.data(), &ls, false);
     } else {
       // the plain adaptive loop in the plan's precision (a temporary plan
@@ -2504,8 +2530,8 @@ rsvd_status rsvd_probe_features(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, 
     f[c].tol = tol ? tol[c] : 0.0;
   }
   if (rsvd_status s = validate(P, C, A, f.data())) return s;
-  if (A[0].kind == RSVD_TILE_RULE)
-    return seterr(RSVD_ERR_UNSUPPORTED, "probe features are built for stored channels");
+  if (A[0].kind == RSVD_TILE_RULE && P->o.precision != RSVD_PREC_BF16X)
+    return seterr(RSVD_ERR_UNSUPPORTED, "tile rules are generated on the tensor-core path only");
   std::vector<float> feat;
   const float* saved = P->o.mlp_weights;
   P->o.mlp_weights = nullptr;

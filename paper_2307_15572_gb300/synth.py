@@ -180,12 +180,13 @@ def rule_params(M=300, seed=SEED_RULE, decay=25.0):
     return c, s, w
 
 
-def learn_channel_params(count=4000, seed=SEED_LEARN, nlo=500, nhi=20000):
+def learn_channel_params(count=4000, seed=SEED_LEARN, nlo=500, nhi=20000, tlo=1e-7, thi=1e-3):
     """Per-channel (n, tol, rule params) for the learned-rank population.
 
     Weights mix exponential and algebraic decay,
     w_m = a exp(-m / tau) + (1 - a) m^-beta, a ~ U[0,1], tau ~ logU[5,200],
-    beta ~ U[1.5, 4]; tol log-uniform in [1e-7, 1e-3]; M = min(n, 1024) bumps.
+    beta ~ U[1.5, 4]; tol log-uniform in [tlo, thi] (default [1e-7, 1e-3]);
+    M = min(n, 1024) bumps.
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -195,7 +196,7 @@ def learn_channel_params(count=4000, seed=SEED_LEARN, nlo=500, nhi=20000):
         a = rng.uniform()
         tau = math.exp(rng.uniform(math.log(5.0), math.log(200.0)))
         beta = rng.uniform(1.5, 4.0)
-        tol = math.exp(rng.uniform(math.log(1e-7), math.log(1e-3)))
+        tol = math.exp(rng.uniform(math.log(tlo), math.log(thi)))
         m = np.arange(1, M + 1, dtype=np.float64)
         w = a * np.exp(-m / tau) + (1 - a) * m ** (-beta)
         c = rng.uniform(0.0, 8.0, size=M)
