@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--rule-steps", type=int, default=2)
     ap.add_argument("--rule-n", type=int, default=200000)
     ap.add_argument("--no-rule", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed default launch shapes")
     return ap.parse_args()
 
 
@@ -189,8 +190,18 @@ def run_gpu(args):
     lib = rsvd
 
     def make_plan(prec):
+        # autotuning happens in the first warm-up step (outside the timed region)
         return rsvd.Plan(max(sizes), k=kcap, p=P_OVER, q=0, tol=TOL, policy="tol", precision=prec, slices=2,
-                         seed=seed, stream=stream.cuda_stream)
+                         seed=seed, stream=stream.cuda_stream, autotune=not args.no_autotune)
+
+    def tune_summary(plan):
+        recs = rsvd.rsvd_plan_tune_records(plan.h)
+        keep = ("kind", "candidates", "choice", "bn", "split_target", "stages", "order")
+        return {"on": not args.no_autotune, "signatures": len(recs),
+                "non_default": sum(1 for r in recs if r["choice"] != 0),
+                "tuning_ms": sum(r["tune_ms"] for r in recs),
+                "choices": [dict({k: r[k] for k in keep}, ms_default=round(r["ms_default"], 4),
+                                 ms_best=round(r["ms_best"], 4)) for r in recs]}
 
     def alloc_factors(device="cuda", pin=False):
         facs, bufs = [], []
@@ -275,6 +286,7 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": tc_bytes_per,
                 "share_of_step": prof["tc_ms"] / ms if ms > 0 else None}
     gpu_launches = int(prof["launches"])
+    tuning = tune_summary(plan)
     plan.close()
 
     # ---- e2e through the C ABI with host buffers
@@ -314,7 +326,8 @@ def run_gpu(args):
                 "ranks": [min(ks_f), max(ks_f)],
                 "roofline": {"bound": "alu", "kernel": "k_tile_mm<double> (FP64 pass over V)",
                              "achieved": f64_tf, "peak": 1.25, "unit": "TFLOP/s", "frac": f64_tf / 1.25,
-                             "peak_source": "nominal FP64 rate of GB300"}}
+                             "peak_source": "nominal FP64 rate of GB300"},
+                "autotune": tune_summary(plan)}
         plan.close()
 
     # ---- matrix-free tile rule: n = 200,000, M = 300 bumps, k = 320, p = 10, q = 1
@@ -373,7 +386,8 @@ def run_gpu(args):
                                        "FP64 Cholesky",
                           "l2": "inputs larger than L2 (no flush)", "max_rel_err": max_err,
                           "verified_tol": bool(max_err <= TOL), "ranks": [min(ks), max(ks)],
-                          "parallelism": "channels per GPU" if ws > 1 else "single GPU"},
+                          "parallelism": "channels per GPU" if ws > 1 else "single GPU",
+                          "autotune": tuning},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                "clocks": clk, "fp64_path": fp64, "rule_path": rule,
                "mixed_over_fp64": (value / fp64["value"]) if fp64 else None}

@@ -234,6 +234,49 @@ rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
 rsvd_status rsvd_plan_set_graphs(rsvd_plan_t plan, int32_t enable);
 rsvd_status rsvd_plan_profile(rsvd_plan_t plan, rsvd_profile* out, int32_t reset);
 
+/* Autotuning of launch shapes (off by default).
+ *
+ * The grouped passes over the channels (Fig. 1 steps 1 and 2 and the power
+ * iterations: the tensor-core products of the mixed path and the FP64
+ * products of the FP64 path) can be launched in several shapes that compute
+ * the same result up to the order of FP32/FP64 summation: the output-column
+ * tile width, the k-split policy (how many work items per SM the split aims
+ * for, and the shortest split), the shared-memory pipeline depth, and the
+ * order in which the persistent CTAs take the channels' work items.  With
+ * autotuning on, the first execution of a pass whose signature (kind of pass,
+ * word counts, every channel's size and column count) this plan has not seen
+ * times every distinct candidate shape on the caller's own data -- one
+ * warm-up launch, then the better of two timed launches each -- keeps the
+ * fastest (the fixed default rule unless another is at least 2% faster) and
+ * runs it; later passes with that signature, in the same call and in later
+ * calls, run the chosen shape without timing.  A call that tunes synchronises
+ * its stream between candidates and is not captured into a CUDA graph (later
+ * calls of the same shape are, if graphs are on).  Enabling drops the plan's
+ * captured graphs; disabling keeps the choices already made (the plan keeps
+ * using them) and stops tuning new signatures.  The tile-rule passes keep
+ * their fixed shapes.  rsvd_plan_tune_records copies up to `cap` records of
+ * the choices, in the order they were made, and sets *count to the number
+ * the plan holds.  For diagnostics, the environment variable
+ * RSVD_TUNE_FORCE=i makes every new signature take candidate i (modulo the
+ * number of candidates) after timing them. */
+enum { RSVD_TUNE_TC = 0, RSVD_TUNE_DENSE_F64 = 1 };
+typedef struct {
+  int32_t kind;            /* RSVD_TUNE_TC or RSVD_TUNE_DENSE_F64                 */
+  int32_t candidates;      /* distinct shapes timed                              */
+  int32_t choice;          /* index of the chosen shape (0: the default rule)    */
+  int32_t bn;              /* output-column tile width                           */
+  int32_t split_target;    /* work items the k split aims for (0: no split)      */
+  int32_t min_split;       /* shortest k split, rows of V                        */
+  int32_t stages;          /* shared-memory pipeline stages (tensor-core pass)   */
+  int32_t order;           /* 1: longest channel first, 0: channel order         */
+  float ms_default;        /* device time of the default shape (best of two)    */
+  float ms_best;           /* device time of the chosen shape                    */
+  float tune_ms;           /* host time spent tuning this signature              */
+} rsvd_tune_record;
+
+rsvd_status rsvd_plan_set_autotune(rsvd_plan_t plan, int32_t enable);
+rsvd_status rsvd_plan_tune_records(rsvd_plan_t plan, rsvd_tune_record* out, int32_t cap, int32_t* count);
+
 /* Exact relative residual with no device allocation (no plan needed).
  *
  * The paper has no counterpart: this is a service for callers that cannot

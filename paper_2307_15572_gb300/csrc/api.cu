@@ -96,6 +96,16 @@ struct rsvd_plan_s {
   struct GraphEntry { std::string key; cudaGraphExec_t exec; long long launches; uint64_t used; };
   std::vector<GraphEntry> gcache;
   uint64_t gclock = 0;
+  // autotuner: launch-shape choice per pass signature (see add_tuned)
+  int autotune = 0;
+  struct TuneEntry { std::string key; rsvd_tune_record rec; };
+  std::vector<TuneEntry> tune;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  const TuneEntry* tuned(const std::string& k) const {
+    for (const auto& t : tune)
+      if (t.key == k) return &t;
+    return nullptr;
+  }
 };
 
 void drop_graphs(rsvd_plan_s* P) {
@@ -216,10 +226,11 @@ void drain_profile(rsvd_plan_s* P) {
   P->ev_next = 0;
 }
 
-// Split a tile count over k so that the grid covers the GPU a couple of times.
-int pick_splits(int64_t tiles, int64_t k, int min_chunk) {
-  if (tiles >= 2 * NSM) return 1;
-  int ks = (int)((2 * NSM + tiles - 1) / tiles);
+// Split a tile count over k so that the grid covers the GPU `target` tiles
+// (by default twice per SM); target 0: no split.
+int pick_splits(int64_t tiles, int64_t k, int min_chunk, int64_t target = 2 * NSM) {
+  if (target <= 0 || tiles >= target) return 1;
+  int ks = (int)((target + tiles - 1) / tiles);
   int maxk = (int)std::max<int64_t>(1, k / min_chunk);
   return std::max(1, std::min(ks, maxk));
 }
@@ -264,6 +275,7 @@ struct Job {
   std::vector<RuleDev> rd;
   __nv_bfloat16* pw[3] = {nullptr, nullptr, nullptr};   // panel words (panel x ldb each)
   double* part = nullptr;               // per (item, warp) partials of one generation launch
+  bool tuning = false;                  // holds a pass the autotuner still has to time
 };
 
 // Tile rule: H words have M padded to whole 64-wide k steps.
@@ -304,8 +316,95 @@ int total_of(Job& J, const std::function<int64_t(int)>& per) {
   return (int)t;
 }
 
+// ------------------------------------------------------------ autotuner
+// A pass with several launch shapes that compute the same result (up to the
+// order of FP32/FP64 summation).  Candidate 0 is the fixed default rule.  The
+// plan's table maps the pass signature to the chosen candidate; until it has
+// one (and while autotuning is on), the first execution outside stream
+// capture times every candidate on the caller's data -- one warm-up launch,
+// then the better of two timed launches each -- and keeps the fastest unless
+// it is within 2% of the default.  Variants only write the pass's output, so
+// running several of them in a row leaves the same result.
+std::string tune_key(const char* kind, std::initializer_list<int64_t> head, const std::vector<int64_t>& per) {
+  std::string k(kind);
+  for (int64_t v : head) k.append((const char*)&v, sizeof(v));
+  for (int64_t v : per) k.append((const char*)&v, sizeof(v));
+  return k;
+}
+
+void add_tuned(Job& J, const std::string& key, const std::vector<rsvd_tune_record>& recs,
+               const std::vector<std::function<rsvd_status()>>& vars) {
+  rsvd_plan_s* P = J.P;
+  if (vars.size() == 1) {
+    J.steps.push_back(vars[0]);
+    return;
+  }
+  J.tuning = true;
+  J.steps.push_back([=]() -> rsvd_status {
+    if (const auto* t = P->tuned(key)) return vars[t->rec.choice]();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (P->st) cudaStreamIsCapturing(P->st, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return vars[0]();
+    for (auto& e : P->tune_ev)
+      if (!e) CK(cudaEventCreate(&e));
+    const int prof = P->profiling;
+    P->profiling = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<float> ms(vars.size(), 3.0e38f);
+    rsvd_status bad = RSVD_OK;
+    if ((bad = vars[0]()) == RSVD_OK) {
+      for (int rep = 0; rep < 2 && !bad; ++rep)
+        for (size_t i = 0; i < vars.size() && !bad; ++i) {
+          cudaEventRecord(P->tune_ev[0], P->st);
+          if ((bad = vars[i]())) break;
+          cudaEventRecord(P->tune_ev[1], P->st);
+          if (cudaEventSynchronize(P->tune_ev[1]) != cudaSuccess) {
+            bad = seterr(RSVD_ERR_CUDA, "autotuner: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+          }
+          float t = 0.f;
+          cudaEventElapsedTime(&t, P->tune_ev[0], P->tune_ev[1]);
+          ms[i] = std::min(ms[i], t);
+        }
+    }
+    P->profiling = prof;
+    if (bad) return bad;
+    size_t best = 0;
+    for (size_t i = 1; i < vars.size(); ++i)
+      if (ms[i] < ms[best]) best = i;
+    if (ms[best] > 0.98f * ms[0]) best = 0;
+    if (const char* f = getenv("RSVD_TUNE_FORCE")) best = (size_t)std::max(0, atoi(f)) % vars.size();
+    rsvd_tune_record r = recs[best];
+    r.candidates = (int32_t)vars.size();
+    r.choice = (int32_t)best;
+    r.ms_default = ms[0];
+    r.ms_best = ms[best];
+    r.tune_ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    P->tune.push_back({key, r});
+    if (getenv("RSVD_DEBUG"))
+      fprintf(stderr, "rsvd autotune: kind %d, %d candidates, choice %d (bn %d, split %d, stages %d, order %d): "
+              "%.3f ms vs default %.3f ms\n", r.kind, r.candidates, r.choice, r.bn, r.split_target, r.stages,
+              r.order, r.ms_best, r.ms_default);
+    return vars[best]();
+  });
+}
+
+// Which candidates to build: the chosen one, all of them (tuning), or the default.
+std::vector<int> tune_pick(Job& J, const std::string& key, size_t ncand) {
+  if (const auto* t = J.P->tuned(key)) return {t->rec.choice};
+  if (J.P->autotune && ncand > 1) {
+    std::vector<int> all(ncand);
+    for (size_t i = 0; i < ncand; ++i) all[i] = (int)i;
+    return all;
+  }
+  return {0};
+}
+
 // ------------------------------------------------------------ step builders
-void add_mm(Job& J, MMKind kind, std::vector<MMDesc> md) {
+std::function<rsvd_status()> make_mm(Job& J, MMKind kind, std::vector<MMDesc> md);
+void add_mm(Job& J, MMKind kind, std::vector<MMDesc> md) { J.steps.push_back(make_mm(J, kind, std::move(md))); }
+
+std::function<rsvd_status()> make_mm(Job& J, MMKind kind, std::vector<MMDesc> md) {
   const int tile = tile_of(kind);
   for (auto& m : md) {
     m.tile = tile;
@@ -324,7 +423,7 @@ void add_mm(Job& J, MMKind kind, std::vector<MMDesc> md) {
   cudaStream_t st = J.P->st;
   const int C = J.C;
   rsvd_plan_s* P = J.P;
-  J.steps.push_back([=]() {
+  return [=]() {
     const bool timed = P->profiling && kind == MMK_DENSE_F64;
     cudaEvent_t a = nullptr, b = nullptr;
     if (timed) timed_begin(P, &a, &b);
@@ -334,7 +433,7 @@ void add_mm(Job& J, MMKind kind, std::vector<MMDesc> md) {
       P->pending.push_back({a, b, 1, 0.0, flops});
     }
     return RSVD_OK;
-  });
+  };
 }
 
 // Gram-like TN product with split partials and fixed-order reduction:
@@ -431,41 +530,82 @@ void cqr2_f64(Job& J, std::function<double*(int)> src, std::function<double*(int
   }
 }
 
-// Y_c = V_c X_c (dense FP64), split over k with atomic accumulation when small.
+// Y_c = V_c X_c (dense FP64), split over k with atomic accumulation when the
+// batch has too few output tiles to fill the GPU.  Autotuned: the split target
+// (1, 2 or 4 tiles per SM, or none) and the shortest split (64 or 128 rows).
 void dense_f64(Job& J, std::function<const double*(int)> X, std::function<double*(int)> Y) {
   int64_t tiles = 0;
   for (int c = 0; c < J.C; ++c) tiles += (int64_t)cdiv(J.d[c].n, 64) * cdiv(J.d[c].l, 64);
-  std::vector<MMDesc> md(J.C);
-  std::vector<ZeroDesc> zd(J.C);
-  bool any_split = false;
-  for (int c = 0; c < J.C; ++c) {
-    const ChanDims& d = J.d[c];
-    MMDesc m{};
-    m.A = J.ch[c].A; m.lda = J.ch[c].lda;
-    m.B = X(c); m.ldb = d.ldt;
-    m.Cm = Y(c); m.ldc = d.ldt;
-    m.m = d.n; m.n = d.l; m.k = d.n;
-    m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64);
-    m.ks = pick_splits(tiles, d.n, 128);
-    m.kchunk = (int)rup(cdiv(d.n, m.ks), 16);
-    m.ks = cdiv(d.n, m.kchunk);
-    m.mode = m.ks > 1 ? MM_ATOMIC : MM_STORE;
-    any_split |= m.ks > 1;
-    md[c] = m;
-    zd[c] = ZeroDesc{Y(c), d.ldt, d.n, d.l, 8};
+  struct Cfg { int target, min_chunk; };
+  const Cfg all[] = {{2, 128}, {1, 128}, {4, 128}, {4, 64}, {0, 128}};
+  auto ks_of = [&](const Cfg& g, int c) {
+    const int n = J.d[c].n;
+    int ks = pick_splits(tiles, n, g.min_chunk, (int64_t)g.target * NSM);
+    const int kchunk = (int)rup(cdiv(n, ks), 16);
+    return std::make_pair(cdiv(n, kchunk), kchunk);
+  };
+  // distinct candidates (by the splits they give every channel)
+  std::vector<Cfg> cands;
+  std::vector<std::vector<int>> sigs;
+  for (const Cfg& g : all) {
+    std::vector<int> sg(J.C);
+    for (int c = 0; c < J.C; ++c) sg[c] = ks_of(g, c).first;
+    if (std::find(sigs.begin(), sigs.end(), sg) == sigs.end()) {
+      sigs.push_back(sg);
+      cands.push_back(g);
+    }
   }
-  if (any_split) {
-    const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
-    const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
-    const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
-    cudaStream_t st = J.P->st;
-    const int C = J.C;
-    J.steps.push_back([=]() {
-      launch_zero(dzd, off, C, tiles64, st);
-      return RSVD_OK;
+  std::vector<int64_t> per;
+  for (int c = 0; c < J.C; ++c) { per.push_back(J.d[c].n); per.push_back(J.d[c].l); }
+  const std::string key = tune_key("f64", {}, per);
+  std::vector<std::function<rsvd_status()>> vars;
+  std::vector<rsvd_tune_record> recs;
+  for (int ci : tune_pick(J, key, cands.size())) {
+    const Cfg g = cands[ci];
+    std::vector<MMDesc> md(J.C);
+    std::vector<ZeroDesc> zd(J.C);
+    bool any_split = false;
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      MMDesc m{};
+      m.A = J.ch[c].A; m.lda = J.ch[c].lda;
+      m.B = X(c); m.ldb = d.ldt;
+      m.Cm = Y(c); m.ldc = d.ldt;
+      m.m = d.n; m.n = d.l; m.k = d.n;
+      m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64);
+      const auto kk = ks_of(g, c);
+      m.ks = kk.first;
+      m.kchunk = kk.second;
+      m.mode = m.ks > 1 ? MM_ATOMIC : MM_STORE;
+      any_split |= m.ks > 1;
+      md[c] = m;
+      zd[c] = ZeroDesc{Y(c), d.ldt, d.n, d.l, 8};
+    }
+    std::function<rsvd_status()> zero;
+    if (any_split) {
+      const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+      const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+      const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
+      cudaStream_t st = J.P->st;
+      const int C = J.C;
+      zero = [=]() {
+        launch_zero(dzd, off, C, tiles64, st);
+        return RSVD_OK;
+      };
+    }
+    auto mm = make_mm(J, MMK_DENSE_F64, md);
+    vars.push_back([=]() {
+      if (zero) zero();
+      return mm();
     });
+    rsvd_tune_record r{};
+    r.kind = RSVD_TUNE_DENSE_F64;
+    r.bn = 64;
+    r.split_target = g.target * NSM;
+    r.min_split = g.min_chunk;
+    recs.push_back(r);
   }
-  add_mm(J, MMK_DENSE_F64, md);
+  add_tuned(J, key, recs, vars);
 }
 
 void lift(Job& J, MMKind kind, std::function<const void*(int)> basis, std::function<const double*(int)> small,
@@ -550,92 +690,153 @@ void build_fp64(Job& J) {
 // --------------------------------------------------------------- mixed path
 rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
                        std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout) {
-  // one grouped tcgen05 launch: Y[:, 0:ncols) = sum words V_a X_b
-  // tile width: all columns in one tile up to the kernel's register
-  // accumulator width (160), else balanced column tiles
+  // one grouped tcgen05 launch: Y[:, 0:ncols) = sum words V_a X_b.
+  // Default shape: all columns in one tile up to the kernel's register
+  // accumulator width (160), else balanced column tiles; k split only when
+  // the batch has fewer than two items per SM; as many pipeline stages as
+  // shared memory holds; items longest channel first.  Autotuned: one or two
+  // more column tiles, the split target (4 items per SM with shorter splits,
+  // or none), a 4-stage pipeline, and the plain channel order.
   int maxnc = 16;
-  for (int c = 0; c < J.C; ++c) maxnc = std::max(maxnc, ncols_of(c));
-  const int ntile = cdiv(maxnc, 160);
-  const int bn = (int)rup(cdiv(maxnc, ntile), 16);
-  std::vector<TcChan> tcs(J.C);
-  int64_t items0 = 0;
-  for (int c = 0; c < J.C; ++c) items0 += (int64_t)cdiv(J.d[c].n, 128) * cdiv(ncols_of(c), bn);
-  bool any_split = false;
-  std::vector<ZeroDesc> zd(J.C);
-  int item = 0;
-  // items numbered longest first: the persistent CTAs take items round-robin,
-  // so this order balances them (longest-processing-time-first)
-  std::vector<int> order(J.C);
-  for (int c = 0; c < J.C; ++c) order[c] = c;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return J.d[a].n > J.d[b].n; });
-  for (int pos = 0; pos < J.C; ++pos) {
-    const int c = order[pos];
-    const ChanDims& d = J.d[c];
-    const int nc = ncols_of(c);
-    TcChan& t = tcs[pos];
-    memset(&t, 0, sizeof(t));
-    const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
-    const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
-    if (!J.measure) {
-      const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, d.n, nc, bn);
-      if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
-    }
-    t.Y = yout(c);
-    t.ldy = d.ldt;
-    t.n = d.n;
-    t.m = d.n;
-    t.mode = TC_STORE;
-    t.ncols = nc;
-    t.mt = cdiv(d.n, 128);
-    t.nt = cdiv(nc, bn);
-    const int kt = cdiv(d.n, 64);
-    int ks = pick_splits(items0, kt, 8);
-    t.kt_per_split = cdiv(kt, ks);
-    t.ks = cdiv(kt, t.kt_per_split);
-    t.atomic = t.ks > 1;
-    any_split |= t.atomic != 0;
-    t.item0 = item;
-    item += t.mt * t.nt * t.ks;
-    zd[c] = ZeroDesc{t.Y, d.ldt, d.n, nc, 4};
+  std::vector<int> nc_of(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    nc_of[c] = ncols_of(c);
+    maxnc = std::max(maxnc, nc_of[c]);
   }
-  const int items = item;
-  if (any_split) {
-    const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
-    const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
-    const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
+  struct Cfg { int bn, target, min_chunk, stages, lpt; };
+  std::vector<Cfg> cands;
+  {
+    const int nt0 = cdiv(maxnc, 160);
+    std::vector<int> bns;
+    for (int nt : {nt0, nt0 + 1, 2 * nt0}) {
+      const int bn = (int)rup(cdiv(maxnc, nt), 16);
+      if ((nt == nt0 || bn >= 32) && std::find(bns.begin(), bns.end(), bn) == bns.end()) bns.push_back(bn);
+    }
+    const int splits[3][2] = {{2, 8}, {4, 4}, {0, 8}};
+    for (int bn : bns)
+      for (const auto& sp : splits)
+        for (int stg : {0, 4}) cands.push_back({bn, sp[0], sp[1], stg, 1});
+    cands.push_back({bns[0], 2, 8, 0, 0});
+  }
+  auto ks_of = [&](const Cfg& g, int c) {
+    int64_t items0 = 0;
+    for (int e = 0; e < J.C; ++e) items0 += (int64_t)cdiv(J.d[e].n, 128) * cdiv(nc_of[e], g.bn);
+    const int kt = cdiv(J.d[c].n, 64);
+    const int ks = pick_splits(items0, kt, g.min_chunk, (int64_t)g.target * NSM);
+    const int kps = cdiv(kt, ks);
+    return std::make_pair(cdiv(kt, kps), kps);
+  };
+  {
+    // drop candidates that give the same launch as an earlier one
+    std::vector<Cfg> uniq;
+    std::vector<std::vector<int>> sigs;
+    for (const Cfg& g : cands) {
+      std::vector<int> sg = {g.bn, std::min(g.stages ? g.stages : 99, tc_stages(sa, sx, g.bn)), g.lpt};
+      for (int c = 0; c < J.C; ++c) sg.push_back(ks_of(g, c).first);
+      if (std::find(sigs.begin(), sigs.end(), sg) == sigs.end()) {
+        sigs.push_back(sg);
+        uniq.push_back(g);
+      }
+    }
+    cands.swap(uniq);
+  }
+  std::vector<int64_t> per;
+  for (int c = 0; c < J.C; ++c) { per.push_back(J.d[c].n); per.push_back(nc_of[c]); }
+  const std::string key = tune_key("tc", {sa, sx}, per);
+  std::vector<std::function<rsvd_status()>> vars;
+  std::vector<rsvd_tune_record> recs;
+  for (int ci : tune_pick(J, key, cands.size())) {
+    const Cfg g = cands[ci];
+    const int bn = g.bn;
+    std::vector<TcChan> tcs(J.C);
+    bool any_split = false;
+    std::vector<ZeroDesc> zd(J.C);
+    int item = 0;
+    // items numbered longest first: the persistent CTAs take items
+    // round-robin, so this order balances them (longest-processing-time-first)
+    std::vector<int> order(J.C);
+    for (int c = 0; c < J.C; ++c) order[c] = c;
+    if (g.lpt) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return J.d[a].n > J.d[b].n; });
+    for (int pos = 0; pos < J.C; ++pos) {
+      const int c = order[pos];
+      const ChanDims& d = J.d[c];
+      const int nc = nc_of[c];
+      TcChan& t = tcs[pos];
+      memset(&t, 0, sizeof(t));
+      const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
+      const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
+      if (!J.measure) {
+        const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, d.n, nc, bn);
+        if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
+      }
+      t.Y = yout(c);
+      t.ldy = d.ldt;
+      t.n = d.n;
+      t.m = d.n;
+      t.mode = TC_STORE;
+      t.ncols = nc;
+      t.mt = cdiv(d.n, 128);
+      t.nt = cdiv(nc, bn);
+      const auto kk = ks_of(g, c);
+      t.ks = kk.first;
+      t.kt_per_split = kk.second;
+      t.atomic = t.ks > 1;
+      any_split |= t.atomic != 0;
+      t.item0 = item;
+      item += t.mt * t.nt * t.ks;
+      zd[c] = ZeroDesc{t.Y, d.ldt, d.n, nc, 4};
+    }
+    const int items = item;
+    std::function<rsvd_status()> zero;
+    if (any_split) {
+      const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+      const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+      const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
+      cudaStream_t st = J.P->st;
+      const int C = J.C;
+      zero = [=]() {
+        launch_zero(dzd, off, C, tiles64, st);
+        return RSVD_OK;
+      };
+    }
+    const TcChan* dtc = J.ar.put(tcs.data(), tcs.size(), 128);
     cudaStream_t st = J.P->st;
+    int* derr = J.P->d_err;
     const int C = J.C;
-    J.steps.push_back([=]() {
-      launch_zero(dzd, off, C, tiles64, st);
+    // algorithmic traffic: every V word, X word and Y element once; MMA flops
+    double bytes = 0.0, flops = 0.0;
+    int npairs = 0;
+    for (int a = 0; a < sa; ++a)
+      for (int x = 0; x < sx; ++x) npairs += (a + x < std::max(sa, sx));
+    for (int c = 0; c < J.C; ++c) {
+      const double n = J.d[c].n, nc = nc_of[c];
+      bytes += n * n * 2.0 * sa + n * nc * 2.0 * sx + n * nc * 4.0;
+      flops += 2.0 * n * n * nc * npairs;
+    }
+    rsvd_plan_s* P = J.P;
+    const int stages = g.stages;
+    vars.push_back([=]() {
+      if (zero) zero();
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (P->profiling) timed_begin(P, &ea, &eb);
+      const int e = tc_launch(dtc, C, items, sa, sx, bn, derr, st, false, stages);
+      if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
+      if (P->profiling) {
+        cudaEventRecord(eb, st);
+        P->pending.push_back({ea, eb, 0, bytes, flops});
+      }
       return RSVD_OK;
     });
+    rsvd_tune_record r{};
+    r.kind = RSVD_TUNE_TC;
+    r.bn = bn;
+    r.split_target = g.target * NSM;
+    r.min_split = g.min_chunk * 64;
+    r.stages = std::min(g.stages ? g.stages : 99, tc_stages(sa, sx, bn));
+    r.order = g.lpt;
+    recs.push_back(r);
   }
-  const TcChan* dtc = J.ar.put(tcs.data(), tcs.size(), 128);
-  cudaStream_t st = J.P->st;
-  int* derr = J.P->d_err;
-  const int C = J.C;
-  // algorithmic traffic: every V word, X word and Y element once; MMA flops
-  double bytes = 0.0, flops = 0.0;
-  int npairs = 0;
-  for (int a = 0; a < sa; ++a)
-    for (int x = 0; x < sx; ++x) npairs += (a + x < std::max(sa, sx));
-  for (int c = 0; c < J.C; ++c) {
-    const double n = J.d[c].n, nc = ncols_of(c);
-    bytes += n * n * 2.0 * sa + n * nc * 2.0 * sx + n * nc * 4.0;
-    flops += 2.0 * n * n * nc * npairs;
-  }
-  rsvd_plan_s* P = J.P;
-  J.steps.push_back([=]() {
-    cudaEvent_t ea = nullptr, eb = nullptr;
-    if (P->profiling) timed_begin(P, &ea, &eb);
-    const int e = tc_launch(dtc, C, items, sa, sx, bn, derr, st);
-    if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
-    if (P->profiling) {
-      cudaEventRecord(eb, st);
-      P->pending.push_back({ea, eb, 0, bytes, flops});
-    }
-    return RSVD_OK;
-  });
+  add_tuned(J, key, recs, vars);
   return RSVD_OK;
 }
 
@@ -2176,7 +2377,7 @@ rsvd_status execute(Job& J, bool stage_inputs, std::vector<ChanResult>& res) {
     CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
     return RSVD_OK;
   };
-  const bool use_graph = P->graphs && !P->profiling && !J.rule && P->st != nullptr;
+  const bool use_graph = P->graphs && !P->profiling && !J.rule && !J.tuning && P->st != nullptr;
   if (!use_graph) {
     if (rsvd_status s = enqueue()) return s;
   } else {
@@ -2477,6 +2678,8 @@ void rsvd_plan_destroy(rsvd_plan_t P) {
   if (P->hp) cudaFreeHost(P->hp);
   if (P->d_err) cudaFree(P->d_err);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->tune_ev)
+    if (e) cudaEventDestroy(e);
   delete P;
 }
 
@@ -2485,6 +2688,24 @@ int64_t rsvd_plan_workspace_bytes(rsvd_plan_t P) { return P ? (int64_t)P->ws_cap
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {
   if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
   P->profiling = enable ? 1 : 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_set_autotune(rsvd_plan_t P, int32_t enable) {
+  if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
+  if (enable && !P->autotune) {
+    if (cudaStreamSynchronize(P->st) != cudaSuccess)
+      return seterr(RSVD_ERR_CUDA, "stream synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    drop_graphs(P);                      // captured with the default shapes
+  }
+  P->autotune = enable ? 1 : 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_tune_records(rsvd_plan_t P, rsvd_tune_record* out, int32_t cap, int32_t* count) {
+  if (!P || !count || cap < 0 || (cap > 0 && !out)) return seterr(RSVD_ERR_INVALID_ARG, "bad argument");
+  *count = (int32_t)P->tune.size();
+  for (int32_t i = 0; i < cap && i < *count; ++i) out[i] = P->tune[i].rec;
   return RSVD_OK;
 }
 

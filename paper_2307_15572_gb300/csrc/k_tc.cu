@@ -610,8 +610,9 @@ int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda, con
 }
 
 template <int SA, int SX, bool RULE>
-static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cudaStream_t st) {
-  const int stages = tc_stages(SA, SX, bn);
+static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cudaStream_t st, int max_stages) {
+  int stages = tc_stages(SA, SX, bn);
+  if (max_stages >= 2 && max_stages < stages) stages = max_stages;
   const int smem = stages * tc_stage_bytes(SA, SX, bn) + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
@@ -626,18 +627,18 @@ static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cu
 }
 
 int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err, cudaStream_t st,
-              bool rule) {
+              bool rule, int max_stages) {
   if (items <= 0) return 0;
   if (bn < 16 || bn > BN_MAX || (bn % 16) != 0) return (int)cudaErrorInvalidValue;
   if (rule) {
-    if (sa == 3 && sx == 3) return launch_t<3, 3, true>(d_ch, C, items, bn, d_err, st);
+    if (sa == 3 && sx == 3) return launch_t<3, 3, true>(d_ch, C, items, bn, d_err, st, max_stages);
     return (int)cudaErrorInvalidValue;
   }
-  if (sa == 1 && sx == 1) return launch_t<1, 1, false>(d_ch, C, items, bn, d_err, st);
-  if (sa == 2 && sx == 1) return launch_t<2, 1, false>(d_ch, C, items, bn, d_err, st);
-  if (sa == 2 && sx == 2) return launch_t<2, 2, false>(d_ch, C, items, bn, d_err, st);
-  if (sa == 3 && sx == 1) return launch_t<3, 1, false>(d_ch, C, items, bn, d_err, st);
-  if (sa == 3 && sx == 3) return launch_t<3, 3, false>(d_ch, C, items, bn, d_err, st);
+  if (sa == 1 && sx == 1) return launch_t<1, 1, false>(d_ch, C, items, bn, d_err, st, max_stages);
+  if (sa == 2 && sx == 1) return launch_t<2, 1, false>(d_ch, C, items, bn, d_err, st, max_stages);
+  if (sa == 2 && sx == 2) return launch_t<2, 2, false>(d_ch, C, items, bn, d_err, st, max_stages);
+  if (sa == 3 && sx == 1) return launch_t<3, 1, false>(d_ch, C, items, bn, d_err, st, max_stages);
+  if (sa == 3 && sx == 3) return launch_t<3, 3, false>(d_ch, C, items, bn, d_err, st, max_stages);
   return (int)cudaErrorInvalidValue;
 }
 

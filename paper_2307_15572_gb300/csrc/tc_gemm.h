@@ -50,7 +50,9 @@ int tc_stages(int sa, int sx, int bn);
 // Launch over `items` work items (sum over channels of mt*nt*ks).
 // Returns a cudaError_t value.
 // rule: the tile-rule generation instantiation (<3, 3>, TC_RULE channels only).
+// max_stages: cap on the shared-memory pipeline depth (0: as many stages as
+// shared memory holds, at most 8; values below 2 mean no cap).
 int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err,
-              cudaStream_t st, bool rule = false);
+              cudaStream_t st, bool rule = false, int max_stages = 0);
 
 }  // namespace rsvd

@@ -65,6 +65,13 @@ class Profile(C.Structure):
                 ("gen_ms", C.c_double), ("gen_flops", C.c_double), ("gen_mma_flops", C.c_double)]
 
 
+class TuneRecord(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("candidates", C.c_int32), ("choice", C.c_int32), ("bn", C.c_int32),
+                ("split_target", C.c_int32), ("min_split", C.c_int32), ("stages", C.c_int32),
+                ("order", C.c_int32), ("ms_default", C.c_float), ("ms_best", C.c_float),
+                ("tune_ms", C.c_float)]
+
+
 _lib = None
 
 
@@ -99,6 +106,10 @@ def load(build=True):
     lib.rsvd_plan_set_profiling.restype = C.c_int
     lib.rsvd_plan_set_graphs.argtypes = [P, C.c_int32]
     lib.rsvd_plan_set_graphs.restype = C.c_int
+    lib.rsvd_plan_set_autotune.argtypes = [P, C.c_int32]
+    lib.rsvd_plan_set_autotune.restype = C.c_int
+    lib.rsvd_plan_tune_records.argtypes = [P, C.POINTER(TuneRecord), C.c_int32, C.POINTER(C.c_int32)]
+    lib.rsvd_plan_tune_records.restype = C.c_int
     lib.rsvd_plan_profile.argtypes = [P, C.POINTER(Profile), C.c_int32]
     lib.rsvd_plan_profile.restype = C.c_int
     lib.rsvd_mlp_param_count.argtypes = [C.c_int32]
@@ -170,6 +181,19 @@ def rsvd_plan_set_profiling(h, enable):
 
 def rsvd_plan_set_graphs(h, enable):
     _check(load().rsvd_plan_set_graphs(h, 1 if enable else 0))
+
+
+def rsvd_plan_set_autotune(h, enable):
+    _check(load().rsvd_plan_set_autotune(h, 1 if enable else 0))
+
+
+def rsvd_plan_tune_records(h):
+    """The plan's autotuning choices, as dicts, in the order they were made."""
+    n = C.c_int32(0)
+    _check(load().rsvd_plan_tune_records(h, None, 0, C.byref(n)))
+    arr = (TuneRecord * max(1, n.value))()
+    _check(load().rsvd_plan_tune_records(h, arr, n.value, C.byref(n)))
+    return [{f: getattr(arr[i], f) for f, _ in TuneRecord._fields_} for i in range(n.value)]
 
 
 def rsvd_plan_profile(h, reset=False):
@@ -292,10 +316,12 @@ def rule(n, c, s, w, eta=0.0, seed=0):
 class Plan:
     """Plan plus torch-allocated output buffers; see include/rsvd.h for the semantics."""
 
-    def __init__(self, n_max, **kw):
+    def __init__(self, n_max, autotune=False, **kw):
         load()
         self.opts = make_opts(n_max, **kw)
         self.h = rsvd_plan(self.opts)
+        if autotune:
+            rsvd_plan_set_autotune(self.h, True)
 
     def close(self):
         if self.h is not None:

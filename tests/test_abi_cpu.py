@@ -42,7 +42,8 @@ def test_struct_layout_matches_header(tmp_path):
     from paper_2307_15572_gb300 import rsvd
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
-    structs = {"rsvd_opts": rsvd.Opts, "rsvd_matrix": rsvd.Matrix, "rsvd_factors": rsvd.Factors}
+    structs = {"rsvd_opts": rsvd.Opts, "rsvd_matrix": rsvd.Matrix, "rsvd_factors": rsvd.Factors,
+               "rsvd_profile": rsvd.Profile, "rsvd_tune_record": rsvd.TuneRecord}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rsvd.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
