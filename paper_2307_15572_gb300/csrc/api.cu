@@ -202,8 +202,8 @@ void run_chol(const Chan* dch, const std::vector<int>& ls, int accumulate, int m
               int conditional, int* coop, cudaStream_t st) {
   const int C = (int)ls.size();
   const size_t esz = f32_chol ? sizeof(float) : sizeof(double);
-  size_t bytes = (size_t)maxl * (maxl + 1) * esz;
-  const size_t b32 = (size_t)maxl * (maxl + 1) * sizeof(float) + 8 * (size_t)maxl * sizeof(float);
+  size_t bytes = (size_t)maxl * (maxl + 1) * esz + (size_t)maxl * sizeof(double);
+  const size_t b32 = (size_t)maxl * (maxl + 1) * sizeof(float) + 9 * (size_t)maxl * sizeof(float);
   if (b32 > bytes) bytes = b32;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (st) cudaStreamIsCapturing(st, &cs);

@@ -175,7 +175,7 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
 // (two 4 x 4 quadrants, so shared-memory reads are float4 and conflict-free),
 // next k step prefetched into registers while the current one is used.
 template <typename TA, typename TB, typename TC, int AL, int ACC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, ACC == ACC_DOT2 ? 1 : 2)
 k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
   // rows padded by 4 floats: the staging stores (8 consecutive threads on 8
   // different k rows) hit 8 distinct banks, and rows stay 16-byte aligned

@@ -125,6 +125,51 @@ void launch_omega_f64(const Chan* d_ch, const int* d_off, int C, int tiles, uint
 // triangular factor of a repeated CholeskyQR).
 // T = double: the ill-conditioned Grams (first CholeskyQR round, W^T W);
 // T = float: the second CholeskyQR round, whose Gram is within ~1e-2 of I.
+// In-place inverse of the upper triangular l x l matrix A (column-major,
+// leading dimension lda, shared memory) by the whole block; rinv (l entries
+// of shared memory) receives the reciprocals of the diagonal first.
+// Column j: X_jj = 1 / A_jj, X[0:j, j] = -X_jj X[0:j, 0:j] A[0:j, j], where
+// the leading block already holds X.  Each row of the product is split over g
+// threads (2 while 2 l rows fit the block), reduced by shuffle.
+// Rows are dealt to at most two passes of the block (l <= 2 nt; the callers'
+// shared-memory bound keeps l below 256).
+template <typename T>
+RSVD_DEV void tri_inv_inplace(T* A, int lda, T* rinv, int l, int tid, int nt) {
+  for (int i = tid; i < l; i += nt) rinv[i] = (T)1 / A[i + (int64_t)i * lda];
+  __syncthreads();
+  if (tid == 0) A[0] = rinv[0];
+  __syncthreads();
+  const int g = (2 * l <= nt) ? 2 : 1;
+  const int p = tid % g;
+  const int rstride = nt / g;
+  for (int j = 1; j < l; ++j) {
+    const T* aj = A + (int64_t)j * lda;
+    T acc[2] = {(T)0, (T)0};
+    int nrow = 0;
+    for (int i = tid / g; i < j && nrow < 2; i += rstride, ++nrow) {
+      T s0 = 0, s1 = 0;
+      int k = i + p;
+      for (; k + g < j; k += 2 * g) {
+        s0 = fma(A[i + (int64_t)k * lda], aj[k], s0);
+        s1 = fma(A[i + (int64_t)(k + g) * lda], aj[k + g], s1);
+      }
+      if (k < j) s0 = fma(A[i + (int64_t)k * lda], aj[k], s0);
+      acc[nrow] = s0 + s1;
+    }
+    if (g == 2) {
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+      acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], 1);
+    }
+    __syncthreads();                        // every read of column j is done
+    const T xjj = rinv[j];
+    nrow = 0;
+    for (int i = tid / g; i < j && nrow < 2; i += rstride, ++nrow)
+      if (p == 0) A[i + (int64_t)j * lda] = -acc[nrow] * xjj;
+    if (tid == 0) A[j + (int64_t)j * lda] = xjj;   // column j is X from here on
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, int accumulate,
                                                   int use_smem, int f32_inverse, int conditional) {
@@ -135,8 +180,9 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
   const int ld = use_smem ? l + 1 : l;       // odd stride: conflict-free column access
   T* Ms = use_smem ? (T*)craw : (T*)h.M;     // working copy of G -> R (column-major)
   const double* G = h.G;
-  __shared__ int fail;
+  __shared__ int fail, s_bad;
   __shared__ double shift;
+  __shared__ T s_rjj, s_inv;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
     fail = 0;
@@ -155,10 +201,21 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
     int bad = 0;
     for (int j = 0; j < l; ++j) {
       __syncthreads();
-      const T d = Ms[j + (int64_t)j * ld];
-      if (!(d > (T)0) || !isfinite(d)) { bad = 1; break; }      // uniform across the block
-      const T rjj = sqrt(d), inv = (T)1 / rjj;
+      // the pivot's square root and reciprocal once, by one thread: on this
+      // GPU an FP64 warp instruction costs the same with one lane or 32
+      if (tid == 0) {
+        const T d = Ms[j + (int64_t)j * ld];
+        const int b = !(d > (T)0) || !isfinite(d);
+        s_bad = b;
+        if (!b) {
+          const T r = sqrt(d);
+          s_rjj = r;
+          s_inv = (T)1 / r;
+        }
+      }
       __syncthreads();
+      if (s_bad) { bad = 1; break; }                                // uniform across the block
+      const T rjj = s_rjj, inv = s_inv;
       for (int i = j + tid; i < l; i += nt)
         Ms[j + (int64_t)i * ld] = (i == j) ? rjj : Ms[j + (int64_t)i * ld] * inv;
       __syncthreads();
@@ -201,12 +258,14 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
     }
   }
   __syncthreads();
-  // R^{-1} column by column, one warp per column, right-looking back
-  // substitution: for i = c .. 0: x_i /= R_ii, then x_k -= R_ki x_i (k < i)
-  // across the lanes.  Columns are dealt round-robin so warps get a mix of
-  // long and short ones.
+  // R^{-1}.  In shared memory: in place, column by column from the left
+  // (the unblocked triangular inverse): with the leading j x j block already
+  // inverted, X_jj = 1 / R_jj and X[0:j, j] = -X_jj X[0:j, 0:j] R[0:j, j],
+  // the rows of that triangular matrix-vector product in parallel (two
+  // threads per row, each half of its terms, while rows fit).  Otherwise
+  // (l past shared memory) one warp per column by back substitution.
   const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
-  if ((f32_inverse || sizeof(T) == 4) && use_smem) {
+  if ((f32_inverse || sizeof(T) == 4) && use_smem && l <= 2 * nt) {
     // FP32 arithmetic on an FP32 copy of R (stride l+1) in shared memory
     float* Rs;
     if (sizeof(T) == 4) {
@@ -225,30 +284,35 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
       }
       __syncthreads();
     }
-    float* x = Rs + (int64_t)l * (l + 1) + (int64_t)warp * l;
-    for (int c = warp; c < l; c += nwarp) {
-      for (int k = lane; k < l; k += 32) x[k] = (k == c) ? 1.0f : 0.0f;
-      __syncwarp();
-      for (int i = c; i >= 0; --i) {
-        const float xi = x[i] / Rs[i + (int64_t)i * (l + 1)];
-        __syncwarp();
-        if (lane == 0) x[i] = xi;
-        const float* ri = Rs + (int64_t)i * (l + 1);
-        for (int k = lane; k < i; k += 32) x[k] = fmaf(-ri[k], xi, x[k]);
-        __syncwarp();
-      }
-      for (int k = lane; k < l; k += 32) h.Ri[k + (int64_t)c * l] = f32_to_f64(x[k]);
-      __syncwarp();
+    float* rinv = Rs + (int64_t)l * (l + 1);
+    tri_inv_inplace<float>(Rs, l + 1, rinv, l, tid, nt);
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e % l, j = e / l;
+      h.Ri[e] = (i <= j) ? f32_to_f64(Rs[i + (int64_t)j * (l + 1)]) : 0.0;
     }
     return;
   }
-  // FP64: R from Ms, the column itself (in h.Ri) as the work vector
+  if (use_smem && sizeof(T) == 8 && l <= 2 * nt) {
+    // FP64 in place; the reciprocals of the diagonal after the factor
+    double* rinv = (double*)((unsigned char*)craw + (size_t)l * ld * sizeof(T));
+    tri_inv_inplace<T>(Ms, ld, (T*)rinv, l, tid, nt);
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e % l, j = e / l;
+      h.Ri[e] = (i <= j) ? (double)Ms[i + (int64_t)j * ld] : 0.0;
+    }
+    return;
+  }
+  // large l, R in global memory: the column itself (in h.Ri) as the work
+  // vector; the reciprocals of the diagonal in G (free once R exists)
+  double* rinv = (double*)h.G;
+  for (int i = tid; i < l; i += nt) rinv[i] = 1.0 / (double)Ms[i + (int64_t)i * ld];
+  __syncthreads();
   for (int c = warp; c < l; c += nwarp) {
     double* x = h.Ri + (int64_t)c * l;
     for (int k = lane; k < l; k += 32) x[k] = (k == c) ? 1.0 : 0.0;
     __syncwarp();
     for (int i = c; i >= 0; --i) {
-      const double xi = x[i] / (double)Ms[i + (int64_t)i * ld];
+      const double xi = x[i] * rinv[i];
       __syncwarp();
       if (lane == 0) x[i] = xi;
       const T* ri = Ms + (int64_t)i * ld;
@@ -258,13 +322,255 @@ __global__ void __launch_bounds__(256) k_chol_inv(const Chan* __restrict__ ch, i
   }
 }
 
+// ------------------------------- register-resident Cholesky + inverse, l <= 128
+// The same factorisation, shift retry and inverse as k_chol_inv, for
+// factors of at most 128 columns, with the matrix in registers: thread
+// (ta, tb) of a 16 x 16 grid holds the upper-triangle elements
+// (ta + 16 p, tb + 16 q), p <= q < 8 (36 blocks; on p == q those with
+// ta <= tb).  Step j of the right-looking factorisation: the owner of (j, j)
+// forms R_jj and its reciprocal; the owners of row j scale it and publish
+// it to shared memory; every thread updates its elements below and right of
+// the pivot from the published row (independent FMAs on registers).  The
+// inverse X = R^{-1} then overwrites R in the same registers, rows from the
+// bottom: X_i,: <- X_i,: / R_ii (X_ii = 1 / R_ii), publish row i of X and
+// column i of R (still R above the diagonal), and X_ab -= R_ai X_ib for
+// a < i <= b (with X_ai starting from 0); the published vectors alternate
+// between two buffers, so one barrier per step suffices.
+__host__ __device__ constexpr int blk36(int p, int q) { return q * (q + 1) / 2 + p; }
+
+template <typename U>
+RSVD_DEV U to_u(double v) { return (U)v; }
+template <>
+RSVD_DEV float to_u<float>(double v) { return f64_to_f32_rn(v); }
+RSVD_DEV double u_to_f64(double v) { return v; }
+RSVD_DEV double u_to_f64(float v) { return f32_to_f64(v); }
+
+// X = R^{-1} in place (registers x, layout as above); rinv (shared) holds
+// 1 / R_ii in U precision on entry.
+template <typename U>
+RSVD_DEV void reg_tri_inv(U (&x)[36], const U* rinv, U (*rowx)[128], U (*colr)[128], int l, int ta, int tb) {
+#pragma unroll
+  for (int pi = 7; pi >= 0; --pi) {
+    if (16 * pi >= l) continue;
+    for (int ti = 15; ti >= 0; --ti) {
+      const int i = 16 * pi + ti;
+      if (i >= l) continue;
+      const int buf = i & 1;
+      const U ri = rinv[i];
+      if (ta == ti) {                          // row i of X: scale, publish (b >= i)
+#pragma unroll
+        for (int q = pi; q < 8; ++q) {
+          const int b = tb + 16 * q;
+          if (b >= i && b < l) {
+            U v = (b == i) ? ri : x[blk36(pi, q)] * ri;
+            x[blk36(pi, q)] = v;
+            rowx[buf][b] = v;
+          }
+        }
+      }
+      if (tb == ti) {                          // column i of R above the diagonal
+#pragma unroll
+        for (int p = 0; p <= pi; ++p) {
+          const int a = ta + 16 * p;
+          if (a < i) colr[buf][a] = x[blk36(p, pi)];
+        }
+      }
+      __syncthreads();
+      U cr[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int a = ta + 16 * p;
+        cr[p] = (p <= pi && a < i) ? colr[buf][a] : (U)0;
+      }
+#pragma unroll
+      for (int q = pi; q < 8; ++q) {
+        const int b = tb + 16 * q;
+        if (b < i || b >= l) continue;
+        const U xb = rowx[buf][b];
+#pragma unroll
+        for (int p = 0; p <= q; ++p) {
+          const int a = ta + 16 * p;
+          if (p <= pi && a < i && a <= b) {
+            const U base = (b == i) ? (U)0 : x[blk36(p, q)];
+            x[blk36(p, q)] = fma(-cr[p], xb, base);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_inv_reg(const Chan* __restrict__ ch, int f32_inverse,
+                                                      int conditional) {
+  const Chan& h = ch[blockIdx.x];
+  if (conditional && !(h.res->flags & FLAG_SHIFTED)) return;
+  const int l = h.l;
+  const double* G = h.G;
+  const int tid = threadIdx.x, ta = tid & 15, tb = tid >> 4;
+  __shared__ T rowb[128];
+  __shared__ T rinv_t[128];
+  __shared__ __align__(16) unsigned char ibuf[2 * 2 * 128 * sizeof(double) + 128 * sizeof(double)];
+  __shared__ int s_bad, fail;
+  __shared__ double s_shift;
+  if (tid < 32) {
+    double tr = 0.0;
+    for (int i = tid; i < l; i += 32) tr += G[i + (int64_t)i * l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (tid == 0) {
+      fail = 0;
+      s_shift = 11.0 * ((double)h.n * l + (double)l * (l + 1)) *
+                (sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08) * tr;
+    }
+  }
+  __syncthreads();
+  T r[36];
+  int bad = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int p = 0; p <= q; ++p) {
+        const int a = ta + 16 * p, b = tb + 16 * q;
+        T v = (T)0;
+        if (a <= b && b < l) {
+          double g = G[a + (int64_t)b * l];
+          if (attempt == 1 && a == b) g += s_shift;
+          v = to_u<T>(g);
+        }
+        r[blk36(p, q)] = v;
+      }
+    bad = 0;
+#pragma unroll
+    for (int pj = 0; pj < 8; ++pj) {
+      if (16 * pj >= l || bad) continue;
+      for (int tj = 0; tj < 16; ++tj) {
+        const int j = 16 * pj + tj;
+        if (j >= l) break;
+        if (ta == tj && tb == tj) {            // the pivot, once
+          const T d = r[blk36(pj, pj)];
+          const int b0 = !(d > (T)0) || !isfinite(d);
+          s_bad = b0;
+          if (!b0) {
+            const T rjj = sqrt(d);
+            rinv_t[j] = (T)1 / rjj;
+            r[blk36(pj, pj)] = rjj;
+          }
+        }
+        __syncthreads();
+        if (s_bad) { bad = 1; break; }         // uniform across the block
+        if (ta == tj) {                        // row j: scale, publish
+          const T inv = rinv_t[j];
+#pragma unroll
+          for (int q = pj; q < 8; ++q) {
+            const int b = tb + 16 * q;
+            if (b > j && b < l) {
+              const T v = r[blk36(pj, q)] * inv;
+              r[blk36(pj, q)] = v;
+              rowb[b] = v;
+            }
+          }
+        }
+        __syncthreads();
+        T ra[8], rbq[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int a = ta + 16 * p, b = tb + 16 * p;
+          ra[p] = (p >= pj && a > j && a < l) ? rowb[a] : (T)0;
+          rbq[p] = (p >= pj && b > j && b < l) ? rowb[b] : (T)0;
+        }
+#pragma unroll
+        for (int q = pj; q < 8; ++q)
+#pragma unroll
+          for (int p = pj; p <= q; ++p) {
+            const int a = ta + 16 * p, b = tb + 16 * q;
+            if (a > j && a <= b && b < l) r[blk36(p, q)] = fma(-ra[p], rbq[q], r[blk36(p, q)]);
+          }
+      }
+    }
+    __syncthreads();
+    if (!bad) break;
+    if (tid == 0) {
+      if (attempt == 0) atomicOr(&h.res->flags, FLAG_SHIFTED);
+      else { fail = 1; atomicOr(&h.res->flags, FLAG_CHOL_FAIL); }
+    }
+    __syncthreads();
+    if (fail) return;
+  }
+  // R (upper, zero below) -> h.R
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int p = 0; p <= q; ++p) {
+      const int a = ta + 16 * p, b = tb + 16 * q;
+      if (a <= b && b < l) h.R[a + (int64_t)b * l] = u_to_f64(r[blk36(p, q)]);
+    }
+  for (int b = tb; b < l; b += 16)
+    for (int a = ta; a < l; a += 16)
+      if (a > b) { h.R[a + (int64_t)b * l] = 0.0; h.Ri[a + (int64_t)b * l] = 0.0; }
+  // R^{-1} -> h.Ri: FP32 on the mixed path (any invertible right factor keeps
+  // the range; the next CholeskyQR round restores orthogonality), else T
+  if (f32_inverse || sizeof(T) == 4) {
+    float x[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) x[k] = (sizeof(T) == 4) ? (float)r[k] : to_u<float>((double)r[k]);
+    float* rinv = (float*)(ibuf + 2 * 2 * 128 * sizeof(float));
+    if (ta == tb) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        if (ta + 16 * p < l) rinv[ta + 16 * p] = 1.0f / x[blk36(p, p)];
+    }
+    __syncthreads();
+    float (*rowx)[128] = (float (*)[128])ibuf;
+    float (*colr)[128] = (float (*)[128])(ibuf + 2 * 128 * sizeof(float));
+    reg_tri_inv<float>(x, rinv, rowx, colr, l, ta, tb);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int p = 0; p <= q; ++p) {
+        const int a = ta + 16 * p, b = tb + 16 * q;
+        if (a <= b && b < l) h.Ri[a + (int64_t)b * l] = f32_to_f64(x[blk36(p, q)]);
+      }
+  } else {
+    double* rinv = (double*)(ibuf + 2 * 2 * 128 * sizeof(double));
+    if (ta == tb) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        if (ta + 16 * p < l) rinv[ta + 16 * p] = 1.0 / (double)r[blk36(p, p)];
+    }
+    __syncthreads();
+    double x[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) x[k] = (double)r[k];
+    double (*rowx)[128] = (double (*)[128])ibuf;
+    double (*colr)[128] = (double (*)[128])(ibuf + 2 * 128 * sizeof(double));
+    reg_tri_inv<double>(x, rinv, rowx, colr, l, ta, tb);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int p = 0; p <= q; ++p) {
+        const int a = ta + 16 * p, b = tb + 16 * q;
+        if (a <= b && b < l) h.Ri[a + (int64_t)b * l] = x[blk36(p, q)];
+      }
+  }
+}
+
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
                      cudaStream_t st, int f32_chol, int conditional) {
+  // the factor (stride l+1) and the l reciprocals of its diagonal; the FP32
+  // inverse of large l also keeps 8 work vectors
   const size_t esz = f32_chol ? sizeof(float) : sizeof(double);
-  size_t bytes = (size_t)max_l * (max_l + 1) * esz;
-  const size_t b32 = (size_t)max_l * (max_l + 1) * sizeof(float) + 8 * (size_t)max_l * sizeof(float);
+  size_t bytes = (size_t)max_l * (max_l + 1) * esz + (size_t)max_l * sizeof(double);
+  const size_t b32 = (size_t)max_l * (max_l + 1) * sizeof(float) + 9 * (size_t)max_l * sizeof(float);
   if (b32 > bytes) bytes = b32;
   const int use_smem = bytes <= 200 * 1024;
+  if (max_l <= 128 && !accumulate) {
+    if (f32_chol) k_chol_inv_reg<float><<<C, 256, 0, st>>>(d_ch, 1, conditional);
+    else k_chol_inv_reg<double><<<C, 256, 0, st>>>(d_ch, f32_inverse, conditional);
+    note_launch();
+    return;
+  }
   if (f32_chol) {
     if (use_smem) {
       cudaFuncSetAttribute(k_chol_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
