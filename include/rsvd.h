@@ -123,10 +123,9 @@ typedef enum { RSVD_MEM_DEVICE = 0, RSVD_MEM_HOST = 1 } rsvd_mem;
  * rule_m values; `data`, `ld` and `mem` are ignored.  The matrix is never
  * stored: every pass generates the entries it reads, row panel by row panel,
  * on the tensor core (BF16x3 factor words, FP32 accumulation; entries
- * accurate to ~1e-6 relative).  Tile rules need precision BF16X and the
- * FIXED, TOL or LEARNED rank policy (LEARNED's last resort is then one run at
- * l_max instead of the adaptive loop, which would regenerate the matrix for
- * every block), and cannot share a call with stored channels
+ * accurate to ~1e-6 relative).  Tile rules need precision BF16X (any rank
+ * policy; the adaptive loop generates the matrix 2 + 2q times per block of
+ * block_b columns) and cannot share a call with stored channels
  * (RSVD_ERR_UNSUPPORTED otherwise).  Tuning: the environment variable
  * RSVD_RULE_PANEL sets the rows generated per panel (default: panels of
  * ~8 GiB of words).

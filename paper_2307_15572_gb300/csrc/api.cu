@@ -1255,6 +1255,34 @@ rsvd_status build_probe(Job& J, float* d_feat, const float* theta, float* d_pred
   return RSVD_OK;
 }
 
+// Tile-rule buffers: factor words per channel, then one panel buffer and
+// partial area shared by the channels (they are generated one after another).
+void lay_rule(Bump& b, const std::vector<ChanDims>& d, const rsvd_matrix* A, int nsl, std::vector<Job::RuleDev>& rd,
+              __nv_bfloat16* (&pw)[3], double*& part, int& panel) {
+  const int C = (int)d.size();
+  rd.assign(C, Job::RuleDev{});
+  int64_t maxldb = 64, maxitems = 1;
+  int maxn = 1;
+  for (int c = 0; c < C; ++c) {
+    Job::RuleDev& r = rd[c];
+    r.M = A[c].rule_m;
+    r.ldh = rule_ldh(r.M);
+    for (int w = 0; w < 3; ++w) r.H[w] = b.take<__nv_bfloat16>((size_t)d[c].n * r.ldh);
+    r.key = rule_key(A[c].rule_seed);
+    r.amp3 = (float)(A[c].rule_eta * 1.7320508075688772);
+    maxldb = std::max<int64_t>(maxldb, d[c].ldb);
+    maxn = std::max(maxn, d[c].n);
+  }
+  panel = rule_panel_rows(maxn, maxldb, nsl);
+  for (int c = 0; c < C; ++c) {
+    const int P = std::min<int>(panel, (int)rup(d[c].n, 128));
+    rd[c].psums = b.take<double>(2 * (size_t)cdiv(d[c].n, P));
+    maxitems = std::max<int64_t>(maxitems, (int64_t)cdiv(d[c].n, 128) * cdiv(P, 128));
+  }
+  for (int w = 0; w < nsl; ++w) pw[w] = b.take<__nv_bfloat16>((size_t)panel * maxldb);
+  part = b.take<double>((size_t)maxitems * 8);
+}
+
 // ------------------------------------------------------------ layout
 // Lay out per-channel buffers; with base == nullptr only measures.  The
 // rank-independent part (staged input, V words, partials, results) comes
@@ -1283,33 +1311,7 @@ void layout(Job& J, Bump& b) {
     }
     h.fro_part = b.take<double>(cdiv(d.n, 8));
   }
-  if (J.rule) {
-    // factor words per channel; one panel buffer and partial area shared by
-    // the channels (they are generated one after another)
-    J.rd.assign(J.C, Job::RuleDev{});
-    int64_t maxldb = 64, maxitems = 1;
-    int maxn = 1;
-    for (int c = 0; c < J.C; ++c) {
-      const ChanDims& d = J.d[c];
-      Job::RuleDev& r = J.rd[c];
-      r.M = J.A[c].rule_m;
-      r.ldh = rule_ldh(r.M);
-      for (int w = 0; w < 3; ++w) r.H[w] = b.take<__nv_bfloat16>((size_t)d.n * r.ldh);
-      r.key = rule_key(J.A[c].rule_seed);
-      r.amp3 = (float)(J.A[c].rule_eta * 1.7320508075688772);
-      maxldb = std::max<int64_t>(maxldb, d.ldb);
-      maxn = std::max(maxn, d.n);
-    }
-    J.panel = rule_panel_rows(maxn, maxldb, J.nsl);
-    for (int c = 0; c < J.C; ++c) {
-      const ChanDims& d = J.d[c];
-      const int P = std::min<int>(J.panel, (int)rup(d.n, 128));
-      J.rd[c].psums = b.take<double>(2 * (size_t)cdiv(d.n, P));
-      maxitems = std::max<int64_t>(maxitems, (int64_t)cdiv(d.n, 128) * cdiv(P, 128));
-    }
-    for (int w = 0; w < J.nsl; ++w) J.pw[w] = b.take<__nv_bfloat16>((size_t)J.panel * maxldb);
-    J.part = b.take<double>((size_t)maxitems * 8);
-  }
+  if (J.rule) lay_rule(b, J.d, J.A, J.nsl, J.rd, J.pw, J.part, J.panel);
   J.d_res = b.take<ChanResult>(J.C);
   for (int c = 0; c < J.C; ++c) {
     const ChanDims& d = J.d[c];
@@ -1367,8 +1369,6 @@ rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_fac
     if (a.kind == RSVD_TILE_RULE) {
       if (P->o.precision != RSVD_PREC_BF16X)
         return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules are generated on the tensor-core path only", c);
-      if (P->o.rank_policy == RSVD_RANK_ADAPTIVE)
-        return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules take the fixed, tolerance or learned policy", c);
       if (a.rule_m < 1 || a.rule_m > 4096)
         return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_m %d outside [1, 4096]", c, a.rule_m);
       if (!a.rule_c || !a.rule_s || !a.rule_w)
@@ -1818,6 +1818,10 @@ void lay_adapt_mixed(Bump& b, const std::vector<ChanDims>& d, int bsz, int nsl, 
   base.assign(C, Chan{});
   for (int c = 0; c < C; ++c) {          // rank-independent prefix: staged input, words, partials
     Chan& h = base[c];
+    if (A[c].kind == RSVD_TILE_RULE) {     // generated in every pass: no input, no words
+      h.fro_part = b.take<double>(cdiv(d[c].n, 8));
+      continue;
+    }
     const double* direct = A[c].mem == RSVD_MEM_HOST ? host_direct(A[c]) : nullptr;
     if (A[c].mem == RSVD_MEM_HOST && !direct) { h.A = b.take<double>((size_t)d[c].n * d[c].n); h.lda = d[c].n; }
     else { h.A = direct ? direct : A[c].data; h.lda = A[c].ld; }
@@ -1895,10 +1899,17 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
   }
   std::vector<AdaptBufsM> ab;
   std::vector<Chan> base;
+  // tile rules: every pass generates the entries it reads (no stored words)
+  const bool rule = C > 0 && A[0].kind == RSVD_TILE_RULE;
+  std::vector<Job::RuleDev> rd;
+  __nv_bfloat16* pw[3] = {nullptr, nullptr, nullptr};
+  double* rpart = nullptr;
+  int rpanel = 0;
   size_t buf_bytes = 0;
   {
     Bump b(nullptr);
     lay_adapt_mixed(b, d, bsz, nsl, ab, base, A, f, P->o.k);
+    if (rule) lay_rule(b, d, A, nsl, rd, pw, rpart, rpanel);
     b.take<ChanResult>(C);
     buf_bytes = (b.off + 4095) & ~(size_t)4095;
   }
@@ -1906,28 +1917,59 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
   if (rsvd_status s = grow_ws(P, buf_bytes + arena_bytes)) return s;
   Bump b(P->ws);
   lay_adapt_mixed(b, d, bsz, nsl, ab, base, A, f, P->o.k);
+  if (rule) lay_rule(b, d, A, nsl, rd, pw, rpart, rpanel);
   ChanResult* d_res = b.take<ChanResult>(C);
   char* arena_dev = P->ws + buf_bytes;
   for (int c = 0; c < C; ++c) base[c].res = d_res + c;
   CK(cudaMemsetAsync(d_res, 0, sizeof(ChanResult) * C, P->st));
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
   for (int c = 0; c < C; ++c)
-    if (A[c].mem == RSVD_MEM_HOST && !host_direct(A[c]))        // staged (not read in place)
+    if (!rule && A[c].mem == RSVD_MEM_HOST && !host_direct(A[c]))        // staged (not read in place)
       CK(cudaMemcpy2DAsync((void*)base[c].A, (size_t)d[c].n * sizeof(double), A[c].data,
                            (size_t)A[c].ld * sizeof(double), (size_t)d[c].n * sizeof(double), d[c].n,
                            cudaMemcpyHostToDevice, P->st));
-  auto new_job = [&](int Cj) {
+  // chan: the job's channel a -> the call's channel (for the rule buffers)
+  auto new_job = [&](int Cj, const std::vector<int>* chan = nullptr) {
     Job J;
     J.P = P; J.C = Cj; J.A = A; J.f = f; J.mixed = true; J.measure = false; J.nsl = nsl; J.q = q;
     J.tol = P->o.tol;
     J.ar.dbase = arena_dev;
     J.d.resize(Cj);
     J.ch.resize(Cj);
+    if (rule) {
+      J.rule = true;
+      J.rd.resize(Cj);
+      for (int a = 0; a < Cj; ++a) J.rd[a] = rd[chan ? (*chan)[a] : a];
+      for (int w = 0; w < 3; ++w) J.pw[w] = pw[w];
+      J.part = rpart;
+      J.panel = rpanel;
+    }
     return J;
   };
-  // words + ||V||^2
+  // one pass over V: tensor-core product of the stored words, or generation
+  // of the rule's entries panel by panel (`gen_first`: also sum ||V||^2 and
+  // the words' remainder for the channel results)
+  auto vpass = [&](Job& J, int sx, std::function<int(int)> ncols, std::function<const __nv_bfloat16*(int, int)> xw,
+                   std::function<float*(int)> y, bool gen_first) -> rsvd_status {
+    if (J.rule) return rule_pass(J, sx, ncols, xw, y, gen_first);
+    return tc_pass_ex(J, nsl, sx, ncols, xw, y);
+  };
+  // words + ||V||^2 (tile rules: the factor words; ||V||^2 comes with the first pass)
   std::vector<double> fro2(C, 0.0), wres2(C, 0.0);
-  {
+  if (rule) {
+    Job J = new_job(C);
+    J.d = d;
+    J.ch = base;
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    const std::vector<RuleDesc> rds = rule_descs(J);
+    cudaStream_t st = P->st;
+    J.steps.push_back([=]() {
+      for (const RuleDesc& r : rds) launch_rule_prep(r, st);
+      return RSVD_OK;
+    });
+    if (J.ar.h.size() > arena_bytes) return seterr(RSVD_ERR_OOM, "descriptor region too small");
+    if (rsvd_status s = run_job(J)) return s;
+  } else {
     Job J = new_job(C);
     J.d = d;
     J.ch = base;
@@ -1964,7 +2006,7 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
       if (active[c]) idx.push_back(c);
     if (idx.empty()) break;
     const int Ca = (int)idx.size();
-    Job J = new_job(Ca);
+    Job J = new_job(Ca, &idx);
     bool first = true;
     for (int a = 0; a < Ca; ++a) {
       const int c = idx[a];
@@ -2019,9 +2061,9 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
     auto Yb = [&](int a) { return cb(a).Yb32; };
     auto qword = [&](int a, int w) { return (const __nv_bfloat16*)(w < nsl ? cb(a).Qw[w] + (int64_t)cols[idx[a]] * J.d[a].ldb : nullptr); };
     // sketch (+ probe columns in the first block)
-    if (rsvd_status s = tc_pass_ex(J, nsl, 1, [&](int a) { return bb(a) + (first ? NPROBE : 0); },
-                                   [&](int a, int w) { return (const __nv_bfloat16*)(w == 0 ? cb(a).Xo : nullptr); },
-                                   Yb)) return s;
+    if (rsvd_status s = vpass(J, 1, [&](int a) { return bb(a) + (first ? NPROBE : 0); },
+                              [&](int a, int w) { return (const __nv_bfloat16*)(w == 0 ? cb(a).Xo : nullptr); },
+                              Yb, first)) return s;
     if (first) {
       std::vector<float*> src(Ca), ag(Ca), rg(Ca);
       std::vector<int64_t> ldt(Ca);
@@ -2046,9 +2088,9 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
     }
     cqr2_mixed(J, nsl);                                     // Q_i (FP32 + words)
     for (int r = 0; r < q; ++r) {
-      if (rsvd_status s = tc_pass_ex(J, nsl, nsl, bb, qword, Yb)) return s;
+      if (rsvd_status s = vpass(J, nsl, bb, qword, Yb, false)) return s;
       cqr2_mixed(J, nsl);
-      if (rsvd_status s = tc_pass_ex(J, nsl, nsl, bb, qword, Yb)) return s;
+      if (rsvd_status s = vpass(J, nsl, bb, qword, Yb, false)) return s;
       if (!first) {
         project_out_f32(J, Qprev, mprev, Yb, bb, Cbuf);
         project_out_f32(J, Qprev, mprev, Yb, bb, Cbuf);
@@ -2065,8 +2107,8 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
       J.d_ch = dA;
     }
     // W_i = V Q_i
-    if (rsvd_status s = tc_pass_ex(J, nsl, nsl, bb, qword,
-                                   [&](int a) { return cb(a).W32 + (int64_t)cols[idx[a]] * J.d[a].ldt; })) return s;
+    if (rsvd_status s = vpass(J, nsl, bb, qword,
+                              [&](int a) { return cb(a).W32 + (int64_t)cols[idx[a]] * J.d[a].ldt; }, false)) return s;
     // R_G <- (I - Q_i Q_i^T) R_G; E_i = ||R_G||^2
     project_out_f32(J, [&](int a) { return (const float*)Qb(a); }, bb, [&](int a) { return cb(a).RG; },
                     [&](int) { return NPROBE; }, Cbuf);
@@ -2086,6 +2128,14 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
       CK(cudaMemcpyAsync(&Ei[(size_t)idx[a] * NPROBE], ab[idx[a]].E, NPROBE * sizeof(double), cudaMemcpyDeviceToHost,
                          P->st));
     CK(cudaStreamSynchronize(P->st));
+    if (rule && first) {                     // ||V||^2 and the remainder of the generated words
+      std::vector<ChanResult> r(C);
+      CK(cudaMemcpy(r.data(), d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost));
+      for (int c = 0; c < C; ++c) {
+        fro2[c] = r[c].fro2;
+        wres2[c] = r[c].wres2;
+      }
+    }
     for (int a = 0; a < Ca; ++a) {
       const int c = idx[a];
       cols[c] += J.d[a].l;
@@ -2112,7 +2162,7 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
     if (cols[c] > 0) idx.push_back(c);
   const int Cf = (int)idx.size();
   if (Cf > 0) {
-    Job J = new_job(Cf);
+    Job J = new_job(Cf, &idx);
     J.policy = RSVD_RANK_TOL;
     for (int a = 0; a < Cf; ++a) {
       const int c = idx[a];
@@ -2571,14 +2621,6 @@ rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factor
     std::vector<rsvd_status> sts(idx.size());
     t0 = now();
     if (attempt == 0) {
-      r = run_fixed_l(P, (int)idx.size(), As.data(), fs.data(), sts.data(), &ls, false);
-    } else if (A[0].kind == RSVD_TILE_RULE) {
-      // tile rules have no adaptive loop (every block would regenerate the
-      // matrix twice): the last resort is one run at the column cap
-      for (size_t i = 0; i < idx.size(); ++i) {
-        ls[i] = (int)std::min<int64_t>(A[idx[i]].n, lcap_opt);
-        lvec[idx[i]] = ls[i];
-      }
       r = run_fixed_l(P, (int)idx.size(), As.data(), fs.data(), sts.data(), &ls, false);
     } else {
       // the plain adaptive loop in the plan's precision (a temporary plan

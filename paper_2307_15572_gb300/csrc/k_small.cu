@@ -608,6 +608,45 @@ template <> struct Vec2<double> { typedef double2 V; static constexpr int N = 2;
 RSVD_DEV float vget(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 RSVD_DEV double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 
+// Sweep count and flags; sigma_i = |M_i| sorted descending (ties by index),
+// X = M_i / sigma_i, Z = J_i into the channel's buffers.
+template <typename T, bool WANT_J>
+RSVD_DEV void jacobi_finish(const Chan& h, const T* Mw, const T* Jw, int lp, int l, int sweep, int max_sweeps) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    h.res->sweeps = sweep + 1;
+    if (sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
+  }
+  __syncthreads();
+  // column norms (unsorted) into scratch
+  for (int cidx = warp; cidx < l; cidx += nwarp) {
+    const T* cc = Mw + (int64_t)cidx * lp;
+    double s = 0.0;
+    for (int rr = lane; rr < l; rr += 32) s += (double)cc[rr] * (double)cc[rr];
+    s = warp_sum(s);
+    if (lane == 0) h.scr[cidx] = sqrt(s);
+  }
+  __syncthreads();
+  // rank sort, descending, ties by index; write sigma, X = M_i / sigma_i, Z = J_i
+  for (int cidx = warp; cidx < l; cidx += nwarp) {
+    const double si = h.scr[cidx];
+    int rank = 0;
+    for (int o = lane; o < l; o += 32) {
+      const double so = h.scr[o];
+      rank += (so > si) || (so == si && o < cidx);
+    }
+    rank = warp_sum(rank);
+    const T* cc = Mw + (int64_t)cidx * lp;
+    const double inv = si > 0.0 ? 1.0 / si : 0.0;
+    for (int rr = lane; rr < l; rr += 32) h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
+    if (WANT_J) {
+      const T* jc = Jw + (int64_t)cidx * lp;
+      for (int rr = lane; rr < l; rr += 32) h.J[rr + (int64_t)rank * l] = (double)jc[rr];
+    }
+    if (lane == 0) h.sig[rank] = si;
+  }
+}
+
 // Columns are stored with stride lp = round_up(l, 8 vectors), rows l..lp-1
 // zero, so each 8-lane group moves 128 contiguous bytes per access
 // (conflict-free) with 16-byte vector loads.
@@ -726,38 +765,93 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
     }
     if (!__syncthreads_or(rotated)) break;     // also the barrier after the last round
   }
-  if (threadIdx.x == 0) {
-    h.res->sweeps = sweep + 1;
-    if (sweep >= max_sweeps) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
+  jacobi_finish<T, WANT_J>(h, Mw, Jw, lp, l, sweep, max_sweeps);
+}
+
+// The same one-sided Jacobi for the mixed path's factors of at most 128
+// columns (FP32, left vectors only, shared memory): column stride 32 NV
+// floats fixed at compile time, one 8-lane group per pair (64 groups cover
+// every pair of a round), and each lane keeps its NV float4 of both columns
+// in registers between the dot products and the rotation.  Same pair
+// schedule, summation order, rotation formulas and stopping rule as
+// k_jacobi<float, false>, so the same results.
+template <int NV>
+__global__ void __launch_bounds__(512) k_jacobi_f32s(const Chan* __restrict__ ch, int max_sweeps) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  constexpr int lp = 32 * NV;
+  const Chan& h = ch[blockIdx.x];
+  const int l = h.l;
+  const int m = l + (l & 1);
+  float* Mw = (float*)sraw;
+  for (int e = threadIdx.x; e < lp * l; e += blockDim.x) {
+    const int i = e % lp, j = e / lp;
+    Mw[e] = (i < l) ? (float)h.R[j + (int64_t)i * l] : 0.0f;      // M = R^T
   }
   __syncthreads();
-  // column norms (unsorted) into scratch
-  for (int cidx = warp; cidx < l; cidx += nwarp) {
-    const T* cc = Mw + (int64_t)cidx * lp;
-    double s = 0.0;
-    for (int rr = lane; rr < l; rr += 32) s += (double)cc[rr] * (double)cc[rr];
-    s = warp_sum(s);
-    if (lane == 0) h.scr[cidx] = sqrt(s);
-  }
-  __syncthreads();
-  // rank sort, descending, ties by index; write sigma, X = M_i / sigma_i, Z = J_i
-  for (int cidx = warp; cidx < l; cidx += nwarp) {
-    const double si = h.scr[cidx];
-    int rank = 0;
-    for (int o = lane; o < l; o += 32) {
-      const double so = h.scr[o];
-      rank += (so > si) || (so == si && o < cidx);
+  const float thr = (float)l * 5.9604645e-8f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane >> 3, gl = lane & 7;
+  const int pi = warp * 4 + grp;                   // this group's pair slot
+  const int npairs = m / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < m - 1; ++r) {
+      int a = -1, b = -1;
+      if (pi < npairs) {
+        if (pi == 0) { a = r; b = m - 1; }
+        else {
+          a = r + pi; if (a >= m - 1) a -= m - 1;
+          b = r - pi; if (b < 0) b += m - 1;
+        }
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= l) a = b = -1;
+      }
+      float4 x[NV], y[NV];
+      float al = 0.0f, be = 0.0f, ga = 0.0f;
+      float4* ca = (float4*)(Mw + (a < 0 ? 0 : a) * lp);
+      float4* cb = (float4*)(Mw + (b < 0 ? 0 : b) * lp);
+      if (a >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          x[v] = ca[gl + 8 * v];
+          y[v] = cb[gl + 8 * v];
+          al = fmaf(x[v].x, x[v].x, al); be = fmaf(y[v].x, y[v].x, be); ga = fmaf(x[v].x, y[v].x, ga);
+          al = fmaf(x[v].y, x[v].y, al); be = fmaf(y[v].y, y[v].y, be); ga = fmaf(x[v].y, y[v].y, ga);
+          al = fmaf(x[v].z, x[v].z, al); be = fmaf(y[v].z, y[v].z, be); ga = fmaf(x[v].z, y[v].z, ga);
+          al = fmaf(x[v].w, x[v].w, al); be = fmaf(y[v].w, y[v].w, be); ga = fmaf(x[v].w, y[v].w, ga);
+        }
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {            // reduce inside the 8-lane group
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      }
+      if (a >= 0 && ga != 0.0f && !(fabsf(ga) <= thr * sqrtf(al * be))) {
+        const float zeta = __fdividef(be - al, 2.0f * ga);
+        const float az = fabsf(zeta);
+        float tf = az > 1e15f ? __fdividef(0.5f, az) : __fdividef(1.0f, az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+        tf = zeta >= 0.0f ? tf : -tf;
+        const float cs = rsqrtf(fmaf(tf, tf, 1.0f));
+        const float sn = cs * tf;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          float4 nx, ny;
+          nx.x = cs * x[v].x - sn * y[v].x; ny.x = sn * x[v].x + cs * y[v].x;
+          nx.y = cs * x[v].y - sn * y[v].y; ny.y = sn * x[v].y + cs * y[v].y;
+          nx.z = cs * x[v].z - sn * y[v].z; ny.z = sn * x[v].z + cs * y[v].z;
+          nx.w = cs * x[v].w - sn * y[v].w; ny.w = sn * x[v].w + cs * y[v].w;
+          ca[gl + 8 * v] = nx;
+          cb[gl + 8 * v] = ny;
+        }
+        rotated = 1;
+      }
+      if (r < m - 2) __syncthreads();
     }
-    rank = warp_sum(rank);
-    const T* cc = Mw + (int64_t)cidx * lp;
-    const double inv = si > 0.0 ? 1.0 / si : 0.0;
-    for (int rr = lane; rr < l; rr += 32) h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
-    if (WANT_J) {
-      const T* jc = Jw + (int64_t)cidx * lp;
-      for (int rr = lane; rr < l; rr += 32) h.J[rr + (int64_t)rank * l] = (double)jc[rr];
-    }
-    if (lane == 0) h.sig[rank] = si;
+    if (!__syncthreads_or(rotated)) break;         // also the barrier after the last round
   }
+  jacobi_finish<float, false>(h, Mw, (const float*)nullptr, lp, l, sweep, max_sweeps);
 }
 
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st) {
@@ -767,6 +861,16 @@ void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st
   const size_t lp = (size_t)((max_l + 8 * ve - 1) / (8 * ve) * (8 * ve));
   const size_t bytes = (fp32 ? 1 : 2) * (size_t)max_l * lp * esz;
   const int use_smem = bytes <= 200 * 1024;
+  if (fp32 && max_l <= 128) {
+    const int nv = (max_l + 31) / 32;
+    const int b2 = max_l * 32 * nv * (int)sizeof(float);
+    void (*kf)(const Chan*, int) = nv == 1 ? k_jacobi_f32s<1> : nv == 2 ? k_jacobi_f32s<2>
+                                 : nv == 3 ? k_jacobi_f32s<3> : k_jacobi_f32s<4>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, b2);
+    kf<<<C, 512, b2, st>>>(d_ch, 60);
+    note_launch();
+    return;
+  }
   if (fp32) {
     if (use_smem) {
       cudaFuncSetAttribute(k_jacobi<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
