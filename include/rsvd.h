@@ -121,11 +121,12 @@ typedef enum { RSVD_MEM_DEVICE = 0, RSVD_MEM_HOST = 1 } rsvd_mem;
  *   key = mix(seed_lo ^ mix(seed_hi)), mix = the 32-bit "lowbias32" hash
  * (arithmetic modulo 2^32).  rule_c, rule_s, rule_w are HOST arrays of
  * rule_m values; `data`, `ld` and `mem` are ignored.  The matrix is never
- * stored: every pass generates the entries it reads, row panel by row panel,
- * on the tensor core (BF16x3 factor words, FP32 accumulation; entries
- * accurate to ~1e-6 relative).  Tile rules need precision BF16X (any rank
- * policy; the adaptive loop generates the matrix 2 + 2q times per block of
- * block_b columns) and cannot share a call with stored channels
+ * stored: every pass generates the entries it reads, row panel by row panel:
+ * with precision BF16X on the tensor core (BF16x3 factor words, FP32
+ * accumulation; entries accurate to ~1e-6 relative), with precision FP64 on
+ * the CUDA cores in FP64 (2 rule_m FP64 flops per entry and pass).  Any rank
+ * policy (the adaptive loop generates the matrix 2 + 2q times per block of
+ * block_b columns).  Tile rules cannot share a call with stored channels
  * (RSVD_ERR_UNSUPPORTED otherwise).  Tuning: the environment variable
  * RSVD_RULE_PANEL sets the rows generated per panel (default: panels of
  * ~8 GiB of words).

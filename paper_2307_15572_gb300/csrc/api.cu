@@ -266,6 +266,7 @@ struct Job {
   int panel = 0;                        // rows of A generated per panel
   struct RuleDev {
     __nv_bfloat16* H[3];
+    double* H64;                        // FP64 path: the factor panel in FP64
     int64_t ldh;
     int M;
     uint32_t key;
@@ -274,6 +275,7 @@ struct Job {
   };
   std::vector<RuleDev> rd;
   __nv_bfloat16* pw[3] = {nullptr, nullptr, nullptr};   // panel words (panel x ldb each)
+  double* p64 = nullptr;                // FP64 path: generated row panel (column-major, panel x n)
   double* part = nullptr;               // per (item, warp) partials of one generation launch
   bool tuning = false;                  // holds a pass the autotuner still has to time
 };
@@ -411,17 +413,17 @@ std::function<rsvd_status()> make_mm(Job& J, MMKind kind, std::vector<MMDesc> md
     m.mt = cdiv(m.m, tile);
     m.nt = cdiv(m.n, tile);
   }
-  std::vector<int> off(J.C + 1, 0);
+  const int C = (int)md.size();               // one descriptor per channel (or per panel)
+  std::vector<int> off(C + 1, 0);
   double flops = 0.0;
-  for (int c = 0; c < J.C; ++c) {
+  for (int c = 0; c < C; ++c) {
     off[c + 1] = off[c] + md[c].mt * md[c].nt * md[c].ks;
     flops += 2.0 * md[c].m * md[c].n * (double)md[c].k;
   }
-  const int tiles = off[J.C];
+  const int tiles = off[C];
   const MMDesc* dmd = J.ar.put(md.data(), md.size());
   const int* doff = J.ar.put(off.data(), off.size());
   cudaStream_t st = J.P->st;
-  const int C = J.C;
   rsvd_plan_s* P = J.P;
   return [=]() {
     const bool timed = P->profiling && kind == MMK_DENSE_F64;
@@ -627,6 +629,81 @@ void lift(Job& J, MMKind kind, std::function<const void*(int)> basis, std::funct
   add_mm(J, kind, md);
 }
 
+// FP64 path, tile rule: one pass Y = V X generates V row panel by row panel
+// in FP64 -- panel = H_rows H^T (H_jm = sqrt(w_m) g_m(x_j), FP64), plus the
+// hash noise -- and multiplies it by X (FP64 CUDA cores throughout; 2M flops
+// per generated entry).  `first` also sums ||V||^2 into the channel result.
+std::vector<RuleDesc64> rule_descs64(Job& J) {
+  std::vector<RuleDesc64> rds(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const rsvd_matrix& A = J.A[c];
+    const int M = A.rule_m;
+    RuleDesc64 r{};
+    r.n = J.d[c].n; r.M = M;
+    r.c = J.ar.put(A.rule_c, M);
+    r.s = J.ar.put(A.rule_s, M);
+    r.w = J.ar.put(A.rule_w, M);
+    r.H = J.rd[c].H64;
+    r.ldh = J.rd[c].ldh;
+    rds[c] = r;
+  }
+  return rds;
+}
+
+void rule_pass64(Job& J, std::function<const double*(int)> X, std::function<double*(int)> Y, bool first) {
+  cudaStream_t st = J.P->st;
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    const Job::RuleDev r = J.rd[c];
+    const int Pr = std::min<int>(J.panel, (int)rup(d.n, 128));
+    const int np = cdiv(d.n, Pr);
+    const double amp3 = J.A[c].rule_eta * 1.7320508075688772;
+    for (int p = 0; p < np; ++p) {
+      const int r0 = p * Pr, rows = std::min(Pr, d.n - r0);
+      MMDesc g{};
+      g.A = r.H64 + (int64_t)r0 * r.ldh; g.lda = r.ldh;
+      g.B = r.H64; g.ldb = r.ldh;
+      g.Cm = J.p64; g.ldc = Pr;
+      g.m = rows; g.n = d.n; g.k = r.M;
+      g.ks = 1; g.kchunk = (int)rup(r.M, 16);
+      g.mode = MM_STORE;
+      J.steps.push_back(make_mm(J, MMK_DENSE_F64, {g}));
+      double* p64 = J.p64;
+      double* part = J.part;
+      double* psum = r.psums + 2 * p;
+      const uint32_t key = r.key;
+      const int n = d.n, ldp = Pr;
+      J.steps.push_back([=]() {
+        launch_rule_noise64(p64, ldp, rows, n, r0, key, amp3, first ? part : nullptr, st);
+        if (first) launch_rule_part_sum(part, kRuleNoiseBlocks, psum, st);
+        return RSVD_OK;
+      });
+      MMDesc t{};
+      t.A = J.p64; t.lda = Pr;
+      t.B = X(c); t.ldb = d.ldt;
+      t.Cm = Y(c) + r0; t.ldc = d.ldt;
+      t.m = rows; t.n = d.l; t.k = d.n;
+      t.ks = 1; t.kchunk = (int)rup(d.n, 16);
+      t.mode = MM_STORE;
+      J.steps.push_back(make_mm(J, MMK_NN_F64, {t}));
+    }
+    if (first) {
+      ChanResult* res = J.ch[c].res;
+      const double* ps = r.psums;
+      J.steps.push_back([=]() {
+        launch_rule_finish(ps, np, res, st);
+        return RSVD_OK;
+      });
+    }
+  }
+}
+
+// One FP64 pass over V: the stored matrix, or the generated tile rule.
+void pass64(Job& J, std::function<const double*(int)> X, std::function<double*(int)> Y, bool first) {
+  if (J.rule) rule_pass64(J, X, Y, first);
+  else dense_f64(J, X, Y);
+}
+
 void build_fp64(Job& J) {
   auto& ch = J.ch;
   const int C = J.C;
@@ -635,26 +712,36 @@ void build_fp64(Job& J) {
   const int* off64 = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
   const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
   const uint64_t seed = J.P->o.seed;
-  J.steps.push_back([=]() {
-    launch_fro2(dch, off64, C, t64, st);
-    launch_fro2_reduce(dch, C, st);
-    launch_omega_f64(dch, off64, C, t64, seed, 0, st);
-    return RSVD_OK;
-  });
+  if (J.rule) {
+    // tile rules: the FP64 factor panel; ||V||^2 comes with the first pass
+    const std::vector<RuleDesc64> rds = rule_descs64(J);
+    J.steps.push_back([=]() {
+      for (const RuleDesc64& r : rds) launch_rule_prep64(r, st);
+      launch_omega_f64(dch, off64, C, t64, seed, 0, st);
+      return RSVD_OK;
+    });
+  } else {
+    J.steps.push_back([=]() {
+      launch_fro2(dch, off64, C, t64, st);
+      launch_fro2_reduce(dch, C, st);
+      launch_omega_f64(dch, off64, C, t64, seed, 0, st);
+      return RSVD_OK;
+    });
+  }
   auto X = [&](int c) { return ch[c].X; };
   auto Y = [&](int c) { return ch[c].Y; };
   auto Q2 = [&](int c) { return ch[c].Q2; };
-  dense_f64(J, [&](int c) { return (const double*)ch[c].X; }, Y);        // Y = V P
+  pass64(J, [&](int c) { return (const double*)ch[c].X; }, Y, true);     // Y = V P
   cqr2_f64(J, Y, X, false);                                              // Q in Y
   bool q_in_y = true;
   for (int r = 0; r < 2 * J.q; ++r) {
-    if (q_in_y) { dense_f64(J, [&](int c) { return (const double*)ch[c].Y; }, X); cqr2_f64(J, X, Q2, false); }
-    else { dense_f64(J, [&](int c) { return (const double*)ch[c].X; }, Y); cqr2_f64(J, Y, Q2, false); }
+    if (q_in_y) { pass64(J, [&](int c) { return (const double*)ch[c].Y; }, X, false); cqr2_f64(J, X, Q2, false); }
+    else { pass64(J, [&](int c) { return (const double*)ch[c].X; }, Y, false); cqr2_f64(J, Y, Q2, false); }
     q_in_y = !q_in_y;
   }
   auto Qb = [&, q_in_y](int c) { return q_in_y ? ch[c].Y : ch[c].X; };
   auto Wb = [&, q_in_y](int c) { return q_in_y ? ch[c].X : ch[c].Y; };
-  dense_f64(J, [&](int c) { return (const double*)Qb(c); }, Wb);          // W = V Q
+  pass64(J, [&](int c) { return (const double*)Qb(c); }, Wb, false);     // W = V Q
   const bool rr = J.P->o.rayleigh_ritz != 0;
   if (rr) {
     // T = Q^T W into R (symmetric); Jacobi SVD of T gives T = X Sigma J^T
@@ -1232,11 +1319,18 @@ rsvd_status build_probe(Job& J, float* d_feat, const float* theta, float* d_pred
            [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return ch[c].G; },
            [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
   } else {
+    if (J.rule) {
+      const std::vector<RuleDesc64> rds = rule_descs64(J);
+      J.steps.push_back([=]() {
+        for (const RuleDesc64& r : rds) launch_rule_prep64(r, st);
+        return RSVD_OK;
+      });
+    }
     J.steps.push_back([=]() {
       launch_omega_f64(dch, off64, C, t64, seed, 0, st, TAG_PROBE);
       return RSVD_OK;
     });
-    dense_f64(J, [&](int c) { return (const double*)ch[c].X; }, [&](int c) { return ch[c].Y; });
+    pass64(J, [&](int c) { return (const double*)ch[c].X; }, [&](int c) { return ch[c].Y; }, true);
     add_tn(J, MMK_GRAM_F64, [&](int c) { return (const void*)ch[c].Y; },
            [&](int c) { return (const void*)ch[c].Y; }, [&](int c) { return ch[c].G; },
            [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
@@ -1257,6 +1351,37 @@ rsvd_status build_probe(Job& J, float* d_feat, const float* theta, float* d_pred
 
 // Tile-rule buffers: factor words per channel, then one panel buffer and
 // partial area shared by the channels (they are generated one after another).
+// FP64 path: the factor panel in FP64 per channel, one FP64 row panel
+// (column-major, panel x n) and the noise kernel's partials.
+int rule_panel_rows64(int64_t maxn) {
+  int64_t p = ((int64_t)8 << 30) / std::max<int64_t>(1, maxn * 8);
+  if (const char* e = getenv("RSVD_RULE_PANEL")) p = std::max<int64_t>(128, atoll(e));
+  p = std::max<int64_t>(128, p / 128 * 128);
+  return (int)std::min<int64_t>(p, rup(maxn, 128));
+}
+
+void lay_rule64(Bump& b, const std::vector<ChanDims>& d, const rsvd_matrix* A, std::vector<Job::RuleDev>& rd,
+                double*& p64, double*& part, int& panel) {
+  const int C = (int)d.size();
+  rd.assign(C, Job::RuleDev{});
+  int maxn = 1;
+  for (int c = 0; c < C; ++c) {
+    Job::RuleDev& r = rd[c];
+    r.M = A[c].rule_m;
+    r.ldh = rule_ldh(r.M);
+    r.H64 = b.take<double>((size_t)d[c].n * r.ldh);
+    r.key = rule_key(A[c].rule_seed);
+    maxn = std::max(maxn, d[c].n);
+  }
+  panel = rule_panel_rows64(maxn);
+  for (int c = 0; c < C; ++c) {
+    const int P = std::min<int>(panel, (int)rup(d[c].n, 128));
+    rd[c].psums = b.take<double>(2 * (size_t)cdiv(d[c].n, P));
+  }
+  p64 = b.take<double>((size_t)panel * maxn);
+  part = b.take<double>(2 * (size_t)kRuleNoiseBlocks);
+}
+
 void lay_rule(Bump& b, const std::vector<ChanDims>& d, const rsvd_matrix* A, int nsl, std::vector<Job::RuleDev>& rd,
               __nv_bfloat16* (&pw)[3], double*& part, int& panel) {
   const int C = (int)d.size();
@@ -1311,7 +1436,8 @@ void layout(Job& J, Bump& b) {
     }
     h.fro_part = b.take<double>(cdiv(d.n, 8));
   }
-  if (J.rule) lay_rule(b, J.d, J.A, J.nsl, J.rd, J.pw, J.part, J.panel);
+  if (J.rule && J.mixed) lay_rule(b, J.d, J.A, J.nsl, J.rd, J.pw, J.part, J.panel);
+  if (J.rule && !J.mixed) lay_rule64(b, J.d, J.A, J.rd, J.p64, J.part, J.panel);
   J.d_res = b.take<ChanResult>(J.C);
   for (int c = 0; c < J.C; ++c) {
     const ChanDims& d = J.d[c];
@@ -1367,8 +1493,6 @@ rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_fac
                     (long long)P->o.n_max);
     if (a.n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: n too large", c);
     if (a.kind == RSVD_TILE_RULE) {
-      if (P->o.precision != RSVD_PREC_BF16X)
-        return seterr(RSVD_ERR_UNSUPPORTED, "channel %d: tile rules are generated on the tensor-core path only", c);
       if (a.rule_m < 1 || a.rule_m > 4096)
         return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_m %d outside [1, 4096]", c, a.rule_m);
       if (!a.rule_c || !a.rule_s || !a.rule_w)
@@ -1446,7 +1570,8 @@ void lay_adapt(Bump& b, const std::vector<ChanDims>& d, int bsz, std::vector<Ada
     x.gpart = b.take<double>((size_t)dd.gsplit * x.lmax * std::max(x.lmax, bsz));
     x.fro_part = b.take<double>(cdiv(dd.n, 64));
     h.n = dd.n; h.k_cap = dd.kcap; h.k_fixed = kfixed; h.ldt = dd.ldt; h.tol = dd.tol;
-    if (A[c].mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)dd.n * dd.n); h.lda = dd.n; }
+    if (A[c].kind == RSVD_TILE_RULE) { h.A = nullptr; h.lda = 0; }     // generated in every pass
+    else if (A[c].mem == RSVD_MEM_HOST) { h.A = b.take<double>((size_t)dd.n * dd.n); h.lda = dd.n; }
     else { h.A = A[c].data; h.lda = A[c].ld; }
     h.gpart = x.gpart;
     h.fro_part = x.fro_part;
@@ -1527,11 +1652,18 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
   // workspace: buffers, then a descriptor region reused by every job
   std::vector<AdaptBufs> ab;
   std::vector<Chan> base;
+  // tile rules: every pass generates FP64 row panels of the rule
+  const bool rule = C > 0 && A[0].kind == RSVD_TILE_RULE;
+  std::vector<Job::RuleDev> rd;
+  double* p64 = nullptr;
+  double* rpart = nullptr;
+  int rpanel = 0;
   const size_t arena_reserve = (size_t)1 << 20 | 0;
   size_t buf_bytes = 0;
   {
     Bump b(nullptr);
     lay_adapt(b, d, bsz, ab, base, A, f, P->o.k);
+    if (rule) lay_rule64(b, d, A, rd, p64, rpart, rpanel);
     b.take<ChanResult>(C);
     buf_bytes = (b.off + 4095) & ~(size_t)4095;
   }
@@ -1539,20 +1671,48 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
   if (rsvd_status s = grow_ws(P, buf_bytes + arena_bytes)) return s;
   Bump b(P->ws);
   lay_adapt(b, d, bsz, ab, base, A, f, P->o.k);
+  if (rule) lay_rule64(b, d, A, rd, p64, rpart, rpanel);
   ChanResult* d_res = b.take<ChanResult>(C);
   char* arena_dev = P->ws + buf_bytes;
   for (int c = 0; c < C; ++c) base[c].res = d_res + c;
   CK(cudaMemsetAsync(d_res, 0, sizeof(ChanResult) * C, P->st));
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
   for (int c = 0; c < C; ++c)
-    if (A[c].mem == RSVD_MEM_HOST)
+    if (!rule && A[c].mem == RSVD_MEM_HOST)
       CK(cudaMemcpy2DAsync((void*)base[c].A, (size_t)d[c].n * sizeof(double), A[c].data,
                            (size_t)A[c].ld * sizeof(double), (size_t)d[c].n * sizeof(double), d[c].n,
                            cudaMemcpyHostToDevice, P->st));
+  // the rule buffers of the job's channels (chan: job channel -> call channel)
+  auto set_rule = [&](Job& J, const std::vector<int>* chan) {
+    if (!rule) return;
+    J.rule = true;
+    J.rd.resize(J.C);
+    for (int a = 0; a < J.C; ++a) J.rd[a] = rd[chan ? (*chan)[a] : a];
+    J.p64 = p64;
+    J.part = rpart;
+    J.panel = rpanel;
+  };
 
-  // ||V||^2 per channel
+  // ||V||^2 per channel (tile rules: the FP64 factor panels; ||V||^2 comes
+  // with the first generated pass)
   std::vector<double> fro2(C, 0.0);
-  {
+  if (rule) {
+    Job J;
+    J.P = P; J.C = C; J.A = A; J.f = f; J.mixed = false; J.measure = false;
+    J.d = d;
+    J.ch = base;
+    J.ar.dbase = arena_dev;
+    set_rule(J, nullptr);
+    J.d_ch = J.ar.put(J.ch.data(), J.ch.size(), 128);
+    const std::vector<RuleDesc64> rds = rule_descs64(J);
+    cudaStream_t st = P->st;
+    J.steps.push_back([=]() {
+      for (const RuleDesc64& r : rds) launch_rule_prep64(r, st);
+      return RSVD_OK;
+    });
+    if (J.ar.h.size() > arena_bytes) return seterr(RSVD_ERR_OOM, "descriptor region too small");
+    if (rsvd_status s = run_job(J)) return s;
+  } else {
     Job J;
     J.P = P; J.C = C; J.A = A; J.f = f; J.mixed = false; J.measure = false;
     J.d = d;
@@ -1596,6 +1756,7 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
     J.d.resize(Ca);
     J.ch.resize(Ca);
     J.ar.dbase = arena_dev;
+    set_rule(J, &idx);
     bool first = true;
     for (int a = 0; a < Ca; ++a) {
       const int c = idx[a];
@@ -1630,13 +1791,13 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
         return RSVD_OK;
       });
     }
-    dense_f64(J, [&](int a) { return (const double*)ab[idx[a]].Xo; }, Yq);        // Y = V P_i
+    pass64(J, [&](int a) { return (const double*)ab[idx[a]].Xo; }, Yq, first);    // Y = V P_i
     if (!first) { project_out(J, Qp, mcols, Yq, Cb); project_out(J, Qp, mcols, Yq, Cb); }
     cqr2_f64(J, Yq, T2, false);
     for (int r = 0; r < q; ++r) {
-      dense_f64(J, [&](int a) { return (const double*)Yq(a); }, Xw);             // V Q_i
+      pass64(J, [&](int a) { return (const double*)Yq(a); }, Xw, false);         // V Q_i
       cqr2_f64(J, Xw, T2, false);
-      dense_f64(J, [&](int a) { return (const double*)Xw(a); }, Yq);             // V Qh
+      pass64(J, [&](int a) { return (const double*)Xw(a); }, Yq, false);         // V Qh
       if (!first) { project_out(J, Qp, mcols, Yq, Cb); project_out(J, Qp, mcols, Yq, Cb); }
       cqr2_f64(J, Yq, T2, false);
     }
@@ -1645,7 +1806,7 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
       project_out(J, Qp, mcols, Yq, Cb);
       cqr2_f64(J, Yq, T2, false);
     }
-    dense_f64(J, [&](int a) { return (const double*)Yq(a); }, Xw);               // W_i = V Q_i
+    pass64(J, [&](int a) { return (const double*)Yq(a); }, Xw, false);           // W_i = V Q_i
     {
       std::vector<SumsqDesc> sd(Ca);
       for (int a = 0; a < Ca; ++a) sd[a] = SumsqDesc{Xw(a), J.d[a].ldt, J.d[a].n, J.d[a].l, 8, ab[idx[a]].E};
@@ -1663,6 +1824,11 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
       CK(cudaMemcpyAsync(&Ei[c], ab[c].E, sizeof(double), cudaMemcpyDeviceToHost, P->st));
     }
     CK(cudaStreamSynchronize(P->st));
+    if (rule && first) {                     // ||V||^2 from the first generated pass
+      std::vector<ChanResult> r(C);
+      CK(cudaMemcpy(r.data(), d_res, sizeof(ChanResult) * C, cudaMemcpyDeviceToHost));
+      for (int c = 0; c < C; ++c) fro2[c] = E[c] = r[c].fro2;
+    }
     for (int a = 0; a < Ca; ++a) {
       const int c = idx[a];
       E[c] -= Ei[c];
@@ -2793,8 +2959,6 @@ rsvd_status rsvd_probe_features(rsvd_plan_t P, int32_t C, const rsvd_matrix* A, 
     f[c].tol = tol ? tol[c] : 0.0;
   }
   if (rsvd_status s = validate(P, C, A, f.data())) return s;
-  if (A[0].kind == RSVD_TILE_RULE && P->o.precision != RSVD_PREC_BF16X)
-    return seterr(RSVD_ERR_UNSUPPORTED, "tile rules are generated on the tensor-core path only");
   std::vector<float> feat;
   const float* saved = P->o.mlp_weights;
   P->o.mlp_weights = nullptr;

@@ -58,6 +58,65 @@ RSVD_DEV double rsum(double v, double* sh) {
   return r;
 }
 
+// FP64 path: H in FP64 (rows j contiguous over m, leading dim ldh >= M;
+// columns M..ldh-1 zero).
+__global__ void __launch_bounds__(256) k_rule_prep64(RuleDesc64 d) {
+  const int64_t total = (int64_t)d.n * d.ldh;
+  const double step = d.n > 1 ? 8.0 / (double)(d.n - 1) : 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / d.ldh), m = (int)(e % d.ldh);
+    double h = 0.0;
+    if (m < d.M) {
+      const double t = step * j - d.c[m];
+      h = sqrt(d.w[m]) * exp(-(t * t) / (2.0 * d.s[m] * d.s[m]));
+    }
+    d.H[e] = h;
+  }
+}
+
+void launch_rule_prep64(const RuleDesc64& d, cudaStream_t st) {
+  const int64_t total = (int64_t)d.n * d.ldh;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_rule_prep64<<<blocks, 256, 0, st>>>(d);
+  note_launch();
+}
+
+// Add the hash noise to a generated FP64 row panel (column-major, rows x n,
+// leading dim ldp; row i is matrix row r0 + i) and, if part is given, write
+// each block's {sum v^2, 0} to part[2 block].  eta = amp3 (num 2^-24) with
+// num = 2 (h >> 8) + 1 - 2^24 exact, amp3 = eta scale * sqrt(3).
+__global__ void __launch_bounds__(256) k_rule_noise64(double* __restrict__ P, int64_t ldp, int rows, int n, int r0,
+                                                      uint32_t key, double amp3, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t total = (int64_t)rows * n;
+  double s2 = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % rows), j = (int)(e / rows);
+    const int gi = r0 + i;
+    const uint32_t lo = (uint32_t)min(gi, j), hi = (uint32_t)max(gi, j);
+    uint32_t h = lowbias32(lo * 0x9E3779B1u + key);
+    h = lowbias32(h ^ (hi * 0x85EBCA77u));
+    const int num = 2 * (int)(h >> 8) + 1 - (1 << 24);
+    double* q = P + i + (int64_t)j * ldp;
+    const double v = *q + amp3 * ((double)num * 5.9604644775390625e-8);
+    *q = v;
+    s2 = fma(v, v, s2);
+  }
+  if (part) {
+    const double t = rsum(s2, sh);
+    if (threadIdx.x == 0) {
+      part[2 * (int64_t)blockIdx.x] = t;
+      part[2 * (int64_t)blockIdx.x + 1] = 0.0;
+    }
+  }
+}
+
+void launch_rule_noise64(double* P, int64_t ldp, int rows, int n, int r0, uint32_t key, double amp3, double* part,
+                         cudaStream_t st) {
+  k_rule_noise64<<<kRuleNoiseBlocks, 256, 0, st>>>(P, ldp, rows, n, r0, key, amp3, part);
+  note_launch();
+}
+
 // out[0..1] = column sums of part (nparts x 2), fixed order.
 __global__ void __launch_bounds__(256) k_rule_part_sum(const double* __restrict__ part, int nparts,
                                                         double* __restrict__ out) {

@@ -115,6 +115,18 @@ struct RuleDesc {
   int64_t ldh;
 };
 void launch_rule_prep(const RuleDesc& d, cudaStream_t st);
+// FP64 path: the factor panel in FP64, and the noise (+ energy partials) of a
+// generated FP64 row panel (kRuleNoiseBlocks pairs in part).
+struct RuleDesc64 {
+  int n, M;
+  const double *c, *s, *w;   // device, M each
+  double* H;
+  int64_t ldh;
+};
+constexpr int kRuleNoiseBlocks = 1216;
+void launch_rule_prep64(const RuleDesc64& d, cudaStream_t st);
+void launch_rule_noise64(double* P, int64_t ldp, int rows, int n, int r0, uint32_t key, double amp3, double* part,
+                         cudaStream_t st);
 void launch_rule_part_sum(const double* part, int nparts, double* out, cudaStream_t st);
 void launch_rule_finish(const double* sums, int npanels, ChanResult* res, cudaStream_t st);
 

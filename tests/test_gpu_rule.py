@@ -113,3 +113,56 @@ def test_rule_full_size_closed_form(lib):
     # small SVD, the generator's ~2e-7 relative rounding bias)
     dev = np.abs(sg - top)
     assert np.all(dev <= eta2 + 2e-6 * lam[0]), (dev.max() / lam[0], np.argmax(dev))
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_rule_fp64_path_matches_oracle(lib, monkeypatch, q):
+    """FP64 path on a tile rule (every pass generates its FP64 row panels on
+    CUDA cores): the all-FP64 bar against the oracle run on the rule's dense
+    matrix -- singular values within 1e-10 relative (above 1e-12 sigma_1),
+    error within 1.05x the oracle's -- with several row panels."""
+    import torch
+    monkeypatch.setenv("RSVD_RULE_PANEL", "1024")
+    n, M, k, p = 2500, 300, 40, 10
+    c, s, w = synth.rule_params(M=M, seed=synth.SEED_RULE)
+    A = tilerule.dense(n, c, s, w, synth.SEED_RULE, 1e-7)
+    o = orsvd.rsvd(A, k=k, p=p, q=q, seed=7)
+    e_o = orsvd.reconstruct_error(A, o.U, o.S, o.V)
+    m = lib.rule(n, c, s, w, eta=1e-7, seed=synth.SEED_RULE)
+    plan = lib.Plan(n, k=k, p=p, q=q, seed=7, precision="fp64")
+    try:
+        st, r = plan.decompose(m, k)
+        assert st >= 0, lib.last_error()
+        assert r["k"] == k and r["l"] == k + p
+        sg = r["S"].cpu().numpy()
+        big = o.S > 1e-12 * o.S[0]
+        assert np.all(np.abs(sg[big] - o.S[big]) <= 1e-10 * o.S[big]), np.max(np.abs(sg - o.S) / o.S)
+        At = torch.as_tensor(A, device="cuda")
+        E = At - (r["U"] * r["S"]) @ r["V"].T
+        err = (torch.linalg.norm(E) / torch.linalg.norm(At)).item()
+        assert err <= 1.05 * e_o, (err, e_o)
+        # ||V||_F^2 from the generated panels: the FP64 estimate agrees with the oracle's
+        assert abs(r["err_est"] - o.err_est) <= 1e-10, (r["err_est"], o.err_est)
+    finally:
+        plan.close()
+
+
+def test_rule_fp64_tolerance_policy(lib):
+    """Tolerance mode on the FP64 path over a generated rule: error <= tol."""
+    import torch
+    n, M = 3000, 300
+    c, s, w = synth.rule_params(M=M, seed=synth.SEED_RULE)
+    A = tilerule.dense(n, c, s, w, synth.SEED_RULE, 1e-7)
+    m = lib.rule(n, c, s, w, eta=1e-7, seed=synth.SEED_RULE)
+    plan = lib.Plan(n, k=90, p=10, q=1, tol=1e-4, policy="tol", seed=5, precision="fp64")
+    try:
+        st, r = plan.decompose(m, 90)
+        assert st >= 0, lib.last_error()
+        At = torch.as_tensor(A, device="cuda")
+        E = At - (r["U"] * r["S"]) @ r["V"].T
+        err = (torch.linalg.norm(E) / torch.linalg.norm(At)).item()
+        assert err <= 1e-4, (err, r["k"])
+        o = orsvd.rsvd(A, tol=1e-4, l=100, q=1, seed=5)
+        assert abs(r["k"] - len(o.S)) <= 1, (r["k"], len(o.S))
+    finally:
+        plan.close()
