@@ -277,6 +277,36 @@ typedef struct {
 rsvd_status rsvd_plan_set_autotune(rsvd_plan_t plan, int32_t enable);
 rsvd_status rsvd_plan_tune_records(rsvd_plan_t plan, rsvd_tune_record* out, int32_t cap, int32_t* count);
 
+/* Basis transformation on the thin factors ("Low-rank interactions"
+ * paragraph, after Eq. (3): V-bar = U^dagger V U operates only on the thin
+ * L and R^dagger).  For factors f of an n x n channel (DEVICE buffers,
+ * k = f->k_out) and a basis B (n x m, DEVICE, column-major, ldb >= n; any B,
+ * not only unitary), writes Lt = B^T U_k (m x k, ldl >= m) and
+ * Rt = B^T V_k (m x k, ldr >= m), FP64, so that
+ *   B^T V B ~ Lt diag(S) Rt^T
+ * at 4 m n k flops instead of the 2 n^2 m + 2 n m^2 of transforming V.
+ * Runs on the plan's stream (its workspace holds two descriptors) and
+ * returns after the stream has completed.  RSVD_ERR_INVALID_ARG for host
+ * factors, bad sizes or pointers; k = 0 writes nothing. */
+rsvd_status rsvd_transform_factors(rsvd_plan_t plan, const rsvd_factors* f, int64_t n, const double* B,
+                                   int64_t ldb, int64_t m, double* Lt, int64_t ldl, double* Rt, int64_t ldr);
+
+/* Symmetric storage.  For symmetric V the singular triplets pair as
+ * v_i = sign(lambda_i) u_i (lambda_i the eigenvalue of magnitude sigma_i), so
+ * V ~ U_k diag(sign_i sigma_i) U_k^T: only U_k, S and the k signs need to be
+ * kept, which is the one-factor reading of the compression ratio below.
+ * signs (DEVICE, k doubles) receives sign(u_i . v_i) = +-1 for the factors f
+ * of an n x n channel (DEVICE buffers); asynchronous on the plan's stream. */
+rsvd_status rsvd_symmetric_signs(rsvd_plan_t plan, const rsvd_factors* f, int64_t n, double* signs);
+
+/* Compression ratio of a rank-k form of an n x n matrix (the paper's
+ * compression-ratio equation in "Randomized matrix decompositions"):
+ * one_factor = 0: n^2 / (2 n k + k) as printed (both factors stored);
+ * one_factor = 1: n^2 / (n k + k) (symmetric storage: U_k and S, signs
+ * folded in), the reading under which a relative rank of 1 % gives C ~ 100
+ * as the text states.  Returns 0 for n < 1 or k < 1. */
+double rsvd_compression_ratio(int64_t n, int32_t k, int32_t one_factor);
+
 /* Exact relative residual with no device allocation (no plan needed).
  *
  * The paper has no counterpart: this is a service for callers that cannot

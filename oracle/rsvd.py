@@ -204,6 +204,19 @@ def compression_ratio(N, R, reading="eq2"):
     return N * N / (1.0 * N * R + R)
 
 
+def transform_factors(U, V, B):
+    """Basis transformation on the thin factors ("Low-rank interactions"
+    paragraph after Eq. (3)): with V ~ U S V^T, B^T V B ~ (B^T U) S (B^T V)^T,
+    so only the thin factors are multiplied by B."""
+    return B.T @ U, B.T @ V
+
+
+def symmetric_signs(U, V):
+    """sign(u_i . v_i): for symmetric input v_i = sign(lambda_i) u_i, so the
+    eigenvalue signs, and V ~ U diag(sign * S) U^T (one factor stored)."""
+    return np.where(np.einsum("ij,ij->j", U, V) >= 0.0, 1.0, -1.0)
+
+
 def relative_rank(N, R):
     """R% = 100 R / N (text after Eq. 2)."""
     return 100.0 * R / N

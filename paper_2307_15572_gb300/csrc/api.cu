@@ -3037,6 +3037,60 @@ rsvd_status rsvd_decompose(rsvd_plan_t P, const rsvd_matrix* A, rsvd_factors* f)
   return rsvd_decompose_batched(P, 1, A, f, nullptr);
 }
 
+rsvd_status rsvd_transform_factors(rsvd_plan_t P, const rsvd_factors* f, int64_t n, const double* B, int64_t ldb,
+                                   int64_t m, double* Lt, int64_t ldl, double* Rt, int64_t ldr) {
+  g_err[0] = 0;
+  if (!P || !f) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  const int k = f->k_out;
+  if (n < 1 || m < 1 || n > 2000000000LL / 64 || m > 2000000000LL / 64)
+    return seterr(RSVD_ERR_INVALID_ARG, "n = %lld, m = %lld outside [1, 3.1e7]", (long long)n, (long long)m);
+  if (k < 0 || k > f->k_cap) return seterr(RSVD_ERR_INVALID_ARG, "k_out %d outside [0, k_cap]", k);
+  if (f->mem != RSVD_MEM_DEVICE) return seterr(RSVD_ERR_INVALID_ARG, "factors must be in device memory");
+  if (!B || ldb < n) return seterr(RSVD_ERR_INVALID_ARG, "bad basis matrix");
+  if (k == 0) return RSVD_OK;
+  if (!f->U || !f->V || f->ldu < n || f->ldv < n) return seterr(RSVD_ERR_INVALID_ARG, "bad factors");
+  if (!Lt || !Rt || ldl < m || ldr < m) return seterr(RSVD_ERR_INVALID_ARG, "bad outputs");
+  if (rsvd_status s = grow_ws(P, 1 << 16)) return s;
+  Job J;
+  J.P = P; J.C = 1; J.measure = false;
+  J.ar.dbase = P->ws;
+  // Lt = B^T U_k, Rt = B^T V_k: B read as the rows of B^T (the FP64 tile
+  // kernel's row-operand form), one launch each
+  auto desc = [&](const double* X, int64_t ldx, double* out, int64_t ldo) {
+    MMDesc d{};
+    d.A = B; d.lda = ldb;
+    d.B = X; d.ldb = ldx;
+    d.Cm = out; d.ldc = ldo;
+    d.m = (int)m; d.n = k; d.k = (int)n;
+    d.ks = 1; d.kchunk = (int)rup(n, 16);
+    d.mode = MM_STORE;
+    return d;
+  };
+  J.steps.push_back(make_mm(J, MMK_GRAM_F64, {desc(f->U, f->ldu, Lt, ldl)}));
+  J.steps.push_back(make_mm(J, MMK_GRAM_F64, {desc(f->V, f->ldv, Rt, ldr)}));
+  return run_job(J);
+}
+
+rsvd_status rsvd_symmetric_signs(rsvd_plan_t P, const rsvd_factors* f, int64_t n, double* signs) {
+  g_err[0] = 0;
+  if (!P || !f) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  const int k = f->k_out;
+  if (n < 1 || n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "n = %lld outside [1, 3.1e7]", (long long)n);
+  if (k < 0 || k > f->k_cap) return seterr(RSVD_ERR_INVALID_ARG, "k_out %d outside [0, k_cap]", k);
+  if (f->mem != RSVD_MEM_DEVICE) return seterr(RSVD_ERR_INVALID_ARG, "factors must be in device memory");
+  if (k == 0) return RSVD_OK;
+  if (!f->U || !f->V || f->ldu < n || f->ldv < n || !signs) return seterr(RSVD_ERR_INVALID_ARG, "bad factors");
+  launch_sym_signs(f->U, f->ldu, f->V, f->ldv, (int)n, k, signs, P->st);
+  CK(cudaGetLastError());
+  return RSVD_OK;
+}
+
+double rsvd_compression_ratio(int64_t n, int32_t k, int32_t one_factor) {
+  if (n < 1 || k < 1) return 0.0;
+  const double N = (double)n, R = (double)k;
+  return N * N / ((one_factor ? 1.0 : 2.0) * N * R + R);
+}
+
 rsvd_status rsvd_reconstruct_error(rsvd_plan_t P, const rsvd_matrix* A, const rsvd_factors* f,
                                    double* rel_err) {
   g_err[0] = 0;

@@ -854,6 +854,29 @@ __global__ void __launch_bounds__(512) k_jacobi_f32s(const Chan* __restrict__ ch
   jacobi_finish<float, false>(h, Mw, (const float*)nullptr, lp, l, sweep, max_sweeps);
 }
 
+// Symmetric storage: for symmetric V the triplets pair as v_i = sign(lambda_i)
+// u_i, so V ~ U_k diag(sign_i sigma_i) U_k^T needs U_k and the signs only;
+// sign_i = sign(u_i . v_i) (one warp per column, fixed-order FP64 sum).
+__global__ void __launch_bounds__(256) k_sym_signs(const double* __restrict__ U, int64_t ldu,
+                                                   const double* __restrict__ V, int64_t ldv, int n, int k,
+                                                   double* __restrict__ signs) {
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (col >= k) return;
+  const double* u = U + (int64_t)col * ldu;
+  const double* v = V + (int64_t)col * ldv;
+  double s = 0.0;
+  for (int r = lane; r < n; r += 32) s = fma(u[r], v[r], s);
+  s = warp_sum(s);
+  if (lane == 0) signs[col] = s >= 0.0 ? 1.0 : -1.0;
+}
+
+void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv, int n, int k, double* signs,
+                      cudaStream_t st) {
+  if (k <= 0) return;
+  k_sym_signs<<<(k + 7) / 8, 256, 0, st>>>(U, ldu, V, ldv, n, k, signs);
+  note_launch();
+}
+
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st) {
   // mixed path (fp32): only the left vectors X are used; FP64 path needs J too
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);

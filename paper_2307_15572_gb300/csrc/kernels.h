@@ -114,6 +114,8 @@ struct RuleDesc {
   __nv_bfloat16* H[3];
   int64_t ldh;
 };
+void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv, int n, int k, double* signs,
+                      cudaStream_t st);
 void launch_rule_prep(const RuleDesc& d, cudaStream_t st);
 // FP64 path: the factor panel in FP64, and the noise (+ energy partials) of a
 // generated FP64 row panel (kRuleNoiseBlocks pairs in part).

@@ -127,6 +127,13 @@ def load(build=True):
     lib.rsvd_reconstruct_error_noalloc.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int64, P, P, C.c_int64,
                                                    C.c_int32, P, P]
     lib.rsvd_reconstruct_error_noalloc.restype = C.c_int
+    lib.rsvd_transform_factors.argtypes = [P, C.POINTER(Factors), C.c_int64, P, C.c_int64, C.c_int64, P, C.c_int64,
+                                           P, C.c_int64]
+    lib.rsvd_transform_factors.restype = C.c_int
+    lib.rsvd_symmetric_signs.argtypes = [P, C.POINTER(Factors), C.c_int64, P]
+    lib.rsvd_symmetric_signs.restype = C.c_int
+    lib.rsvd_compression_ratio.argtypes = [C.c_int64, C.c_int32, C.c_int32]
+    lib.rsvd_compression_ratio.restype = C.c_double
     lib.rsvd_rule_rows.argtypes = [P, C.POINTER(Matrix), C.c_int64, C.c_int32, P, C.c_int64]
     lib.rsvd_rule_rows.restype = C.c_int
     _lib = lib
@@ -243,6 +250,20 @@ def rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, str
 def rsvd_rule_rows(h, mat, r0, rows, out, ldo):
     """Rows r0..r0+rows-1 of a tile rule into the device FP32 buffer `out` (row-major, ld ldo)."""
     return _check(load().rsvd_rule_rows(h, C.byref(mat), int(r0), int(rows), out, int(ldo)))
+
+
+def rsvd_transform_factors(h, fac, n, B, ldb, m, Lt, ldl, Rt, ldr):
+    """Lt = B^T U_k, Rt = B^T V_k (device pointers, column-major)."""
+    return _check(load().rsvd_transform_factors(h, C.byref(fac), int(n), B, int(ldb), int(m), Lt, int(ldl), Rt,
+                                                int(ldr)))
+
+
+def rsvd_symmetric_signs(h, fac, n, signs):
+    return _check(load().rsvd_symmetric_signs(h, C.byref(fac), int(n), signs))
+
+
+def rsvd_compression_ratio(n, k, one_factor=False):
+    return load().rsvd_compression_ratio(int(n), int(k), 1 if one_factor else 0)
 
 
 def rsvd_reconstruct_error(h, mat, fac):

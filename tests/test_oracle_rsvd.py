@@ -226,3 +226,42 @@ def test_compression_ratio_readings():
         assert abs(eq2 / (f[key] / 2) - 1) < 0.01
     assert f["channel_n_min"] % (f["mesh_np"] * f["mesh_nq"]) == 0
     assert f["channel_n_max"] % (f["mesh_np"] * f["mesh_nq"]) == 0
+
+
+def _mixed_sign_symmetric(n, lam, seed):
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((n, len(lam))))
+    Q = Q * np.sign(np.diag(R))
+    return Q @ np.diag(lam) @ Q.T, Q
+
+
+def test_transform_factors_exact_low_rank():
+    """Closed form: for exactly rank-r input and l >= r the factors are exact,
+    and B^T A B equals (B^T U) S (B^T V)^T for any B (not only unitary)."""
+    n, r, m = 200, 12, 37
+    lam = np.array([5.0, -4.0, 3.0, -2.5, 2.0, 1.5, -1.2, 1.0, 0.8, -0.6, 0.5, 0.3])
+    A, _ = _mixed_sign_symmetric(n, lam, 3)
+    res = rsvd.rsvd(A, k=r, p=8, q=0, seed=4)
+    B = np.random.default_rng(5).standard_normal((n, m))
+    Lt, Rt = rsvd.transform_factors(res.U, res.V, B)
+    ref = B.T @ A @ B
+    got = (Lt * res.S) @ Rt.T
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
+    # a plausible slip -- the left factor used on both sides, which drops the
+    # signs of the negative eigenvalues -- is far off
+    assert np.max(np.abs((Lt * res.S) @ Lt.T - ref)) > 1e-2 * np.max(np.abs(ref))
+
+
+def test_symmetric_signs_recover_eigenvalue_signs():
+    """Closed form: the signs are those of the eigenvalues, in the order of
+    |lambda|, and U diag(sign S) U^T reproduces A (one stored factor)."""
+    n = 150
+    lam = np.array([-6.0, 5.0, -3.0, 2.0, -1.0, 0.5])
+    A, _ = _mixed_sign_symmetric(n, lam, 7)
+    res = rsvd.rsvd(A, k=6, p=6, q=0, seed=1)
+    sg = rsvd.symmetric_signs(res.U, res.V)
+    order = np.argsort(-np.abs(lam))
+    assert np.array_equal(sg, np.sign(lam[order]))
+    assert np.allclose(res.S, np.abs(lam[order]), rtol=1e-12)
+    A1 = (res.U * (sg * res.S)) @ res.U.T
+    assert np.max(np.abs(A1 - A)) <= 1e-12 * np.max(np.abs(A))
