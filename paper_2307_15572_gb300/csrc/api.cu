@@ -610,7 +610,7 @@ void dense_f64(Job& J, std::function<const double*(int)> X, std::function<double
   add_tuned(J, key, recs, vars);
 }
 
-void lift(Job& J, MMKind kind, std::function<const void*(int)> basis, std::function<const double*(int)> small,
+void lift(Job& J, MMKind kind, std::function<const void*(int)> basis, std::function<const void*(int)> small,
           std::function<double*(int)> out, std::function<int64_t(int)> ldo, std::function<const double*(int)> scale) {
   std::vector<MMDesc> md(J.C);
   for (int c = 0; c < J.C; ++c) {
@@ -1036,6 +1036,16 @@ rsvd_status pass_over(Job& J, int sa, int sx, int ncols_of_pass, bool first) {
   return tc_pass_ex(J, sa, sx, ncols, xw, y);
 }
 
+// The register Cholesky (l <= 128) also leaves an FP32 copy of R^{-1} in
+// Ri32 where the job has that buffer; the triangular solves then read FP32
+// operands only (the cp.async tile kernel).
+bool ri32_ok(const Job& J) {
+  if (J.max_l > 128) return false;
+  for (int c = 0; c < J.C; ++c)
+    if (!J.ch[c].Ri32) return false;
+  return true;
+}
+
 // CholeskyQR2 of Y32[:, 0:l) -> Q32 (FP32) and its BF16 words in Xb[:, 0:l).
 void cqr2_mixed(Job& J, int nsl_out) {
   auto& ch = J.ch;
@@ -1049,12 +1059,13 @@ void cqr2_mixed(Job& J, int nsl_out) {
            [&](int c) { return (const void*)in(c); }, [&](int c) { return ch[c].G; },
            [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
     add_chol(J, 0, round == 1 ? 1 : 0);
+    const bool b32 = ri32_ok(J);
     std::vector<MMDesc> md(J.C);
     for (int c = 0; c < J.C; ++c) {
       const ChanDims& d = J.d[c];
       MMDesc m{};
       m.A = in(c); m.lda = d.ldt;
-      m.B = ch[c].Ri; m.ldb = d.l;
+      m.B = b32 ? (const void*)ch[c].Ri32 : (const void*)ch[c].Ri; m.ldb = d.l;
       m.Cm = out(c); m.ldc = d.ldt;
       m.m = d.n; m.n = d.l; m.k = d.l;
       m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64); m.ks = 1; m.kchunk = (int)rup(d.l, 16);
@@ -1066,7 +1077,7 @@ void cqr2_mixed(Job& J, int nsl_out) {
       }
       md[c] = m;
     }
-    add_mm(J, MMK_NN_F32_F64B, md);
+    add_mm(J, b32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
   }
   // Conditional third round, only for channels whose Cholesky needed the
   // shift: shifted CholeskyQR leaves Q orthonormal to about kappa(Y)^2 u only,
@@ -1092,12 +1103,13 @@ void cqr2_mixed(Job& J, int nsl_out) {
       return RSVD_OK;
     });
   }
+  const bool b32 = ri32_ok(J);
   std::vector<MMDesc> md(J.C);
   for (int c = 0; c < J.C; ++c) {
     const ChanDims& d = J.d[c];
     MMDesc m{};
     m.A = ch[c].Q32; m.lda = d.ldt;
-    m.B = ch[c].Ri; m.ldb = d.l;
+    m.B = b32 ? (const void*)ch[c].Ri32 : (const void*)ch[c].Ri; m.ldb = d.l;
     m.Cm = ch[c].T32; m.ldc = d.ldt;
     m.m = d.n; m.n = d.l; m.k = d.l;
     m.ks = 1; m.kchunk = (int)rup(d.l, 16);
@@ -1108,7 +1120,7 @@ void cqr2_mixed(Job& J, int nsl_out) {
     m.cond = flags(c);
     md[c] = m;
   }
-  add_mm(J, MMK_NN_F32_F64B, md);
+  add_mm(J, b32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
   {
     const Chan* dch = J.d_ch;
     const int C = J.C;
@@ -1267,9 +1279,20 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
     launch_select(dsw, C, policy, tol, 1, st);
     return RSVD_OK;
   });
-  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Q32; }, [&](int c) { return (const double*)ch[c].J; },
+  // the lifts read X~ in FP32 (the FP32 basis bounds their accuracy anyway)
+  const bool b32 = ri32_ok(J);
+  if (b32) {
+    const Chan* dsw2 = dsw;
+    J.steps.push_back([=]() {
+      launch_j_to_f32(dsw2, C, maxl, st);
+      return RSVD_OK;
+    });
+  }
+  const MMKind lk = b32 ? MMK_NN_F32_OUT64_B32 : MMK_NN_F32_OUT64;
+  auto xs = [&](int c) { return b32 ? (const void*)ch[c].Ri32 : (const void*)ch[c].J; };
+  lift(J, lk, [&](int c) { return (const void*)ch[c].Q32; }, xs,
        [&](int c) { return ch[c].U; }, [&](int c) { return ch[c].ldu; }, [&](int c) { return (const double*)nullptr; });
-  lift(J, MMK_NN_F32_OUT64, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const double*)ch[c].J; },
+  lift(J, lk, [&](int c) { return (const void*)ch[c].Y32; }, xs,
        [&](int c) { return ch[c].V; }, [&](int c) { return ch[c].ldv; }, [&](int c) { return (const double*)ch[c].scr; });
   const int maxk = J.max_kcap;
   J.steps.push_back([=]() {
@@ -1457,6 +1480,7 @@ void layout(Job& J, Bump& b) {
       h.X = b.take<double>(T); h.Y = b.take<double>(T); h.Q2 = b.take<double>(T);
       h.gpart = b.take<double>((size_t)d.gsplit * L2);
     } else {
+      h.Ri32 = b.take<float>(L2);
       for (int s = 0; s < J.nsl; ++s) h.Xb[s] = b.take<__nv_bfloat16>((size_t)d.lw * d.ldb);
       h.Y32 = b.take<float>((size_t)d.ldt * d.lw);
       h.Q32 = b.take<float>((size_t)d.ldt * d.l);

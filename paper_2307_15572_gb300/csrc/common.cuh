@@ -191,6 +191,7 @@ struct Chan {
   double* G;                // Gram
   double* R;                // Cholesky factor (upper), accumulates R = R2 R1
   double* Ri;               // inverse of the last Cholesky factor
+  float* Ri32;              // optional FP32 copy of Ri (mixed path, l <= 128), then of the lift's X
   double* M;                // Jacobi working matrix (then left vectors X_svd)
   double* J;                // Jacobi rotations (right vectors)
   double* sig;              // singular values (l)

@@ -170,6 +170,79 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
   }
 }
 
+// Epilogue of the 128 x 128 tiles: the thread's 8 x 8 block (rows tx*4+q and
+// 64+tx*4+q, columns ty*4+j and 64+ty*4+j) to the output -- store, atomic add
+// (k split), subtract, or split partial -- with the optional column scale and
+// BF16 word slices of the result.
+template <typename TC>
+RSVD_DEV void mm128_store(const MMDesc* __restrict__ dp, const float (&acc)[8][8], int split, int m0, int n0,
+                          int ncols, int tx, int ty) {
+  const int dm = dp->m, mode = dp->mode, nsl = dp->nsl;
+  const int64_t ldc = dp->ldc, pstride = dp->pstride, ldsl = dp->ldsl;
+  const double* __restrict__ colscale = dp->colscale;
+  TC* __restrict__ Cp = (TC*)dp->Cm + (mode == MM_PARTIAL ? (int64_t)split * pstride : 0);
+  __nv_bfloat16* sl0 = dp->sl[0];
+  __nv_bfloat16* sl1 = dp->sl[1];
+  __nv_bfloat16* sl2 = dp->sl[2];
+  // each thread owns rows {r4, r4+1, r4+2, r4+3} (two such groups) of 8
+  // columns: full groups go out as one vector store per column
+  const bool vec_ok = (mode == MM_STORE) && (sizeof(TC) == 4) && ((ldc & 3) == 0) &&
+                      ((((uintptr_t)Cp) & 15) == 0);
+#pragma unroll
+  for (int ig = 0; ig < 2; ++ig) {
+    const int r4 = m0 + ig * 64 + tx * 4;
+    if (r4 >= dm) continue;
+    const bool full = r4 + 3 < dm;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + j - 4);
+      if (gn >= ncols) continue;
+      float v[4];
+      const float cs = colscale ? f64_to_f32_rn(colscale[gn]) : 1.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = acc[ig * 4 + q][j] * cs;
+      TC* dst = Cp + r4 + (int64_t)gn * ldc;
+      if (mode == MM_SUB) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (r4 + q < dm) dst[q] = dst[q] - (TC)v[q];
+      } else if (full && vec_ok) {
+        *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (r4 + q < dm) store_out(dst + q, v[q], mode == MM_ATOMIC);
+      }
+      if (nsl > 0) {
+        const int64_t o = r4 + (int64_t)gn * ldsl;
+        __nv_bfloat16 w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float r = v[q];
+          w0[q] = __float2bfloat16_rn(r);
+          r -= __bfloat162float(w0[q]);
+          w1[q] = __float2bfloat16_rn(r);
+          r -= __bfloat162float(w1[q]);
+          w2[q] = __float2bfloat16_rn(r);
+        }
+        if (full && ((ldsl & 3) == 0)) {
+          *(uint2*)(sl0 + o) = make_uint2(pack_bf2(w0[0], w0[1]), pack_bf2(w0[2], w0[3]));
+          if (nsl > 1) *(uint2*)(sl1 + o) = make_uint2(pack_bf2(w1[0], w1[1]), pack_bf2(w1[2], w1[3]));
+          if (nsl > 2) *(uint2*)(sl2 + o) = make_uint2(pack_bf2(w2[0], w2[1]), pack_bf2(w2[2], w2[3]));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (r4 + q >= dm) continue;
+            sl0[o + q] = w0[q];
+            if (nsl > 1) sl1[o + q] = w1[q];
+            if (nsl > 2) sl2[o + q] = w2[q];
+          }
+        }
+      }
+    }
+  }
+}
+
 // FP32-compute tiles (Grams of FP32 data, triangular solve, lift): 128 x 128
 // output tile, k steps of 8, 256 threads with an 8 x 8 register block each
 // (two 4 x 4 quadrants, so shared-memory reads are float4 and conflict-free),
@@ -186,9 +259,8 @@ k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) 
   const MMDesc* __restrict__ dp = md + c;
   if (dp->cond && !(*dp->cond & FLAG_SHIFTED)) return;
   const int dm = dp->m, dn = dp->n, dk = dp->k, mt = dp->mt, nt = dp->nt, kchunk = dp->kchunk;
-  const int mode = dp->mode, sym = dp->sym, nsl = dp->nsl;
-  const int64_t lda = dp->lda, ldb = dp->ldb, ldc = dp->ldc, pstride = dp->pstride, ldsl = dp->ldsl;
-  const double* __restrict__ colscale = dp->colscale;
+  const int sym = dp->sym;
+  const int64_t lda = dp->lda, ldb = dp->ldb;
   int local = t - off[c];
   const int per_split = mt * nt;
   const int split = local / per_split;
@@ -278,67 +350,121 @@ k_tile_mm128(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) 
     }
   }
 
-  TC* __restrict__ Cp = (TC*)dp->Cm + (mode == MM_PARTIAL ? (int64_t)split * pstride : 0);
-  __nv_bfloat16* sl0 = dp->sl[0];
-  __nv_bfloat16* sl1 = dp->sl[1];
-  __nv_bfloat16* sl2 = dp->sl[2];
-  // each thread owns rows {r4, r4+1, r4+2, r4+3} (two such groups) of 8
-  // columns: full groups go out as one vector store per column
-  const bool vec_ok = (mode == MM_STORE) && (sizeof(TC) == 4) && ((ldc & 3) == 0) &&
-                      ((((uintptr_t)Cp) & 15) == 0);
+  mm128_store<TC>(dp, acc, split, m0, n0, ncols, tx, ty);
+}
+
+// The same 128 x 128 FP32 tiles with both operands FP32 in global memory,
+// fed by cp.async into a 4-stage shared-memory ring: the loads of k step
+// s + 3 are in flight while step s is computed, so the global latency (the
+// tile's k extent is often only l = 128, 16 steps) is hidden instead of
+// exposed once per step as with register staging.  Tall column-major A
+// (ACOL) moves in 16-byte copies where the leading dimension and base allow,
+// row-style A (a Gram's Y^T) and B in 4-byte copies; out-of-range elements
+// are zero-filled by the copy itself.
+RSVD_DEV void cp_async4(void* sdst, const void* gsrc, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(bytes) : "memory");
+}
+RSVD_DEV void cp_async16(void* sdst, const void* gsrc, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(bytes) : "memory");
+}
+RSVD_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+RSVD_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename TC, int AL>
+__global__ void __launch_bounds__(256, 2)
+k_tile_mm128_cp(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
+  constexpr int S = 4;
+  __shared__ __align__(16) float As[S][8][132];
+  __shared__ __align__(16) float Bs[S][8][132];
+  const int t = blockIdx.x;
+  const int c = find_chan(off, C, t);
+  const MMDesc* __restrict__ dp = md + c;
+  if (dp->cond && !(*dp->cond & FLAG_SHIFTED)) return;
+  const int dm = dp->m, dn = dp->n, dk = dp->k, mt = dp->mt, nt = dp->nt, kchunk = dp->kchunk;
+  const int sym = dp->sym;
+  const int64_t lda = dp->lda, ldb = dp->ldb;
+  int local = t - off[c];
+  const int per_split = mt * nt;
+  const int split = local / per_split;
+  local -= split * per_split;
+  const int mi = local / nt, ni = local % nt;
+  if (sym && ni < mi) return;
+  const int m0 = mi * 128, n0 = ni * 128;
+  const int ncols = dp->ncols_dev ? min(dn, *dp->ncols_dev) : dn;
+  if (n0 >= ncols) return;
+  const int kb = split * kchunk;
+  const int ke = min(dk, kb + kchunk);
+  const float* __restrict__ A = (const float*)dp->A;
+  const float* __restrict__ B = (const float*)dp->B;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool a16 = AL == ACOL && (lda & 3) == 0 && (((uintptr_t)A) & 15) == 0;
+  const int nk = ke > kb ? (ke - kb + 7) / 8 : 0;
+
+  auto issue = [&](int step) {
+    const int buf = step % S, k0 = kb + 8 * step;
+    if (AL == ACOL && a16) {
+      const int kk = tid >> 5, mm = 4 * (tid & 31);
+      const int gm = m0 + mm, gk = k0 + kk;
+      int bytes = 0;
+      if (gk < ke && gm < dm) bytes = 4 * min(4, dm - gm);
+      cp_async16(&As[buf][kk][mm], bytes ? (const void*)(A + gm + (int64_t)gk * lda) : (const void*)A, bytes);
+    } else {
 #pragma unroll
-  for (int ig = 0; ig < 2; ++ig) {
-    const int r4 = m0 + ig * 64 + tx * 4;
-    if (r4 >= dm) continue;
-    const bool full = r4 + 3 < dm;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int gn = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + j - 4);
-      if (gn >= ncols) continue;
-      float v[4];
-      const float cs = colscale ? f64_to_f32_rn(colscale[gn]) : 1.0f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = acc[ig * 4 + q][j] * cs;
-      TC* dst = Cp + r4 + (int64_t)gn * ldc;
-      if (mode == MM_SUB) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (r4 + q < dm) dst[q] = dst[q] - (TC)v[q];
-      } else if (full && vec_ok) {
-        *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (r4 + q < dm) store_out(dst + q, v[q], mode == MM_ATOMIC);
-      }
-      if (nsl > 0) {
-        const int64_t o = r4 + (int64_t)gn * ldsl;
-        __nv_bfloat16 w0[4], w1[4], w2[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float r = v[q];
-          w0[q] = __float2bfloat16_rn(r);
-          r -= __bfloat162float(w0[q]);
-          w1[q] = __float2bfloat16_rn(r);
-          r -= __bfloat162float(w1[q]);
-          w2[q] = __float2bfloat16_rn(r);
-        }
-        if (full && ((ldsl & 3) == 0)) {
-          *(uint2*)(sl0 + o) = make_uint2(pack_bf2(w0[0], w0[1]), pack_bf2(w0[2], w0[3]));
-          if (nsl > 1) *(uint2*)(sl1 + o) = make_uint2(pack_bf2(w1[0], w1[1]), pack_bf2(w1[2], w1[3]));
-          if (nsl > 2) *(uint2*)(sl2 + o) = make_uint2(pack_bf2(w2[0], w2[1]), pack_bf2(w2[2], w2[3]));
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (r4 + q >= dm) continue;
-            sl0[o + q] = w0[q];
-            if (nsl > 1) sl1[o + q] = w1[q];
-            if (nsl > 2) sl2[o + q] = w2[q];
-          }
-        }
+      for (int p = 0; p < 4; ++p) {
+        const int e = tid + p * 256;
+        int mm, kk;
+        if (AL == AROW) { kk = e & 7; mm = e >> 3; } else { mm = e & 127; kk = e >> 7; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        const bool in = gm < dm && gk < ke;
+        const float* src = in ? (AL == AROW ? A + (int64_t)gm * lda + gk : A + gm + (int64_t)gk * lda) : A;
+        cp_async4(&As[buf][kk][mm], src, in ? 4 : 0);
       }
     }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int e = tid + p * 256;
+      const int kk = e & 7, nn = e >> 3;
+      const int gk = k0 + kk, gn = n0 + nn;
+      const bool in = gn < ncols && gk < ke;
+      cp_async4(&Bs[buf][kk][nn], in ? (const void*)(B + gk + (int64_t)gn * ldb) : (const void*)B, in ? 4 : 0);
+    }
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll
+  for (int s0 = 0; s0 < S - 1; ++s0) {
+    if (s0 < nk) issue(s0);
+    cp_async_commit();
   }
+  for (int step = 0; step < nk; ++step) {
+    cp_async_wait<S - 2>();
+    __syncthreads();                       // step's tiles landed; step - 1's buffer is free
+    if (step + S - 1 < nk) issue(step + S - 1);
+    cp_async_commit();
+    const int buf = step % S;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const float4 a0 = *(const float4*)&As[buf][kk][tx * 4];
+      const float4 a1 = *(const float4*)&As[buf][kk][64 + tx * 4];
+      const float4 b0 = *(const float4*)&Bs[buf][kk][ty * 4];
+      const float4 b1 = *(const float4*)&Bs[buf][kk][64 + ty * 4];
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+  cp_async_wait<0>();
+  mm128_store<TC>(dp, acc, split, m0, n0, ncols, tx, ty);
 }
 
 // Sum the split partials of a Gram / inner product in a fixed order; for a
@@ -365,7 +491,8 @@ __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* 
 
 int tile_of(MMKind kind) {
   switch (kind) {
-    case MMK_NN_F32_F64B: case MMK_NN_F32_OUT64: case MMK_GRAM_F32: return 128;
+    case MMK_NN_F32_F64B: case MMK_NN_F32_OUT64: case MMK_GRAM_F32: case MMK_NN_F32:
+    case MMK_NN_F32_OUT64_B32: return 128;
     default: return 64;
   }
 }
@@ -380,7 +507,9 @@ void launch_tile_mm(MMKind kind, const MMDesc* d_md, const int* d_off, int C, in
     case MMK_GRAM_DOT2: k_tile_mm<float, float, double, AROW, ACC_DOT2><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
     case MMK_NN_F32_F64B: k_tile_mm128<float, double, float, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
     case MMK_NN_F32_OUT64: k_tile_mm128<float, double, double, ACOL, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
-    case MMK_GRAM_F32: k_tile_mm128<float, float, double, AROW, ACC_F32><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_GRAM_F32: k_tile_mm128_cp<double, AROW><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_NN_F32: k_tile_mm128_cp<float, ACOL><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
+    case MMK_NN_F32_OUT64_B32: k_tile_mm128_cp<double, ACOL><<<tiles, 256, 0, st>>>(d_md, d_off, C); break;
   }
   note_launch();
 }

@@ -525,13 +525,21 @@ __global__ void __launch_bounds__(256) k_chol_inv_reg(const Chan* __restrict__ c
     float (*rowx)[128] = (float (*)[128])ibuf;
     float (*colr)[128] = (float (*)[128])(ibuf + 2 * 128 * sizeof(float));
     reg_tri_inv<float>(x, rinv, rowx, colr, l, ta, tb);
+    float* ri32 = h.Ri32;
 #pragma unroll
     for (int q = 0; q < 8; ++q)
 #pragma unroll
       for (int p = 0; p <= q; ++p) {
         const int a = ta + 16 * p, b = tb + 16 * q;
-        if (a <= b && b < l) h.Ri[a + (int64_t)b * l] = f32_to_f64(x[blk36(p, q)]);
+        if (a <= b && b < l) {
+          h.Ri[a + (int64_t)b * l] = f32_to_f64(x[blk36(p, q)]);
+          if (ri32) ri32[a + (int64_t)b * l] = x[blk36(p, q)];
+        }
       }
+    if (ri32)
+      for (int b = tb; b < l; b += 16)
+        for (int a = ta; a < l; a += 16)
+          if (a > b) ri32[a + (int64_t)b * l] = 0.0f;
   } else {
     double* rinv = (double*)(ibuf + 2 * 2 * 128 * sizeof(double));
     if (ta == tb) {
@@ -874,6 +882,21 @@ void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv
                       cudaStream_t st) {
   if (k <= 0) return;
   k_sym_signs<<<(k + 7) / 8, 256, 0, st>>>(U, ldu, V, ldv, n, k, signs);
+  note_launch();
+}
+
+// X~ (J, FP64, l x l) -> Ri32 (FP32) for the FP32 lifts, per channel.
+__global__ void __launch_bounds__(256) k_j_to_f32(const Chan* __restrict__ ch) {
+  const Chan& h = ch[blockIdx.y];
+  const int64_t total = (int64_t)h.l * h.l;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    h.Ri32[e] = f64_to_f32_rn(h.J[e]);
+}
+
+void launch_j_to_f32(const Chan* d_ch, int C, int max_l, cudaStream_t st) {
+  if (C <= 0) return;
+  const int bx = std::max(1, std::min(64, (max_l * max_l + 255) / 256));
+  k_j_to_f32<<<dim3(bx, C), 256, 0, st>>>(d_ch);
   note_launch();
 }
 

@@ -19,7 +19,9 @@ enum MMKind {
   MMK_GRAM_DOT2 = 3,     // partial C_s = Y_s^T Z_s, FP32 data, compensated (Dot2) -> FP64
   MMK_NN_F32_F64B = 4,   // C(FP32) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
   MMK_NN_F32_OUT64 = 5,  // C(FP64) = A(FP32) B(FP64 rounded to FP32), FP32 FMA
-  MMK_GRAM_F32 = 6       // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
+  MMK_GRAM_F32 = 6,      // partial C_s = Y_s^T Z_s, FP32 data, FP32 FMA -> FP64 partials
+  MMK_NN_F32 = 7,        // C(FP32) = A(FP32) B(FP32), FP32 FMA
+  MMK_NN_F32_OUT64_B32 = 8   // C(FP64) = A(FP32) B(FP32), FP32 FMA
 };
 
 struct MMDesc {
@@ -114,6 +116,7 @@ struct RuleDesc {
   __nv_bfloat16* H[3];
   int64_t ldh;
 };
+void launch_j_to_f32(const Chan* d_ch, int C, int max_l, cudaStream_t st);
 void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv, int n, int k, double* signs,
                       cudaStream_t st);
 void launch_rule_prep(const RuleDesc& d, cudaStream_t st);
