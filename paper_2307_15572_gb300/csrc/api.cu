@@ -1046,6 +1046,23 @@ bool ri32_ok(const Job& J) {
   return true;
 }
 
+// FP32 copy of a small per-channel FP64 operand into Ri32 (count <= l * l).
+void add_cvt_f32(Job& J, std::function<const double*(int)> src, std::function<int64_t(int)> count) {
+  std::vector<CvtDesc> cd(J.C);
+  int64_t mx = 0;
+  for (int c = 0; c < J.C; ++c) {
+    cd[c] = CvtDesc{src(c), J.ch[c].Ri32, count(c)};
+    mx = std::max(mx, cd[c].count);
+  }
+  const CvtDesc* dcd = J.ar.put(cd.data(), cd.size());
+  const int C = J.C;
+  cudaStream_t st = J.P->st;
+  J.steps.push_back([=]() {
+    launch_cvt_f32(dcd, C, mx, st);
+    return RSVD_OK;
+  });
+}
+
 // CholeskyQR2 of Y32[:, 0:l) -> Q32 (FP32) and its BF16 words in Xb[:, 0:l).
 void cqr2_mixed(Job& J, int nsl_out) {
   auto& ch = J.ch;
@@ -1236,6 +1253,10 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
          [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
   // probe residual R = V G - Q C in place of V G, then its column energies
   {
+    bool c32 = ri32_ok(J);                                  // C (l x s) must fit the l x l FP32 scratch
+    for (int c = 0; c < J.C; ++c) c32 = c32 && J.d[c].s <= J.d[c].l;
+    if (c32) add_cvt_f32(J, [&](int c) { return (const double*)ch[c].C64; },
+                         [&](int c) { return (int64_t)J.d[c].l * J.d[c].s; });
     std::vector<MMDesc> md(J.C);
     std::vector<SumsqDesc> sd(J.C);
     for (int c = 0; c < J.C; ++c) {
@@ -1243,7 +1264,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
       float* VG = ch[c].Y32 + (int64_t)d.l * d.ldt;
       MMDesc m{};
       m.A = ch[c].Q32; m.lda = d.ldt;
-      m.B = ch[c].C64; m.ldb = d.l;
+      m.B = c32 ? (const void*)ch[c].Ri32 : (const void*)ch[c].C64; m.ldb = d.l;
       m.Cm = VG; m.ldc = d.ldt;
       m.m = d.n; m.n = d.s; m.k = d.l;
       m.ks = 1; m.kchunk = (int)rup(d.l, 16);
@@ -1251,7 +1272,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
       md[c] = m;
       sd[c] = SumsqDesc{VG, d.ldt, d.n, d.s, 4, ch[c].est_part};
     }
-    add_mm(J, MMK_NN_F32_F64B, md);
+    add_mm(J, c32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
     const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
     const int s_max = NPROBE;
     J.steps.push_back([=]() {
@@ -1281,13 +1302,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   });
   // the lifts read X~ in FP32 (the FP32 basis bounds their accuracy anyway)
   const bool b32 = ri32_ok(J);
-  if (b32) {
-    const Chan* dsw2 = dsw;
-    J.steps.push_back([=]() {
-      launch_j_to_f32(dsw2, C, maxl, st);
-      return RSVD_OK;
-    });
-  }
+  if (b32) add_cvt_f32(J, [&](int c) { return (const double*)ch[c].J; }, [&](int c) { return (int64_t)J.d[c].l * J.d[c].l; });
   const MMKind lk = b32 ? MMK_NN_F32_OUT64_B32 : MMK_NN_F32_OUT64;
   auto xs = [&](int c) { return b32 ? (const void*)ch[c].Ri32 : (const void*)ch[c].J; };
   lift(J, lk, [&](int c) { return (const void*)ch[c].Q32; }, xs,

@@ -885,18 +885,18 @@ void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv
   note_launch();
 }
 
-// X~ (J, FP64, l x l) -> Ri32 (FP32) for the FP32 lifts, per channel.
-__global__ void __launch_bounds__(256) k_j_to_f32(const Chan* __restrict__ ch) {
-  const Chan& h = ch[blockIdx.y];
-  const int64_t total = (int64_t)h.l * h.l;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    h.Ri32[e] = f64_to_f32_rn(h.J[e]);
+// FP64 -> FP32 copies of small per-channel operands (the lift's X~, the
+// probe coefficients C) for the FP32 tile products, one grid row per channel.
+__global__ void __launch_bounds__(256) k_cvt_f32(const CvtDesc* __restrict__ d) {
+  const CvtDesc c = d[blockIdx.y];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < c.count; e += (int64_t)gridDim.x * blockDim.x)
+    c.dst[e] = f64_to_f32_rn(c.src[e]);
 }
 
-void launch_j_to_f32(const Chan* d_ch, int C, int max_l, cudaStream_t st) {
-  if (C <= 0) return;
-  const int bx = std::max(1, std::min(64, (max_l * max_l + 255) / 256));
-  k_j_to_f32<<<dim3(bx, C), 256, 0, st>>>(d_ch);
+void launch_cvt_f32(const CvtDesc* d_desc, int C, int64_t max_count, cudaStream_t st) {
+  if (C <= 0 || max_count <= 0) return;
+  const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(64, (max_count + 255) / 256));
+  k_cvt_f32<<<dim3(bx, C), 256, 0, st>>>(d_desc);
   note_launch();
 }
 

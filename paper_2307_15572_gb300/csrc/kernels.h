@@ -116,7 +116,8 @@ struct RuleDesc {
   __nv_bfloat16* H[3];
   int64_t ldh;
 };
-void launch_j_to_f32(const Chan* d_ch, int C, int max_l, cudaStream_t st);
+struct CvtDesc { const double* src; float* dst; int64_t count; };
+void launch_cvt_f32(const CvtDesc* d_desc, int C, int64_t max_count, cudaStream_t st);
 void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv, int n, int k, double* signs,
                       cudaStream_t st);
 void launch_rule_prep(const RuleDesc& d, cudaStream_t st);
