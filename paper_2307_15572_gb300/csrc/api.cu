@@ -1163,6 +1163,45 @@ Chan* reorth_x(Job& J) {
   for (auto& h : sw) h.M = h.J;                     // Cholesky works in (and X~ lands in) J
   Chan* dsw = J.ar.put(sw.data(), sw.size(), 128);
   auto& ch = J.ch;
+  if (ri32_ok(J)) {
+    // l <= 128: the Jacobi left its columns M unnormalised in FP32 (X = M D).
+    // G = D (M^T M) D with M^T M from the compensated (Dot2) Gram, FP32
+    // Cholesky R^T R = G, and X~ = M D + M (D (R^{-1} - I)): FP64 where it
+    // matters, the small correction as an FP32 product (no FP64 l^3 work).
+    add_tn_ex(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].M; },
+              [&](int c) { return (const void*)ch[c].M; }, [&](int c) { return ch[c].G; },
+              [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true,
+              [&](int c) { return J.d[c].l; }, [&](int c) { return (int64_t)J.d[c].l; }, [&](int) { return 1; });
+    const int C = J.C, maxl = J.max_l;
+    cudaStream_t st = J.P->st;
+    const std::vector<int> ls = chan_ls(J);
+    int* coop = J.P->d_coop;
+    const Chan* dch = J.d_ch;
+    J.steps.push_back([=]() {
+      launch_reorth(0, dch, C, maxl, st);              // G = D (M^T M) D
+      run_chol(dsw, ls, 0, maxl, 0, 1, 0, coop, st);  // X^T X ~ I: an FP32 factor is enough
+      launch_reorth(1, dch, C, maxl, st);              // Ri32 = D (R^{-1} - I)
+      return RSVD_OK;
+    });
+    std::vector<MMDesc> md(J.C);
+    for (int c = 0; c < J.C; ++c) {
+      const int l = J.d[c].l;
+      MMDesc m{};
+      m.A = ch[c].M; m.lda = l;                       // FP32 M
+      m.B = ch[c].Ri32; m.ldb = l;
+      m.Cm = ch[c].J; m.ldc = l;
+      m.m = l; m.n = l; m.k = l;
+      m.ks = 1; m.kchunk = (int)rup(l, 16);
+      m.mode = MM_STORE;
+      md[c] = m;
+    }
+    add_mm(J, MMK_NN_F32_OUT64_B32, md);
+    J.steps.push_back([=]() {
+      launch_reorth(2, dch, C, maxl, st);              // J += M D
+      return RSVD_OK;
+    });
+    return dsw;
+  }
   add_tn_ex(J, MMK_GRAM_F64, [&](int c) { return (const void*)ch[c].M; }, [&](int c) { return (const void*)ch[c].M; },
             [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true,
             [&](int c) { return J.d[c].l; }, [&](int c) { return (int64_t)J.d[c].l; }, [&](int) { return 1; });
@@ -2012,6 +2051,7 @@ struct AdaptBufsM {
   double *Cb, *E;
   double *Gs, *Rs, *Ris, *Ms, *Js, *sigs, *scrs;
   double *Gf, *Rf, *Rif, *Mf, *Jf, *sigf, *scrf, *C64f, *est;
+  float *Ri32s, *Ri32f;
   double *gpart;
   int lmax;
 };
@@ -2053,10 +2093,12 @@ void lay_adapt_mixed(Bump& b, const std::vector<ChanDims>& d, int bsz, int nsl, 
     const size_t sb = (size_t)bsz * (bsz + 32);
     x.Gs = b.take<double>(sb); x.Rs = b.take<double>(sb); x.Ris = b.take<double>(sb);
     x.Ms = b.take<double>(sb); x.Js = b.take<double>(sb);
+    x.Ri32s = b.take<float>((size_t)bsz * bsz);
     x.sigs = b.take<double>(bsz); x.scrs = b.take<double>(bsz);
     const size_t sf = (size_t)x.lmax * (x.lmax + 32);
     x.Gf = b.take<double>(sf); x.Rf = b.take<double>(sf); x.Rif = b.take<double>(sf);
     x.Mf = b.take<double>(sf); x.Jf = b.take<double>(sf);
+    x.Ri32f = b.take<float>((size_t)x.lmax * std::max(x.lmax, NPROBE));
     x.sigf = b.take<double>(x.lmax); x.scrf = b.take<double>(x.lmax);
     x.C64f = b.take<double>((size_t)x.lmax * NPROBE);
     x.est = b.take<double>((size_t)NPROBE * (1 + x.lmax));
@@ -2233,6 +2275,7 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
       h.l = J.d[a].l;
       h.col0 = cols[c];
       h.G = x.Gs; h.R = x.Rs; h.Ri = x.Ris; h.M = x.Ms; h.J = x.Js; h.sig = x.sigs; h.scr = x.scrs;
+      h.Ri32 = x.Ri32s;
       h.T32 = x.T32;
       h.Q32 = x.Q32 + (int64_t)cols[c] * d[c].ldt;
       for (int w = 0; w < nsl; ++w) h.Xb[w] = x.Qw[w] + (int64_t)cols[c] * d[c].ldb;
@@ -2380,6 +2423,7 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
       Chan h = base[c];
       h.l = dd.l; h.lw = dd.lw; h.k_cap = dd.kcap;
       h.G = x.Gf; h.R = x.Rf; h.Ri = x.Rif; h.M = x.Mf; h.J = x.Jf; h.sig = x.sigf; h.scr = x.scrf;
+      h.Ri32 = x.Ri32f;
       h.Q32 = x.Q32; h.Y32 = x.W32; h.C64 = x.C64f; h.est_part = x.est;
       J.ch[a] = h;
       J.max_l = std::max(J.max_l, dd.l);

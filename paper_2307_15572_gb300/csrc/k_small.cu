@@ -618,7 +618,10 @@ RSVD_DEV double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 
 // Sweep count and flags; sigma_i = |M_i| sorted descending (ties by index),
 // X = M_i / sigma_i, Z = J_i into the channel's buffers.
-template <typename T, bool WANT_J>
+// M32 (and the channel has its FP32 scratch Ri32): store the sorted columns
+// M_i unnormalised as FP32 (exact copies of the FP32 Jacobi columns) in h.M's
+// buffer instead of X = M_i / sigma_i in FP64.
+template <typename T, bool WANT_J, bool M32 = false>
 RSVD_DEV void jacobi_finish(const Chan& h, const T* Mw, const T* Jw, int lp, int l, int sweep, int max_sweeps) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   if (threadIdx.x == 0) {
@@ -646,7 +649,12 @@ RSVD_DEV void jacobi_finish(const Chan& h, const T* Mw, const T* Jw, int lp, int
     rank = warp_sum(rank);
     const T* cc = Mw + (int64_t)cidx * lp;
     const double inv = si > 0.0 ? 1.0 / si : 0.0;
-    for (int rr = lane; rr < l; rr += 32) h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
+    if (M32 && h.Ri32) {                    // the FP32 re-orthonormalisation follows (see reorth_x)
+      float* m32 = (float*)h.M;
+      for (int rr = lane; rr < l; rr += 32) m32[rr + (int64_t)rank * l] = (float)cc[rr];
+    } else {
+      for (int rr = lane; rr < l; rr += 32) h.M[rr + (int64_t)rank * l] = (double)cc[rr] * inv;
+    }
     if (WANT_J) {
       const T* jc = Jw + (int64_t)cidx * lp;
       for (int rr = lane; rr < l; rr += 32) h.J[rr + (int64_t)rank * l] = (double)jc[rr];
@@ -777,7 +785,8 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
 }
 
 // The same one-sided Jacobi for the mixed path's factors of at most 128
-// columns (FP32, left vectors only, shared memory): column stride 32 NV
+// columns (FP32, left vectors only, shared memory; the sorted columns leave
+// unnormalised in FP32 for the re-orthonormalisation): column stride 32 NV
 // floats fixed at compile time, one 8-lane group per pair (64 groups cover
 // every pair of a round), and each lane keeps its NV float4 of both columns
 // in registers between the dot products and the rotation.  Same pair
@@ -859,7 +868,7 @@ __global__ void __launch_bounds__(512) k_jacobi_f32s(const Chan* __restrict__ ch
     }
     if (!__syncthreads_or(rotated)) break;         // also the barrier after the last round
   }
-  jacobi_finish<float, false>(h, Mw, (const float*)nullptr, lp, l, sweep, max_sweeps);
+  jacobi_finish<float, false, true>(h, Mw, (const float*)nullptr, lp, l, sweep, max_sweeps);
 }
 
 // Symmetric storage: for symmetric V the triplets pair as v_i = sign(lambda_i)
@@ -897,6 +906,58 @@ void launch_cvt_f32(const CvtDesc* d_desc, int C, int64_t max_count, cudaStream_
   if (C <= 0 || max_count <= 0) return;
   const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(64, (max_count + 255) / 256));
   k_cvt_f32<<<dim3(bx, C), 256, 0, st>>>(d_desc);
+  note_launch();
+}
+
+// Re-orthonormalisation of the FP32 Jacobi vectors X = M D (M the FP32
+// columns, D = diag(1 / sigma), sigma_i = |M_i|; l <= 128):
+//   G = D (M^T M) D  (M^T M from the compensated Gram),
+//   X~ = X R^{-1} = M D + M (D (R^{-1} - I))  with R^T R = G,
+// the second term small (R ~ I), so it is formed in FP32 and the first in FP64.
+RSVD_DEV void reorth_inv(const Chan& h, double* inv) {
+  for (int i = threadIdx.x; i < h.l; i += blockDim.x) {
+    const double si = h.sig[i];
+    inv[i] = si > 0.0 ? 1.0 / si : 0.0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_reorth_scale(const Chan* __restrict__ ch) {
+  __shared__ double inv[128];
+  const Chan& h = ch[blockIdx.y];
+  reorth_inv(h, inv);
+  const int l = h.l;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x)
+    h.G[e] *= inv[e % l] * inv[e / l];
+}
+
+__global__ void __launch_bounds__(256) k_reorth_prep(const Chan* __restrict__ ch) {
+  __shared__ double inv[128];
+  const Chan& h = ch[blockIdx.y];
+  reorth_inv(h, inv);
+  const int l = h.l;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) {
+    const int i = e % l, j = e / l;
+    h.Ri32[e] = f64_to_f32_rn(inv[i] * (h.Ri[e] - (i == j ? 1.0 : 0.0)));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_reorth_add(const Chan* __restrict__ ch) {
+  __shared__ double inv[128];
+  const Chan& h = ch[blockIdx.y];
+  reorth_inv(h, inv);
+  const int l = h.l;
+  const float* m32 = (const float*)h.M;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x)
+    h.J[e] = fma((double)m32[e], inv[e / l], h.J[e]);
+}
+
+void launch_reorth(int stage, const Chan* d_ch, int C, int max_l, cudaStream_t st) {
+  if (C <= 0) return;
+  const dim3 grid(std::max(1, std::min(16, (max_l * max_l + 255) / 256)), C);
+  if (stage == 0) k_reorth_scale<<<grid, 256, 0, st>>>(d_ch);
+  else if (stage == 1) k_reorth_prep<<<grid, 256, 0, st>>>(d_ch);
+  else k_reorth_add<<<grid, 256, 0, st>>>(d_ch);
   note_launch();
 }
 

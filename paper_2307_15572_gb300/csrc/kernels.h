@@ -116,6 +116,9 @@ struct RuleDesc {
   __nv_bfloat16* H[3];
   int64_t ldh;
 };
+// Re-orthonormalisation steps of the FP32 Jacobi vectors (l <= 128): 0 scale
+// the Gram of M by D on both sides, 1 Ri32 = D (R^{-1} - I), 2 J += M D.
+void launch_reorth(int stage, const Chan* d_ch, int C, int max_l, cudaStream_t st);
 struct CvtDesc { const double* src; float* dst; int64_t count; };
 void launch_cvt_f32(const CvtDesc* d_desc, int C, int64_t max_count, cudaStream_t st);
 void launch_sym_signs(const double* U, int64_t ldu, const double* V, int64_t ldv, int n, int k, double* signs,
