@@ -77,7 +77,13 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
   const int ke = min(dk, kb + kchunk);
   const TA* __restrict__ A = (const TA*)dp->A;
   const TB* __restrict__ B = (const TB*)dp->B;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // each warp owns a 4 x 8 patch of the 16 x 16 grid of 4 x 4 output blocks
+  // (rows ty, columns tx): reads of B are conflict-free, and in a Gram's
+  // diagonal tile two warps lie wholly below the diagonal and skip their
+  // arithmetic (the reduction mirrors the upper triangle)
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int ty = 4 * (w >> 1) + (lane >> 3), tx = 8 * (w & 1) + (lane & 7);
+  const bool lower = sym && mi == ni && ty > tx;
 
   T acc[4][4], cmp[4][4];
 #pragma unroll
@@ -110,33 +116,36 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
       Bs[kk][nn] = v;
     }
     __syncthreads();
+    if (!lower) {
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      T a[4], b[4];
+      for (int kk = 0; kk < 16; ++kk) {
+        T a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (ACC == ACC_DOT2) {
-            const float p = (float)a[i] * (float)b[j];
-            const float pe = fmaf((float)a[i], (float)b[j], -p);
-            float s, se;
-            two_sum((float)acc[i][j], p, s, se);
-            acc[i][j] = s;
-            cmp[i][j] += se + pe;
-          } else {
-            acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) {
+            if (ACC == ACC_DOT2) {
+              const float p = (float)a[i] * (float)b[j];
+              const float pe = fmaf((float)a[i], (float)b[j], -p);
+              float s, se;
+              two_sum((float)acc[i][j], p, s, se);
+              acc[i][j] = s;
+              cmp[i][j] += se + pe;
+            } else {
+              acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
           }
-        }
+      }
     }
     __syncthreads();
   }
 
   TC* __restrict__ Cp = (TC*)dp->Cm + (mode == MM_PARTIAL ? (int64_t)split * pstride : 0);
+  if (lower) return;                             // never read (mirrored from the upper triangle)
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int gm = m0 + ty * 4 + i;
@@ -481,7 +490,7 @@ __global__ void k_reduce_partials(const MMDesc* __restrict__ md, double* const* 
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     int i = e % d.m, j = e / d.m;
     int si = i, sj = j;
-    if (d.sym && (i / d.tile) > (j / d.tile)) { si = j; sj = i; }
+    if (d.sym && i > j) { si = j; sj = i; }      // only the upper triangle is computed
     double s = 0.0;
     for (int p = 0; p < ks; ++p) s += P[(int64_t)p * d.pstride + si + (int64_t)sj * d.ldc];
     out[i + (int64_t)j * d.m] = s;
