@@ -6,7 +6,8 @@
  * library adds a small learned model that predicts, per channel and
  * tolerance, the rank and oversampling from a cheap probe sketch, so that one
  * fixed-rank pass replaces the blocks of the adaptive loop; the adaptive loop
- * remains its fallback and judge (RSVD_RANK_LEARNED in rsvd.h).
+ * remains its fallback, and the rank rule's error check decides whether a
+ * predicted rank is accepted (RSVD_RANK_LEARNED in rsvd.h).
  *
  * Network: x (d) -> tanh(x W1 + b1) (128) -> tanh(. W2 + b2) (128) -> . W3 + b3 (2),
  * outputs (log k, log p).  Parameter blob (FP32, device, caller-owned), row-major:

@@ -2814,9 +2814,10 @@ rsvd_status run_probe(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors*
 // Learned rank: probe -> features -> network -> per-channel
 // l = 1.2 (k^ + p^), one fixed-l decomposition (reusing the probe's V words);
 // channels whose rank rule misses the tolerance get one retry at 1.5 l, then
-// the adaptive loop in the plan's precision (for tile rules: one run at the
-// column cap) -- the plain method stays both the fallback and the judge.  A channel that already drew all the columns
-// it may (n or l_max) keeps its best factors and TOL_NOT_MET.
+// the adaptive loop in the plan's precision (stored channels and tile rules
+// alike); every result is accepted only by the rank rule's error check.  A
+// channel that already drew all the columns it may (n or l_max) keeps its
+// best factors and TOL_NOT_MET.
 rsvd_status run_learned(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f, rsvd_status* per_item) {
   if (!P->o.mlp_weights) return seterr(RSVD_ERR_INVALID_ARG, "learned rank needs mlp_weights");
   const int lcap_opt = P->o.l_max > 0 ? P->o.l_max : 1024;
