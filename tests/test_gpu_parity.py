@@ -332,3 +332,31 @@ def test_mixed_pinned_and_pageable_host_inputs(lib):
                 assert abs(e - e0) <= 1e-3 * e0
         finally:
             plan.close()
+
+
+def test_mixed_pinned_host_input_never_staged(lib):
+    """Host-resident channel: on the mixed path a page-locked FP64 V is read
+    once, in place, by the conversion kernel and never copied to the device;
+    the plan's workspace holds only the BF16 words (4 B per entry with two
+    words) and the n x l work, so channels whose FP64 matrix exceeds HBM while
+    their words fit are decomposed from host memory."""
+    torch = _torch()
+    n = 6000
+    A = synth.batch_channel(9, n)
+    pinned = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.as_tensor(A))
+    pageable = np.ascontiguousarray(A)
+    sizes = {}
+    for name, host in (("pinned", pinned), ("pageable", pageable)):
+        plan = lib.Plan(n, k=118, p=10, q=0, seed=4, tol=1e-4, policy="tol", precision="bf16x")
+        try:
+            st, r = plan.decompose(host, 128)
+            assert st >= 0, lib.last_error()
+            e = plan.reconstruct_error(torch.as_tensor(A, device="cuda"), r)
+            assert e <= 1e-4
+            sizes[name] = lib.load().rsvd_plan_workspace_bytes(plan.h)
+        finally:
+            plan.close()
+    # the staged (pageable) run needs the FP64 copy of V; the pinned run does not
+    assert sizes["pageable"] - sizes["pinned"] >= 8 * n * n * 0.99, sizes
+    assert sizes["pinned"] < 8 * n * n, sizes
