@@ -1271,9 +1271,13 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
     });
   } else {
     J.steps.push_back([=]() {
-      if (!skip_convert) launch_convert_slices(dch, off8, C, t8, nsl, st);
-      launch_fro2_reduce_rows(dch, C, 8, st);         // partials are kept from the convert pass
-      launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
+      if (!skip_convert) {
+        launch_convert_omega(dch, off8, t8, off64, t64, C, nsl, seed, pseed, nsl, st);   // words, P and probes
+        launch_fro2_reduce_rows(dch, C, 8, st);
+      } else {
+        launch_fro2_reduce_rows(dch, C, 8, st);       // partials are kept from the probe job's conversion
+        launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
+      }
       return RSVD_OK;
     });
   }

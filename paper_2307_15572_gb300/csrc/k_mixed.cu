@@ -46,10 +46,8 @@ RSVD_DEV double bsum(double v, double* sh) {
 // from the FP32 values (relative error ~1e-7) and summed in FP64 per tile;
 // so is the energy of the remainder the words leave out (wres_part), which
 // the probe error estimate cannot see and the rank rule adds back.
-__global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
-                                                 const int* __restrict__ off, int C, int nsl) {
+RSVD_DEV void convert_body(const Chan* __restrict__ ch, const int* __restrict__ off, int C, int nsl, int t) {
   __shared__ double sh[32];
-  const int t = blockIdx.x;
   const int c = find_chan(off, C, t);
   const Chan& h = ch[c];
   const int b = t - off[c];
@@ -114,6 +112,11 @@ __global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch,
   }
 }
 
+__global__ void __launch_bounds__(256) k_convert(const Chan* __restrict__ ch, const int* __restrict__ off, int C,
+                                                 int nsl) {
+  convert_body(ch, off, C, nsl, blockIdx.x);
+}
+
 void launch_convert_slices(const Chan* d_ch, const int* d_off, int C, int tiles, int nsl,
                            cudaStream_t st) {
   if (tiles > 0) { k_convert<<<tiles, 256, 0, st>>>(d_ch, d_off, C, nsl); note_launch(); }
@@ -122,11 +125,8 @@ void launch_convert_slices(const Chan* d_ch, const int* d_off, int C, int tiles,
 // Columns [j0, j1) of the X words: j < l are sketch columns (global column
 // col0 + j, TAG_OMEGA), j >= l probe columns (column j - l, TAG_RESID).
 // Word 0 holds the BF16 value, which is exact, so higher words are zero.
-__global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
-                                                    const int* __restrict__ off, int C,
-                                                    uint64_t seed, int col0, int j0, int j1,
-                                                    uint64_t pseed, int nsl, uint32_t tag) {
-  const int t = blockIdx.x;
+RSVD_DEV void omega_body(const Chan* __restrict__ ch, const int* __restrict__ off, int C, uint64_t seed, int col0,
+                         int j0, int j1, uint64_t pseed, int nsl, uint32_t tag, int t) {
   const int c = find_chan(off, C, t);
   const Chan& h = ch[c];
   const int r0 = (t - off[c]) * 64;
@@ -143,6 +143,34 @@ __global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch,
     h.Xb[0][o] = __float2bfloat16_rn(g);
     for (int w = 1; w < nsl; ++w) h.Xb[w][o] = __float2bfloat16_rn(0.0f);
   }
+}
+
+__global__ void __launch_bounds__(256) k_omega_bf16(const Chan* __restrict__ ch, const int* __restrict__ off, int C,
+                                                    uint64_t seed, int col0, int j0, int j1, uint64_t pseed, int nsl,
+                                                    uint32_t tag) {
+  omega_body(ch, off, C, seed, col0, j0, j1, pseed, nsl, tag, blockIdx.x);
+}
+
+// The conversion (HBM-bound) and the sketch matrix (Philox + Box-Muller,
+// ALU-bound) in one grid: their blocks are interleaved evenly, so the SMs
+// generate P while the conversion waits on memory.  Block b is P block
+// floor(b t64 / total) if that count steps at b, else conversion block
+// b - floor((b + 1) t64 / total).
+__global__ void __launch_bounds__(256) k_convert_omega(const Chan* __restrict__ ch, const int* __restrict__ off8,
+                                                       int t8, const int* __restrict__ off64, int t64, int C, int nsl,
+                                                       uint64_t seed, uint64_t pseed, int onsl) {
+  const int64_t total = (int64_t)t8 + t64;
+  const int64_t b = blockIdx.x;
+  const int64_t lo = b * t64 / total, hi = (b + 1) * t64 / total;
+  if (hi > lo) omega_body(ch, off64, C, seed, 0, 0, 1 << 30, pseed, onsl, TAG_OMEGA, (int)lo);
+  else convert_body(ch, off8, C, nsl, (int)(b - hi));
+}
+
+void launch_convert_omega(const Chan* d_ch, const int* d_off8, int t8, const int* d_off64, int t64, int C, int nsl,
+                          uint64_t seed, uint64_t pseed, int onsl, cudaStream_t st) {
+  if (t8 + t64 <= 0) return;
+  k_convert_omega<<<t8 + t64, 256, 0, st>>>(d_ch, d_off8, t8, d_off64, t64, C, nsl, seed, pseed, onsl);
+  note_launch();
 }
 
 void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,

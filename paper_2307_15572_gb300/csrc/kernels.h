@@ -145,6 +145,10 @@ void launch_convert_slices(const Chan* d_ch, const int* d_off_rows, int C, int t
 void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uint64_t seed,
                        int col0, int j0, int j1, uint64_t pseed, int nsl, cudaStream_t st,
                        uint32_t tag = TAG_OMEGA);
+// launch_convert_slices and the full launch_omega_bf16 (col0 = 0, all columns,
+// TAG_OMEGA) as one interleaved grid.
+void launch_convert_omega(const Chan* d_ch, const int* d_off8, int t8, const int* d_off64, int t64, int C, int nsl,
+                          uint64_t seed, uint64_t pseed, int onsl, cudaStream_t st);
 // 19 rank-model features per channel from its probe singular values (h.sig).
 void launch_features(const Chan* d_ch, int C, double tol, float* feat, cudaStream_t st);
 void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st);
