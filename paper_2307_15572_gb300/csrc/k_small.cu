@@ -1199,40 +1199,46 @@ void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ sign fix
+// Flip (u_i, v_i) so that the largest-magnitude entry of u_i is positive
+// (ties: lowest row).  Magnitudes are compared as the integer bit patterns of
+// |u| (monotonic for finite values) and signs flipped by the sign bit, so the
+// scan and the flip stay off this part's narrow FP64 pipe.
 __global__ void __launch_bounds__(256) k_signfix(const Chan* __restrict__ ch) {
-  __shared__ double sv[256];
+  __shared__ unsigned long long sv[256];
   __shared__ int si[256];
   const Chan& h = ch[blockIdx.x];
   const int col = blockIdx.y;
   if (col >= h.res->k_out || h.U == nullptr) return;
-  double* u = h.U + (int64_t)col * h.ldu;
-  double best = -1.0;
+  unsigned long long* u = (unsigned long long*)(h.U + (int64_t)col * h.ldu);
+  const unsigned long long mag = 0x7FFFFFFFFFFFFFFFull, sgn = 0x8000000000000000ull;
+  unsigned long long best = 0;
   int bi = 0x7fffffff;
   for (int r = threadIdx.x; r < h.n; r += blockDim.x) {
-    const double a = fabs(u[r]);
-    if (a > best) { best = a; bi = r; }
+    const unsigned long long a = u[r] & mag;
+    if (bi == 0x7fffffff || a > best) { best = a; bi = r; }
   }
   sv[threadIdx.x] = best;
   si[threadIdx.x] = bi;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
-      const double ob = sv[threadIdx.x + s];
+      const unsigned long long ob = sv[threadIdx.x + s];
       const int oi = si[threadIdx.x + s];
-      if (ob > sv[threadIdx.x] || (ob == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+      if (oi != 0x7fffffff &&
+          (si[threadIdx.x] == 0x7fffffff || ob > sv[threadIdx.x] || (ob == sv[threadIdx.x] && oi < si[threadIdx.x]))) {
         sv[threadIdx.x] = ob;
         si[threadIdx.x] = oi;
       }
     }
     __syncthreads();
   }
-  const double pivot = u[si[0]];
+  const bool neg = si[0] != 0x7fffffff && (u[si[0]] & sgn) && (u[si[0]] & mag);
   __syncthreads();
-  if (pivot < 0.0) {
-    for (int r = threadIdx.x; r < h.n; r += blockDim.x) u[r] = -u[r];
+  if (neg) {
+    for (int r = threadIdx.x; r < h.n; r += blockDim.x) u[r] ^= sgn;
     if (h.V) {
-      double* v = h.V + (int64_t)col * h.ldv;
-      for (int r = threadIdx.x; r < h.n; r += blockDim.x) v[r] = -v[r];
+      unsigned long long* v = (unsigned long long*)(h.V + (int64_t)col * h.ldv);
+      for (int r = threadIdx.x; r < h.n; r += blockDim.x) v[r] ^= sgn;
     }
   }
 }
