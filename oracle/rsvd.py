@@ -133,11 +133,14 @@ def rsvd(V, k=None, p=5, q=0, seed=0, tol=None, P=None, rayleigh_ritz=False,
 
 
 def reconstruct_error(V, U, S, W):
-    """Exact ||V - U diag(S) W^T||_F / ||V||_F in FP64."""
+    """Exact ||V - U diag(S) W^T||_F / ||V||_F in FP64.
+
+    The relative error is undefined for V = 0; there the absolute residual
+    ||U diag(S) W^T||_F is returned (0 for empty or zero factors)."""
     V = np.asarray(V, dtype=np.float64)
     D = V - (U * S[None, :]) @ W.T
     nv = np.linalg.norm(V)
-    return float(np.linalg.norm(D) / nv) if nv > 0 else 0.0
+    return float(np.linalg.norm(D) / nv) if nv > 0 else float(np.linalg.norm(D))
 
 
 def eckart_young(sigma_sorted, k):

@@ -265,3 +265,16 @@ def test_symmetric_signs_recover_eigenvalue_signs():
     assert np.allclose(res.S, np.abs(lam[order]), rtol=1e-12)
     A1 = (res.U * (sg * res.S)) @ res.U.T
     assert np.max(np.abs(A1 - A)) <= 1e-12 * np.max(np.abs(A))
+
+
+def test_reconstruct_error_of_zero_matrix_is_absolute():
+    # relative error is undefined for V = 0: the absolute residual is reported
+    n, k = 30, 3
+    rng = np.random.default_rng(21)
+    U = rng.standard_normal((n, k))
+    W = rng.standard_normal((n, k))
+    S = np.array([3.0, 2.0, 0.5])
+    Z = np.zeros((n, n))
+    direct = np.sqrt(np.sum(((U * S) @ W.T) ** 2))
+    assert abs(rsvd.reconstruct_error(Z, U, S, W) - direct) <= 1e-14 * direct
+    assert rsvd.reconstruct_error(Z, U[:, :0], S[:0], W[:, :0]) == 0.0

@@ -21,13 +21,44 @@ def test_noise_hash_symmetric_and_moments():
 
 
 def test_mix32_reference_values():
-    # lowbias32 is a bijection on 32-bit words with mix(0) = 0; check a few
-    # algebraic properties rather than stored values
+    # lowbias32 is a bijection on 32-bit words with mix(0) = 0
     x = np.arange(1, 1 << 16, dtype=np.uint64)
     h = tilerule.mix32(x)
     assert int(tilerule.mix32(0)) == 0
     assert len(np.unique(h)) == len(x)
     assert np.all(h < (1 << 32))
+
+
+def _lowbias32_inverse(x):
+    # The inverse published with lowbias32 (C. Wellons, hash-prospector):
+    # undo the xorshifts and multiply by the modular inverses of the two
+    # multipliers (0x846CA68B^-1 = 0x43021123, 0x7FEB352D^-1 = 0x1D69E2A5).
+    x = int(x) & 0xFFFFFFFF
+    x ^= x >> 16
+    x = (x * 0x43021123) & 0xFFFFFFFF
+    x ^= (x >> 15) ^ (x >> 30)
+    x = (x * 0x1D69E2A5) & 0xFFFFFFFF
+    x ^= x >> 16
+    return x
+
+
+def test_mix32_known_answers():
+    # Step-by-step trace of the published definition for x = 1:
+    #   x ^= x >> 16      -> 0x00000001
+    #   x *= 0x7FEB352D   -> 0x7FEB352D
+    #   x ^= x >> 15      -> 0x7FEB352D ^ 0x0000FFD6 = 0x7FEBCAFB
+    #   x *= 0x846CA68B   -> 0x6889F849   (mod 2^32)
+    #   x ^= x >> 16      -> 0x6889F849 ^ 0x00006889 = 0x688990C0
+    assert int(tilerule.mix32(1)) == 0x688990C0
+    assert int(tilerule.mix32(0x12345678)) == 0xF5E71C96
+    assert int(tilerule.mix32(0xFFFFFFFF)) == 0x6768824A
+    # the published inverse undoes it on arbitrary words, which fixes both
+    # multipliers and all three shifts
+    rng = np.random.default_rng(11)
+    xs = rng.integers(0, 1 << 32, size=4096, dtype=np.uint64)
+    hs = tilerule.mix32(xs)
+    assert all(_lowbias32_inverse(h) == int(x) for h, x in zip(hs, xs))
+    assert (0x846CA68B * 0x43021123) & 0xFFFFFFFF == 1 and (0x7FEB352D * 0x1D69E2A5) & 0xFFFFFFFF == 1
 
 
 def test_closed_form_spectrum_matches_dense():
