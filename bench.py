@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--rule-n", type=int, default=200000)
     ap.add_argument("--no-rule", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="fixed default launch shapes")
+    ap.add_argument("--no-graphs", action="store_true", help="direct launches instead of CUDA-graph replay")
+    ap.add_argument("--prof-steps", type=int, default=5, help="profiled (per-kernel event) steps after timing")
+    ap.add_argument("--no-rule-verify", action="store_true", help="skip the exact FP64 residual of the rule")
     return ap.parse_args()
 
 
@@ -96,13 +99,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def bf16_peak():
+def bf16_peak(sustained=False):
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
     if os.path.exists(p):
         d = json.load(open(p))
-        if "bf16_tflops" in d:
-            return float(d["bf16_tflops"]), "measured (burst)"
-    return 1900.0, "fallback"
+        if key in d:
+            return float(d[key]), "measured (%s)" % ("sustained" if sustained else "burst")
+    return (1700.0 if sustained else 1900.0), "fallback"
 
 
 def tc_traffic_record():
@@ -189,10 +193,13 @@ def run_gpu(args):
     kcap = L_COLS - P_OVER
     lib = rsvd
 
-    def make_plan(prec):
+    def make_plan(prec, graphs=False):
         # autotuning happens in the first warm-up step (outside the timed region)
-        return rsvd.Plan(max(sizes), k=kcap, p=P_OVER, q=0, tol=TOL, policy="tol", precision=prec, slices=2,
-                         seed=seed, stream=stream.cuda_stream, autotune=not args.no_autotune)
+        pl = rsvd.Plan(max(sizes), k=kcap, p=P_OVER, q=0, tol=TOL, policy="tol", precision=prec, slices=2,
+                       seed=seed, stream=stream.cuda_stream, autotune=not args.no_autotune)
+        if graphs:
+            rsvd.rsvd_plan_set_graphs(pl.h, True)
+        return pl
 
     def tune_summary(plan):
         recs = rsvd.rsvd_plan_tune_records(plan.h)
@@ -266,28 +273,55 @@ def run_gpu(args):
             ks.append(f.k_out)
         return max(errs), ks
 
-    # ---- mixed path (headline)
-    plan = make_plan("bf16x")
-    rsvd.rsvd_plan_set_profiling(plan.h, True)
+    # ---- mixed path (headline): the whole grouped decomposition replayed from
+    # a CUDA graph (captured in the warm-up), no per-kernel events
+    plan = make_plan("bf16x", graphs=not args.no_graphs)
     facs, bufs = alloc_factors()
-    ms, wall, prof, clk = timed_steps(plan, facs, args.steps, args.warmup, descs, clocks=(rank == 0))
+    ms, wall, prof_h, clk = timed_steps(plan, facs, args.steps, args.warmup, descs, clocks=(rank == 0))
     max_err, ks = verify(plan, facs)
     tot, ms_max = reduce_runs(entries * args.steps, ms)
     value = tot / (ms_max / 1e3)
-    hbm_peak, peak_kind = peaks()
-    tc_ms_per = prof["tc_ms"] / max(1, prof["tc_launches"])
-    tc_bytes_per = prof["tc_bytes"] / max(1, prof["tc_launches"])
-    achieved = tc_bytes_per / (tc_ms_per / 1e3) / 1e9 if tc_ms_per > 0 else 0.0
-    ratio = tc_traffic_record()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": (ratio * tc_bytes_per) if ratio else None,
-                "kernel": "k_tc_gemm (tcgen05 pass over V words)", "peak_source": peak_kind,
-                "launches": prof["tc_launches"], "avg_launch_ms": tc_ms_per,
-                "algorithmic_bytes_per_launch": tc_bytes_per,
-                "share_of_step": prof["tc_ms"] / ms if ms > 0 else None}
-    gpu_launches = int(prof["launches"])
+    gpu_launches = int(prof_h["launches"])
     tuning = tune_summary(plan)
+    # the same steps again with CUDA events around the passes over V (direct
+    # launches: events inside a replayed graph are not per launch), for the
+    # per-kernel rooflines
+    rsvd.rsvd_plan_set_graphs(plan.h, False)
+    rsvd.rsvd_plan_set_profiling(plan.h, True)
+    ms_p, _, prof, _ = timed_steps(plan, facs, args.prof_steps, 1, descs)
     plan.close()
+    hbm_peak, peak_kind = peaks()
+    ratio = tc_traffic_record()
+    kern = []
+    if prof["cvt_launches"]:
+        c_ms = prof["cvt_ms"] / prof["cvt_launches"]
+        c_bytes = prof["cvt_bytes"] / prof["cvt_launches"]
+        c_ach = c_bytes / (c_ms / 1e3) / 1e9
+        kern.append({"bound": "hbm", "achieved": c_ach, "peak": hbm_peak, "unit": "GB/s", "frac": c_ach / hbm_peak,
+                     "traffic": None, "kernel": "k_convert_omega (FP64 V -> BF16 words, ||V||^2, P)",
+                     "peak_source": peak_kind, "launches": prof["cvt_launches"], "avg_launch_ms": c_ms,
+                     "algorithmic_bytes_per_launch": c_bytes,
+                     "bytes_per_unit": "8 B read + 2 B per word written per V entry, + P words",
+                     "share_of_step": prof["cvt_ms"] / ms_p})
+    if prof["tc_launches"]:
+        tc_ms_per = prof["tc_ms"] / prof["tc_launches"]
+        tc_bytes_per = prof["tc_bytes"] / prof["tc_launches"]
+        achieved = tc_bytes_per / (tc_ms_per / 1e3) / 1e9
+        kern.append({"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": (ratio * tc_bytes_per) if ratio else None,
+                     "kernel": "k_tc_gemm (tcgen05 pass over V words)", "peak_source": peak_kind,
+                     "launches": prof["tc_launches"], "avg_launch_ms": tc_ms_per,
+                     "algorithmic_bytes_per_launch": tc_bytes_per,
+                     "bytes_per_unit": "2 B per word per V entry, + X words and Y once",
+                     "share_of_step": prof["tc_ms"] / ms_p})
+    kern.sort(key=lambda r: -r["share_of_step"])
+    roofline = dict(kern[0]) if kern else None
+    if roofline is not None:
+        roofline["note"] = ("dominant kernel of the step by share (CUDA events over %d profiled steps of the "
+                            "same workload, direct launches); 'others' lists the other timed kernels"
+                            % args.prof_steps)
+        roofline["others"] = kern[1:]
+        roofline["profiled_ms_per_step"] = ms_p / args.prof_steps
 
     # ---- e2e through the C ABI with host buffers
     e2e = None
@@ -298,7 +332,7 @@ def run_gpu(args):
             h.copy_(A)
             hmats.append(h)
         hdescs = [rsvd.dense(h) for h in hmats]
-        plan = make_plan("bf16x")
+        plan = make_plan("bf16x", graphs=not args.no_graphs)
         hf, hb = alloc_factors("cpu", pin=True)
         ms_e, wall_e, prof_e, _ = timed_steps(plan, hf, args.e2e_steps, 1, hdescs)
         h2d = sum(8 * n * n for n in sizes)
@@ -348,23 +382,47 @@ def run_gpu(args):
         g_ms = prof_r["gen_ms"] / max(1, prof_r["gen_launches"])
         g_alg = prof_r["gen_flops"] / max(1, prof_r["gen_launches"])
         g_mma = prof_r["gen_mma_flops"] / max(1, prof_r["gen_launches"])
-        bpk, bsrc = bf16_peak()
+        t_ms = prof_r["tc_ms"] / max(1, prof_r["tc_launches"])
+        t_bytes = prof_r["tc_bytes"] / max(1, prof_r["tc_launches"])
+        t_flops = prof_r["tc_flops"] / max(1, prof_r["tc_launches"])
+        hbm_peak, peak_kind = peaks()
+        bps, bps_src = bf16_peak(sustained=True)
+        g_ach = g_alg / (g_ms / 1e3) / 1e12 if g_ms else 0.0
+        rule_exact = None
+        if not args.no_rule_verify:
+            # every entry regenerated in FP64 on the device (outside the timed region)
+            t0v = time.perf_counter()
+            rule_exact = {"rel_err": rsvd.rsvd_reconstruct_error(plan.h, rm, rf),
+                          "seconds": time.perf_counter() - t0v,
+                          "how": "rsvd_reconstruct_error on the tile rule: all n^2 entries regenerated in FP64 "
+                                 "(FP64 factor panel products + hash noise) against U diag(S) V^T"}
         rule = {"value": tot_r / (ms_r / 1e3), "unit": UNIT,
                 "ms_per_step": ms_r / args.rule_steps, "steps": args.rule_steps,
                 "workload": "rule: Gaussian-bump tile rule, n = %d, M = 300, w_m = e^-m/25, hash noise 1e-7; "
                             "k = 320, p = 10, q = 1, 2 words; every pass generates its entries" % rn,
                 "err_est": rf.err_est, "status": int(rf.status), "k": rf.k_out,
+                "exact_residual": rule_exact,
+                "verified": (rule_exact["rel_err"] <= rf.err_est) if rule_exact else None,
                 "passes_per_step": 2 * rq + 2,
-                "roofline": {"bound": "tensor", "kernel": "k_tc_gemm<3, 3, true> (tile-rule generation, two epilogue groups)",
-                             "achieved": g_mma / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
-                             "peak": bpk, "unit": "TFLOP/s",
-                             "frac": (g_mma / (g_ms / 1e3) / 1e12) / bpk if g_ms else 0.0,
-                             "achieved_algorithmic": g_alg / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
-                             "peak_source": bsrc, "launches": prof_r["gen_launches"], "avg_launch_ms": g_ms,
+                "roofline": {"bound": "tensor",
+                             "kernel": "k_tc_gemm<3, 3, true> (tile-rule generation, two epilogue groups)",
+                             "achieved": g_ach, "peak": bps, "unit": "TFLOP/s", "frac": g_ach / bps,
+                             "peak_source": bps_src + " (the generator runs inside a seconds-long step)",
+                             "flops_per_unit": "2 M = 600 flops per generated entry (algorithmic)",
+                             "launches": prof_r["gen_launches"], "avg_launch_ms": g_ms,
                              "share_of_step": prof_r["gen_ms"] / ms_r if ms_r else None,
-                             "note": "achieved counts the issued BF16 word products (6 per entry term, "
-                                     "M padded to 320); achieved_algorithmic counts 2 M flops per entry"},
-                "product_pass_ms": prof_r["tc_ms"] / max(1, prof_r["tc_launches"])}
+                             "issued_tflops": g_mma / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
+                             "note": "issued_tflops counts the BF16 word products the kernel issues (6 per "
+                                     "entry term, M padded to 320), 6.4x the algorithmic work; frac is on "
+                                     "algorithmic flops"},
+                "product_roofline": {"bound": "hbm", "kernel": "k_tc_gemm<2, 2> (panel words x X words)",
+                                     "achieved": t_bytes / (t_ms / 1e3) / 1e9 if t_ms else 0.0,
+                                     "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": (t_bytes / (t_ms / 1e3) / 1e9) / hbm_peak if t_ms else 0.0,
+                                     "tflops_issued": t_flops / (t_ms / 1e3) / 1e12 if t_ms else 0.0,
+                                     "launches": prof_r["tc_launches"], "avg_launch_ms": t_ms,
+                                     "algorithmic_bytes_per_launch": t_bytes,
+                                     "share_of_step": prof_r["tc_ms"] / ms_r if ms_r else None}}
         plan.close()
         del rb
 
@@ -397,6 +455,24 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def cpu_model():
+    """CPU model of the host running the oracle (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 # ------------------------------------------------------------ oracle timing
 def cpu_oracle(mats, sizes, seed, budget_s):
     """The oracle as it stands, on the host cores, over channels until the budget."""
@@ -416,7 +492,7 @@ def cpu_oracle(mats, sizes, seed, budget_s):
         if t_total > budget_s:
             break
     cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": done_entries / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": done_entries / t_total, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": "%d of %d channels (sum n^2 = %.3g), tol 1e-4, l = %d, q = 0, numpy FP64"
                       % (used, len(host), done_entries, L_COLS),
             "seconds": t_total}
@@ -476,7 +552,8 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "batch40 (see gb300 arm)", "tol": TOL, "l": L_COLS, "q": 0},
            "impl": "reference",
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     if dist is not None:

@@ -191,18 +191,26 @@ rsvd_status rsvd_decompose_batched(rsvd_plan_t plan, int32_t C, const rsvd_matri
                                    rsvd_factors* f, rsvd_status* per_item);
 
 /* Exact relative residual ||A - U diag(S) V^T||_F / ||A||_F of the rank-f->k_out
- * factors, accumulated in FP64 over every entry of a stored channel.
- * *rel_err is a host pointer.  Tile rules: RSVD_ERR_UNSUPPORTED (generate
- * their rows with rsvd_rule_rows). */
+ * factors, accumulated in FP64 over every entry (the paper's validation of
+ * a rank-R_SVD form, "Randomized matrix decompositions" paragraph).  Stored
+ * channels (device or host A and factors) are read as they are.  Tile rules
+ * are regenerated: every entry is rebuilt in FP64 from the rule's definition
+ * (the FP64 factor panel sqrt(w_m) g_m(x_j), its products and the hash
+ * noise) and compared with the factors tile by tile, nothing of A being
+ * stored -- 2 n^2 (rule_m + k) FP64 flops, e.g. about a minute at
+ * n = 200,000 on this part's FP64 rate.  For A = 0 the absolute residual
+ * ||U diag(S) V^T||_F is returned.  *rel_err is a host pointer; synchronous.
+ * The plan's workspace grows by n * rule_m doubles for a tile rule. */
 rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
                                    const rsvd_factors* f, double* rel_err);
 
 /* Launch accounting of the plan's own kernels, for benchmarks.  When enabled
  * (rsvd_plan_set_profiling(plan, 1)), each decomposition records CUDA events
- * on the plan's stream around every tensor-core pass and every FP64 dense
- * pass over V and adds their device time and algorithmic traffic (bytes of V
- * words, X words and Y read or written once, as the roofline counts them) to
- * the counters below.  Kernel launches are counted whether or not timing is
+ * on the plan's stream around every tensor-core pass, every FP64 dense pass
+ * over V, every tile-rule generation and every conversion of V into words,
+ * and adds their device time and algorithmic traffic (bytes of V words, X
+ * words and Y read or written once, as the roofline counts them) to the
+ * counters below.  Kernel launches are counted whether or not timing is
  * enabled.  rsvd_plan_profile copies the counters (host struct) and, if
  * `reset` is non-zero, zeroes them. */
 typedef struct {
@@ -218,6 +226,9 @@ typedef struct {
   double gen_ms;
   double gen_flops;        /* algorithmic: 2 M per generated entry               */
   double gen_mma_flops;    /* issued: 6 word products x 2 x (M padded to 64)     */
+  int64_t cvt_launches;    /* conversions of stored FP64 V into BF16 words       */
+  double cvt_ms;
+  double cvt_bytes;        /* 8 B read + 2 B per word written per entry          */
 } rsvd_profile;
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
@@ -316,21 +327,27 @@ double rsvd_compression_ratio(int64_t n, int32_t k, int32_t one_factor);
  * cudaMalloc/cudaFree synchronise the device in the middle of a pipeline.
  * It computes the same quantity as rsvd_reconstruct_error,
  * ||A - U diag(S) V^T||_F / ||A||_F in FP64, but keeps its per-tile partial
- * sums in a fixed 1 MiB array that the library holds on every GPU that loads
- * it, until the process exits.
+ * sums in a fixed array of 2 x 1,216 doubles (19 KiB) that the library holds
+ * on every GPU that loads it, until the process exits.
  *
- *   A (n x n, leading dim lda >= n), U (n x k, ldu >= n), S (k),
- *   V (n x k, ldv >= n): DEVICE pointers, column-major as elsewhere;
- *   rel_err: DEVICE pointer to one double, written asynchronously;
+ *   A (n x n, leading dim lda >= n; any matrix, read column-major
+ *   A[r + c*lda]), U (n x k, ldu >= n), S (k), V (n x k, ldv >= n): DEVICE
+ *   pointers, column-major as elsewhere;
+ *   rel_err: DEVICE pointer to one double, written asynchronously (for A = 0
+ *   the absolute residual ||U diag(S) V^T||_F);
  *   stream: cudaStream_t (NULL = legacy default stream).
- * Returns RSVD_ERR_INVALID_ARG for n < 1, n > RSVD_NOALLOC_MAX_N, k < 0 or a
- * bad pointer or leading dimension (nothing is launched then), RSVD_ERR_CUDA
- * if a CUDA call fails.  It calls no cudaMalloc, cudaFree or allocating
- * library routine.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before capturing any stream on the device.  All calls on one device
- * share the array, so calls that overlap on the GPU (concurrent streams, or
- * several host threads) race and must be serialised by the caller. */
+ * n is limited to RSVD_NOALLOC_MAX_N.  Returns RSVD_ERR_INVALID_ARG for
+ * n < 1, n > RSVD_NOALLOC_MAX_N, k < 0 or a bad pointer or leading dimension
+ * (nothing is launched then), RSVD_ERR_CUDA if a CUDA call fails; the reason
+ * is in rsvd_last_error_string().  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before capturing any stream on the device, and do not
+ * call the entry point again after a cudaDeviceReset in the same process
+ * (the looked-up address belonged to the old context).  All calls on one
+ * device share the array, so calls that overlap on the GPU (concurrent
+ * streams, or several host threads) race and must be serialised by the
+ * caller. */
 #define RSVD_NOALLOC_MAX_N 16384
 rsvd_status rsvd_reconstruct_error_noalloc(const double* A, int64_t lda, int64_t n, const double* U,
                                            int64_t ldu, const double* S, const double* V, int64_t ldv,

@@ -64,6 +64,21 @@ rsvd_status seterr(rsvd_status s, const char* fmt, ...) {
                     #call, cudaGetErrorString(e_));                                          \
   } while (0)
 
+}  // namespace
+
+namespace rsvd {
+void clear_error_text() { g_err[0] = 0; }
+rsvd_status set_error_text(rsvd_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+}  // namespace rsvd
+
+namespace {
+
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -86,7 +101,7 @@ struct rsvd_plan_s {
   int profiling = 0;
   rsvd_profile prof{};
   std::vector<cudaEvent_t> ev_pool;
-  struct Timed { cudaEvent_t a, b; int kind; double bytes, flops; };   // kind 0 tc, 1 FP64, 2 rule generation
+  struct Timed { cudaEvent_t a, b; int kind; double bytes, flops; };   // kind 0 tc, 1 FP64, 2 rule generation, 3 conversion
   std::vector<Timed> pending;
   size_t ev_next = 0;
   long long launch_base = 0;
@@ -183,7 +198,7 @@ void timed_begin(rsvd_plan_s* P, cudaEvent_t* a, cudaEvent_t* b) {
 // Small SVD of every channel's factor: one CTA per channel while the factor
 // fits its shared memory, else the cooperative kernel (several CTAs per
 // channel; not while the stream is being captured into a graph).
-void run_jacobi(const Chan* dch, const std::vector<int>& ls, int fp32, int maxl, int* coop, cudaStream_t st) {
+void run_jacobi(const Chan* dch, const std::vector<int>& ls, int fp32, int maxl, int* coop, int* err, cudaStream_t st) {
   const int C = (int)ls.size();
   const int ve = fp32 ? 4 : 2;
   const size_t lp = (size_t)((maxl + 8 * ve - 1) / (8 * ve) * (8 * ve));
@@ -191,7 +206,7 @@ void run_jacobi(const Chan* dch, const std::vector<int>& ls, int fp32, int maxl,
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (st) cudaStreamIsCapturing(st, &cs);
   if (bytes > 200 * 1024 && cs == cudaStreamCaptureStatusNone &&
-      launch_jacobi_coop(dch, ls.data(), C, fp32, coop, st) == 0)
+      launch_jacobi_coop(dch, ls.data(), C, fp32, coop, err, st) == 0)
     return;
   launch_jacobi(dch, C, fp32, maxl, st);
 }
@@ -199,7 +214,7 @@ void run_jacobi(const Chan* dch, const std::vector<int>& ls, int fp32, int maxl,
 // Cholesky + inverse of every channel's Gram: one CTA per channel while the
 // factor fits its shared memory, else the cooperative kernel.
 void run_chol(const Chan* dch, const std::vector<int>& ls, int accumulate, int maxl, int f32inv, int f32_chol,
-              int conditional, int* coop, cudaStream_t st) {
+              int conditional, int* coop, int* err, cudaStream_t st) {
   const int C = (int)ls.size();
   const size_t esz = f32_chol ? sizeof(float) : sizeof(double);
   size_t bytes = (size_t)maxl * (maxl + 1) * esz + (size_t)maxl * sizeof(double);
@@ -208,7 +223,7 @@ void run_chol(const Chan* dch, const std::vector<int>& ls, int accumulate, int m
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (st) cudaStreamIsCapturing(st, &cs);
   if (bytes > 200 * 1024 && cs == cudaStreamCaptureStatusNone &&
-      launch_chol_coop(dch, ls.data(), C, accumulate, f32_chol, conditional, coop, st) == 0)
+      launch_chol_coop(dch, ls.data(), C, accumulate, f32_chol, conditional, coop, err, st) == 0)
     return;
   launch_chol_inv(dch, C, accumulate, maxl, f32inv, st, f32_chol, conditional);
 }
@@ -220,6 +235,7 @@ void drain_profile(rsvd_plan_s* P) {
     cudaEventElapsedTime(&ms, t.a, t.b);
     if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
     else if (t.kind == 2) { P->prof.gen_launches++; P->prof.gen_ms += ms; P->prof.gen_flops += t.flops; P->prof.gen_mma_flops += t.bytes; }
+    else if (t.kind == 3) { P->prof.cvt_launches++; P->prof.cvt_ms += ms; P->prof.cvt_bytes += t.bytes; }
     else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
   }
   P->pending.clear();
@@ -500,8 +516,9 @@ void add_chol(Job& J, int accumulate, int f32_chol = 0) {
   cudaStream_t st = J.P->st;
   const std::vector<int> ls = chan_ls(J);
   int* coop = J.P->d_coop;
+  int* derr_w = J.P->d_err;
   J.steps.push_back([=]() {
-    run_chol(dch, ls, accumulate, maxl, f32inv, f32_chol, 0, coop, st);
+    run_chol(dch, ls, accumulate, maxl, f32inv, f32_chol, 0, coop, derr_w, st);
     return RSVD_OK;
   });
 }
@@ -530,6 +547,54 @@ void cqr2_f64(Job& J, std::function<double*(int)> src, std::function<double*(int
     }
     add_mm(J, MMK_NN_F64, md);
   }
+  // Conditional third round for the channels whose Cholesky needed the shift
+  // (shifted CholeskyQR3, Fukaya et al. 2020): the shifted factor leaves Q
+  // orthonormal only to about kappa(Y)^2 u, one more round restores it (and
+  // accumulates its factor into R).  Other channels skip every launch at its
+  // first instruction.
+  auto flags = [&](int c) {
+    return (const int*)((uintptr_t)J.ch[c].res + offsetof(ChanResult, flags));
+  };
+  add_tn_ex(J, MMK_GRAM_F64, [&](int c) { return (const void*)src(c); }, [&](int c) { return (const void*)src(c); },
+            [&](int c) { return J.ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true,
+            [&](int c) { return J.d[c].n; }, [&](int c) { return J.d[c].ldt; },
+            [&](int c) { return J.d[c].gsplit; }, flags);
+  {
+    const Chan* dch = J.d_ch;
+    const int maxl = J.max_l;
+    cudaStream_t st = J.P->st;
+    const std::vector<int> ls = chan_ls(J);
+    int* coop = J.P->d_coop;
+    int* derr_w = J.P->d_err;
+    const int acc = acc_R ? 1 : 0;
+    J.steps.push_back([=]() {
+      run_chol(dch, ls, acc, maxl, 0, 0, 1, coop, derr_w, st);
+      return RSVD_OK;
+    });
+  }
+  std::vector<MMDesc> md(J.C);
+  std::vector<CopyDesc> cd(J.C);
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    MMDesc m{};
+    m.A = src(c); m.lda = d.ldt;
+    m.B = J.ch[c].Ri; m.ldb = d.l;
+    m.Cm = tmp(c); m.ldc = d.ldt;
+    m.m = d.n; m.n = d.l; m.k = d.l;
+    m.mt = cdiv(d.n, 64); m.nt = cdiv(d.l, 64); m.ks = 1; m.kchunk = (int)rup(d.l, 16);
+    m.mode = MM_STORE;
+    m.cond = flags(c);
+    md[c] = m;
+    cd[c] = CopyDesc{tmp(c), src(c), (int64_t)d.ldt * d.l, flags(c)};
+  }
+  add_mm(J, MMK_NN_F64, md);
+  const CopyDesc* dcd = J.ar.put(cd.data(), cd.size());
+  const int C = J.C;
+  cudaStream_t st = J.P->st;
+  J.steps.push_back([=]() {
+    launch_copy64_if_shifted(dcd, C, st);
+    return RSVD_OK;
+  });
 }
 
 // Y_c = V_c X_c (dense FP64), split over k with atomic accumulation when the
@@ -757,8 +822,9 @@ void build_fp64(Job& J) {
   std::vector<int> ls(C);
   for (int c = 0; c < C; ++c) ls[c] = J.d[c].l;
   int* coop = J.P->d_coop;
+  int* derr_w = J.P->d_err;
   J.steps.push_back([=]() {
-    run_jacobi(dch, ls, 0, maxl, coop, st);
+    run_jacobi(dch, ls, 0, maxl, coop, derr_w, st);
     launch_select(dch, C, policy, tol, 0, st);
     return RSVD_OK;
   });
@@ -1115,8 +1181,9 @@ void cqr2_mixed(Job& J, int nsl_out) {
     cudaStream_t st = J.P->st;
     const std::vector<int> ls = chan_ls(J);
     int* coop = J.P->d_coop;
+  int* derr_w = J.P->d_err;
     J.steps.push_back([=]() {
-      run_chol(dch, ls, 0, maxl, 1, 0, 1, coop, st);
+      run_chol(dch, ls, 0, maxl, 1, 0, 1, coop, derr_w, st);
       return RSVD_OK;
     });
   }
@@ -1176,10 +1243,11 @@ Chan* reorth_x(Job& J) {
     cudaStream_t st = J.P->st;
     const std::vector<int> ls = chan_ls(J);
     int* coop = J.P->d_coop;
+  int* derr_w = J.P->d_err;
     const Chan* dch = J.d_ch;
     J.steps.push_back([=]() {
       launch_reorth(0, dch, C, maxl, st);              // G = D (M^T M) D
-      run_chol(dsw, ls, 0, maxl, 0, 1, 0, coop, st);  // X^T X ~ I: an FP32 factor is enough
+      run_chol(dsw, ls, 0, maxl, 0, 1, 0, coop, derr_w, st);  // X^T X ~ I: an FP32 factor is enough
       launch_reorth(1, dch, C, maxl, st);              // Ri32 = D (R^{-1} - I)
       return RSVD_OK;
     });
@@ -1210,8 +1278,9 @@ Chan* reorth_x(Job& J) {
     cudaStream_t st = J.P->st;
     const std::vector<int> ls = chan_ls(J);
     int* coop = J.P->d_coop;
+  int* derr_w = J.P->d_err;
     J.steps.push_back([=]() {
-      run_chol(dsw, ls, 0, maxl, 0, 1, 0, coop, st);   // X^T X ~ I: an FP32 factor is enough
+      run_chol(dsw, ls, 0, maxl, 0, 1, 0, coop, derr_w, st);   // X^T X ~ I: an FP32 factor is enough
       return RSVD_OK;
     });
   }
@@ -1270,9 +1339,21 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
       return RSVD_OK;
     });
   } else {
+    // algorithmic traffic of the conversion: V read once (8 B), its words and
+    // P's words written once
+    double cbytes = 0.0;
+    for (int c = 0; c < C; ++c)
+      cbytes += (double)J.d[c].n * J.d[c].n * (8.0 + 2.0 * nsl) + (double)J.d[c].n * J.d[c].lw * 2.0 * nsl;
+    rsvd_plan_s* P = J.P;
     J.steps.push_back([=]() {
       if (!skip_convert) {
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (P->profiling) timed_begin(P, &ea, &eb);
         launch_convert_omega(dch, off8, t8, off64, t64, C, nsl, seed, pseed, nsl, st);   // words, P and probes
+        if (P->profiling) {
+          cudaEventRecord(eb, st);
+          P->pending.push_back({ea, eb, 3, cbytes, 0.0});
+        }
         launch_fro2_reduce_rows(dch, C, 8, st);
       } else {
         launch_fro2_reduce_rows(dch, C, 8, st);       // partials are kept from the probe job's conversion
@@ -1333,8 +1414,9 @@ rsvd_status build_mixed(Job& J, bool skip_convert = false) {
   std::vector<int> ls(C);
   for (int c = 0; c < C; ++c) ls[c] = J.d[c].l;
   int* coop = J.P->d_coop;
+  int* derr_w = J.P->d_err;
   J.steps.push_back([=]() {
-    run_jacobi(dch, ls, 1, maxl, coop, st);
+    run_jacobi(dch, ls, 1, maxl, coop, derr_w, st);
     return RSVD_OK;
   });
   const Chan* dsw = reorth_x(J);                 // X~ in J
@@ -1559,6 +1641,20 @@ void layout(Job& J, Bump& b) {
   }
 }
 
+// Parameters of a tile rule: 1 <= rule_m <= 4096 finite centres, widths s > 0,
+// weights w >= 0, noise amplitude >= 0.
+rsvd_status check_rule(const rsvd_matrix& a) {
+  if (a.rule_m < 1 || a.rule_m > 4096) return seterr(RSVD_ERR_INVALID_ARG, "rule_m %d outside [1, 4096]", a.rule_m);
+  if (!a.rule_c || !a.rule_s || !a.rule_w) return seterr(RSVD_ERR_INVALID_ARG, "rule parameter array is NULL");
+  for (int m = 0; m < a.rule_m; ++m)
+    if (!std::isfinite(a.rule_c[m]) || !(a.rule_s[m] > 0.0) || !std::isfinite(a.rule_s[m]) || !(a.rule_w[m] >= 0.0) ||
+        !std::isfinite(a.rule_w[m]))
+      return seterr(RSVD_ERR_INVALID_ARG, "rule term %d needs finite c, s > 0, w >= 0", m);
+  if (!(a.rule_eta >= 0.0) || !std::isfinite(a.rule_eta))
+    return seterr(RSVD_ERR_INVALID_ARG, "rule_eta must be finite and >= 0");
+  return RSVD_OK;
+}
+
 rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_factors* f) {
   if (!P) return seterr(RSVD_ERR_INVALID_ARG, "plan is NULL");
   if (C < 1) return seterr(RSVD_ERR_INVALID_ARG, "channel count %d < 1", C);
@@ -1575,16 +1671,7 @@ rsvd_status validate(const rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_fac
                     (long long)P->o.n_max);
     if (a.n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: n too large", c);
     if (a.kind == RSVD_TILE_RULE) {
-      if (a.rule_m < 1 || a.rule_m > 4096)
-        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_m %d outside [1, 4096]", c, a.rule_m);
-      if (!a.rule_c || !a.rule_s || !a.rule_w)
-        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule parameter array is NULL", c);
-      for (int m = 0; m < a.rule_m; ++m)
-        if (!std::isfinite(a.rule_c[m]) || !(a.rule_s[m] > 0.0) || !std::isfinite(a.rule_s[m]) ||
-            !(a.rule_w[m] >= 0.0) || !std::isfinite(a.rule_w[m]))
-          return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule term %d needs finite c, s > 0, w >= 0", c, m);
-      if (!(a.rule_eta >= 0.0) || !std::isfinite(a.rule_eta))
-        return seterr(RSVD_ERR_INVALID_ARG, "channel %d: rule_eta must be finite and >= 0", c);
+      if (rsvd_status s = check_rule(a)) return s;
     } else {
       if (!a.data) return seterr(RSVD_ERR_INVALID_ARG, "channel %d: data is NULL", c);
       if (a.ld < a.n)
@@ -1958,8 +2045,9 @@ rsvd_status run_adaptive(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd_facto
     std::vector<int> ls(Cf);
     for (int a = 0; a < Cf; ++a) ls[a] = J.d[a].l;
     int* coop = P->d_coop;
+    int* derr_w = P->d_err;
     J.steps.push_back([=]() {
-      run_jacobi(dch, ls, 0, maxl, coop, st);
+      run_jacobi(dch, ls, 0, maxl, coop, derr_w, st);
       launch_select(dch, Cf, RSVD_RANK_TOL, tol, 0, st);
       return RSVD_OK;
     });
@@ -2472,8 +2560,9 @@ rsvd_status run_adaptive_mixed(rsvd_plan_s* P, int C, const rsvd_matrix* A, rsvd
       std::vector<int> ls(Cf);
       for (int a = 0; a < Cf; ++a) ls[a] = J.d[a].l;
       int* coop = P->d_coop;
+    int* derr_w = P->d_err;
       J.steps.push_back([=]() {
-        run_jacobi(d0, ls, 1, maxl, coop, st);
+        run_jacobi(d0, ls, 1, maxl, coop, derr_w, st);
         return RSVD_OK;
       });
     }
@@ -3064,13 +3153,7 @@ rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int3
   if (A->kind != RSVD_TILE_RULE) return seterr(RSVD_ERR_INVALID_ARG, "matrix is not a tile rule");
   const rsvd_matrix& a = *A;
   if (a.n < 1 || a.n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "n = %lld out of range", (long long)a.n);
-  if (a.rule_m < 1 || a.rule_m > 4096) return seterr(RSVD_ERR_INVALID_ARG, "rule_m %d outside [1, 4096]", a.rule_m);
-  if (!a.rule_c || !a.rule_s || !a.rule_w) return seterr(RSVD_ERR_INVALID_ARG, "rule parameter array is NULL");
-  for (int m = 0; m < a.rule_m; ++m)
-    if (!std::isfinite(a.rule_c[m]) || !(a.rule_s[m] > 0.0) || !std::isfinite(a.rule_s[m]) || !(a.rule_w[m] >= 0.0) ||
-        !std::isfinite(a.rule_w[m]))
-      return seterr(RSVD_ERR_INVALID_ARG, "rule term %d needs finite c, s > 0, w >= 0", m);
-  if (!(a.rule_eta >= 0.0) || !std::isfinite(a.rule_eta)) return seterr(RSVD_ERR_INVALID_ARG, "bad rule_eta");
+  if (rsvd_status s = check_rule(a)) return s;
   if (r0 < 0 || rows < 1 || r0 + rows > a.n)
     return seterr(RSVD_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, n)", (long long)r0, (long long)(r0 + rows));
   if (ldo < a.n) return seterr(RSVD_ERR_INVALID_ARG, "ldo < n");
@@ -3183,36 +3266,40 @@ rsvd_status rsvd_reconstruct_error(rsvd_plan_t P, const rsvd_matrix* A, const rs
                                    double* rel_err) {
   g_err[0] = 0;
   if (!P || !A || !f || !rel_err) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
-  if (A->kind != RSVD_DENSE_F64)
-    return seterr(RSVD_ERR_UNSUPPORTED, "matrix kind %d not handled by this entry point", A->kind);
+  if (A->kind != RSVD_DENSE_F64 && A->kind != RSVD_TILE_RULE)
+    return seterr(RSVD_ERR_INVALID_ARG, "matrix kind %d unknown", A->kind);
+  const bool rule = A->kind == RSVD_TILE_RULE;
   const int64_t n = A->n;
   const int k = f->k_out;
-  if (n < 1 || n > P->o.n_max || !A->data || A->ld < n) return seterr(RSVD_ERR_INVALID_ARG, "bad matrix");
+  if (n < 1 || n > P->o.n_max) return seterr(RSVD_ERR_INVALID_ARG, "bad matrix size");
+  if (rule) {
+    if (n > 2000000000LL / 64) return seterr(RSVD_ERR_INVALID_ARG, "n too large");
+    if (rsvd_status s = check_rule(*A)) return s;
+  } else if (!A->data || A->ld < n) {
+    return seterr(RSVD_ERR_INVALID_ARG, "bad matrix");
+  }
   if (k < 0 || k > f->k_cap) return seterr(RSVD_ERR_INVALID_ARG, "k_out %d outside [0, k_cap]", k);
   if (k > 0 && (!f->U || !f->V || !f->S || f->ldu < n || f->ldv < n))
     return seterr(RSVD_ERR_INVALID_ARG, "bad factors");
-  const int tiles = resid_tiles((int)n);
-  Bump b(nullptr);
-  const bool hA = A->mem == RSVD_MEM_HOST, hF = f->mem == RSVD_MEM_HOST;
+  const int blocks = resid_blocks(n);
+  const bool hA = !rule && A->mem == RSVD_MEM_HOST, hF = f->mem == RSVD_MEM_HOST;
+  const int M = rule ? A->rule_m : 0;
+  const int64_t ldh = rule ? rup(M, 16) : 0;
   for (int pass = 0; pass < 2; ++pass) {
     Bump bb(pass == 0 ? nullptr : P->ws);
     double* a = hA ? bb.take<double>((size_t)n * n) : nullptr;
     double* u = hF ? bb.take<double>((size_t)n * std::max(k, 1)) : nullptr;
     double* v = hF ? bb.take<double>((size_t)n * std::max(k, 1)) : nullptr;
     double* s = hF ? bb.take<double>(std::max(k, 1)) : nullptr;
-    double* part = bb.take<double>(2 * (size_t)tiles);
+    double* H = rule ? bb.take<double>((size_t)n * ldh) : nullptr;
+    double* par = rule ? bb.take<double>(3 * (size_t)M) : nullptr;
+    double* part = bb.take<double>(2 * (size_t)blocks);
     if (pass == 0) {
       if (rsvd_status st = grow_ws(P, bb.off + 4096)) return st;
       continue;
     }
-    if (rsvd_status st = grow_pinned(P, 2 * (size_t)tiles * sizeof(double) + 64)) return st;
-    const double* dA = A->data;
-    int64_t lda = A->ld;
-    if (hA) {
-      CK(cudaMemcpy2DAsync(a, n * sizeof(double), A->data, A->ld * sizeof(double), n * sizeof(double), n,
-                           cudaMemcpyHostToDevice, P->st));
-      dA = a; lda = n;
-    }
+    if (rsvd_status st = grow_pinned(P, std::max(2 * (size_t)blocks, 3 * (size_t)M) * sizeof(double) + 64))
+      return st;
     const double *dU = f->U, *dV = f->V, *dS = f->S;
     int64_t ldu = f->ldu, ldv = f->ldv;
     if (hF && k > 0) {
@@ -3223,15 +3310,36 @@ rsvd_status rsvd_reconstruct_error(rsvd_plan_t P, const rsvd_matrix* A, const rs
       CK(cudaMemcpyAsync(s, f->S, k * sizeof(double), cudaMemcpyHostToDevice, P->st));
       dU = u; dV = v; dS = s; ldu = n; ldv = n;
     }
-    launch_resid(dA, lda, dU, ldu, dV, ldv, dS, (int)n, k, part, P->st);
+    if (rule) {
+      // every entry regenerated in FP64 from the rule's definition
+      double* hpar = (double*)P->hp;
+      memcpy(hpar, A->rule_c, sizeof(double) * M);
+      memcpy(hpar + M, A->rule_s, sizeof(double) * M);
+      memcpy(hpar + 2 * M, A->rule_w, sizeof(double) * M);
+      CK(cudaMemcpyAsync(par, hpar, 3 * sizeof(double) * M, cudaMemcpyHostToDevice, P->st));
+      RuleDesc64 rd{};
+      rd.n = (int)n; rd.M = M; rd.c = par; rd.s = par + M; rd.w = par + 2 * M;
+      rd.H = H; rd.ldh = ldh;
+      launch_rule_prep64(rd, P->st);
+      launch_resid_rule(H, ldh, M, rule_key(A->rule_seed), A->rule_eta * 1.7320508075688772, dU, ldu, dV, ldv,
+                        dS, (int)n, k, part, P->st);
+    } else {
+      const double* dA = A->data;
+      int64_t lda = A->ld;
+      if (hA) {
+        CK(cudaMemcpy2DAsync(a, n * sizeof(double), A->data, A->ld * sizeof(double), n * sizeof(double), n,
+                             cudaMemcpyHostToDevice, P->st));
+        dA = a; lda = n;
+      }
+      launch_resid(dA, lda, dU, ldu, dV, ldv, dS, (int)n, k, part, P->st);
+    }
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(P->hp, part, 2 * (size_t)tiles * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    CK(cudaMemcpyAsync(P->hp, part, 2 * (size_t)blocks * sizeof(double), cudaMemcpyDeviceToHost, P->st));
     CK(cudaStreamSynchronize(P->st));
   }
-  (void)b;
   const double* hp = (const double*)P->hp;
   double r2 = 0.0, a2 = 0.0;
-  for (int t = 0; t < tiles; ++t) { r2 += hp[2 * t]; a2 += hp[2 * t + 1]; }
+  for (int t = 0; t < blocks; ++t) { r2 += hp[2 * t]; a2 += hp[2 * t + 1]; }
   *rel_err = a2 > 0.0 ? sqrt(r2 / a2) : sqrt(r2);
   return RSVD_OK;
 }

@@ -125,7 +125,7 @@ RSVD_DEV int find_chan(const int* __restrict__ off, int C, int t) {
 
 // Device error word codes (set with atomicCAS so the first error wins).
 enum : int { DERR_NONE = 0, DERR_TIMEOUT_TMA = 1, DERR_TIMEOUT_MMA = 2, DERR_TIMEOUT_EPI = 3,
-             DERR_BAD_ARG = 4 };
+             DERR_BAD_ARG = 4, DERR_TIMEOUT_BARRIER = 5 };
 
 RSVD_DEV void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);

@@ -12,6 +12,8 @@
 // converged channels idle.  The barrier's spin is bounded (an expired wait sets
 // an error word and every CTA returns).  A second kernel normalises, sorts and
 // writes X (= M_i / sigma_i), J and sigma exactly as the single-CTA kernel does.
+#include <stdlib.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -29,7 +31,12 @@ struct CoopMap {
 // [3] sweeps done, [4 + s * C + c] channel c rotated in sweep s.
 static constexpr int kCoopSweeps = 60;
 
-RSVD_DEV bool coop_barrier(int* ws, unsigned int nblocks) {
+// Grid barrier with a bounded spin.  A wait that exceeds ctl.budget clocks
+// records the expiry (ws[2] for the grid, DERR_TIMEOUT_BARRIER in the plan's
+// error word for the host) and every CTA returns at its next barrier.  The
+// verdict is taken once per CTA, by thread 0, and shared, so all threads of a
+// CTA return together.
+RSVD_DEV bool coop_barrier(int* ws, unsigned int nblocks, const CoopCtl& ctl) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -45,14 +52,24 @@ RSVD_DEV bool coop_barrier(int* ws, unsigned int nblocks) {
     } else {
       const long long t0 = clock64();
       while (*gen == g) {
-        if (clock64() - t0 > (1ll << 32)) { ok = 0; atomicExch(ws + 2, 1); break; }
+        if (clock64() - t0 > ctl.budget) {
+          ok = 0;
+          atomicExch(ws + 2, 1);
+          set_err(ctl.err, DERR_TIMEOUT_BARRIER);
+          break;
+        }
       }
     }
     __threadfence();
+    if (*(volatile int*)(ws + 2) != 0) ok = 0;
   }
   __syncthreads();
-  return ok && *(volatile int*)(ws + 2) == 0;
+  return ok != 0;
 }
+
+// Test hook (ctl.stall): CTA 0 leaves before its first barrier, like a
+// participant that never arrives; the others' bounded waits then expire.
+RSVD_DEV bool coop_stalled(const CoopCtl& ctl) { return ctl.stall && blockIdx.x == 0; }
 
 template <typename T> struct CVec;
 template <> struct CVec<float> { typedef float4 V; static constexpr int N = 4; };
@@ -65,7 +82,7 @@ RSVD_DEV double cget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 // this point of the pipeline), columns of stride lp = round_up(l, 8 vectors).
 template <typename T, bool WANT_J>
 __global__ void __launch_bounds__(256) k_jacobi_coop(const Chan* __restrict__ ch, const __grid_constant__ CoopMap map,
-                                                     int* __restrict__ ws) {
+                                                     int* __restrict__ ws, const CoopCtl ctl) {
   typedef typename CVec<T>::V V;
   constexpr int VE = CVec<T>::N;
   // channel of this CTA
@@ -88,7 +105,8 @@ __global__ void __launch_bounds__(256) k_jacobi_coop(const Chan* __restrict__ ch
   // rounds per sweep: the longest channel's
   int mmax = 2;
   for (int cc = 0; cc < map.C; ++cc) mmax = max(mmax, ch[cc].l + (ch[cc].l & 1));
-  if (!coop_barrier(ws, map.nblocks)) return;
+  if (coop_stalled(ctl)) return;
+  if (!coop_barrier(ws, map.nblocks, ctl)) return;
   const T eps = (sizeof(T) == 8) ? (T)1.1102230246251565e-16 : (T)5.9604645e-8;
   const T thr = (T)l * eps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -97,7 +115,7 @@ __global__ void __launch_bounds__(256) k_jacobi_coop(const Chan* __restrict__ ch
   const int npairs = m / 2;
   bool active = true;                      // this channel not yet converged
   int sweep = 0;
-  for (; sweep < kCoopSweeps; ++sweep) {
+  for (; sweep < ctl.max_sweeps; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < mmax - 1; ++r) {
       if (active && r < m - 1) {
@@ -174,11 +192,11 @@ __global__ void __launch_bounds__(256) k_jacobi_coop(const Chan* __restrict__ ch
           rotated = 1;
         }
       }
-      if (!coop_barrier(ws, map.nblocks)) return;
+      if (!coop_barrier(ws, map.nblocks, ctl)) return;
     }
     // sweep done: record, agree, stop when every channel is converged
     if (__syncthreads_or(rotated) && threadIdx.x == 0) atomicOr(ws + 4 + sweep * map.C + c, 1);
-    if (!coop_barrier(ws, map.nblocks)) return;
+    if (!coop_barrier(ws, map.nblocks, ctl)) return;
     __shared__ int any;
     if (threadIdx.x == 0) {
       any = 0;
@@ -193,7 +211,8 @@ __global__ void __launch_bounds__(256) k_jacobi_coop(const Chan* __restrict__ ch
 
 // Column norms, sort (descending, ties by index), X = M_i / sigma_i, J, sigma.
 template <typename T, bool WANT_J>
-__global__ void __launch_bounds__(512) k_jacobi_coop_finish(const Chan* __restrict__ ch, const int* __restrict__ ws) {
+__global__ void __launch_bounds__(512) k_jacobi_coop_finish(const Chan* __restrict__ ch, const int* __restrict__ ws,
+                                                             int max_sweeps) {
   constexpr int VE = CVec<T>::N;
   const Chan& h = ch[blockIdx.x];
   const int l = h.l;
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(512) k_jacobi_coop_finish(const Chan* __restri
   const int sweeps = ws[3];
   if (threadIdx.x == 0) {
     h.res->sweeps = sweeps;
-    if (sweeps >= kCoopSweeps && ws[4 + (kCoopSweeps - 1) * gridDim.x + blockIdx.x])
+    if (sweeps >= max_sweeps && ws[4 + (max_sweeps - 1) * gridDim.x + blockIdx.x])
       atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
     if (ws[2]) atomicOr(&h.res->flags, FLAG_JACOBI_CAP);
   }
@@ -247,7 +266,8 @@ __global__ void __launch_bounds__(512) k_jacobi_coop_finish(const Chan* __restri
 // through L2.  ws: [0..2] barrier, [4 + a * C + c] channel c failed in attempt a.
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_coop(const Chan* __restrict__ ch, const __grid_constant__ CoopMap map,
-                                                   int* __restrict__ ws, int accumulate, int conditional) {
+                                                   int* __restrict__ ws, int accumulate, int conditional,
+                                                   const CoopCtl ctl) {
   int c = 0;
   while (c + 1 < map.C && map.first[c + 1] <= (int)blockIdx.x) ++c;
   const int rank = blockIdx.x - map.first[c], ncta = map.first[c + 1] - map.first[c];
@@ -289,7 +309,8 @@ __global__ void __launch_bounds__(256) k_chol_coop(const Chan* __restrict__ ch, 
         const double g = G[e] + ((attempt == 1 && i == j) ? shift : 0.0);
         __stcg(Ms + e, (T)g);
       }
-    if (!coop_barrier(ws, map.nblocks)) return;
+    if (attempt == 0 && coop_stalled(ctl)) return;
+    if (!coop_barrier(ws, map.nblocks, ctl)) return;
     for (int j = 0; j < lmax; ++j) {
       const bool act = work && !failed && j < l;
       if (act) {
@@ -305,7 +326,7 @@ __global__ void __launch_bounds__(256) k_chol_coop(const Chan* __restrict__ ch, 
           }
         }
       }
-      if (!coop_barrier(ws, map.nblocks)) return;
+      if (!coop_barrier(ws, map.nblocks, ctl)) return;
       if (act && !failed) {
         // the pivot is replaced only now: every CTA of the channel has read it
         if (rank == 0 && tid == 0) {
@@ -319,7 +340,7 @@ __global__ void __launch_bounds__(256) k_chol_coop(const Chan* __restrict__ ch, 
             __stcg(colb + a, fma(-__ldcg(Ms + j + (int64_t)a * l), rb, __ldcg(colb + a)));
         }
       }
-      if (!coop_barrier(ws, map.nblocks)) return;
+      if (!coop_barrier(ws, map.nblocks, ctl)) return;
     }
     if (work && attempt == 0 && failed && rank == 0 && tid == 0) atomicOr(&h.res->flags, FLAG_SHIFTED);
     // no early exit: if any channel retries, every CTA takes part in the
@@ -372,6 +393,22 @@ __global__ void __launch_bounds__(256) k_chol_coop_copy(const Chan* __restrict__
     h.R[e] = h.G[e];
 }
 
+int jacobi_max_sweeps() {
+  int v = 60;
+  if (const char* e = getenv("RSVD_JACOBI_MAX_SWEEPS")) v = atoi(e);
+  return v < 1 ? 1 : v > 60 ? 60 : v;
+}
+
+CoopCtl coop_ctl(int* err) {
+  CoopCtl c{err, 1ll << 32, 0, jacobi_max_sweeps()};
+  if (const char* e = getenv("RSVD_WAIT_CLOCKS")) {
+    const long long v = atoll(e);
+    if (v >= 0) c.budget = v;
+  }
+  if (const char* e = getenv("RSVD_TEST_STALL_BARRIER")) c.stall = atoi(e) == 1;
+  return c;
+}
+
 static bool coop_map(const void* fn, const int* h_l, int C, CoopMap& map) {
   if (C < 1 || C > kCoopMaxChannels) return false;
   int dev = 0, nsm = 0, coop = 0, per = 0;
@@ -408,13 +445,14 @@ static bool coop_map(const void* fn, const int* h_l, int C, CoopMap& map) {
 }
 
 int launch_chol_coop(const Chan* d_ch, const int* h_l, int C, int accumulate, int f32_chol, int conditional,
-                     int* coop_ws, cudaStream_t st) {
+                     int* coop_ws, int* err, cudaStream_t st) {
   if (!coop_ws) return -1;
   const void* fn = f32_chol ? (const void*)k_chol_coop<float> : (const void*)k_chol_coop<double>;
   CoopMap map;
   if (!coop_map(fn, h_l, C, map)) return -1;
   if (cudaMemsetAsync(coop_ws, 0, sizeof(int) * (4 + 2 * (size_t)C), st) != cudaSuccess) return -1;
-  void* args[] = {(void*)&d_ch, (void*)&map, (void*)&coop_ws, (void*)&accumulate, (void*)&conditional};
+  CoopCtl ctl = coop_ctl(err);
+  void* args[] = {(void*)&d_ch, (void*)&map, (void*)&coop_ws, (void*)&accumulate, (void*)&conditional, (void*)&ctl};
   if (cudaLaunchCooperativeKernel(fn, dim3(map.nblocks), dim3(256), args, 0, st) != cudaSuccess) {
     cudaGetLastError();
     return -1;
@@ -427,22 +465,24 @@ int launch_chol_coop(const Chan* d_ch, const int* h_l, int C, int accumulate, in
   return 0;
 }
 
-int launch_jacobi_coop(const Chan* d_ch, const int* h_l, int C, int fp32, int* coop_ws, cudaStream_t st) {
+int launch_jacobi_coop(const Chan* d_ch, const int* h_l, int C, int fp32, int* coop_ws, int* err, cudaStream_t st) {
   if (!coop_ws) return -1;
   const void* fn = fp32 ? (const void*)k_jacobi_coop<float, false> : (const void*)k_jacobi_coop<double, true>;
   CoopMap map;
   if (!coop_map(fn, h_l, C, map)) return -1;
   const size_t wsb = sizeof(int) * (4 + (size_t)kCoopSweeps * C);
   if (cudaMemsetAsync(coop_ws, 0, wsb, st) != cudaSuccess) return -1;
-  void* args[] = {(void*)&d_ch, (void*)&map, (void*)&coop_ws};
+  CoopCtl ctl = coop_ctl(err);
+  if (ctl.max_sweeps > kCoopSweeps) ctl.max_sweeps = kCoopSweeps;   // the workspace holds kCoopSweeps flags
+  void* args[] = {(void*)&d_ch, (void*)&map, (void*)&coop_ws, (void*)&ctl};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(map.nblocks), dim3(256), args, 0, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
   note_launch();
-  if (fp32) k_jacobi_coop_finish<float, false><<<C, 512, 0, st>>>(d_ch, coop_ws);
-  else k_jacobi_coop_finish<double, true><<<C, 512, 0, st>>>(d_ch, coop_ws);
+  if (fp32) k_jacobi_coop_finish<float, false><<<C, 512, 0, st>>>(d_ch, coop_ws, ctl.max_sweeps);
+  else k_jacobi_coop_finish<double, true><<<C, 512, 0, st>>>(d_ch, coop_ws, ctl.max_sweeps);
   note_launch();
   return 0;
 }

@@ -968,29 +968,30 @@ void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st
   const size_t lp = (size_t)((max_l + 8 * ve - 1) / (8 * ve) * (8 * ve));
   const size_t bytes = (fp32 ? 1 : 2) * (size_t)max_l * lp * esz;
   const int use_smem = bytes <= 200 * 1024;
+  const int sweeps = jacobi_max_sweeps();
   if (fp32 && max_l <= 128) {
     const int nv = (max_l + 31) / 32;
     const int b2 = max_l * 32 * nv * (int)sizeof(float);
     void (*kf)(const Chan*, int) = nv == 1 ? k_jacobi_f32s<1> : nv == 2 ? k_jacobi_f32s<2>
                                  : nv == 3 ? k_jacobi_f32s<3> : k_jacobi_f32s<4>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, b2);
-    kf<<<C, 512, b2, st>>>(d_ch, 60);
+    kf<<<C, 512, b2, st>>>(d_ch, sweeps);
     note_launch();
     return;
   }
   if (fp32) {
     if (use_smem) {
       cudaFuncSetAttribute(k_jacobi<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      k_jacobi<float, false><<<C, 512, bytes, st>>>(d_ch, 1, 60);
+      k_jacobi<float, false><<<C, 512, bytes, st>>>(d_ch, 1, sweeps);
     } else {
-      k_jacobi<float, false><<<C, 512, 0, st>>>(d_ch, 0, 60);
+      k_jacobi<float, false><<<C, 512, 0, st>>>(d_ch, 0, sweeps);
     }
   } else {
     if (use_smem) {
       cudaFuncSetAttribute(k_jacobi<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      k_jacobi<double, true><<<C, 512, bytes, st>>>(d_ch, 1, 60);
+      k_jacobi<double, true><<<C, 512, bytes, st>>>(d_ch, 1, sweeps);
     } else {
-      k_jacobi<double, true><<<C, 512, 0, st>>>(d_ch, 0, 60);
+      k_jacobi<double, true><<<C, 512, 0, st>>>(d_ch, 0, sweeps);
     }
   }
   note_launch();
@@ -1178,6 +1179,18 @@ __global__ void __launch_bounds__(256) k_copy_t_to_q(const Chan* __restrict__ ch
   const int64_t total = (int64_t)h.l * h.ldt;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     h.Q32[e] = h.T32[e];
+}
+
+__global__ void __launch_bounds__(256) k_copy64_if(const CopyDesc* __restrict__ cd) {
+  const CopyDesc d = cd[blockIdx.y];
+  if (!(*d.flags & FLAG_SHIFTED)) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.count; e += (int64_t)gridDim.x * blockDim.x)
+    d.dst[e] = d.src[e];
+}
+void launch_copy64_if_shifted(const CopyDesc* d_cd, int C, cudaStream_t st) {
+  if (C < 1) return;
+  k_copy64_if<<<dim3(64, C), 256, 0, st>>>(d_cd);
+  note_launch();
 }
 
 void launch_copy_t_to_q_if_shifted(const Chan* d_ch, int C, cudaStream_t st) {

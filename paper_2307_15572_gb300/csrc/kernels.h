@@ -67,6 +67,9 @@ void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32
                      cudaStream_t st, int f32_chol = 0, int conditional = 0);
 // Q32 <- T32 (n x l) for channels whose result flags carry FLAG_SHIFTED.
 void launch_copy_t_to_q_if_shifted(const Chan* d_ch, int C, cudaStream_t st);
+// dst <- src (count doubles) for channels whose *flags carries FLAG_SHIFTED.
+struct CopyDesc { const double* src; double* dst; int64_t count; const int* flags; };
+void launch_copy64_if_shifted(const CopyDesc* d_cd, int C, cudaStream_t st);
 // One-sided Jacobi SVD of M = R^T (FP64 or FP32 arithmetic); writes sig, M <- left
 // vectors, J <- right vectors, sorted by descending sigma.
 void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st);
@@ -76,11 +79,23 @@ void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st
 // not launch (the caller then runs launch_jacobi).
 constexpr int kCoopMaxChannels = 512;
 constexpr int kCoopWsInts = 4 + 60 * kCoopMaxChannels;
-int launch_jacobi_coop(const Chan* d_ch, const int* h_l, int C, int fp32, int* coop_ws, cudaStream_t st);
+// Controls of the cooperative kernels' grid barriers and of the Jacobi sweep
+// cap.  err: the plan's device error word (DERR_TIMEOUT_BARRIER when a
+// barrier wait expires; the call then returns RSVD_ERR_TIMEOUT).  budget:
+// clocks one barrier wait may spin (default 2^32, about two seconds).
+// stall: test hook, CTA 0 never arrives, so the other CTAs' waits expire.
+// max_sweeps: Jacobi sweep cap (default 60; reaching it with pairs still
+// rotating gives RSVD_ERR_NOT_CONVERGED).  coop_ctl fills them from the
+// environment: RSVD_WAIT_CLOCKS, RSVD_TEST_STALL_BARRIER (1 = on),
+// RSVD_JACOBI_MAX_SWEEPS (1..60) -- diagnostics for tests.
+struct CoopCtl { int* err; long long budget; int stall; int max_sweeps; };
+CoopCtl coop_ctl(int* err);
+int jacobi_max_sweeps();
+int launch_jacobi_coop(const Chan* d_ch, const int* h_l, int C, int fp32, int* coop_ws, int* err, cudaStream_t st);
 // Cholesky + inverse (launch_chol_inv's contract, FP64 inverse) on a
 // cooperative grid; same return convention.
 int launch_chol_coop(const Chan* d_ch, const int* h_l, int C, int accumulate, int f32_chol, int conditional,
-                     int* coop_ws, cudaStream_t st);
+                     int* coop_ws, int* err, cudaStream_t st);
 // Rank selection (fixed or tolerance) from sig and ||A||^2 (FP64 identity),
 // or from the probe residual (mixed path).  Writes S and ChanResult.
 // Probe rule: with s Gaussian probe columns g_j the energies
@@ -154,8 +169,20 @@ void launch_features(const Chan* d_ch, int C, double tol, float* feat, cudaStrea
 void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st);
 
 // ------------------------------------------------------------ exact residual
-int resid_tiles(int n);
+// Both write resid_blocks(n) partial pairs {residual^2, ||A||^2} to part.
+// A is read column-major (A[r + c lda]).  The rule form regenerates every
+// entry in FP64: H (n x ldh, row j contiguous over m) from launch_rule_prep64
+// plus the hash noise (amp3 = noise scale * sqrt(3)).
+int resid_blocks(int64_t n);
 void launch_resid(const double* A, int64_t lda, const double* U, int64_t ldu, const double* V, int64_t ldv,
                   const double* S, int n, int k, double* part, cudaStream_t st);
+void launch_resid_rule(const double* H, int64_t ldh, int M, uint32_t key, double amp3, const double* U,
+                       int64_t ldu, const double* V, int64_t ldv, const double* S, int n, int k, double* part,
+                       cudaStream_t st);
+
+// Error text of the calling thread (rsvd_last_error_string) for entry points
+// outside the plan code: clear it on entry, set it with a failure.
+void clear_error_text();
+rsvd_status set_error_text(rsvd_status s, const char* fmt, ...);
 
 }  // namespace rsvd

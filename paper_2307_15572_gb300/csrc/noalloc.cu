@@ -4,33 +4,35 @@
 // Who needs it: callers whose device memory is fully reserved up front by
 // their own pool (a further cudaMalloc would fail or break the budget), and
 // callers that must not let cudaMalloc/cudaFree synchronise the device in
-// the middle of a pipeline.  rsvd_reconstruct_error keeps its per-tile
+// the middle of a pipeline.  rsvd_reconstruct_error keeps its per-CTA
 // partial sums in the plan's workspace, which a plan may have to grow with
 // cudaMalloc; this variant keeps them in the fixed array below instead.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (1 MiB) until the process exits, and every call on that
-// GPU shares it.  Host code cannot use the symbol as a device address (in
-// host code it is only a stand-in), so the address is looked up with
+// library holds it until the process exits, and every call on that GPU
+// shares it.  Host code cannot use the symbol as a device address (in host
+// code it is only a stand-in), so the address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, the first
-// time the entry point runs there.
+// time the entry point runs there.  The looked-up address belongs to the
+// device's context of that moment: after cudaDeviceReset the entry point
+// must not be called again in the same process.
 #include <mutex>
 
 #include "kernels.h"
 
 namespace rsvd {
 
-static constexpr int NOALLOC_MAX_N = RSVD_NOALLOC_MAX_N;
-static constexpr int NOALLOC_MAX_TILES = ((NOALLOC_MAX_N + 63) / 64) * ((NOALLOC_MAX_N + 63) / 64);
+// two doubles per residual CTA: residual^2 and ||A||^2 partials; every call
+// writes all of the pairs it then reads, so nothing needs clearing
+static constexpr int NOALLOC_MAX_PARTS = 152 * 8;
+static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_PARTS];
 
-// two doubles per 64 x 64 tile: residual^2 and ||A||^2 partials
-static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_TILES];
-
-// Fixed-order sum of the tile partials; writes sqrt(r2 / a2) to *out.
-__global__ void k_noalloc_finish(const double* __restrict__ part, int tiles, double* __restrict__ out) {
+// Fixed-order sum of the partials; writes sqrt(r2 / a2) to *out (the
+// absolute residual sqrt(r2) when A = 0, where the ratio is undefined).
+__global__ void k_noalloc_finish(const double* __restrict__ part, int parts, double* __restrict__ out) {
   __shared__ double s0[256], s1[256];
   double r2 = 0.0, a2 = 0.0;
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+  for (int t = threadIdx.x; t < parts; t += blockDim.x) {
     r2 += part[2 * t];
     a2 += part[2 * t + 1];
   }
@@ -77,16 +79,25 @@ extern "C" rsvd_status rsvd_reconstruct_error_noalloc(const double* A, int64_t l
                                                       const double* V, int64_t ldv, int32_t k,
                                                       double* rel_err, void* stream) {
   using namespace rsvd;
-  if (n < 1 || n > NOALLOC_MAX_N) return RSVD_ERR_INVALID_ARG;
-  if (!A || lda < n || !rel_err || k < 0) return RSVD_ERR_INVALID_ARG;
-  if (k > 0 && (!U || !S || !V || ldu < n || ldv < n)) return RSVD_ERR_INVALID_ARG;
+  clear_error_text();
+  if (n < 1 || n > RSVD_NOALLOC_MAX_N)
+    return set_error_text(RSVD_ERR_INVALID_ARG, "n = %lld outside [1, %d] (RSVD_NOALLOC_MAX_N)", (long long)n,
+                          RSVD_NOALLOC_MAX_N);
+  if (!A || lda < n || !rel_err || k < 0)
+    return set_error_text(RSVD_ERR_INVALID_ARG, "bad matrix, leading dimension, output pointer or k");
+  if (k > 0 && (!U || !S || !V || ldu < n || ldv < n))
+    return set_error_text(RSVD_ERR_INVALID_ARG, "bad factor pointer or leading dimension");
+  const int parts = resid_blocks(n);
+  if (parts > NOALLOC_MAX_PARTS) return set_error_text(RSVD_ERR_INVALID_ARG, "too many partial sums");
   double* part = nullptr;
-  if (scratch_ptr(&part) != cudaSuccess) return RSVD_ERR_CUDA;
+  if (cudaError_t e = scratch_ptr(&part))
+    return set_error_text(RSVD_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  (void)cudaGetLastError();   // a launch error left by an earlier, unrelated call is not this call's
   cudaStream_t st = (cudaStream_t)stream;
-  const int tiles = resid_tiles((int)n);
-  // every tile writes its own pair of partials, so nothing needs clearing
   launch_resid(A, lda, U, ldu, V, ldv, S, (int)n, k, part, st);
-  k_noalloc_finish<<<1, 256, 0, st>>>(part, tiles, rel_err);
+  k_noalloc_finish<<<1, 256, 0, st>>>(part, parts, rel_err);
   note_launch(1);
-  return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+  if (cudaError_t e = cudaGetLastError())
+    return set_error_text(RSVD_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+  return RSVD_OK;
 }

@@ -62,7 +62,8 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("tc_launches", C.c_int64), ("tc_ms", C.c_double),
                 ("tc_bytes", C.c_double), ("tc_flops", C.c_double), ("f64_launches", C.c_int64),
                 ("f64_ms", C.c_double), ("f64_flops", C.c_double), ("gen_launches", C.c_int64),
-                ("gen_ms", C.c_double), ("gen_flops", C.c_double), ("gen_mma_flops", C.c_double)]
+                ("gen_ms", C.c_double), ("gen_flops", C.c_double), ("gen_mma_flops", C.c_double),
+                ("cvt_launches", C.c_int64), ("cvt_ms", C.c_double), ("cvt_bytes", C.c_double)]
 
 
 class TuneRecord(C.Structure):

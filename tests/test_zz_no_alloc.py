@@ -5,11 +5,13 @@ memory while checking a decomposition (a fully pre-reserved memory pool, or a
 pipeline that must not be synchronised by cudaMalloc/cudaFree).  It keeps its
 partial sums in a fixed array shared by all calls, so this test checks two
 calls in a row -- the second reuses what the first left behind -- against
-rsvd_reconstruct_error on the same factors.  The file name makes pytest
+rsvd_reconstruct_error on the same factors and against the oracle's plain
+FP64 residual of the same A and factors.  The file name makes pytest
 collect it last.
 """
 import pytest
 
+from oracle import rsvd as orsvd
 from paper_2307_15572_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -35,9 +37,13 @@ def test_noalloc_residual_matches_plan_residual_twice(lib):
         assert st2 == 0
         torch.cuda.synchronize()
         got = float(out.item())
-        # same FP64 arithmetic, same tile partials; only the final summation
+        # same FP64 arithmetic, same partials; only the final summation
         # order differs (device tree vs host loop)
         assert abs(got - ref) <= 1e-12 * max(ref, 1e-300), (n, got, ref)
+        # and the oracle on the same A and factors (k FP64 products per entry)
+        ora = orsvd.reconstruct_error(A.cpu().numpy(), r["U"].cpu().numpy(), r["S"].cpu().numpy(),
+                                      r["V"].cpu().numpy())
+        assert abs(got - ora) <= 1e-12 * ora + 1e-13, (n, got, ora)
         results.append(got)
     assert results[0] != results[1]
 
