@@ -405,15 +405,16 @@ def run_gpu(args):
                 "verified": (rule_exact["rel_err"] <= rf.err_est) if rule_exact else None,
                 "passes_per_step": 2 * rq + 2,
                 "roofline": {"bound": "tensor",
-                             "kernel": "k_tc_gemm<3, 3, true> (tile-rule generation, two epilogue groups)",
+                             "kernel": "k_tc_gemm<2, 2, true> (tile-rule generation, FP16 factor words, "
+                                       "two epilogue groups)",
                              "achieved": g_ach, "peak": bps, "unit": "TFLOP/s", "frac": g_ach / bps,
                              "peak_source": bps_src + " (the generator runs inside a seconds-long step)",
                              "flops_per_unit": "2 M = 600 flops per generated entry (algorithmic)",
                              "launches": prof_r["gen_launches"], "avg_launch_ms": g_ms,
                              "share_of_step": prof_r["gen_ms"] / ms_r if ms_r else None,
                              "issued_tflops": g_mma / (g_ms / 1e3) / 1e12 if g_ms else 0.0,
-                             "note": "issued_tflops counts the BF16 word products the kernel issues (6 per "
-                                     "entry term, M padded to 320), 6.4x the algorithmic work; frac is on "
+                             "note": "issued_tflops counts the FP16 word products the kernel issues (3 per "
+                                     "entry term, M padded to 320), 3.2x the algorithmic work; frac is on "
                                      "algorithmic flops"},
                 "product_roofline": {"bound": "hbm", "kernel": "k_tc_gemm<2, 2> (panel words x X words)",
                                      "achieved": t_bytes / (t_ms / 1e3) / 1e9 if t_ms else 0.0,

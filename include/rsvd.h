@@ -122,7 +122,8 @@ typedef enum { RSVD_MEM_DEVICE = 0, RSVD_MEM_HOST = 1 } rsvd_mem;
  * (arithmetic modulo 2^32).  rule_c, rule_s, rule_w are HOST arrays of
  * rule_m values; `data`, `ld` and `mem` are ignored.  The matrix is never
  * stored: every pass generates the entries it reads, row panel by row panel:
- * with precision BF16X on the tensor core (BF16x3 factor words, FP32
+ * with precision BF16X on the tensor core (the factor sqrt(w_m) g_m(x_j) as
+ * two FP16 words scaled by a power of two, three word products, FP32
  * accumulation; entries accurate to ~1e-6 relative), with precision FP64 on
  * the CUDA cores in FP64 (2 rule_m FP64 flops per entry and pass).  Any rank
  * policy (the adaptive loop generates the matrix 2 + 2q times per block of
@@ -225,7 +226,7 @@ typedef struct {
   int64_t gen_launches;    /* tile-rule generation launches (one per row panel)  */
   double gen_ms;
   double gen_flops;        /* algorithmic: 2 M per generated entry               */
-  double gen_mma_flops;    /* issued: 6 word products x 2 x (M padded to 64)     */
+  double gen_mma_flops;    /* issued: 3 word products x 2 x (M padded to 64)     */
   int64_t cvt_launches;    /* conversions of stored FP64 V into BF16 words       */
   double cvt_ms;
   double cvt_bytes;        /* 8 B read + 2 B per word written per entry          */

@@ -281,7 +281,8 @@ struct Job {
   bool probe_job = false;
   int panel = 0;                        // rows of A generated per panel
   struct RuleDev {
-    __nv_bfloat16* H[3];
+    __half* H[2];                       // factor words (FP16, scaled by hscale)
+    double hscale;
     double* H64;                        // FP64 path: the factor panel in FP64
     int64_t ldh;
     int M;
@@ -845,7 +846,7 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
                        std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout) {
   // one grouped tcgen05 launch: Y[:, 0:ncols) = sum words V_a X_b.
   // Default shape: all columns in one tile up to the kernel's register
-  // accumulator width (160), else balanced column tiles; k split only when
+  // accumulator width (TC_BN_NARROW), else balanced column tiles; k split only when
   // the batch has fewer than two items per SM; as many pipeline stages as
   // shared memory holds; items longest channel first.  Autotuned: one or two
   // more column tiles, the split target (4 items per SM with shorter splits,
@@ -859,7 +860,7 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
   struct Cfg { int bn, target, min_chunk, stages, lpt; };
   std::vector<Cfg> cands;
   {
-    const int nt0 = cdiv(maxnc, 160);
+    const int nt0 = cdiv(maxnc, TC_BN_NARROW);
     std::vector<int> bns;
     for (int nt : {nt0, nt0 + 1, 2 * nt0}) {
       const int bn = (int)rup(cdiv(maxnc, nt), 16);
@@ -916,8 +917,8 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
       const int nc = nc_of[c];
       TcChan& t = tcs[pos];
       memset(&t, 0, sizeof(t));
-      const __nv_bfloat16* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
-      const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
+      const void* A[3] = {J.ch[c].Ab[0], J.ch[c].Ab[1], J.ch[c].Ab[2]};
+      const void* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
       if (!J.measure) {
         const int e = tc_encode(&t, A, sa, d.ldb, X, sx, d.ldb, d.n, d.n, nc, bn);
         if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
@@ -1018,7 +1019,8 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
     const int Pr = std::min<int>(J.panel, (int)rup(d.n, 128));
     const int np = cdiv(d.n, Pr);
     const int nc = ncols_of(c);
-    const int ntile = cdiv(std::max(nc, 16), 160);
+    const bool wide = (nsl == 2 && sx == 2) || (nsl == 3 && sx == 3);   // the wide instantiations
+    const int ntile = cdiv(std::max(nc, 16), wide ? TC_BN_MAX : TC_BN_NARROW);
     const int bn = (int)rup(cdiv(std::max(nc, 16), ntile), 16);
     for (int p = 0; p < np; ++p) {
       const int r0 = p * Pr, rows = std::min(Pr, d.n - r0);
@@ -1027,33 +1029,51 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
       memset(&g, 0, sizeof(g));
       memset(&t, 0, sizeof(t));
       if (!J.measure) {
-        const __nv_bfloat16* HA[3] = {r.H[0], r.H[1], r.H[2]};
-        const __nv_bfloat16* HX[3] = {r.H[0] + (int64_t)r0 * r.ldh, r.H[1] + (int64_t)r0 * r.ldh,
-                                      r.H[2] + (int64_t)r0 * r.ldh};
-        int e = tc_encode(&g, HA, 3, r.ldh, HX, 3, r.ldh, d.n, r.M, rows, gbn);
+        const void* HA[2] = {r.H[0], r.H[1]};
+        const void* HX[2] = {r.H[0] + (int64_t)r0 * r.ldh, r.H[1] + (int64_t)r0 * r.ldh};
+        int e = tc_encode(&g, HA, 2, r.ldh, HX, 2, r.ldh, d.n, r.M, rows, gbn, 1);
         if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
-        const __nv_bfloat16* PA[3] = {J.pw[0], J.pw[1], J.pw[2]};
-        const __nv_bfloat16* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
+        const void* PA[3] = {J.pw[0], J.pw[1], J.pw[2]};
+        const void* X[3] = {xword(c, 0), xword(c, 1), xword(c, 2)};
         e = tc_encode(&t, PA, nsl, d.ldb, X, sx, d.ldb, rows, d.n, nc, bn);
         if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
       }
       g.n = r.M; g.m = d.n; g.ncols = rows;
       g.mt = cdiv(d.n, 128); g.nt = cdiv(rows, gbn); g.ks = 1; g.kt_per_split = cdiv(r.M, 64);
       g.mode = TC_RULE;
-      g.chunk_kt = 1;              // each 64-wide step from zero: round-toward-zero bias ~2e-7
+      // each 64-wide k step accumulated from zero, the chunk sums added to
+      // nearest: longer chunks let the tensor core's truncating accumulation
+      // bias the entries measurably (two steps per chunk raised the exact
+      // residual of the n = 200,000 rule from 1.6e-6 to 2.0e-6)
+      g.chunk_kt = 1;
       for (int w = 0; w < nsl; ++w) g.W[w] = J.pw[w];
       g.ldw = d.ldb; g.nw = nsl; g.r0 = r0;
       g.eta_key = r.key; g.eta_amp3 = r.amp3;
+      g.hinv = (float)(1.0 / r.hscale);
       g.part = first ? J.part : nullptr;
       t.Y = yout(c) + r0; t.ldy = d.ldt;
       t.n = d.n; t.m = rows; t.ncols = nc;
-      t.mt = cdiv(rows, 128); t.nt = cdiv(nc, bn); t.ks = 1; t.kt_per_split = cdiv(d.n, 64);
+      t.mt = cdiv(rows, 128); t.nt = cdiv(nc, bn);
+      {
+        // the panel has few output tiles (rows / 128 x 2-3) and a long k
+        // extent (n): split k so the persistent CTAs get ~4 items each
+        const int kt = cdiv(d.n, 64);
+        const int ks = pick_splits((int64_t)t.mt * t.nt, kt, 8, 4 * NSM);
+        t.kt_per_split = cdiv(kt, ks);
+        t.ks = cdiv(kt, t.kt_per_split);
+        t.atomic = t.ks > 1;
+      }
       t.mode = TC_STORE;
-      const int gitems = g.mt * g.nt, titems = t.mt * t.nt;
+      const int gitems = g.mt * g.nt, titems = t.mt * t.nt * t.ks;
       const TcChan* dg = J.ar.put(&g, 1, 128);
       const TcChan* dt = J.ar.put(&t, 1, 128);
+      const ZeroDesc zd{t.Y, d.ldt, rows, nc, 4};
+      const ZeroDesc* dzd = t.atomic ? J.ar.put(&zd, 1) : nullptr;
+      const int zoff[2] = {0, cdiv(rows, 64)};
+      const int* dzoff = t.atomic ? J.ar.put(zoff, 2) : nullptr;
+      const int ztiles = zoff[1];
       const double gflops = 2.0 * d.n * (double)rows * r.M;                // algorithmic
-      const double gmma = 2.0 * d.n * (double)rows * r.ldh * 6;            // issued word products
+      const double gmma = 2.0 * d.n * (double)rows * r.ldh * 3;            // issued word products
       double tpairs = 0;
       for (int a = 0; a < nsl; ++a)
         for (int x = 0; x < sx; ++x) tpairs += (a + x < std::max(nsl, sx));
@@ -1064,13 +1084,14 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
       J.steps.push_back([=]() {
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (P->profiling) timed_begin(P, &ea, &eb);
-        int e = tc_launch(dg, 1, gitems, 3, 3, gbn, derr, st, true);
+        int e = tc_launch(dg, 1, gitems, 2, 2, gbn, derr, st, true);
         if (e) return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
         if (P->profiling) {
           cudaEventRecord(eb, st);
           P->pending.push_back({ea, eb, 2, gmma, gflops});
         }
         if (first) launch_rule_part_sum(part, gitems * 4, psum, st);
+        if (dzd) launch_zero(dzd, dzoff, 1, ztiles, st);     // the k splits accumulate into Y
         if (P->profiling) timed_begin(P, &ea, &eb);
         e = tc_launch(dt, 1, titems, nsl, sx, bn, derr, st);
         if (e) return seterr(RSVD_ERR_CUDA, "tcgen05 GEMM launch failed: %s", cudaGetErrorString((cudaError_t)e));
@@ -1312,8 +1333,9 @@ std::vector<RuleDesc> rule_descs(Job& J) {
     r.c = J.ar.put(A.rule_c, M);
     r.s = J.ar.put(A.rule_s, M);
     r.w = J.ar.put(A.rule_w, M);
-    for (int w = 0; w < 3; ++w) r.H[w] = J.rd[c].H[w];
+    for (int w = 0; w < 2; ++w) r.H[w] = J.rd[c].H[w];
     r.ldh = J.rd[c].ldh;
+    r.hscale = J.rd[c].hscale;
     rds[c] = r;
   }
   return rds;
@@ -1555,7 +1577,8 @@ void lay_rule(Bump& b, const std::vector<ChanDims>& d, const rsvd_matrix* A, int
     Job::RuleDev& r = rd[c];
     r.M = A[c].rule_m;
     r.ldh = rule_ldh(r.M);
-    for (int w = 0; w < 3; ++w) r.H[w] = b.take<__nv_bfloat16>((size_t)d[c].n * r.ldh);
+    for (int w = 0; w < 2; ++w) r.H[w] = b.take<__half>((size_t)d[c].n * r.ldh);
+    r.hscale = rule_hscale(A[c].rule_w, r.M);
     r.key = rule_key(A[c].rule_seed);
     r.amp3 = (float)(A[c].rule_eta * 1.7320508075688772);
     maxldb = std::max<int64_t>(maxldb, d[c].ldb);
@@ -3160,13 +3183,13 @@ rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int3
   const int n = (int)a.n, M = a.rule_m;
   const int64_t ldh = rule_ldh(M);
   // workspace: H words, parameters, one descriptor
-  const size_t hbytes = ((size_t)n * ldh * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
+  const size_t hbytes = ((size_t)n * ldh * sizeof(__half) + 255) & ~(size_t)255;
   const size_t pbytes = ((3 * (size_t)M * sizeof(double)) + 255) & ~(size_t)255;
-  if (rsvd_status s = grow_ws(P, 3 * hbytes + pbytes + sizeof(TcChan) + 256)) return s;
-  __nv_bfloat16* H[3];
-  for (int w = 0; w < 3; ++w) H[w] = (__nv_bfloat16*)(P->ws + w * hbytes);
-  double* dpar = (double*)(P->ws + 3 * hbytes);
-  TcChan* dtc = (TcChan*)(P->ws + 3 * hbytes + pbytes);
+  if (rsvd_status s = grow_ws(P, 2 * hbytes + pbytes + sizeof(TcChan) + 256)) return s;
+  __half* H[2];
+  for (int w = 0; w < 2; ++w) H[w] = (__half*)(P->ws + w * hbytes);
+  double* dpar = (double*)(P->ws + 2 * hbytes);
+  TcChan* dtc = (TcChan*)(P->ws + 2 * hbytes + pbytes);
   if (rsvd_status s = grow_pinned(P, pbytes + sizeof(TcChan) + 64)) return s;
   double* hpar = (double*)P->hp;
   memcpy(hpar, a.rule_c, sizeof(double) * M);
@@ -3175,9 +3198,9 @@ rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int3
   TcChan* htc = (TcChan*)(P->hp + pbytes);
   memset(htc, 0, sizeof(TcChan));
   const int gbn = std::min(128, (int)rup(rows, 16));
-  const __nv_bfloat16* HA[3] = {H[0], H[1], H[2]};
-  const __nv_bfloat16* HX[3] = {H[0] + r0 * ldh, H[1] + r0 * ldh, H[2] + r0 * ldh};
-  if (int e = tc_encode(htc, HA, 3, ldh, HX, 3, ldh, n, M, rows, gbn))
+  const void* HA[2] = {H[0], H[1]};
+  const void* HX[2] = {H[0] + r0 * ldh, H[1] + r0 * ldh};
+  if (int e = tc_encode(htc, HA, 2, ldh, HX, 2, ldh, n, M, rows, gbn, 1))
     return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
   htc->Y = out; htc->ldy = ldo;
   htc->n = M; htc->m = n; htc->ncols = rows;
@@ -3187,15 +3210,18 @@ rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int3
   htc->nw = 0; htc->r0 = (int)r0;
   htc->eta_key = rule_key(a.rule_seed);
   htc->eta_amp3 = (float)(a.rule_eta * 1.7320508075688772);
+  const double hscale = rule_hscale(a.rule_w, M);
+  htc->hinv = (float)(1.0 / hscale);
   CK(cudaMemcpyAsync(dpar, hpar, pbytes, cudaMemcpyHostToDevice, P->st));
   CK(cudaMemcpyAsync(dtc, htc, sizeof(TcChan), cudaMemcpyHostToDevice, P->st));
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
   RuleDesc rdsc{};
   rdsc.n = n; rdsc.M = M; rdsc.c = dpar; rdsc.s = dpar + M; rdsc.w = dpar + 2 * M;
-  for (int w = 0; w < 3; ++w) rdsc.H[w] = H[w];
+  for (int w = 0; w < 2; ++w) rdsc.H[w] = H[w];
   rdsc.ldh = ldh;
+  rdsc.hscale = hscale;
   launch_rule_prep(rdsc, P->st);
-  if (int e = tc_launch(dtc, 1, htc->mt * htc->nt, 3, 3, gbn, P->d_err, P->st, true))
+  if (int e = tc_launch(dtc, 1, htc->mt * htc->nt, 2, 2, gbn, P->d_err, P->st, true))
     return seterr(RSVD_ERR_CUDA, "tile-rule generation launch failed: %s", cudaGetErrorString((cudaError_t)e));
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));

@@ -7,13 +7,18 @@
 // generates every entry it reads (n^2 M multiply-adds on the tensor core),
 // nothing of A is kept between panels or passes.
 #include <algorithm>
+#include <cmath>
 
 #include "kernels.h"
 
 namespace rsvd {
 
-// H as BF16 words of its FP32 value (rows j contiguous over m, leading dim
-// ldh >= M; columns M..ldh-1 are zero).  The exponentials are FP64.
+// H as two FP16 words of its FP32 value times hscale (rows j contiguous over
+// m, leading dim ldh >= M; columns M..ldh-1 are zero).  The exponentials are
+// FP64.  hscale puts the largest factor entry at 2^14 (FP16 overflows past
+// 65504), so entries down to ~2^-24 / hscale keep their relative precision
+// and smaller ones carry at most 2^-25 / hscale absolute error: ~2^-39 of
+// the largest entry, negligible in every product.  hi + lo keeps 22 bits.
 __global__ void __launch_bounds__(256) k_rule_prep(RuleDesc d) {
   const int64_t total = (int64_t)d.n * d.ldh;
   const double step = d.n > 1 ? 8.0 / (double)(d.n - 1) : 0.0;
@@ -23,16 +28,21 @@ __global__ void __launch_bounds__(256) k_rule_prep(RuleDesc d) {
     if (m < d.M) {
       const double t = step * j - d.c[m];
       const double g = exp(-(t * t) / (2.0 * d.s[m] * d.s[m]));
-      h = f64_to_f32_rn(sqrt(d.w[m]) * g);
+      h = f64_to_f32_rn(sqrt(d.w[m]) * g * d.hscale);
     }
-    __nv_bfloat16 q = __float2bfloat16_rn(h);
-    d.H[0][e] = q;
-    float r = h - __bfloat162float(q);
-    q = __float2bfloat16_rn(r);
-    d.H[1][e] = q;
-    r -= __bfloat162float(q);
-    d.H[2][e] = __float2bfloat16_rn(r);
+    const __half hi = __float2half_rn(h);
+    d.H[0][e] = hi;
+    d.H[1][e] = __float2half_rn(h - __half2float(hi));     // the remainder is exact in FP32
   }
+}
+
+double rule_hscale(const double* w, int M) {
+  double mx = 0.0;
+  for (int m = 0; m < M; ++m) mx = std::max(mx, w[m]);
+  if (!(mx > 0.0)) return 1.0;
+  int e = 14 - (int)std::ceil(std::log2(std::sqrt(mx)));
+  e = std::max(-60, std::min(60, e));
+  return std::ldexp(1.0, e);
 }
 
 void launch_rule_prep(const RuleDesc& d, cudaStream_t st) {

@@ -1,6 +1,6 @@
 // Tensor-core passes over V for the mixed path: Y = V X on sm_103a.  The
 // same kernel also generates the entries of a tile rule (TC_RULE): with H the
-// n x M matrix of sqrt(w_m) g_m(x_j) in BF16 words, a panel of rule rows is
+// n x M matrix of sqrt(w_m) g_m(x_j) in FP16 words, a panel of rule rows is
 // H H_panel^T, to which the epilogue adds the hash noise before splitting the
 // entries into the words the next pass reads.
 //
@@ -124,6 +124,11 @@ RSVD_DEV uint32_t idesc_bf16(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+// The same with A = B = F16 (format code 0 in both operand fields).
+RSVD_DEV uint32_t idesc_f16(int bn) {
+  return (1u << 4) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
 RSVD_DEV void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -151,6 +156,30 @@ RSVD_DEV void tmem_ld16_nw(uint32_t taddr, uint32_t* r) {
 
 RSVD_DEV void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 columns of the warp's 32 TMEM lanes (valid after tmem_wait_ld), and the
+// matching store.
+RSVD_DEV void tmem_ld32_nw(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+RSVD_DEV void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
 RSVD_DEV void tmem_st16(uint32_t taddr, const uint32_t* r) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -174,7 +203,12 @@ RSVD_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" :::
 // A channel may ask for shorter chunks (chunk_kt): the tile-rule generator,
 // whose k extent is only M, takes one 64-wide step per chunk.
 static constexpr int CHUNK_KT = 8;
-static constexpr int BN_MAX = 160;            // register accumulator width
+// Register accumulator width of the epilogue: 160 columns for most launches;
+// the wide instantiation (176) serves the passes whose column count splits
+// better into two tiles of up to 176 than into three of up to 160 (the tile
+// rule's 330 columns), at the cost of 16 more registers per thread.
+static constexpr int BN_NARROW = TC_BN_NARROW;
+static constexpr int BN_MAX = TC_BN_MAX;
 static constexpr int NTHREADS = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
 static constexpr int NTHREADS_RULE = 320;     // generation: warps 0-3 and 6-9 epilogue (two groups)
 
@@ -210,30 +244,40 @@ RSVD_DEV void tc_item(const TcChan* __restrict__ chs, int C, int item, int bn, T
 // row j of the generated block = matrix column j; column col = matrix row
 // r0 + col): noise, words, energy, remainder.  The inner hash of the noise is
 // mix(min(i, j) * C1 + key): the row's is computed once per tile (hrow), the
-// 16 columns' by 16 lanes and broadcast.  All lanes take part (shuffles);
-// `live` masks the stores of rows past the end.
+// 16 columns' by 16 lanes and broadcast.  All lanes take part (shuffles).
+// The 16 entries are made first, with no branch between them, so their hash
+// chains interleave; then the words of the live ones are stored (`live`
+// masks rows past the end, nj the columns past the end).  Constants:
+// amp_s = sqrt(3) eta 2^-24 (the noise numerator is an odd integer below
+// 2^24), hinv2 = hscale^-2 (a power of two: the scaling is exact).
 template <int NW, bool WY>
 RSVD_DEV void rule_group(const uint32_t (&r)[16], int row, bool live, int col0, int ncols, int r0, uint32_t hrow,
-                         uint32_t key, float amp3, __nv_bfloat16* W0, __nv_bfloat16* W1, __nv_bfloat16* W2,
-                         int64_t ldw, float* Y, int64_t ldy, float& s2, float& r2, int lane) {
+                         uint32_t key, float amp_s, float hinv2, __nv_bfloat16* W0, __nv_bfloat16* W1,
+                         __nv_bfloat16* W2, int64_t ldw, float* Y, int64_t ldy, float& s2, float& r2, int lane) {
   const int i0 = r0 + col0;
   const uint32_t hcol = lowbias32((uint32_t)(i0 + (lane & 15)) * 0x9E3779B1u + key);
+  const uint32_t rowc = (uint32_t)row * 0x85EBCA77u;
+  float v[16];
 #pragma unroll
   for (int jj = 0; jj < 16; ++jj) {
     const uint32_t hc = __shfl_sync(0xffffffffu, hcol, jj);
-    if (col0 + jj >= ncols) break;                     // uniform across the warp
     const int i = i0 + jj;
-    const bool rowlo = row <= i;
-    const uint32_t h = lowbias32((rowlo ? hrow : hc) ^ ((uint32_t)(rowlo ? i : row) * 0x85EBCA77u));
-    const float eta = amp3 * ((float)(2 * (int)(h >> 8) + 1 - (1 << 24)) * 5.9604644775390625e-8f);
-    const float v = __uint_as_float(r[jj]) + eta;
-    if (!live) continue;
-    s2 = fmaf(v, v, s2);
+    const uint32_t h = lowbias32(row <= i ? (hrow ^ ((uint32_t)i * 0x85EBCA77u)) : (hc ^ rowc));
+    const float eta = (float)(2 * (int)(h >> 8) + 1 - (1 << 24)) * amp_s;
+    v[jj] = fmaf(__uint_as_float(r[jj]), hinv2, eta);
+  }
+  if (!live) return;
+  const int nj = ncols - col0;                         // uniform across the warp
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) {
+    if (jj >= nj) break;
+    const float x = v[jj];
+    s2 = fmaf(x, x, s2);
     const int64_t o = row + (int64_t)(col0 + jj) * ldw;
     if (NW > 0) {
-      __nv_bfloat16 q = __float2bfloat16_rn(v);
+      __nv_bfloat16 q = __float2bfloat16_rn(x);
       W0[o] = q;
-      float rem = v - __bfloat162float(q);             // exact
+      float rem = x - __bfloat162float(q);             // exact
       if (NW > 1) {
         q = __float2bfloat16_rn(rem);
         W1[o] = q;
@@ -246,7 +290,7 @@ RSVD_DEV void rule_group(const uint32_t (&r)[16], int row, bool live, int col0, 
       }
       r2 = fmaf(rem, rem, r2);
     }
-    if (WY) Y[row + (int64_t)(col0 + jj) * ldy] = v;
+    if (WY) Y[row + (int64_t)(col0 + jj) * ldy] = x;
   }
 }
 
@@ -254,7 +298,7 @@ RSVD_DEV void rule_group(const uint32_t (&r)[16], int row, bool live, int col0, 
 // The k-step counter (stage ring) and the chunk counter (TMEM ping-pong)
 // run on across items, so the producer loads item i+1 and the MMA warp
 // computes it while the epilogue warps still store item i.
-template <int SA, int SX, bool RULE>
+template <int SA, int SX, bool RULE, int BNM = BN_NARROW>
 __global__ void __launch_bounds__(RULE ? NTHREADS_RULE : NTHREADS, 1)
 k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
@@ -322,7 +366,8 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
   } else if (warp == 5) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t idesc = idesc_bf16(bn);
+      // the tile-rule generator multiplies FP16 factor words, the passes BF16 words
+      const uint32_t idesc = RULE ? idesc_f16(bn) : idesc_bf16(bn);
       bool ok = true;
       int g = 0, gc = 0;                           // k steps, chunks consumed by this CTA
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
@@ -413,7 +458,8 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
       const int ncols = ch->ncols, nw = ch->nw, r0 = ch->r0;
       const int64_t ldy = ch->ldy, ldw = ch->ldw;
       const uint32_t key = ch->eta_key;
-      const float amp3 = ch->eta_amp3;
+      const float amp_s = ch->eta_amp3 * 5.9604644775390625e-8f;     // x 2^-24: exact
+      const float hinv2 = ch->hinv * ch->hinv;                         // >= 2^-120: normal
       float* Y = ch->Y;
       __nv_bfloat16* W0 = ch->W[0];
       __nv_bfloat16* W1 = ch->W[1];
@@ -426,8 +472,12 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
         int ok = 1;
         if (lane == 0) {
           const long long t0 = clock64();
+          // the other group holds the chunks before this one: back off
+          // between polls so the spin does not take issue slots from its
+          // warps on the same schedulers
           while (*(volatile int*)consumed < 4 * gc) {
             if (clock64() - t0 > (1ll << 32)) { ok = 0; break; }
+            __nanosleep(128);
           }
           if (ok) ok = mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u) ? 1 : 0;
         }
@@ -439,17 +489,31 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
         }
         tc_fence_after();
         const uint32_t ta = tmem + lanes + (uint32_t)(b * bn);
+        // 32 columns per round trip (bn is a multiple of 32 here: gbn <= 128
+        // is rounded to 16, and a 16-column tail takes the narrow form)
 #pragma unroll 1
-        for (int g = 0; g < bn; g += 16) {
-          uint32_t r[16], f[16];
-          tmem_ld16_nw(ta + (uint32_t)g, r);
-          if (c > 0) tmem_ld16_nw(fin + (uint32_t)g, f);
-          tmem_wait_ld();
-          if (c > 0) {
+        for (int g = 0; g < bn; g += 32) {
+          if (g + 32 <= bn) {
+            uint32_t r[32], f[32];
+            tmem_ld32_nw(ta + (uint32_t)g, r);
+            if (c > 0) tmem_ld32_nw(fin + (uint32_t)g, f);
+            tmem_wait_ld();
+            if (c > 0) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(f[j]));
+              for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(f[j]));
+            }
+            tmem_st32(fin + (uint32_t)g, r);
+          } else {
+            uint32_t r[16], f[16];
+            tmem_ld16_nw(ta + (uint32_t)g, r);
+            if (c > 0) tmem_ld16_nw(fin + (uint32_t)g, f);
+            tmem_wait_ld();
+            if (c > 0) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(f[j]));
+            }
+            tmem_st16(fin + (uint32_t)g, r);
           }
-          tmem_st16(fin + (uint32_t)g, r);
         }
         tmem_wait_st();
         tc_fence_before();
@@ -469,13 +533,13 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
           tmem_ld16_nw(fin + (uint32_t)g, r);
           tmem_wait_ld();
           if (Y) {
-            rule_group<0, true>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            rule_group<0, true>(r, row, live, col0, ncols, r0, hrow, key, amp_s, hinv2, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
           } else if (nw == 2) {
-            rule_group<2, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            rule_group<2, false>(r, row, live, col0, ncols, r0, hrow, key, amp_s, hinv2, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
           } else if (nw == 3) {
-            rule_group<3, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            rule_group<3, false>(r, row, live, col0, ncols, r0, hrow, key, amp_s, hinv2, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
           } else {
-            rule_group<1, false>(r, row, live, col0, ncols, r0, hrow, key, amp3, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
+            rule_group<1, false>(r, row, live, col0, ncols, r0, hrow, key, amp_s, hinv2, W0, W1, W2, ldw, Y, ldy, s2, r2, lane);
           }
         }
       }
@@ -506,7 +570,7 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
       const TcChan* ch = I.ch;
       const int chunk = ch->chunk_kt > 0 ? ch->chunk_kt : CHUNK_KT;
       const int nchunks = (I.nk + chunk - 1) / chunk;
-      float acc[BN_MAX];
+      float acc[BNM];
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int b = gc & 1;
         int ok = 0;
@@ -521,16 +585,16 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * bn);
         // 32 columns per wait (two 16-column loads in flight)
 #pragma unroll
-        for (int g32 = 0; g32 < (BN_MAX + 31) / 32; ++g32) {
+        for (int g32 = 0; g32 < (BNM + 31) / 32; ++g32) {
           if (g32 * 32 < bn) {
             uint32_t r[32];
             tmem_ld16_nw(ta + (uint32_t)(g32 * 32), r);
-            const bool two = g32 * 32 + 16 < bn && g32 * 32 + 16 < BN_MAX;
+            const bool two = g32 * 32 + 16 < bn && g32 * 32 + 16 < BNM;
             if (two) tmem_ld16_nw(ta + (uint32_t)(g32 * 32 + 16), r + 16);
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              if (g32 * 32 + j < BN_MAX && (j < 16 || two)) {
+              if (g32 * 32 + j < BNM && (j < 16 || two)) {
                 const float v = __uint_as_float(r[j]);
                 acc[g32 * 32 + j] = c == 0 ? v : acc[g32 * 32 + j] + v;
               }
@@ -542,7 +606,7 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
       }
       if (nchunks == 0) {
 #pragma unroll
-        for (int j = 0; j < BN_MAX; ++j) acc[j] = 0.0f;
+        for (int j = 0; j < BNM; ++j) acc[j] = 0.0f;
       }
       if (healthy) healthy = (*(volatile int*)err == 0);
       healthy = __shfl_sync(0xffffffffu, healthy, 0);
@@ -555,7 +619,7 @@ k_tc_gemm(const TcChan* __restrict__ chs, int C, int items, int bn, int stages, 
         const int ncols = ch->ncols;
         const int atomic = ch->atomic;
 #pragma unroll
-        for (int j = 0; j < BN_MAX; ++j) {
+        for (int j = 0; j < BNM; ++j) {
           const int col = n0 + j;
           if (j < bn && col < ncols) {
             float* dst = Y + row + (int64_t)col * ldy;
@@ -588,40 +652,41 @@ static int get_encode() {
 }
 
 static int encode2d(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer, int64_t ld_elems,
-                    int box_outer) {
+                    int box_outer, int f16) {
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
   cuuint64_t strides[1] = {(cuuint64_t)(ld_elems * 2)};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_outer};
   cuuint32_t estr[2] = {1, 1};
-  const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+  const CUresult r = g_encode(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                              const_cast<void*>(ptr), dims, strides,
                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
-int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda, const __nv_bfloat16* const* X,
-              int sx, int64_t ldx, int m, int n, int ncols, int bn) {
+int tc_encode(TcChan* h, const void* const* A, int sa, int64_t lda, const void* const* X, int sx, int64_t ldx,
+              int m, int n, int ncols, int bn, int f16) {
   if (get_encode()) return -1;
   for (int a = 0; a < sa; ++a)
-    if (int e = encode2d(&h->tmA[a], A[a], n, m, lda, BM)) return e;
+    if (int e = encode2d(&h->tmA[a], A[a], n, m, lda, BM, f16)) return e;
   for (int x = 0; x < sx; ++x)
-    if (int e = encode2d(&h->tmX[x], X[x], n, ncols, ldx, bn)) return e;
+    if (int e = encode2d(&h->tmX[x], X[x], n, ncols, ldx, bn, f16)) return e;
   return 0;
 }
 
-template <int SA, int SX, bool RULE>
+template <int SA, int SX, bool RULE, int BNM = BN_NARROW>
 static int launch_t(const TcChan* d_ch, int C, int items, int bn, int* d_err, cudaStream_t st, int max_stages) {
   int stages = tc_stages(SA, SX, bn);
   if (max_stages >= 2 && max_stages < stages) stages = max_stages;
   const int smem = stages * tc_stage_bytes(SA, SX, bn) + 1024 + 256;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SA, SX, RULE, BNM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       nsm < 1)
     nsm = 148;
   const int grid = items < nsm ? items : nsm;                  // persistent: one CTA per SM
-  k_tc_gemm<SA, SX, RULE><<<grid, RULE ? NTHREADS_RULE : NTHREADS, smem, st>>>(d_ch, C, items, bn, stages, d_err);
+  k_tc_gemm<SA, SX, RULE, BNM><<<grid, RULE ? NTHREADS_RULE : NTHREADS, smem, st>>>(d_ch, C, items, bn, stages, d_err);
   note_launch();
   return (int)cudaGetLastError();
 }
@@ -631,7 +696,12 @@ int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int*
   if (items <= 0) return 0;
   if (bn < 16 || bn > BN_MAX || (bn % 16) != 0) return (int)cudaErrorInvalidValue;
   if (rule) {
-    if (sa == 3 && sx == 3) return launch_t<3, 3, true>(d_ch, C, items, bn, d_err, st, max_stages);
+    if (sa == 2 && sx == 2 && bn <= 128) return launch_t<2, 2, true>(d_ch, C, items, bn, d_err, st, max_stages);
+    return (int)cudaErrorInvalidValue;
+  }
+  if (bn > BN_NARROW) {
+    if (sa == 2 && sx == 2) return launch_t<2, 2, false, BN_MAX>(d_ch, C, items, bn, d_err, st, max_stages);
+    if (sa == 3 && sx == 3) return launch_t<3, 3, false, BN_MAX>(d_ch, C, items, bn, d_err, st, max_stages);
     return (int)cudaErrorInvalidValue;
   }
   if (sa == 1 && sx == 1) return launch_t<1, 1, false>(d_ch, C, items, bn, d_err, st, max_stages);

@@ -124,13 +124,17 @@ void launch_sumsq(const SumsqDesc* d_sd, int C, cudaStream_t st);
 void launch_colsumsq(const SumsqDesc* d_sd, int C, int max_cols, cudaStream_t st);
 
 // --------------------------------------------------------------- tile rule
-// H (n x M, ldh) = sqrt(w_m) g_m(x_j) as three BF16 words of its FP32 value.
+// H (n x M, ldh) = sqrt(w_m) g_m(x_j), scaled by hscale (a power of two that
+// puts max H at 2^14), as two FP16 words of its FP32 value.
 struct RuleDesc {
   int n, M;
   const double *c, *s, *w;   // device, M each
-  __nv_bfloat16* H[3];
+  __half* H[2];
   int64_t ldh;
+  double hscale;
 };
+// The power of two hscale for the rule weights (max sqrt(w_m) to 2^14).
+double rule_hscale(const double* w, int M);
 // Re-orthonormalisation steps of the FP32 Jacobi vectors (l <= 128): 0 scale
 // the Gram of M by D on both sides, 1 Ri32 = D (R^{-1} - I), 2 J += M D.
 void launch_reorth(int stage, const Chan* d_ch, int C, int max_l, cudaStream_t st);

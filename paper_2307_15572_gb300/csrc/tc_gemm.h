@@ -35,13 +35,20 @@ struct alignas(64) TcChan {
   int r0;
   uint32_t eta_key;
   float eta_amp3;       // sqrt(3) * eta amplitude
+  float hinv;           // 1 / hscale of the FP16 factor words: entry = acc * hinv * hinv
   double* part;
 };
 
-// Encode the maps of one channel (host).  Returns 0 on success.
-int tc_encode(TcChan* h, const __nv_bfloat16* const* A, int sa, int64_t lda_elems,
-              const __nv_bfloat16* const* X, int sx, int64_t ldx_elems, int m, int n, int ncols,
-              int bn);
+// Encode the maps of one channel (host).  Returns 0 on success.  f16: the
+// words are FP16 (the tile-rule factor), else BF16.
+int tc_encode(TcChan* h, const void* const* A, int sa, int64_t lda_elems, const void* const* X, int sx,
+              int64_t ldx_elems, int m, int n, int ncols, int bn, int f16 = 0);
+
+// Widest output-column tile of one work item (the epilogue's register
+// accumulator): up to TC_BN_NARROW for every word combination, up to
+// TC_BN_MAX for the two-word passes (2, 2) and (3, 3).
+constexpr int TC_BN_NARROW = 160;
+constexpr int TC_BN_MAX = 176;
 
 // Shared memory bytes per stage and stage count for a configuration.
 int tc_stage_bytes(int sa, int sx, int bn);
@@ -49,7 +56,8 @@ int tc_stages(int sa, int sx, int bn);
 
 // Launch over `items` work items (sum over channels of mt*nt*ks).
 // Returns a cudaError_t value.
-// rule: the tile-rule generation instantiation (<3, 3>, TC_RULE channels only).
+// rule: the tile-rule generation instantiation (<2, 2> FP16 words, TC_RULE
+// channels only).
 // max_stages: cap on the shared-memory pipeline depth (0: as many stages as
 // shared memory holds, at most 8; values below 2 mean no cap).
 int tc_launch(const TcChan* d_ch, int C, int items, int sa, int sx, int bn, int* d_err,
