@@ -236,13 +236,14 @@ rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
 
 /* CUDA graphs (off by default).  When enabled, and the plan's stream is not
  * the legacy default stream and profiling is off, each fixed/tolerance/learned
- * decomposition of stored channels is captured once per shape (channel sizes,
- * options, the plan's buffers and staged host inputs) and replayed on later
- * calls of the same shape; device input and output pointers may change
+ * decomposition -- stored channels or tile rules -- is captured once per
+ * shape (channel sizes, options, the plan's buffers and staged host inputs;
+ * for tile rules also rule_m, rule_seed, rule_eta and the scale of the
+ * weights) and replayed on later calls of the same shape; device input and
+ * output pointers and the rule's centres, widths and weights may change
  * between replays.  Up to 8 graphs are kept (least recently used evicted);
- * growing the workspace drops them.  The adaptive loop and tile rules are not
- * captured (they synchronise per block / generate per panel).  Disabling
- * frees the graphs. */
+ * growing the workspace drops them.  The adaptive loop is not captured (it
+ * synchronises per block).  Disabling frees the graphs. */
 rsvd_status rsvd_plan_set_graphs(rsvd_plan_t plan, int32_t enable);
 rsvd_status rsvd_plan_profile(rsvd_plan_t plan, rsvd_profile* out, int32_t reset);
 

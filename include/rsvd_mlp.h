@@ -54,6 +54,24 @@ rsvd_status rsvd_mlp_loss_grad(const float* theta, int32_t d, const float* X, co
 rsvd_status rsvd_mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t nparams, int32_t t,
                           float lr, float beta1, float beta2, float eps, void* stream);
 
+/* Standardisation of training data: mean and sd (device, d floats each) of
+ * the columns of X (N x d, row-major), sums in FP64, the population standard
+ * deviation floored at sd_floor (> 0); Xn (N x d) = (X - mean) / sd.  Used
+ * on the features and on the targets before training. */
+rsvd_status rsvd_mlp_standardize(const float* X, int32_t N, int32_t d, float sd_floor, float* mean, float* sd,
+                                 float* Xn, void* stream);
+
+/* Fold the standardisation into a network trained on standardised data, so
+ * that `out` (a separate blob of the same size) takes raw features and gives
+ * raw targets: W1 / sd_x, b1 - (mean_x / sd_x) W1, W3 sd_t, b3 sd_t + mean_t. */
+rsvd_status rsvd_mlp_fold(const float* theta, int32_t d, const float* mean_x, const float* sd_x,
+                          const float* mean_t, const float* sd_t, float* out, void* stream);
+
+/* Minibatch gather: dst[r, :] = src[idx[r], :] for r < B, rows of `cols`
+ * floats (idx: B int64 row numbers on the device, drawn by the caller). */
+rsvd_status rsvd_mlp_gather_rows(const float* src, const int64_t* idx, int32_t B, int32_t cols, float* dst,
+                                 void* stream);
+
 /* Probe features of C channels (FP32, C x RSVD_MLP_FEATURES row-major, device)
  * using the plan's precision and seed; tol: host array of C tolerances.
  * Synchronous. */

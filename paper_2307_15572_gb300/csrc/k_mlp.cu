@@ -135,6 +135,85 @@ __global__ void __launch_bounds__(H) k_mlp_infer(const float* __restrict__ theta
 
 using namespace rsvd;
 
+// Column statistics of X (N x d, row-major): mean and standard deviation
+// (population, floored at sd_floor), sums in FP64 in a fixed order (one block
+// per column); then Xn = (X - mean) / sd.
+__global__ void k_colstats(const float* __restrict__ X, int N, int d, float sd_floor, float* __restrict__ mean,
+                           float* __restrict__ sd) {
+  __shared__ double s1[256], s2[256];
+  const int col = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    const double x = X[(int64_t)r * d + col];
+    a += x;
+    b = fma(x, x, b);
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      s1[threadIdx.x] += s1[threadIdx.x + h];
+      s2[threadIdx.x] += s2[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = s1[0] / N;
+    const double var = s2[0] / N - m * m;
+    mean[col] = (float)m;
+    sd[col] = fmaxf((float)sqrt(var > 0.0 ? var : 0.0), sd_floor);
+  }
+}
+
+__global__ void k_standardize(const float* __restrict__ X, int N, int d, const float* __restrict__ mean,
+                              const float* __restrict__ sd, float* __restrict__ Xn) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)N * d) return;
+  const int col = (int)(e % d);
+  Xn[e] = (X[e] - mean[col]) / sd[col];
+}
+
+// A network trained on standardised inputs and targets, rewritten to take
+// raw ones: x_n W1 + b1 = x (W1 / sd_x) + (b1 - (mu_x / sd_x) W1), and
+// y = y_n sd_t + mu_t, i.e. W3 sd_t and b3 sd_t + mu_t (one thread per output
+// parameter; the b1 sums run over d in order).
+__global__ void k_fold(const float* __restrict__ th, int d, const float* __restrict__ mx, const float* __restrict__ sx,
+                       const float* __restrict__ mt, const float* __restrict__ st, float* __restrict__ out) {
+  const MlpView v = view(th, d);
+  const MlpView o = view(out, d);
+  const int64_t np = (int64_t)d * H + H + (int64_t)H * H + H + 2 * H + 2;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= np) return;
+  const int64_t ob1 = (int64_t)d * H, oW2 = ob1 + H, ob2 = oW2 + (int64_t)H * H, oW3 = ob2 + H, ob3 = oW3 + 2 * H;
+  float* w = (float*)o.W1;
+  if (e < ob1) {
+    const int i = (int)(e / H);
+    w[e] = v.W1[e] / sx[i];
+  } else if (e < oW2) {
+    const int h = (int)(e - ob1);
+    float s = v.b1[h];
+    for (int i = 0; i < d; ++i) s -= (mx[i] / sx[i]) * v.W1[(int64_t)i * H + h];
+    w[e] = s;
+  } else if (e < oW3) {
+    w[e] = th[e];
+  } else if (e < ob3) {
+    w[e] = th[e] * st[(e - oW3) % 2];
+  } else {
+    const int j = (int)(e - ob3);
+    w[e] = th[e] * st[j] + mt[j];
+  }
+}
+
+// dst[r, :] = src[idx[r], :] (rows of `cols` floats).
+__global__ void k_gather_rows(const float* __restrict__ src, const int64_t* __restrict__ idx, int B, int cols,
+                              float* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  dst[e] = src[idx[r] * cols + c];
+}
+
 extern "C" {
 
 int64_t rsvd_mlp_param_count(int32_t d) {
@@ -191,6 +270,35 @@ rsvd_status rsvd_mlp_adam(float* theta, const float* grad, float* m, float* v, i
   const float c1 = 1.0f - powf(beta1, (float)t), c2 = 1.0f - powf(beta2, (float)t);
   k_adam<<<nb(nparams), 256, 0, (cudaStream_t)stream>>>(theta, grad, m, v, nparams, lr, beta1, beta2, eps, c1, c2);
   note_launch(1);
+  return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+}
+
+rsvd_status rsvd_mlp_standardize(const float* X, int32_t N, int32_t d, float sd_floor, float* mean, float* sd,
+                                 float* Xn, void* stream) {
+  if (!X || !mean || !sd || !Xn || N < 1 || d < 1 || !(sd_floor > 0.0f)) return RSVD_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_colstats<<<d, 256, 0, st>>>(X, N, d, sd_floor, mean, sd);
+  const int64_t tot = (int64_t)N * d;
+  k_standardize<<<(int)((tot + 255) / 256), 256, 0, st>>>(X, N, d, mean, sd, Xn);
+  note_launch(2);
+  return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+}
+
+rsvd_status rsvd_mlp_fold(const float* theta, int32_t d, const float* mean_x, const float* sd_x,
+                          const float* mean_t, const float* sd_t, float* out, void* stream) {
+  if (!theta || !mean_x || !sd_x || !mean_t || !sd_t || !out || d < 1 || out == theta) return RSVD_ERR_INVALID_ARG;
+  const int64_t np = rsvd_mlp_param_count(d);
+  k_fold<<<(int)((np + 255) / 256), 256, 0, (cudaStream_t)stream>>>(theta, d, mean_x, sd_x, mean_t, sd_t, out);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+}
+
+rsvd_status rsvd_mlp_gather_rows(const float* src, const int64_t* idx, int32_t B, int32_t cols, float* dst,
+                                 void* stream) {
+  if (!src || !idx || !dst || B < 1 || cols < 1) return RSVD_ERR_INVALID_ARG;
+  const int64_t tot = (int64_t)B * cols;
+  k_gather_rows<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src, idx, B, cols, dst);
+  note_launch();
   return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
 }
 

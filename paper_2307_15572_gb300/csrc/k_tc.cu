@@ -29,6 +29,7 @@
 // own copies and frees TMEM before returning.
 #include <cudaTypedefs.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include "tc_gemm.h"
 

@@ -10,8 +10,9 @@ network trains on standardised features and targets; the standardisation is
 then folded into the first and last layers, so the stored parameter blob takes
 the library's raw features (as RSVD_RANK_LEARNED feeds them).
 
-torch is used only for device buffers and minibatch index plumbing; every
-forward, backward and Adam step runs in the library's kernels.
+torch is used only for device buffers and to draw the minibatch row numbers;
+the standardisation, gathers, every forward, backward and Adam step and the
+folding run in the library's kernels.
 """
 
 import math
@@ -98,50 +99,44 @@ def init_params(d, seed):
 
 def train(X, T, steps=3000, batch=256, lr=2e-3, seed=0, log_every=0):
     """Train on device tensors X (N x d) and T (N x 2); returns (theta with the
-    standardisation folded in, loss history)."""
+    standardisation folded in, loss history).  The standardisation, the
+    minibatch gathers, every forward/backward/Adam step and the final folding
+    run in the library's kernels; torch provides the buffers and draws the
+    minibatch row numbers."""
     import torch
-    d = X.shape[1]
-    H = rsvd.MLP_HIDDEN
-    mu = X.mean(0)
-    sd = X.std(0).clamp_min(1e-6)
-    tm = T.mean(0)
-    ts = T.std(0).clamp_min(1e-6)
-    Xn = ((X - mu) / sd).contiguous()
-    Tn = ((T - tm) / ts).contiguous()
+    N, d = X.shape
+    X = X.contiguous()
+    T = T.contiguous()
     n = rsvd.rsvd_mlp_param_count(d)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    mx, sx = torch.empty(d, **f32), torch.empty(d, **f32)
+    mt, st = torch.empty(2, **f32), torch.empty(2, **f32)
+    Xn, Tn = torch.empty((N, d), **f32), torch.empty((N, 2), **f32)
+    rsvd.rsvd_mlp_standardize(X.data_ptr(), N, d, 1e-6, mx.data_ptr(), sx.data_ptr(), Xn.data_ptr())
+    rsvd.rsvd_mlp_standardize(T.data_ptr(), N, 2, 1e-6, mt.data_ptr(), st.data_ptr(), Tn.data_ptr())
     theta = torch.as_tensor(init_params(d, seed), device="cuda")
-    m = torch.zeros(n, device="cuda")
-    v = torch.zeros(n, device="cuda")
-    g = torch.zeros(n, device="cuda")
-    B = min(batch, X.shape[0])
-    work = torch.empty(rsvd.rsvd_mlp_work_floats(d, B), device="cuda")
-    loss = torch.zeros(1, device="cuda")
+    m = torch.zeros(n, **f32)
+    v = torch.zeros(n, **f32)
+    g = torch.zeros(n, **f32)
+    B = min(batch, N)
+    work = torch.empty(rsvd.rsvd_mlp_work_floats(d, B), **f32)
+    loss = torch.zeros(1, **f32)
+    xb, tb = torch.empty((B, d), **f32), torch.empty((B, 2), **f32)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
     hist = []
     for t in range(1, steps + 1):
-        idx = torch.randint(0, X.shape[0], (B,), device="cuda", generator=gen)
-        xb = Xn.index_select(0, idx).contiguous()
-        tb = Tn.index_select(0, idx).contiguous()
+        idx = torch.randint(0, N, (B,), device="cuda", generator=gen)
+        rsvd.rsvd_mlp_gather_rows(Xn.data_ptr(), idx.data_ptr(), B, d, xb.data_ptr())
+        rsvd.rsvd_mlp_gather_rows(Tn.data_ptr(), idx.data_ptr(), B, 2, tb.data_ptr())
         rsvd.rsvd_mlp_loss_grad(theta.data_ptr(), d, xb.data_ptr(), tb.data_ptr(), B, g.data_ptr(),
                                 loss.data_ptr(), work.data_ptr())
         rsvd.rsvd_mlp_adam(theta.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), n, t, lr)
         if log_every and t % log_every == 0:
             hist.append(float(loss.item()))
-    # fold the standardisation: x_n W1 + b1 = x (W1 / sd) + (b1 - (mu / sd) W1);
-    # y = y_n * ts + tm  ->  W3 ts, b3 ts + tm
-    W1 = theta[: d * H].view(d, H)
-    b1 = theta[d * H: d * H + H]
-    W1f = W1 / sd[:, None]
-    b1f = b1 - (mu / sd) @ W1
-    o3 = d * H + H + H * H + H
-    W3 = theta[o3: o3 + 2 * H].view(H, 2)
-    b3 = theta[o3 + 2 * H: o3 + 2 * H + 2]
-    out = theta.clone()
-    out[: d * H] = W1f.reshape(-1)
-    out[d * H: d * H + H] = b1f
-    out[o3: o3 + 2 * H] = (W3 * ts[None, :]).reshape(-1)
-    out[o3 + 2 * H: o3 + 2 * H + 2] = b3 * ts + tm
+    out = torch.empty_like(theta)
+    rsvd.rsvd_mlp_fold(theta.data_ptr(), d, mx.data_ptr(), sx.data_ptr(), mt.data_ptr(), st.data_ptr(),
+                       out.data_ptr())
     return out, hist
 
 

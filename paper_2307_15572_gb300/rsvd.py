@@ -123,6 +123,12 @@ def load(build=True):
     lib.rsvd_mlp_loss_grad.restype = C.c_int
     lib.rsvd_mlp_adam.argtypes = [P, P, P, P, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, P]
     lib.rsvd_mlp_adam.restype = C.c_int
+    lib.rsvd_mlp_standardize.argtypes = [P, C.c_int32, C.c_int32, C.c_float, P, P, P, P]
+    lib.rsvd_mlp_standardize.restype = C.c_int
+    lib.rsvd_mlp_fold.argtypes = [P, C.c_int32, P, P, P, P, P, P]
+    lib.rsvd_mlp_fold.restype = C.c_int
+    lib.rsvd_mlp_gather_rows.argtypes = [P, P, C.c_int32, C.c_int32, P, P]
+    lib.rsvd_mlp_gather_rows.restype = C.c_int
     lib.rsvd_probe_features.argtypes = [P, C.c_int32, C.POINTER(Matrix), C.POINTER(C.c_double), P]
     lib.rsvd_probe_features.restype = C.c_int
     lib.rsvd_reconstruct_error_noalloc.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int64, P, P, C.c_int64,
@@ -233,6 +239,18 @@ def rsvd_mlp_loss_grad(theta, d, X, T, B, grad, loss, work, stream=None):
 
 def rsvd_mlp_adam(theta, grad, m, v, nparams, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     return _check(load().rsvd_mlp_adam(theta, grad, m, v, nparams, t, lr, beta1, beta2, eps, stream))
+
+
+def rsvd_mlp_standardize(X, N, d, sd_floor, mean, sd, Xn, stream=None):
+    return _check(load().rsvd_mlp_standardize(X, N, d, sd_floor, mean, sd, Xn, stream))
+
+
+def rsvd_mlp_fold(theta, d, mean_x, sd_x, mean_t, sd_t, out, stream=None):
+    return _check(load().rsvd_mlp_fold(theta, d, mean_x, sd_x, mean_t, sd_t, out, stream))
+
+
+def rsvd_mlp_gather_rows(src, idx, B, cols, dst, stream=None):
+    return _check(load().rsvd_mlp_gather_rows(src, idx, B, cols, dst, stream))
 
 
 def rsvd_probe_features(h, mats, tols, features):

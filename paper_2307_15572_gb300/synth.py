@@ -206,6 +206,28 @@ def learn_channel_params(count=4000, seed=SEED_LEARN, nlo=500, nhi=20000, tlo=1e
     return out
 
 
+def sweep_channel_params(count=400, seed=SEED_SWEEP, nlo=2000, nhi=40000, expo=2.41, M=300):
+    """Tile-rule channels of the full mixed sweep: sizes drawn from
+    p(n) ~ n^-expo on [nlo, nhi] (inverse CDF; expo 2.41 puts the expected
+    total of 400 channels at ~150 GB of FP64 entries), each with the
+    Gaussian-bump rule's layout (M bumps, centres ~ U[0, 8], widths
+    log-uniform in [0.05, 1]) and its own decay w_m = e^{-m / tau},
+    tau log-uniform in [10, 50], noise seed and scale 1e-7."""
+    rng = np.random.default_rng(seed)
+    out = []
+    g = 1.0 - expo
+    for _ in range(count):
+        u = rng.uniform()
+        n = int(round((nlo ** g + u * (nhi ** g - nlo ** g)) ** (1.0 / g)))
+        tau = math.exp(rng.uniform(math.log(10.0), math.log(50.0)))
+        m = np.arange(1, M + 1, dtype=np.float64)
+        c = rng.uniform(0.0, 8.0, size=M)
+        s = np.exp(rng.uniform(math.log(0.05), math.log(1.0), size=M))
+        out.append(dict(n=n, c=c, s=s, w=np.exp(-m / tau), tau=tau, eta=1e-7,
+                        seed=int(rng.integers(0, 2**63 - 1))))
+    return out
+
+
 def mixed_decay_spectrum(n, a, tau, beta):
     """sigma_i = a exp(-i / tau) + (1 - a) i^-beta, i = 1..n."""
     i = np.arange(1, n + 1, dtype=np.float64)

@@ -141,3 +141,44 @@ def test_learned_beats_adaptive_mixed(lib, trained):
     assert np.all(ea[oka] <= tols[oka]) and np.all(el[oka] <= tols[oka])
     assert pl < pa
     assert tl < ta
+
+
+def test_standardize_fold_gather_match_oracle(lib):
+    """The training driver's data steps in the library's kernels: column
+    standardisation against numpy's mean and population deviation, the
+    folded network against the oracle network on standardised data, and the
+    minibatch gather."""
+    import torch
+    rng = np.random.default_rng(9)
+    N, d = 300, 19
+    X = rng.standard_normal((N, d)) * rng.uniform(0.1, 20, d) + rng.uniform(-5, 5, d)
+    T = rng.standard_normal((N, 2)) * [2.0, 0.5] + [4.0, 1.0]
+    f32 = dict(dtype=torch.float32, device="cuda")
+    Xg, Tg = torch.as_tensor(X, **f32), torch.as_tensor(T, **f32)
+    mx, sx, Xn = torch.empty(d, **f32), torch.empty(d, **f32), torch.empty((N, d), **f32)
+    mt, st, Tn = torch.empty(2, **f32), torch.empty(2, **f32), torch.empty((N, 2), **f32)
+    lib.rsvd_mlp_standardize(Xg.data_ptr(), N, d, 1e-6, mx.data_ptr(), sx.data_ptr(), Xn.data_ptr())
+    lib.rsvd_mlp_standardize(Tg.data_ptr(), N, 2, 1e-6, mt.data_ptr(), st.data_ptr(), Tn.data_ptr())
+    Xf = Xg.double().cpu().numpy()                    # the FP32 data both sides see
+    assert np.allclose(mx.cpu().numpy(), Xf.mean(0), rtol=1e-6, atol=1e-6)
+    assert np.allclose(sx.cpu().numpy(), Xf.std(0), rtol=1e-6)
+    Xn_o = (Xf - Xf.mean(0)) / Xf.std(0)
+    assert np.max(np.abs(Xn.cpu().numpy() - Xn_o)) <= 1e-5
+    # folding: the folded blob on raw features equals the trained blob on
+    # standardised features, rescaled to raw targets
+    theta = omlp.init(d, 6) + 0.05 * rng.standard_normal(omlp.n_params(d))
+    th = torch.as_tensor(theta, **f32)
+    folded = torch.empty_like(th)
+    lib.rsvd_mlp_fold(th.data_ptr(), d, mx.data_ptr(), sx.data_ptr(), mt.data_ptr(), st.data_ptr(),
+                      folded.data_ptr())
+    Y = torch.empty((N, 2), **f32)
+    lib.rsvd_mlp_forward(folded.data_ptr(), d, Xg.data_ptr(), N, Y.data_ptr())
+    yn, _ = omlp.forward(theta.astype(np.float32).astype(np.float64), Xn_o)
+    Tf = Tg.double().cpu().numpy()
+    yo = yn * Tf.std(0) + Tf.mean(0)
+    assert np.max(np.abs(Y.cpu().numpy() - yo)) <= 1e-4 * max(1.0, np.abs(yo).max())
+    # gather
+    idx = torch.as_tensor(rng.integers(0, N, 77), dtype=torch.int64, device="cuda")
+    G = torch.empty((77, d), **f32)
+    lib.rsvd_mlp_gather_rows(Xg.data_ptr(), idx.data_ptr(), 77, d, G.data_ptr())
+    assert torch.equal(G, Xg.index_select(0, idx))

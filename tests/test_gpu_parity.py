@@ -360,3 +360,41 @@ def test_mixed_pinned_host_input_never_staged(lib):
     # the staged (pageable) run needs the FP64 copy of V; the pinned run does not
     assert sizes["pageable"] - sizes["pinned"] >= 8 * n * n * 0.99, sizes
     assert sizes["pinned"] < 8 * n * n, sizes
+
+
+@pytest.mark.parametrize("policy", ["fixed", "adaptive"])
+def test_fp64_pinned_host_read_in_place(lib, monkeypatch, policy):
+    """Host-resident channel on the FP64 path: when its staged copy would not
+    fit the device (forced here with RSVD_HOST_IN_PLACE=1), every FP64 pass
+    reads the page-locked V in place over the CPU-GPU link.  The workspace
+    then holds no copy of V, and the result equals the device-resident run
+    (the same kernels; only the order of the split-k atomic additions can
+    differ) and the oracle's singular values."""
+    torch = _torch()
+    n, k = 3000, 40
+    A = synth.planted_haar(n, synth.spectrum_exp(n, 10.0), 31)
+    pinned = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.as_tensor(A))
+    dev = torch.as_tensor(A, device="cuda")
+    kw = dict(k=k, p=10, q=1, seed=4) if policy == "fixed" else dict(tol=1e-6, policy="adaptive", block_b=16, seed=4)
+    out = {}
+    for name, src in (("device", dev), ("host", pinned)):
+        if name == "host":
+            monkeypatch.setenv("RSVD_HOST_IN_PLACE", "1")
+        plan = lib.Plan(n, precision="fp64", **kw)
+        try:
+            st, r = plan.decompose(src, 128)
+            assert st >= 0, lib.last_error()
+            out[name] = (r["S"].cpu().numpy(), r["U"].cpu().numpy(), lib.load().rsvd_plan_workspace_bytes(plan.h))
+        finally:
+            plan.close()
+        monkeypatch.delenv("RSVD_HOST_IN_PLACE", raising=False)
+    (sd, ud, wd), (sh, uh, wh) = out["device"], out["host"]
+    assert len(sd) == len(sh)
+    assert np.max(np.abs(sd - sh) / sd) <= 1e-12
+    assert np.max(np.abs(ud - uh)) <= 1e-9
+    assert wh < 8 * n * n, wh
+    if policy == "fixed":
+        o = orsvd.rsvd(A, k=k, p=10, q=1, seed=4)
+        big = o.S > 1e-12 * o.S[0]
+        assert np.all(np.abs(sh[big] - o.S[big]) <= 1e-10 * o.S[big])
