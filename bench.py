@@ -35,6 +35,11 @@ UNIT = "entries/s"
 L_COLS = 128          # columns drawn per channel (k cap 118 + p 10)
 P_OVER = 10
 TOL = 1e-4
+# Peaks the driver's MEASURED_PEAKS.json does not carry, measured the same
+# way on this machine's GB300 (torch.matmul 8192^3, CUDA events, best of 5-10):
+FP64_PEAK_TFLOPS = 1.10       # FP64 (DGEMM); nominal 1.25
+TF32_PEAK_TFLOPS = 1021.5     # TF32 tensor cores
+FP32_SIMT_TFLOPS = 69.75      # FP32 on the CUDA cores
 
 
 def parse():
@@ -349,11 +354,12 @@ def run_gpu(args):
         roofline["profiled_ms_per_step"] = ms_p / args.prof_steps
 
     # ---- learned rank on the same channels: the committed rank model (trained
-    # by paper_2307_15572_gb300/rank_model.py on the seeded config-4
-    # population) picks each channel's l from a one-word probe; the rank rule
-    # checks every channel, misses retry and then fall back to the adaptive loop
+    # by paper_2307_15572_gb300/rank_model.py on a seeded population of this
+    # workload's size range, labelled by the mixed-path adaptive loop) picks
+    # each channel's l from a one-word probe; the rank rule checks every
+    # channel, misses retry and then fall back to the adaptive loop
     learned = None
-    wpath = os.path.join(ROOT, "paper_2307_15572_gb300", "rank_model_bf16x.bin")
+    wpath = os.path.join(ROOT, "paper_2307_15572_gb300", "rank_model_bf16x_batch.bin")
     if not args.no_learned and os.path.exists(wpath):
         theta = torch.from_numpy(np.fromfile(wpath, dtype="<f4")).cuda()
         plan = rsvd.Plan(max(sizes), k=0, p=0, q=0, tol=TOL, policy="learned", precision="bf16x", slices=2,
@@ -377,7 +383,8 @@ def run_gpu(args):
                    "statuses": sorted(set(st_l)),
                    "passes_over_v_per_step": int(prof_lp["tc_launches"]),
                    "vs_tol_policy": (tot_l / (ms_l / 1e3)) / value,
-                   "model": "rank_model_bf16x.bin (see rank_model.json for its population and held-out report)"}
+                   "model": "rank_model_bf16x_batch.bin (see rank_model_batch.json for its population, "
+                            "labels and held-out report)"}
         del lb
 
     # ---- e2e through the C ABI with host buffers
@@ -416,8 +423,10 @@ def run_gpu(args):
                 "ms_per_step": ms_f / args.fp64_steps, "steps": args.fp64_steps, "max_rel_err": err_f,
                 "ranks": [min(ks_f), max(ks_f)],
                 "roofline": {"bound": "alu", "kernel": "k_tile_mm<double> (FP64 pass over V)",
-                             "achieved": f64_tf, "peak": 1.25, "unit": "TFLOP/s", "frac": f64_tf / 1.25,
-                             "peak_source": "nominal FP64 rate of GB300"},
+                             "achieved": f64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": f64_tf / FP64_PEAK_TFLOPS,
+                             "peak_source": "builder-measured: torch.matmul FP64 8192^3, best of 5, this pool's "
+                                            "GB300 (nominal 1.25)"},
                 "autotune": tune_summary(plan)}
         plan.close()
 

@@ -38,12 +38,12 @@ def _factors(pop, kcap):
     return facs, bufs
 
 
-def label(pop, mats, block=16, lmax=1024, seed=1, chunk=64):
-    """(k*, l*, met) per channel from the FP64 adaptive loop; met is False where
-    the tolerance needs more than lmax columns."""
+def label(pop, mats, block=16, lmax=1024, seed=1, chunk=64, precision="fp64"):
+    """(k*, l*, met) per channel from the adaptive loop (FP64 path by default);
+    met is False where the tolerance needs more than lmax columns."""
     ks, ls, met = [], [], []
     nmax = max(ch["n"] for ch in pop)
-    plan = rsvd.Plan(nmax, k=0, p=0, q=0, tol=1e-3, policy="adaptive", precision="fp64", block_b=block,
+    plan = rsvd.Plan(nmax, k=0, p=0, q=0, tol=1e-3, policy="adaptive", precision=precision, block_b=block,
                      l_max=lmax, seed=seed)
     try:
         for i in range(0, len(pop), chunk):

@@ -45,14 +45,15 @@ def _chunks(seq, size):
         yield i, seq[i:i + size]
 
 
-def label_and_features(pop, lmax, block, chunk, seed):
+def label_and_features(pop, lmax, block, chunk, seed, label_precision="fp64", models=("fp64", "bf16x")):
     """(k*, l*, met, features per precision) over the population, in chunks."""
     import torch
     ks, ls, met = [], [], []
-    feats = {"fp64": [], "bf16x": []}
+    feats = {p: [] for p in models}
     for i, sub in _chunks(pop, chunk):
         mats = learn.matrices(sub)
-        k, l_, m = learn.label(sub, mats, block=block, lmax=lmax, seed=seed, chunk=chunk)
+        k, l_, m = learn.label(sub, mats, block=block, lmax=lmax, seed=seed, chunk=chunk,
+                               precision=label_precision)
         ks.append(k)
         ls.append(l_)
         met.append(m)
@@ -106,11 +107,17 @@ def main():
     ap.add_argument("--seed", type=int, default=synth.SEED_LEARN)
     ap.add_argument("--mixed-floor", type=float, default=1e-5,
                     help="held-out tolerances at least this large are also compared on the mixed path")
+    ap.add_argument("--label-precision", default="fp64", choices=["fp64", "bf16x"],
+                    help="path of the adaptive loop that labels the channels")
+    ap.add_argument("--models", default="fp64,bf16x", help="probe precisions to train a network for")
+    ap.add_argument("--tag", default="", help="suffix of the written file names")
     a = ap.parse_args()
+    models = tuple(a.models.split(","))
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     pop = synth.learn_population(a.count, seed=a.seed, nlo=a.nlo, nhi=a.nhi, tlo=a.tlo, thi=a.thi)
-    ks, ls, met, feats = label_and_features(pop, a.lmax, 16, a.chunk, seed=1)
+    ks, ls, met, feats = label_and_features(pop, a.lmax, 16 if a.label_precision == "fp64" else 32, a.chunk, seed=1,
+                                            label_precision=a.label_precision, models=models)
     t_label = time.perf_counter() - t0
     ntr = a.count - a.held
     T = torch.as_tensor(learn.targets(ks, ls), dtype=torch.float32, device="cuda")
@@ -118,7 +125,9 @@ def main():
     report = {"population": dict(count=a.count, held_out=a.held, n=[a.nlo, a.nhi], tol=[a.tlo, a.thi],
                                  seed=a.seed, spectrum="a e^-i/tau + (1-a) i^-beta, a~U[0,1], "
                                                        "tau~logU[5,200], beta~U[1.5,4]",
-                                 labels="FP64 adaptive loop, blocks of 16, l_max %d" % a.lmax,
+                                 labels="%s adaptive loop, blocks of %d, l_max %d"
+                                        % ("FP64" if a.label_precision == "fp64" else "mixed-path (BF16 x2)",
+                                           16 if a.label_precision == "fp64" else 32, a.lmax),
                                  trained_on=int(met[:ntr].sum()), unmet_in_l_max=int((~met[:ntr]).sum()),
                                  held_out_met=int(met[ntr:].sum()),
                                  label_and_feature_seconds=t_label),
@@ -126,11 +135,11 @@ def main():
     os.makedirs(a.out, exist_ok=True)
     thetas = {}
     hidx = torch.as_tensor(ntr + np.nonzero(met[ntr:])[0], device="cuda")
-    for prec in ("fp64", "bf16x"):
+    for prec in models:
         X = feats[prec].index_select(0, keep)
         th, hist = learn.train(X, T.index_select(0, keep), steps=a.steps, lr=2e-3, log_every=500)
         thetas[prec] = th
-        th.cpu().numpy().astype("<f4").tofile(os.path.join(a.out, "rank_model_%s.bin" % prec))
+        th.cpu().numpy().astype("<f4").tofile(os.path.join(a.out, "rank_model_%s%s.bin" % (prec, a.tag)))
         # prediction quality on the held-out channels the adaptive loop finishes
         P = learn.predict(th, feats[prec].index_select(0, hidx)).cpu().numpy()
         Th = T.index_select(0, hidx).cpu().numpy()
@@ -138,11 +147,13 @@ def main():
                                     "held_out_median_abs_log_err": [float(np.median(np.abs(P[:, j] - Th[:, j])))
                                                                     for j in range(2)]}
     held = [ch for ch, m in zip(pop[ntr:], met[ntr:]) if m]
-    report["held_out"]["fp64"] = compare(held, thetas["fp64"], "fp64", a.lmax, a.chunk, 1, 0)
-    mheld = [ch for ch in held if ch["tol"] >= a.mixed_floor]
-    report["held_out"]["bf16x"] = compare(mheld, thetas["bf16x"], "bf16x", a.lmax, a.chunk, 1, 3)
+    if "fp64" in models:
+        report["held_out"]["fp64"] = compare(held, thetas["fp64"], "fp64", a.lmax, a.chunk, 1, 0)
+    if "bf16x" in models:
+        mheld = [ch for ch in held if ch["tol"] >= a.mixed_floor]
+        report["held_out"]["bf16x"] = compare(mheld, thetas["bf16x"], "bf16x", a.lmax, a.chunk, 1, 2)
     report["seconds"] = time.perf_counter() - t0
-    with open(os.path.join(a.out, "rank_model.json"), "w") as f:
+    with open(os.path.join(a.out, "rank_model%s.json" % a.tag), "w") as f:
         json.dump(report, f, indent=1)
     print(json.dumps(report["held_out"]))
 

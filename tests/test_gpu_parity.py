@@ -383,7 +383,7 @@ def test_fp64_pinned_host_read_in_place(lib, monkeypatch, policy):
             monkeypatch.setenv("RSVD_HOST_IN_PLACE", "1")
         plan = lib.Plan(n, precision="fp64", **kw)
         try:
-            st, r = plan.decompose(src, 128)
+            st, r = plan.decompose(src, 256)             # tol 1e-6 needs rank ~140 here
             assert st >= 0, lib.last_error()
             out[name] = (r["S"].cpu().numpy(), r["U"].cpu().numpy(), lib.load().rsvd_plan_workspace_bytes(plan.h))
         finally:
