@@ -91,6 +91,73 @@ k_tile_mm(const MMDesc* __restrict__ md, const int* __restrict__ off, int C) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) { acc[i][j] = 0; cmp[i][j] = 0; }
 
+  if constexpr (ACC == ACC_DOT2) {
+    // The compensated Gram: the next 16-wide k slice is loaded into registers
+    // while the current one is consumed from the other shared-memory buffer,
+    // so the global loads overlap the arithmetic and one barrier separates
+    // the slices (the generic loop below waits on both).
+    __shared__ T As2[2][16][64 + 4];
+    __shared__ T Bs2[2][16][64 + 4];
+    T ra[4], rb[4];
+    auto load = [&](int k0) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int e = tid + p * 256;
+        int mm, kk;
+        if (AL == AROW) { mm = e >> 4; kk = e & 15; }
+        else { mm = e & 63; kk = e >> 6; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        ra[p] = (gm < dm && gk < ke) ? (T)(AL == AROW ? A[(int64_t)gm * lda + gk] : A[gm + (int64_t)gk * lda]) : (T)0;
+        const int kb2 = e & 15, nn = e >> 4;
+        const int gk2 = k0 + kb2, gn = n0 + nn;
+        rb[p] = (gn < ncols && gk2 < ke) ? (T)B[gk2 + (int64_t)gn * ldb] : (T)0;
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int e = tid + p * 256;
+        int mm, kk;
+        if (AL == AROW) { mm = e >> 4; kk = e & 15; }
+        else { mm = e & 63; kk = e >> 6; }
+        As2[buf][kk][mm] = ra[p];
+        Bs2[buf][e & 15][e >> 4] = rb[p];
+      }
+    };
+    if (kb < ke) {
+      load(kb);
+      store(0);
+      __syncthreads();
+    }
+    int buf = 0;
+    for (int k0 = kb; k0 < ke; k0 += 16, buf ^= 1) {
+      const bool more = k0 + 16 < ke;
+      if (more) load(k0 + 16);
+      if (!lower) {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          float a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = (float)As2[buf][kk][ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = (float)Bs2[buf][kk][tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float p = a[i] * b[j];
+              const float pe = fmaf(a[i], b[j], -p);
+              float sv, se;
+              two_sum((float)acc[i][j], p, sv, se);
+              acc[i][j] = sv;
+              cmp[i][j] += se + pe;
+            }
+        }
+      }
+      if (more) store(buf ^ 1);
+      __syncthreads();
+    }
+  } else
   for (int k0 = kb; k0 < ke; k0 += 16) {
     // A tile: 64 (m) x 16 (k) -> As[k][m]
 #pragma unroll

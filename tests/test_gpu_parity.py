@@ -393,7 +393,7 @@ def test_fp64_pinned_host_read_in_place(lib, monkeypatch, policy):
     assert len(sd) == len(sh)
     assert np.max(np.abs(sd - sh)) <= 1e-12 * sd[0]
     assert np.max(np.abs(ud - uh)) <= 1e-9
-    assert wh < 8 * n * n, wh
+    assert wh == wd, (wh, wd)                     # no staged copy: the device-resident layout
     if policy == "fixed":
         o = orsvd.rsvd(A, k=k, p=10, q=1, seed=4)
         big = o.S > 1e-12 * o.S[0]
