@@ -344,6 +344,23 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": tc_bytes_per,
                      "bytes_per_unit": "2 B per word per V entry, + X words and Y once",
                      "share_of_step": prof["tc_ms"] / ms_p})
+    if prof.get("gram_launches"):
+        # the FP64-grade Grams of CholeskyQR: algorithmic flops (2 n l^2 per
+        # Gram) against the measured FP64 peak they replace, issued slice
+        # products against the sustained BF16 peak
+        g_ms = prof["gram_ms"] / prof["gram_launches"]
+        g_tf = prof["gram_flops"] / prof["gram_launches"] / (g_ms / 1e3) / 1e12
+        g_mma = prof["gram_mma_flops"] / prof["gram_launches"] / (g_ms / 1e3) / 1e12
+        bf16_s, bf16_kind = bf16_peak(sustained=True)
+        kern.append({"bound": "tensor", "achieved": g_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": g_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_gram_tc + k_gram_tc_reduce (FP64-grade Gram of the n x l FP32 panels, exact "
+                               "BF16 slices on tcgen05)",
+                     "peak_source": "FP64 DGEMM, builder-measured (the precision the Gram delivers)",
+                     "launches": prof["gram_launches"], "avg_launch_ms": g_ms,
+                     "algorithmic_flops_per_launch": prof["gram_flops"] / prof["gram_launches"],
+                     "issued_tflops": g_mma, "issued_frac_of_bf16": g_mma / bf16_s, "bf16_peak_source": bf16_kind,
+                     "share_of_step": prof["gram_ms"] / ms_p})
     kern.sort(key=lambda r: -r["share_of_step"])
     roofline = dict(kern[0]) if kern else None
     if roofline is not None:
@@ -508,8 +525,8 @@ def run_gpu(args):
                                       % (args.channels, args.nmin, args.nmax),
                           "channels": args.channels, "sum_n2_per_gpu": entries, "tol": TOL, "l": L_COLS,
                           "q": 0, "words": 2, "policy": "tol",
-                          "precision": "V and X as 2 BF16 words, FP32 accumulate; compensated-FP64 Gram, "
-                                       "FP64 Cholesky",
+                          "precision": "V and X as 2 BF16 words, FP32 accumulate; FP64-grade Grams (exact BF16 "
+                                       "slices on the tensor cores), FP64 Cholesky",
                           "l2": "inputs larger than L2 (no flush)", "max_rel_err": max_err,
                           "verified_tol": bool(max_err <= TOL), "ranks": [min(ks), max(ks)],
                           "parallelism": ("fixed set split by LPT over %d GPUs" % ws if args.split == "fixed"

@@ -208,8 +208,8 @@ rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
 /* Launch accounting of the plan's own kernels, for benchmarks.  When enabled
  * (rsvd_plan_set_profiling(plan, 1)), each decomposition records CUDA events
  * on the plan's stream around every tensor-core pass, every FP64 dense pass
- * over V, every tile-rule generation and every conversion of V into words,
- * and adds their device time and algorithmic traffic (bytes of V words, X
+ * over V, every tile-rule generation, every conversion of V into words and
+ * every tensor-core Gram of CholeskyQR, and adds their device time and algorithmic traffic (bytes of V words, X
  * words and Y read or written once, as the roofline counts them) to the
  * counters below.  Kernel launches are counted whether or not timing is
  * enabled.  rsvd_plan_profile copies the counters (host struct) and, if
@@ -230,6 +230,10 @@ typedef struct {
   int64_t cvt_launches;    /* conversions of stored FP64 V into BF16 words       */
   double cvt_ms;
   double cvt_bytes;        /* 8 B read + 2 B per word written per entry          */
+  int64_t gram_launches;   /* tensor-core Grams Y^T Y of n x l FP32 panels        */
+  double gram_ms;          /* (both kernels: slice products and tile reduction)  */
+  double gram_flops;       /* algorithmic: 2 n l^2 per Gram                      */
+  double gram_mma_flops;   /* issued: 21 slice products x 2 x 128^3 per tile     */
 } rsvd_profile;
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
@@ -303,6 +307,31 @@ rsvd_status rsvd_plan_tune_records(rsvd_plan_t plan, rsvd_tune_record* out, int3
  * factors, bad sizes or pointers; k = 0 writes nothing. */
 rsvd_status rsvd_transform_factors(rsvd_plan_t plan, const rsvd_factors* f, int64_t n, const double* B,
                                    int64_t ldb, int64_t m, double* Lt, int64_t ldl, double* Rt, int64_t ldr);
+
+/* FP64-grade Gram G = Y^T Y of an FP32 panel: the Gram of CholeskyQR
+ * (Fukaya, Nakatsukasa, Yanagisawa & Yamamoto, 2014), which orthonormalises
+ * the sketch Y = A Omega of the paper's step 1 and factors W^T W of the
+ * projection on the mixed path.  Y (DEVICE, n x l FP32, column-major,
+ * ldy >= n) and G (DEVICE, l x l FP64, column-major, leading dim l, both
+ * triangles written).
+ *   method RSVD_GRAM_TC: tensor cores; each 128-row tile of Y is split into
+ *     six exact BF16 fixed-point slices (Ozaki, Ogita, Oishi & Rump, 2012),
+ *     the leading slice products summed exactly in TMEM and the tiles in
+ *     double-float.  Needs l <= 128, ldy a multiple of 4 and Y 16-byte
+ *     aligned.
+ *   method RSVD_GRAM_DOT2: CUDA cores, compensated dot products (Ogita,
+ *     Rump & Oishi, 2005), any l.
+ * Both agree with the exact Gram of the FP32 data to about 1e-14 of
+ * ||y_i|| ||y_j||.  The decompositions of the mixed path use RSVD_GRAM_TC
+ * where every channel has l <= 128 (unless the environment variable
+ * RSVD_GRAM=dot2 is set when the call is built).  Uses the plan's workspace
+ * and stream and returns after the stream has completed.
+ * RSVD_ERR_INVALID_ARG for NULL pointers, n < 1, l < 1, ldy < n or a bad
+ * method; RSVD_ERR_UNSUPPORTED for RSVD_GRAM_TC with l > 128 or a misaligned
+ * Y; RSVD_ERR_TIMEOUT if a bounded device wait expired. */
+enum { RSVD_GRAM_TC = 0, RSVD_GRAM_DOT2 = 1 };
+rsvd_status rsvd_gram_f32(rsvd_plan_t plan, const float* Y, int64_t ldy, int64_t n, int32_t l, double* G,
+                          int32_t method);
 
 /* Symmetric storage.  For symmetric V the singular triplets pair as
  * v_i = sign(lambda_i) u_i (lambda_i the eigenvalue of magnitude sigma_i), so

@@ -258,6 +258,67 @@ rsvd_status rsvd_rule_rows(rsvd_plan_t P, const rsvd_matrix* A, int64_t r0, int3
   return RSVD_OK;
 }
 
+rsvd_status rsvd_gram_f32(rsvd_plan_t P, const float* Y, int64_t ldy, int64_t n, int32_t l, double* G,
+                          int32_t method) {
+  g_err[0] = 0;
+  if (!P || !Y || !G) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n > 2000000000LL / 64 || l < 1 || l > 4096 || ldy < n)
+    return seterr(RSVD_ERR_INVALID_ARG, "n = %lld, l = %d, ldy = %lld out of range", (long long)n, l, (long long)ldy);
+  const int nn = (int)n;
+  if (method == RSVD_GRAM_TC) {
+    if (l > 128) return seterr(RSVD_ERR_UNSUPPORTED, "tensor-core Gram needs l <= 128 (l = %d)", l);
+    if ((ldy % 4) != 0 || ((uintptr_t)Y % 16) != 0)
+      return seterr(RSVD_ERR_UNSUPPORTED, "tensor-core Gram needs ldy %% 4 == 0 and a 16-byte aligned Y");
+    const int nt = cdiv(nn, 128);
+    const size_t pb = ((size_t)gram_tc_part_floats(nn) * sizeof(float) + 255) & ~(size_t)255;
+    const size_t eb = ((size_t)nt * 128 * sizeof(int) + 255) & ~(size_t)255;
+    if (rsvd_status s = grow_ws(P, pb + eb + sizeof(GramTcDesc) + 256)) return s;
+    if (rsvd_status s = grow_pinned(P, sizeof(GramTcDesc))) return s;
+    GramTcDesc* hd = (GramTcDesc*)P->hp;
+    *hd = GramTcDesc{Y, ldy, nn, l, 0, nt, (float*)P->ws, (int*)(P->ws + pb), G};
+    GramTcDesc* dd = (GramTcDesc*)(P->ws + pb + eb);
+    CK(cudaMemcpyAsync(dd, hd, sizeof(GramTcDesc), cudaMemcpyHostToDevice, P->st));
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+    if (int e = launch_gram_tc(dd, 1, nt, P->d_err, P->st))
+      return seterr(RSVD_ERR_CUDA, "tensor-core Gram launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  } else if (method == RSVD_GRAM_DOT2) {
+    const int gs = std::max(1, std::min(cdiv(nn, 512), 64));
+    MMDesc m{};
+    m.A = Y; m.lda = ldy; m.B = Y; m.ldb = ldy;
+    m.m = l; m.n = l; m.k = nn;
+    m.mt = cdiv(l, 64); m.nt = cdiv(l, 64);
+    m.kchunk = (int)rup(cdiv(nn, gs), 16);
+    m.ks = cdiv(nn, m.kchunk);
+    m.mode = MM_PARTIAL; m.sym = 1;
+    m.ldc = l; m.pstride = (int64_t)l * l;
+    m.tile = tile_of(MMK_GRAM_DOT2);
+    const int tiles = m.mt * m.nt * m.ks;
+    const size_t gb = ((size_t)m.ks * l * l * sizeof(double) + 255) & ~(size_t)255;
+    if (rsvd_status s = grow_ws(P, gb + 256 + 256)) return s;
+    if (rsvd_status s = grow_pinned(P, 256)) return s;
+    m.Cm = P->ws;
+    char* hp = (char*)P->hp;
+    memcpy(hp, &m, sizeof(MMDesc));
+    const int off[2] = {0, tiles};
+    memcpy(hp + 192, off, sizeof(off));
+    memcpy(hp + 208, &G, sizeof(double*));
+    static_assert(sizeof(MMDesc) <= 192, "descriptor block");
+    CK(cudaMemcpyAsync(P->ws + gb, hp, 256, cudaMemcpyHostToDevice, P->st));
+    const MMDesc* dm = (const MMDesc*)(P->ws + gb);
+    launch_tile_mm(MMK_GRAM_DOT2, dm, (const int*)(P->ws + gb + 192), 1, tiles, P->st);
+    launch_reduce_partials(dm, (double* const*)(P->ws + gb + 208), 1, l * l, P->st);
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  } else {
+    return seterr(RSVD_ERR_INVALID_ARG, "unknown Gram method %d", method);
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  CK(cudaGetLastError());
+  if (herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", herr);
+  return RSVD_OK;
+}
+
 rsvd_status rsvd_decompose(rsvd_plan_t P, const rsvd_matrix* A, rsvd_factors* f) {
   return rsvd_decompose_batched(P, 1, A, f, nullptr);
 }

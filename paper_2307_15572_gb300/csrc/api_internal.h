@@ -183,6 +183,7 @@ enum JobKind { JOB_MAIN = 0, JOB_PROBE = 1 };
 
 struct ProbeOut { float* feat = nullptr; float* pred = nullptr; };
 
+bool gram_tc_enabled(const Job& J);
 rsvd_status grow_pinned(rsvd_plan_s* P, size_t bytes);
 rsvd_status grow_ws(rsvd_plan_s* P, size_t bytes);
 void timed_begin(rsvd_plan_s* P, cudaEvent_t* a, cudaEvent_t* b);

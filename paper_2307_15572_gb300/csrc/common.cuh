@@ -199,6 +199,8 @@ struct Chan {
   double* scr;              // l doubles of scratch (unsorted column norms)
   double* gpart;            // Gram partials
   int gsplit;               // number of row splits of the Gram
+  float* gtc_part;          // tensor-core Gram tile partials (mixed path, l <= 128), or null
+  int* gtc_exp;             // their column exponents
   double* fro_part;         // ||A||^2 partials (one per 64-row block; 8-row on the mixed path)
   // mixed path
   double* wres_part;        // word-split remainder energy partials (one per 8-row block)

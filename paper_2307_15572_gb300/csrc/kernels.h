@@ -52,6 +52,22 @@ void launch_tile_mm(MMKind kind, const MMDesc* d_md, const int* d_off, int C, in
 void launch_reduce_partials(const MMDesc* d_md, double* const* d_out, int C, int max_elems,
                             cudaStream_t st);
 
+// Tensor-core Gram G = Y^T Y of an FP32 panel (mixed path, l <= 128) to
+// FP64-grade accuracy: per channel the panel (column-major, ldy a multiple of
+// 4, 16-byte aligned), the workspace of its 128-row tiles (gram_tc_part_floats
+// floats, 128 ints per tile) and the FP64 output (l x l, leading dim l, both
+// triangles).  Two launches; returns a cudaError_t value.
+struct GramTcDesc {
+  const float* Y; int64_t ldy;
+  int n, l;
+  int tile0, ntiles;        // first tile of the channel in the launch, its tile count
+  float* part;              // ntiles x {hi, lo} x 128 x 128
+  int* exps;                // ntiles x 128 column exponents
+  double* G;
+};
+int launch_gram_tc(const GramTcDesc* d_gd, int C, int tiles, int* d_err, cudaStream_t st);
+int gram_tc_part_floats(int n);
+
 // ------------------------------------------------------------ small kernels
 // ||A||_F^2 partials per 64-row block, non-finite detection (dense input).
 void launch_fro2(const Chan* d_ch, const int* d_off_rows64, int C, int tiles, cudaStream_t st);

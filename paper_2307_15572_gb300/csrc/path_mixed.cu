@@ -315,6 +315,49 @@ void add_cvt_f32(Job& J, std::function<const double*(int)> src, std::function<in
   });
 }
 
+// G = Y^T Y of each channel's n x l FP32 panel (leading dim ldt) into its G:
+// on the tensor cores (k_gram_tc, split into exact BF16 slices) where the job
+// allows it, else with the compensated (Dot2) Gram on the CUDA cores.  Both
+// are FP64-grade.
+void add_gram32(Job& J, std::function<const float*(int)> src) {
+  auto& ch = J.ch;
+  bool tc = gram_tc_enabled(J);
+  for (int c = 0; c < J.C && tc; ++c)
+    tc = ch[c].gtc_part && ch[c].gtc_exp && (J.d[c].ldt % 4) == 0 && ((uintptr_t)src(c) % 16) == 0;
+  if (!tc) {
+    add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)src(c); }, [&](int c) { return (const void*)src(c); },
+           [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+    return;
+  }
+  std::vector<GramTcDesc> gd(J.C);
+  int tiles = 0;
+  double flops = 0.0, mma = 0.0;
+  for (int c = 0; c < J.C; ++c) {
+    const ChanDims& d = J.d[c];
+    const int nt = cdiv(d.n, 128);
+    gd[c] = GramTcDesc{src(c), d.ldt, d.n, d.l, tiles, nt, ch[c].gtc_part, ch[c].gtc_exp, ch[c].G};
+    tiles += nt;
+    flops += 2.0 * d.n * d.l * d.l;
+    mma += 21.0 * 2.0 * 128.0 * 128.0 * 128.0 * nt;
+  }
+  const GramTcDesc* dgd = J.ar.put(gd.data(), gd.size());
+  const int C = J.C;
+  rsvd_plan_s* P = J.P;
+  cudaStream_t st = P->st;
+  int* derr = P->d_err;
+  J.steps.push_back([=]() {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (P->profiling) timed_begin(P, &ea, &eb);
+    if (int e = launch_gram_tc(dgd, C, tiles, derr, st))
+      return seterr(RSVD_ERR_CUDA, "tensor-core Gram launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    if (P->profiling) {
+      cudaEventRecord(eb, st);
+      P->pending.push_back({ea, eb, 4, mma, flops});
+    }
+    return RSVD_OK;
+  });
+}
+
 // CholeskyQR2 of Y32[:, 0:l) -> Q32 (FP32) and its BF16 words in Xb[:, 0:l).
 void cqr2_mixed(Job& J, int nsl_out) {
   auto& ch = J.ch;
@@ -322,11 +365,14 @@ void cqr2_mixed(Job& J, int nsl_out) {
     auto in = [&, round](int c) { return round == 0 ? ch[c].Y32 : ch[c].T32; };
     auto out = [&, round](int c) { return round == 0 ? ch[c].T32 : ch[c].Q32; };
     // round 0: Y has kappa up to ~1e5, so the Gram needs FP64-grade accuracy
-    // (compensated Dot2); round 1: Q1 is orthonormal to ~1e-2, a plain FP32
-    // Gram is accurate enough
-    add_tn(J, round == 0 ? MMK_GRAM_DOT2 : MMK_GRAM_F32, [&](int c) { return (const void*)in(c); },
-           [&](int c) { return (const void*)in(c); }, [&](int c) { return ch[c].G; },
-           [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+    // (tensor-core slices or compensated Dot2); round 1: Q1 is orthonormal to
+    // ~1e-2, a plain FP32 Gram is accurate enough
+    if (round == 0)
+      add_gram32(J, [&](int c) { return (const float*)in(c); });
+    else
+      add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)in(c); },
+             [&](int c) { return (const void*)in(c); }, [&](int c) { return ch[c].G; },
+             [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
     add_chol(J, 0, round == 1 ? 1 : 0);
     const bool b32 = ri32_ok(J);
     std::vector<MMDesc> md(J.C);
@@ -593,8 +639,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
   }
   const int maxl = J.max_l;
   // W^T W = R^T R
-  add_tn(J, MMK_GRAM_DOT2, [&](int c) { return (const void*)ch[c].Y32; }, [&](int c) { return (const void*)ch[c].Y32; },
-         [&](int c) { return ch[c].G; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].l; }, true);
+  add_gram32(J, [&](int c) { return (const float*)ch[c].Y32; });
   add_chol(J, 0);
   const int policy = J.policy;
   const double tol = J.tol;

@@ -88,6 +88,7 @@ void drain_profile(rsvd_plan_s* P) {
     if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
     else if (t.kind == 2) { P->prof.gen_launches++; P->prof.gen_ms += ms; P->prof.gen_flops += t.flops; P->prof.gen_mma_flops += t.bytes; }
     else if (t.kind == 3) { P->prof.cvt_launches++; P->prof.cvt_ms += ms; P->prof.cvt_bytes += t.bytes; }
+    else if (t.kind == 4) { P->prof.gram_launches++; P->prof.gram_ms += ms; P->prof.gram_flops += t.flops; P->prof.gram_mma_flops += t.bytes; }
     else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
   }
   P->pending.clear();
@@ -101,6 +102,15 @@ int pick_splits(int64_t tiles, int64_t k, int min_chunk, int64_t target) {
   int ks = (int)((target + tiles - 1) / tiles);
   int maxk = (int)std::max<int64_t>(1, k / min_chunk);
   return std::max(1, std::min(ks, maxk));
+}
+
+// The tensor-core Gram (k_gram_tc) serves the mixed path's n x l Grams when
+// every channel has l <= 128 (one 128 x 128 accumulator per level); the
+// environment variable RSVD_GRAM=dot2 keeps the CUDA-core compensated Gram.
+bool gram_tc_enabled(const Job& J) {
+  if (!J.mixed || J.max_l < 1 || J.max_l > 128) return false;
+  const char* e = getenv("RSVD_GRAM");
+  return !(e && strcmp(e, "dot2") == 0);
 }
 
 // Everything one batched call needs.
@@ -467,6 +477,10 @@ void layout(Job& J, Bump& b) {
       h.Q32 = b.take<float>((size_t)d.ldt * d.l);
       h.T32 = b.take<float>((size_t)d.ldt * d.l);
       h.gpart = b.take<double>((size_t)d.gsplit * d.l * std::max(d.l, d.s));
+      if (gram_tc_enabled(J)) {
+        h.gtc_part = b.take<float>((size_t)gram_tc_part_floats(d.n));
+        h.gtc_exp = b.take<int>((size_t)cdiv(d.n, 128) * 128);
+      }
       h.C64 = b.take<double>((size_t)d.l * std::max(d.s, 1));
       h.est_part = b.take<double>((size_t)std::max(d.s, 1) * (1 + d.l));
     }

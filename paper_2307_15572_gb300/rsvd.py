@@ -63,7 +63,9 @@ class Profile(C.Structure):
                 ("tc_bytes", C.c_double), ("tc_flops", C.c_double), ("f64_launches", C.c_int64),
                 ("f64_ms", C.c_double), ("f64_flops", C.c_double), ("gen_launches", C.c_int64),
                 ("gen_ms", C.c_double), ("gen_flops", C.c_double), ("gen_mma_flops", C.c_double),
-                ("cvt_launches", C.c_int64), ("cvt_ms", C.c_double), ("cvt_bytes", C.c_double)]
+                ("cvt_launches", C.c_int64), ("cvt_ms", C.c_double), ("cvt_bytes", C.c_double),
+                ("gram_launches", C.c_int64), ("gram_ms", C.c_double), ("gram_flops", C.c_double),
+                ("gram_mma_flops", C.c_double)]
 
 
 class TuneRecord(C.Structure):
@@ -143,6 +145,8 @@ def load(build=True):
     lib.rsvd_compression_ratio.restype = C.c_double
     lib.rsvd_rule_rows.argtypes = [P, C.POINTER(Matrix), C.c_int64, C.c_int32, P, C.c_int64]
     lib.rsvd_rule_rows.restype = C.c_int
+    lib.rsvd_gram_f32.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, P, C.c_int32]
+    lib.rsvd_gram_f32.restype = C.c_int
     _lib = lib
     return lib
 
@@ -269,6 +273,14 @@ def rsvd_reconstruct_error_noalloc(A, lda, n, U, ldu, S, V, ldv, k, rel_err, str
 def rsvd_rule_rows(h, mat, r0, rows, out, ldo):
     """Rows r0..r0+rows-1 of a tile rule into the device FP32 buffer `out` (row-major, ld ldo)."""
     return _check(load().rsvd_rule_rows(h, C.byref(mat), int(r0), int(rows), out, int(ldo)))
+
+
+RSVD_GRAM_TC, RSVD_GRAM_DOT2 = 0, 1
+
+
+def rsvd_gram_f32(h, Y, ldy, n, l, G, method=RSVD_GRAM_TC):
+    """G = Y^T Y (FP64-grade) of the device FP32 panel Y (n x l, column-major, ld ldy) into device G (l x l)."""
+    return _check(load().rsvd_gram_f32(h, Y, int(ldy), int(n), int(l), G, int(method)))
 
 
 def rsvd_transform_factors(h, fac, n, B, ldb, m, Lt, ldl, Rt, ldr):
