@@ -209,7 +209,8 @@ rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
  * (rsvd_plan_set_profiling(plan, 1)), each decomposition records CUDA events
  * on the plan's stream around every tensor-core pass, every FP64 dense pass
  * over V, every tile-rule generation, every conversion of V into words and
- * every tensor-core Gram of CholeskyQR, and adds their device time and algorithmic traffic (bytes of V words, X
+ * every tensor-core Gram of CholeskyQR and every tensor-core tall x small
+ * product, and adds their device time and algorithmic traffic (bytes of V words, X
  * words and Y read or written once, as the roofline counts them) to the
  * counters below.  Kernel launches are counted whether or not timing is
  * enabled.  rsvd_plan_profile copies the counters (host struct) and, if
@@ -234,6 +235,9 @@ typedef struct {
   double gram_ms;          /* (both kernels: slice products and tile reduction)  */
   double gram_flops;       /* algorithmic: 2 n l^2 per Gram                      */
   double gram_mma_flops;   /* issued: 21 slice products x 2 x 128^3 per tile     */
+  int64_t nn_launches;     /* tensor-core tall x small products (Y R^-1, lifts)   */
+  double nn_ms;
+  double nn_flops;         /* algorithmic: 2 n l N per product                   */
 } rsvd_profile;
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
@@ -319,19 +323,39 @@ rsvd_status rsvd_transform_factors(rsvd_plan_t plan, const rsvd_factors* f, int6
  *     the leading slice products summed exactly in TMEM and the tiles in
  *     double-float.  Needs l <= 128, ldy a multiple of 4 and Y 16-byte
  *     aligned.
+ *   method RSVD_GRAM_TC_F32: the same with three slices and only the exact
+ *     products (the Gram of Y rounded to 24 fractional bits of its tile-
+ *     column maxima): FP32-grade, for a Y that is already nearly
+ *     orthonormal (CholeskyQR's second round).
  *   method RSVD_GRAM_DOT2: CUDA cores, compensated dot products (Ogita,
  *     Rump & Oishi, 2005), any l.
- * Both agree with the exact Gram of the FP32 data to about 1e-14 of
- * ||y_i|| ||y_j||.  The decompositions of the mixed path use RSVD_GRAM_TC
+ * RSVD_GRAM_TC and RSVD_GRAM_DOT2 agree with the exact Gram of the FP32 data
+ * to about 1e-13 of ||y_i|| ||y_j||, RSVD_GRAM_TC_F32 to about 2^-23.  The decompositions of the mixed path use RSVD_GRAM_TC
  * where every channel has l <= 128 (unless the environment variable
  * RSVD_GRAM=dot2 is set when the call is built).  Uses the plan's workspace
  * and stream and returns after the stream has completed.
  * RSVD_ERR_INVALID_ARG for NULL pointers, n < 1, l < 1, ldy < n or a bad
- * method; RSVD_ERR_UNSUPPORTED for RSVD_GRAM_TC with l > 128 or a misaligned
- * Y; RSVD_ERR_TIMEOUT if a bounded device wait expired. */
-enum { RSVD_GRAM_TC = 0, RSVD_GRAM_DOT2 = 1 };
+ * method; RSVD_ERR_UNSUPPORTED for a tensor-core method with l > 128 or a
+ * misaligned Y; RSVD_ERR_TIMEOUT if a bounded device wait expired. */
+enum { RSVD_GRAM_TC = 0, RSVD_GRAM_DOT2 = 1, RSVD_GRAM_TC_F32 = 2 };
 rsvd_status rsvd_gram_f32(rsvd_plan_t plan, const float* Y, int64_t ldy, int64_t n, int32_t l, double* G,
                           int32_t method);
+
+/* Tall x small product C = A B on the tensor cores, FP32-grade: the product
+ * behind CholeskyQR's Q = Y R^{-1} and the lifts U = Q X, V = W X Sigma^{-1}
+ * of the paper's step 3 on the mixed path.  A (DEVICE, n x K FP32,
+ * column-major, lda >= n), B (DEVICE, K x N, FP64 if b_fp64 else FP32,
+ * column-major, ldb >= K), C (DEVICE, n x N, FP64 if c_fp64 else FP32,
+ * column-major, ldc >= n), 1 <= K, N <= 128.  Each row of A and each column
+ * of B is split into three 8-bit fixed-point BF16 slices (after a power-of-
+ * two scaling), the slice products summed exactly in TMEM: C is the exact
+ * product of A and B rounded to 24 fractional bits of their row (column)
+ * maxima, rounded once to FP32 (C FP64: that FP32 value, widened).  Uses the
+ * plan's workspace and stream and returns after the stream has completed.
+ * RSVD_ERR_INVALID_ARG for NULL pointers or bad sizes, RSVD_ERR_UNSUPPORTED
+ * for K or N above 128, RSVD_ERR_TIMEOUT if a bounded device wait expired. */
+rsvd_status rsvd_panel_product(rsvd_plan_t plan, const float* A, int64_t lda, int64_t n, int32_t K, const void* B,
+                               int64_t ldb, int32_t b_fp64, int32_t N, void* C, int64_t ldc, int32_t c_fp64);
 
 /* Symmetric storage.  For symmetric V the singular triplets pair as
  * v_i = sign(lambda_i) u_i (lambda_i the eigenvalue of magnitude sigma_i), so

@@ -265,7 +265,7 @@ rsvd_status rsvd_gram_f32(rsvd_plan_t P, const float* Y, int64_t ldy, int64_t n,
   if (n < 1 || n > 2000000000LL / 64 || l < 1 || l > 4096 || ldy < n)
     return seterr(RSVD_ERR_INVALID_ARG, "n = %lld, l = %d, ldy = %lld out of range", (long long)n, l, (long long)ldy);
   const int nn = (int)n;
-  if (method == RSVD_GRAM_TC) {
+  if (method == RSVD_GRAM_TC || method == RSVD_GRAM_TC_F32) {
     if (l > 128) return seterr(RSVD_ERR_UNSUPPORTED, "tensor-core Gram needs l <= 128 (l = %d)", l);
     if ((ldy % 4) != 0 || ((uintptr_t)Y % 16) != 0)
       return seterr(RSVD_ERR_UNSUPPORTED, "tensor-core Gram needs ldy %% 4 == 0 and a 16-byte aligned Y");
@@ -279,7 +279,7 @@ rsvd_status rsvd_gram_f32(rsvd_plan_t P, const float* Y, int64_t ldy, int64_t n,
     GramTcDesc* dd = (GramTcDesc*)(P->ws + pb + eb);
     CK(cudaMemcpyAsync(dd, hd, sizeof(GramTcDesc), cudaMemcpyHostToDevice, P->st));
     CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
-    if (int e = launch_gram_tc(dd, 1, nt, P->d_err, P->st))
+    if (int e = launch_gram_tc(dd, 1, nt, method == RSVD_GRAM_TC_F32 ? 1 : 0, P->d_err, P->st))
       return seterr(RSVD_ERR_CUDA, "tensor-core Gram launch failed: %s", cudaGetErrorString((cudaError_t)e));
   } else if (method == RSVD_GRAM_DOT2) {
     const int gs = std::max(1, std::min(cdiv(nn, 512), 64));
@@ -304,10 +304,10 @@ rsvd_status rsvd_gram_f32(rsvd_plan_t P, const float* Y, int64_t ldy, int64_t n,
     memcpy(hp + 208, &G, sizeof(double*));
     static_assert(sizeof(MMDesc) <= 192, "descriptor block");
     CK(cudaMemcpyAsync(P->ws + gb, hp, 256, cudaMemcpyHostToDevice, P->st));
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
     const MMDesc* dm = (const MMDesc*)(P->ws + gb);
     launch_tile_mm(MMK_GRAM_DOT2, dm, (const int*)(P->ws + gb + 192), 1, tiles, P->st);
     launch_reduce_partials(dm, (double* const*)(P->ws + gb + 208), 1, l * l, P->st);
-    CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
   } else {
     return seterr(RSVD_ERR_INVALID_ARG, "unknown Gram method %d", method);
   }
@@ -315,6 +315,38 @@ rsvd_status rsvd_gram_f32(rsvd_plan_t P, const float* Y, int64_t ldy, int64_t n,
   CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
   CK(cudaGetLastError());
+  if (herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", herr);
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_panel_product(rsvd_plan_t P, const float* A, int64_t lda, int64_t n, int32_t K, const void* B,
+                               int64_t ldb, int32_t b_fp64, int32_t N, void* Cout, int64_t ldc, int32_t c_fp64) {
+  g_err[0] = 0;
+  if (!P || !A || !B || !Cout) return seterr(RSVD_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n > 2000000000LL / 64 || K < 1 || N < 1 || lda < n || ldb < K || ldc < n)
+    return seterr(RSVD_ERR_INVALID_ARG, "n = %lld, K = %d, N = %d or a leading dimension out of range", (long long)n,
+                  K, N);
+  if (K > 128 || N > 128) return seterr(RSVD_ERR_UNSUPPORTED, "tensor-core product needs K, N <= 128");
+  const size_t ib = ((size_t)nn_tc_img_bytes() + 255) & ~(size_t)255;
+  if (rsvd_status s = grow_ws(P, ib + 512 + 256 + sizeof(NnTcDesc))) return s;
+  if (rsvd_status s = grow_pinned(P, sizeof(NnTcDesc))) return s;
+  NnTcDesc* hd = (NnTcDesc*)P->hp;
+  memset(hd, 0, sizeof(NnTcDesc));
+  hd->A = A; hd->lda = lda;
+  hd->n = (int)n; hd->K = K; hd->N = N;
+  hd->B = B; hd->ldb = ldb; hd->b64 = b_fp64 ? 1 : 0;
+  hd->bimg = P->ws;
+  hd->fexp = (int*)(P->ws + ib);
+  if (c_fp64) hd->C64 = (double*)Cout; else hd->C32 = (float*)Cout;
+  hd->ldc = ldc;
+  NnTcDesc* dd = (NnTcDesc*)(P->ws + ib + 512);
+  CK(cudaMemcpyAsync(dd, hd, sizeof(NnTcDesc), cudaMemcpyHostToDevice, P->st));
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->st));
+  if (int e = launch_nn_tc(dd, 1, cdiv((int)n, 128), P->d_err, P->st))
+    return seterr(RSVD_ERR_CUDA, "tensor-core product launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
   if (herr) return seterr(RSVD_ERR_TIMEOUT, "a bounded device wait expired (code %d)", herr);
   return RSVD_OK;
 }

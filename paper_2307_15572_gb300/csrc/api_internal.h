@@ -184,6 +184,8 @@ enum JobKind { JOB_MAIN = 0, JOB_PROBE = 1 };
 struct ProbeOut { float* feat = nullptr; float* pred = nullptr; };
 
 bool gram_tc_enabled(const Job& J);
+bool nn_tc_enabled(const Job& J);
+void add_nn(Job& J, MMKind kind, std::vector<MMDesc> md);
 rsvd_status grow_pinned(rsvd_plan_s* P, size_t bytes);
 rsvd_status grow_ws(rsvd_plan_s* P, size_t bytes);
 void timed_begin(rsvd_plan_s* P, cudaEvent_t* a, cudaEvent_t* b);

@@ -201,6 +201,8 @@ struct Chan {
   int gsplit;               // number of row splits of the Gram
   float* gtc_part;          // tensor-core Gram tile partials (mixed path, l <= 128), or null
   int* gtc_exp;             // their column exponents
+  void* nn_bimg;            // tensor-core tall x small products: the small operand's slice image
+  int* nn_fexp;             // and its column exponents
   double* fro_part;         // ||A||^2 partials (one per 64-row block; 8-row on the mixed path)
   // mixed path
   double* wres_part;        // word-split remainder energy partials (one per 8-row block)

@@ -22,7 +22,8 @@
 // column maxima give the exponents, the slices go to shared memory in the
 // 128B-swizzled K-major layout (M = columns of Y, K = rows of the tile), one
 // thread issues the 21 slice-pair MMAs (M = N = 128, K = 16, eight k steps)
-// into the four accumulators, and the epilogue (eight warps: TMEM lane
+// into the four accumulators (an FP32-grade form takes three slices and the
+// six exact products of levels 2-4), and the epilogue (eight warps: TMEM lane
 // quarter x column half) adds the three exact levels and the rest into a
 // double-float pair (hi, lo) per entry -- exact but for the rest -- and
 // stores the upper triangle with the tile's column exponents.
@@ -54,16 +55,25 @@ RSVD_DEV int gt_chan(const GramTcDesc* __restrict__ gd, int C, int t) {
   return lo;
 }
 
-// 2^k as FP32 for k <= 127 (0 below the normal range).
-RSVD_DEV float gt_pow2f(int k) { return k < -126 ? 0.0f : __uint_as_float((uint32_t)(127 + k) << 23); }
-
-RSVD_DEV uint32_t gt_pack(float lo, float hi) {
-  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);   // both exact: at most nine significant bits
-  return *reinterpret_cast<const uint32_t*>(&p);
-}
-
-RSVD_DEV void gt_st16(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+// Rows 64h .. 64h + 63 of tile t, column m (zero outside n x l): 16-byte
+// loads along the column.
+RSVD_DEV void gt_load(const GramTcDesc* __restrict__ gd, int C, int t, int m, int h, float (&v)[64]) {
+  const GramTcDesc* g = gd + gt_chan(gd, C, t);
+  const int r0 = (t - g->tile0) * GT_ROWS + 64 * h;
+  const int rows = g->n - r0;
+  if (m < g->l && rows >= 64) {
+    const float4* src = reinterpret_cast<const float4*>(g->Y + (int64_t)m * g->ldy + r0);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float4 f = __ldg(src + q);
+      v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+    }
+  } else {
+    const float* src = g->Y + (int64_t)m * g->ldy + r0;
+    const bool col = m < g->l;
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = (col && k < rows) ? __ldg(src + k) : 0.0f;
+  }
 }
 
 // Slice pairs (s, t) in issue order and their accumulator (0: level 2,
@@ -74,6 +84,10 @@ __constant__ unsigned char c_gt_pairs[21][3] = {
     {0, 4, 3}, {1, 3, 3}, {2, 2, 3}, {3, 1, 3}, {4, 0, 3},
     {0, 3, 3}, {1, 2, 3}, {2, 1, 3}, {3, 0, 3}};
 
+// NS = 6: 21 products, FP64-grade; NS = 3: the 6 products of levels 2-4
+// (all exact), the Gram of the operand rounded to 24 fractional bits of its
+// tile-column maxima: FP32-grade.
+template <int NS>
 __global__ void __launch_bounds__(GT_THREADS, 1)
 k_gram_tc(const GramTcDesc* __restrict__ gd, int C, int tiles, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
@@ -97,69 +111,31 @@ k_gram_tc(const GramTcDesc* __restrict__ gd, int C, int tiles, int* __restrict__
   const int qd = warp & 3, chalf = warp >> 2;        // epilogue: TMEM lanes 32 qd.., columns 64 chalf..
   int it = 0;
   bool healthy = true;
+  float v[64];
+  if (blockIdx.x < tiles) gt_load(gd, C, blockIdx.x, m, h, v);
   for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
     const GramTcDesc* g = gd + gt_chan(gd, C, t);
     const int local = t - g->tile0;
-    const int r0 = local * GT_ROWS;
-    const int n = g->n, l = g->l;
+    const int l = g->l;
 
-    // ---- the thread's 64 entries and the column maximum
-    float v[64];
+    // ---- the column maximum of the loaded entries
     float mx = 0.0f;
-    if (m < l) {
-      const float* src = g->Y + (int64_t)m * g->ldy + r0 + 64 * h;
-      const int rows = n - (r0 + 64 * h);
-      if (rows >= 64) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float4 f = __ldg(reinterpret_cast<const float4*>(src) + q);
-          v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = k < rows ? __ldg(src + k) : 0.0f;
-      }
-#pragma unroll
-      for (int k = 0; k < 64; ++k) mx = fmaxf(mx, fabsf(v[k]));
-    } else {
-#pragma unroll
-      for (int k = 0; k < 64; ++k) v[k] = 0.0f;
-    }
+    for (int k = 0; k < 64; ++k) mx = fmaxf(mx, fabsf(v[k]));
     smax[h * 128 + m] = mx;
     __syncthreads();
-    // cm < 2^e for normal cm; zero and subnormal maxima take the floor -126,
-    // a non-finite one the ceiling (and propagates through the slices)
-    const float cm = fmaxf(smax[m], smax[128 + m]);
-    int e = (int)((__float_as_uint(cm) >> 23) & 0xFFu) - 126;
-    e = max(-126, min(126, e));
+    // a non-finite maximum takes the ceiling exponent (and propagates through
+    // the slices)
+    const int e = slice_exp(fmaxf(smax[m], smax[128 + m]));
     if (h == 0) g->exps[local * 128 + m] = e;
-    const float sc = gt_pow2f(-e);
-
-    // ---- six slices, 8 rows (one 16-byte chunk per slice) at a time
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      uint32_t w[GT_SLICES][4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        float x0 = v[8 * q + 2 * p] * sc, x1 = v[8 * q + 2 * p + 1] * sc;
-#pragma unroll
-        for (int s = 0; s < GT_SLICES; ++s) {
-          const float up = __uint_as_float((uint32_t)(127 + 8 * (s + 1)) << 23);
-          const float dn = __uint_as_float((uint32_t)(127 - 8 * (s + 1)) << 23);
-          const float d0 = rintf(x0 * up) * dn, d1 = rintf(x1 * up) * dn;
-          x0 -= d0;                                    // exact: the bits below 2^(-8(s+1))
-          x1 -= d1;
-          w[s][p] = gt_pack(d0, d1);
-        }
-      }
-      const uint32_t off = (uint32_t)(h * GT_HALF_BYTES + m * 128 + ((q ^ (m & 7)) << 4));
-#pragma unroll
-      for (int s = 0; s < GT_SLICES; ++s)
-        gt_st16(sbase + (uint32_t)(s * GT_SLICE_BYTES) + off, w[s][0], w[s][1], w[s][2], w[s][3]);
-    }
+    slice_row64<NS>(v, pow2f_exp(-e), m, h, [&](int s, uint32_t off, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+      st_shared_v4(sbase + (uint32_t)(s * GT_SLICE_BYTES) + off, a, b, c, d);
+    });
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
+    // the next tile's entries load while this one is multiplied and stored
+    if (t + (int)gridDim.x < tiles) gt_load(gd, C, t + gridDim.x, m, h, v);
 
     // ---- the 21 slice-pair products into the four accumulators
     if (tid == 0) {
@@ -167,7 +143,7 @@ k_gram_tc(const GramTcDesc* __restrict__ gd, int C, int tiles, int* __restrict__
       const uint32_t idesc = idesc_bf16(128);
       int last = -1;
 #pragma unroll 1
-      for (int p = 0; p < 21; ++p) {
+      for (int p = 0; p < (NS == 6 ? 21 : 6); ++p) {
         const int sa = c_gt_pairs[p][0], sb = c_gt_pairs[p][1], acc = c_gt_pairs[p][2];
         const bool first = acc != last;
         last = acc;
@@ -204,7 +180,7 @@ k_gram_tc(const GramTcDesc* __restrict__ gd, int C, int tiles, int* __restrict__
         tmem_ld16_nw(ta, a2);
         tmem_ld16_nw(ta + 128, a3);
         tmem_ld16_nw(ta + 256, a4);
-        tmem_ld16_nw(ta + 384, ar);
+        if (NS == 6) tmem_ld16_nw(ta + 384, ar);
         tmem_wait_ld();
         if (i < l) {
 #pragma unroll
@@ -212,7 +188,7 @@ k_gram_tc(const GramTcDesc* __restrict__ gd, int C, int tiles, int* __restrict__
             const int j = j0 + jj;
             if (j < i || j >= l) continue;
             const float v2 = __uint_as_float(a2[jj]), v3 = __uint_as_float(a3[jj]);
-            const float v4 = __uint_as_float(a4[jj]), vr = __uint_as_float(ar[jj]);
+            const float v4 = __uint_as_float(a4[jj]), vr = NS == 6 ? __uint_as_float(ar[jj]) : 0.0f;
             float s1 = v2 + v3, bb = s1 - v2;
             const float e1 = (v2 - (s1 - bb)) + (v3 - bb);
             const float s2 = s1 + v4;
@@ -264,12 +240,12 @@ k_gram_tc_reduce(const GramTcDesc* __restrict__ gd, int C) {
       const int f = __ldg(ex + i) + __ldg(ex + j);
       const float bh = __ldg(P), bl = __ldg(P + 128 * 128);
       if (f > F) {                                    // a larger unit: rescale the sum (exactly)
-        const float r = gt_pow2f(F - f);
+        const float r = pow2f_exp(F - f);
         sh *= r;
         sl *= r;
         F = f;
       }
-      const float w = gt_pow2f(f - F);
+      const float w = pow2f_exp(f - F);
       gt_df_add(sh, sl, bh * w, bl * w);
     }
     const double u = __longlong_as_double((long long)(1023 + F) << 52);   // 2^F, |F| <= 252
@@ -280,16 +256,20 @@ k_gram_tc_reduce(const GramTcDesc* __restrict__ gd, int C) {
   (void)C;
 }
 
-int launch_gram_tc(const GramTcDesc* d_gd, int C, int tiles, int* d_err, cudaStream_t st) {
+int launch_gram_tc(const GramTcDesc* d_gd, int C, int tiles, int fp32_grade, int* d_err, cudaStream_t st) {
   if (tiles <= 0 || C <= 0) return 0;
-  const cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
+  // both forms take the six-slice shared memory: one CTA per SM, so that no
+  // second CTA waits on the TMEM allocation
+  const cudaError_t e = cudaFuncSetAttribute(fp32_grade ? k_gram_tc<3> : k_gram_tc<6>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
   if (e != cudaSuccess) return (int)e;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       nsm < 1)
     nsm = 148;
   const int grid = tiles < nsm ? tiles : nsm;
-  k_gram_tc<<<grid, GT_THREADS, GT_SMEM, st>>>(d_gd, C, tiles, d_err);
+  if (fp32_grade) k_gram_tc<3><<<grid, GT_THREADS, GT_SMEM, st>>>(d_gd, C, tiles, d_err);
+  else k_gram_tc<6><<<grid, GT_THREADS, GT_SMEM, st>>>(d_gd, C, tiles, d_err);
   note_launch();
   k_gram_tc_reduce<<<dim3(64, C), 256, 0, st>>>(d_gd, C);
   note_launch();

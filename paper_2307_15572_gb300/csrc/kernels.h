@@ -65,8 +65,37 @@ struct GramTcDesc {
   int* exps;                // ntiles x 128 column exponents
   double* G;
 };
-int launch_gram_tc(const GramTcDesc* d_gd, int C, int tiles, int* d_err, cudaStream_t st);
+// fp32_grade: three slices and the exact products of levels 2-4 only.
+int launch_gram_tc(const GramTcDesc* d_gd, int C, int tiles, int fp32_grade, int* d_err, cudaStream_t st);
 int gram_tc_part_floats(int n);
+
+// Tensor-core product C = A B of a tall FP32 panel A (n x K, K <= 128,
+// column-major lda) and a small B (K x N, N <= 128, FP32 or FP64 (b64),
+// column-major ldb, columns optionally scaled by colscale): C32 (FP32, with
+// nsl BF16 words into sl) or C64 (FP64), leading dim ldc; columns from
+// *ncols_dev on are not written; channels with cond set and the shifted
+// flag clear are skipped.  bimg (nn_tc_img_bytes(), 16-byte aligned) and
+// fexp (128 ints) are per-channel scratch.  Two launches.
+struct NnTcDesc {
+  const float* A; int64_t lda;
+  int n, K, N;
+  int tile0;
+  const void* B; int64_t ldb;
+  int b64;
+  const double* colscale;
+  void* bimg;
+  int* fexp;
+  float* C32;
+  double* C64;
+  int64_t ldc;
+  __nv_bfloat16* sl[3];
+  int64_t ldsl;
+  int nsl;
+  const int* ncols_dev;
+  const int* cond;
+};
+int launch_nn_tc(const NnTcDesc* d_nd, int C, int tiles, int* d_err, cudaStream_t st);
+int nn_tc_img_bytes();
 
 // ------------------------------------------------------------ small kernels
 // ||A||_F^2 partials per 64-row block, non-finite detection (dense input).

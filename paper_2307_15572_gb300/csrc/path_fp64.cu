@@ -173,7 +173,8 @@ void lift(Job& J, MMKind kind, std::function<const void*(int)> basis, std::funct
     m.ncols_dev = &J.d_res[c].k_out;
     md[c] = m;
   }
-  add_mm(J, kind, md);
+  if (J.mixed) add_nn(J, kind, md);      // the tensor-core product where it applies
+  else add_mm(J, kind, md);
 }
 
 // FP64 path, tile rule: one pass Y = V X generates V row panel by row panel

@@ -315,11 +315,70 @@ void add_cvt_f32(Job& J, std::function<const double*(int)> src, std::function<in
   });
 }
 
+// Tall x small products C = A B of the mixed path (CholeskyQR's Y R^{-1},
+// the lifts, the re-orthonormalisation of X): on the tensor cores
+// (k_nn_tc, exact BF16 slices, FP32-grade) where the job allows it and every
+// product is a plain store with k, n <= 128, else the CUDA-core FP32 kernel.
+void add_nn(Job& J, MMKind kind, std::vector<MMDesc> md) {
+  const bool out64 = kind == MMK_NN_F32_OUT64 || kind == MMK_NN_F32_OUT64_B32;
+  const bool b64 = kind == MMK_NN_F32_F64B || kind == MMK_NN_F32_OUT64;
+  bool tc = nn_tc_enabled(J) && (out64 || kind == MMK_NN_F32 || kind == MMK_NN_F32_F64B) &&
+            (int)md.size() == J.C;
+  for (int c = 0; c < (int)md.size() && tc; ++c) {
+    const MMDesc& m = md[c];
+    tc = m.mode == MM_STORE && m.k >= 1 && m.k <= 128 && m.n >= 1 && m.n <= 128 && m.m >= 1 &&
+         J.ch[c].nn_bimg && J.ch[c].nn_fexp && (!out64 || m.nsl == 0);
+  }
+  if (!tc) {
+    add_mm(J, kind, std::move(md));
+    return;
+  }
+  std::vector<NnTcDesc> nd(J.C);
+  int tiles = 0;
+  double flops = 0.0;
+  for (int c = 0; c < J.C; ++c) {
+    const MMDesc& m = md[c];
+    NnTcDesc x{};
+    x.A = (const float*)m.A; x.lda = m.lda;
+    x.n = m.m; x.K = m.k; x.N = m.n;
+    x.tile0 = tiles;
+    x.B = m.B; x.ldb = m.ldb; x.b64 = b64 ? 1 : 0;
+    x.colscale = m.colscale;
+    x.bimg = J.ch[c].nn_bimg; x.fexp = J.ch[c].nn_fexp;
+    if (out64) x.C64 = (double*)m.Cm; else x.C32 = (float*)m.Cm;
+    x.ldc = m.ldc;
+    for (int w = 0; w < 3; ++w) x.sl[w] = m.sl[w];
+    x.ldsl = m.ldsl; x.nsl = m.nsl;
+    x.ncols_dev = m.ncols_dev;
+    x.cond = m.cond;
+    nd[c] = x;
+    tiles += cdiv(m.m, 128);
+    flops += 2.0 * m.m * (double)m.n * m.k;
+  }
+  const NnTcDesc* dnd = J.ar.put(nd.data(), nd.size());
+  const int C = J.C;
+  rsvd_plan_s* P = J.P;
+  cudaStream_t st = P->st;
+  int* derr = P->d_err;
+  J.steps.push_back([=]() {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (P->profiling) timed_begin(P, &ea, &eb);
+    if (int e = launch_nn_tc(dnd, C, tiles, derr, st))
+      return seterr(RSVD_ERR_CUDA, "tensor-core product launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    if (P->profiling) {
+      cudaEventRecord(eb, st);
+      P->pending.push_back({ea, eb, 5, 0.0, flops});
+    }
+    return RSVD_OK;
+  });
+}
+
 // G = Y^T Y of each channel's n x l FP32 panel (leading dim ldt) into its G:
 // on the tensor cores (k_gram_tc, split into exact BF16 slices) where the job
 // allows it, else with the compensated (Dot2) Gram on the CUDA cores.  Both
-// are FP64-grade.
-void add_gram32(Job& J, std::function<const float*(int)> src) {
+// are FP64-grade; fp32_grade asks only for FP32 accuracy (the tensor-core
+// form then takes three slices instead of six).
+void add_gram32(Job& J, std::function<const float*(int)> src, bool fp32_grade) {
   auto& ch = J.ch;
   bool tc = gram_tc_enabled(J);
   for (int c = 0; c < J.C && tc; ++c)
@@ -338,7 +397,7 @@ void add_gram32(Job& J, std::function<const float*(int)> src) {
     gd[c] = GramTcDesc{src(c), d.ldt, d.n, d.l, tiles, nt, ch[c].gtc_part, ch[c].gtc_exp, ch[c].G};
     tiles += nt;
     flops += 2.0 * d.n * d.l * d.l;
-    mma += 21.0 * 2.0 * 128.0 * 128.0 * 128.0 * nt;
+    mma += (fp32_grade ? 6.0 : 21.0) * 2.0 * 128.0 * 128.0 * 128.0 * nt;
   }
   const GramTcDesc* dgd = J.ar.put(gd.data(), gd.size());
   const int C = J.C;
@@ -348,7 +407,7 @@ void add_gram32(Job& J, std::function<const float*(int)> src) {
   J.steps.push_back([=]() {
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (P->profiling) timed_begin(P, &ea, &eb);
-    if (int e = launch_gram_tc(dgd, C, tiles, derr, st))
+    if (int e = launch_gram_tc(dgd, C, tiles, fp32_grade ? 1 : 0, derr, st))
       return seterr(RSVD_ERR_CUDA, "tensor-core Gram launch failed: %s", cudaGetErrorString((cudaError_t)e));
     if (P->profiling) {
       cudaEventRecord(eb, st);
@@ -366,9 +425,10 @@ void cqr2_mixed(Job& J, int nsl_out) {
     auto out = [&, round](int c) { return round == 0 ? ch[c].T32 : ch[c].Q32; };
     // round 0: Y has kappa up to ~1e5, so the Gram needs FP64-grade accuracy
     // (tensor-core slices or compensated Dot2); round 1: Q1 is orthonormal to
-    // ~1e-2, a plain FP32 Gram is accurate enough
-    if (round == 0)
-      add_gram32(J, [&](int c) { return (const float*)in(c); });
+    // ~1e-2 and an FP32 Gram would do, but the tensor-core Gram is faster
+    // than the CUDA-core FP32 one as well
+    if (round == 0 || gram_tc_enabled(J))
+      add_gram32(J, [&](int c) { return (const float*)in(c); }, round == 1);
     else
       add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)in(c); },
              [&](int c) { return (const void*)in(c); }, [&](int c) { return ch[c].G; },
@@ -392,7 +452,7 @@ void cqr2_mixed(Job& J, int nsl_out) {
       }
       md[c] = m;
     }
-    add_mm(J, b32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
+    add_nn(J, b32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
   }
   // Conditional third round, only for channels whose Cholesky needed the
   // shift: shifted CholeskyQR leaves Q orthonormal to about kappa(Y)^2 u only,
@@ -436,7 +496,7 @@ void cqr2_mixed(Job& J, int nsl_out) {
     m.cond = flags(c);
     md[c] = m;
   }
-  add_mm(J, b32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
+  add_nn(J, b32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
   {
     const Chan* dch = J.d_ch;
     const int C = J.C;
@@ -495,7 +555,7 @@ Chan* reorth_x(Job& J) {
       m.mode = MM_STORE;
       md[c] = m;
     }
-    add_mm(J, MMK_NN_F32_OUT64_B32, md);
+    add_nn(J, MMK_NN_F32_OUT64_B32, md);
     J.steps.push_back([=]() {
       launch_reorth(2, dch, C, maxl, st);              // J += M D
       return RSVD_OK;
@@ -639,7 +699,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
   }
   const int maxl = J.max_l;
   // W^T W = R^T R
-  add_gram32(J, [&](int c) { return (const float*)ch[c].Y32; });
+  add_gram32(J, [&](int c) { return (const float*)ch[c].Y32; }, false);
   add_chol(J, 0);
   const int policy = J.policy;
   const double tol = J.tol;

@@ -88,6 +88,7 @@ void drain_profile(rsvd_plan_s* P) {
     if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
     else if (t.kind == 2) { P->prof.gen_launches++; P->prof.gen_ms += ms; P->prof.gen_flops += t.flops; P->prof.gen_mma_flops += t.bytes; }
     else if (t.kind == 3) { P->prof.cvt_launches++; P->prof.cvt_ms += ms; P->prof.cvt_bytes += t.bytes; }
+    else if (t.kind == 5) { P->prof.nn_launches++; P->prof.nn_ms += ms; P->prof.nn_flops += t.flops; }
     else if (t.kind == 4) { P->prof.gram_launches++; P->prof.gram_ms += ms; P->prof.gram_flops += t.flops; P->prof.gram_mma_flops += t.bytes; }
     else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }
   }
@@ -111,6 +112,15 @@ bool gram_tc_enabled(const Job& J) {
   if (!J.mixed || J.max_l < 1 || J.max_l > 128) return false;
   const char* e = getenv("RSVD_GRAM");
   return !(e && strcmp(e, "dot2") == 0);
+}
+
+// The tensor-core tall x small products (k_nn_tc) serve the mixed path's
+// products with an l x l (or l x k) right operand when every l <= 128;
+// RSVD_NN=simt keeps the CUDA-core FP32 products.
+bool nn_tc_enabled(const Job& J) {
+  if (!J.mixed || J.max_l < 1 || J.max_l > 128) return false;
+  const char* e = getenv("RSVD_NN");
+  return !(e && strcmp(e, "simt") == 0);
 }
 
 // Everything one batched call needs.
@@ -480,6 +490,10 @@ void layout(Job& J, Bump& b) {
       if (gram_tc_enabled(J)) {
         h.gtc_part = b.take<float>((size_t)gram_tc_part_floats(d.n));
         h.gtc_exp = b.take<int>((size_t)cdiv(d.n, 128) * 128);
+      }
+      if (nn_tc_enabled(J)) {
+        h.nn_bimg = b.take<unsigned char>((size_t)nn_tc_img_bytes());
+        h.nn_fexp = b.take<int>(128);
       }
       h.C64 = b.take<double>((size_t)d.l * std::max(d.s, 1));
       h.est_part = b.take<double>((size_t)std::max(d.s, 1) * (1 + d.l));

@@ -151,4 +151,78 @@ RSVD_DEV void tmem_st16(uint32_t taddr, const uint32_t* r) {
 
 RSVD_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completing on an mbarrier armed with the byte count.
+RSVD_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// ------------------------------------------------ exact fixed-point slices
+// Helpers of the split products (tensor-core Gram and tall x small
+// products): an FP32 value x with |x| < 1 is cut into slices
+// a_s = rint(r 2^(8s)) 2^(-8s) of the running remainder r (s = 1, 2, ...),
+// integers of at most nine bits times powers of two, exact in BF16.
+
+// 2^k as FP32 for k <= 127 (0 below the normal range).
+RSVD_DEV float pow2f_exp(int k) { return k < -126 ? 0.0f : __uint_as_float((uint32_t)(127 + k) << 23); }
+
+// Exponent e with m < 2^e for a finite maximum magnitude m (zero and
+// subnormal: -126; clamped to [-126, 126] so that 2^-e is a normal FP32).
+RSVD_DEV int slice_exp(float m) {
+  const int e = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 126;
+  return max(-126, min(126, e));
+}
+
+RSVD_DEV uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+RSVD_DEV void st_shared_v4(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// The NS slices of 64 consecutive k values of one operand row (v, scaled by
+// sc to |x| < 1), laid out as 128B-swizzled K-major images of NS slices: in
+// slice s, the k half `half` at half * 16 KiB, 128 rows of 128 bytes, 16-byte
+// chunks xor-ed with row & 7 (the layout of a TMA 128B-swizzled box).  St is
+// called as st(s, byte offset within the slice, four 32-bit words).
+template <int NS, class St>
+RSVD_DEV void slice_row64(const float (&v)[64], float sc, int row, int half, St st) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    uint32_t w[NS][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float x0 = v[8 * q + 2 * p] * sc, x1 = v[8 * q + 2 * p + 1] * sc;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const float up = __uint_as_float((uint32_t)(127 + 8 * (s + 1)) << 23);
+        const float dn = __uint_as_float((uint32_t)(127 - 8 * (s + 1)) << 23);
+        // round to nearest even by adding and removing 1.5 * 2^23 (exact for
+        // |x up| < 2^22; here |x up| <= 256)
+        const float d0 = ((x0 * up + 12582912.0f) - 12582912.0f) * dn;
+        const float d1 = ((x1 * up + 12582912.0f) - 12582912.0f) * dn;
+        x0 -= d0;                                    // exact: the bits below 2^(-8(s+1))
+        x1 -= d1;
+        w[s][p] = pack_bf16x2(d0, d1);
+      }
+    }
+    const uint32_t off = (uint32_t)(half * 16384 + row * 128 + ((q ^ (row & 7)) << 4));
+#pragma unroll
+    for (int s = 0; s < NS; ++s) st(s, off, w[s][0], w[s][1], w[s][2], w[s][3]);
+  }
+}
+
+// Exact x * 2^k for a normal FP64 x with a normal result (integer pipe);
+// zero and non-finite x are returned unchanged.
+RSVD_DEV double scale_pow2_f64(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) return x;
+  return __longlong_as_double(b + ((long long)k << 52));
+}
 }  // namespace rsvd

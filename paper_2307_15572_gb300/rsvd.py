@@ -65,7 +65,8 @@ class Profile(C.Structure):
                 ("gen_ms", C.c_double), ("gen_flops", C.c_double), ("gen_mma_flops", C.c_double),
                 ("cvt_launches", C.c_int64), ("cvt_ms", C.c_double), ("cvt_bytes", C.c_double),
                 ("gram_launches", C.c_int64), ("gram_ms", C.c_double), ("gram_flops", C.c_double),
-                ("gram_mma_flops", C.c_double)]
+                ("gram_mma_flops", C.c_double), ("nn_launches", C.c_int64), ("nn_ms", C.c_double),
+                ("nn_flops", C.c_double)]
 
 
 class TuneRecord(C.Structure):
@@ -147,6 +148,9 @@ def load(build=True):
     lib.rsvd_rule_rows.restype = C.c_int
     lib.rsvd_gram_f32.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, P, C.c_int32]
     lib.rsvd_gram_f32.restype = C.c_int
+    lib.rsvd_panel_product.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, P, C.c_int64, C.c_int32, C.c_int32, P,
+                                       C.c_int64, C.c_int32]
+    lib.rsvd_panel_product.restype = C.c_int
     _lib = lib
     return lib
 
@@ -275,12 +279,18 @@ def rsvd_rule_rows(h, mat, r0, rows, out, ldo):
     return _check(load().rsvd_rule_rows(h, C.byref(mat), int(r0), int(rows), out, int(ldo)))
 
 
-RSVD_GRAM_TC, RSVD_GRAM_DOT2 = 0, 1
+RSVD_GRAM_TC, RSVD_GRAM_DOT2, RSVD_GRAM_TC_F32 = 0, 1, 2
 
 
 def rsvd_gram_f32(h, Y, ldy, n, l, G, method=RSVD_GRAM_TC):
     """G = Y^T Y (FP64-grade) of the device FP32 panel Y (n x l, column-major, ld ldy) into device G (l x l)."""
     return _check(load().rsvd_gram_f32(h, Y, int(ldy), int(n), int(l), G, int(method)))
+
+
+def rsvd_panel_product(h, A, lda, n, K, B, ldb, b_fp64, N, Cout, ldc, c_fp64):
+    """C = A B on the tensor cores (device pointers, column-major; A FP32 n x K, B K x N, K, N <= 128)."""
+    return _check(load().rsvd_panel_product(h, A, int(lda), int(n), int(K), B, int(ldb), int(bool(b_fp64)), int(N),
+                                            Cout, int(ldc), int(bool(c_fp64))))
 
 
 def rsvd_transform_factors(h, fac, n, B, ldb, m, Lt, ldl, Rt, ldr):

@@ -10,7 +10,8 @@ Bounds (of ||y_i|| ||y_j||): each entry is represented to 2^-49 of its
 tile-column maximum, the dropped slice products are below 2^-47 of a row's
 product and the one rounded accumulator (slice levels 5-7) holds terms below
 2^-23 of the total, so the tensor-core Gram is good to ~1e-13 typically and
-the test allows 2e-12; the FP64 matrix product itself carries about
+the test allows 2e-12 (the FP32-grade three-slice form: 1e-6); the FP64
+matrix product itself carries about
 n 2^-53 of sum |y_i||y_j|.  An FP32-grade Gram (error ~1e-7) or a slice
 layout error fails both checks by orders of magnitude.
 """
@@ -21,7 +22,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-TC, DOT2 = 0, 1
+TC, DOT2, TC_F32 = 0, 1, 2
 
 
 def _panel(rng, n, l, kind):
@@ -73,6 +74,9 @@ def test_gram_matches_definition(lib, n, l, kind):
     try:
         for method in (TC, DOT2):
             _check(Y, _gram(lib, plan, Y, method), 2e-12)
+        # the FP32-grade form: operands rounded to 24 fractional bits of the
+        # tile-column maxima, products exact
+        _check(Y, _gram(lib, plan, Y, TC_F32), 1e-6)
         # a leading dimension with padding rows after n
         _check(Y, _gram(lib, plan, Y, TC, ldy=(n + 3) // 4 * 4 + 8), 2e-12)
     finally:
