@@ -209,8 +209,8 @@ rsvd_status rsvd_reconstruct_error(rsvd_plan_t plan, const rsvd_matrix* A,
  * (rsvd_plan_set_profiling(plan, 1)), each decomposition records CUDA events
  * on the plan's stream around every tensor-core pass, every FP64 dense pass
  * over V, every tile-rule generation, every conversion of V into words and
- * every tensor-core Gram of CholeskyQR and every tensor-core tall x small
- * product, and adds their device time and algorithmic traffic (bytes of V words, X
+ * every tensor-core Gram of CholeskyQR, every tensor-core tall x small
+ * product and every pass reading FP64 V directly, and adds their device time and algorithmic traffic (bytes of V words, X
  * words and Y read or written once, as the roofline counts them) to the
  * counters below.  Kernel launches are counted whether or not timing is
  * enabled.  rsvd_plan_profile copies the counters (host struct) and, if
@@ -238,6 +238,10 @@ typedef struct {
   int64_t nn_launches;     /* tensor-core tall x small products (Y R^-1, lifts)   */
   double nn_ms;
   double nn_flops;         /* algorithmic: 2 n l N per product                   */
+  int64_t f64in_launches;  /* tensor-core passes reading stored FP64 V directly  */
+  double f64in_ms;
+  double f64in_bytes;      /* 8 B per V entry, + X words and Y once              */
+  double f64in_flops;      /* MMA flops (2 n^2 N per word pair)                  */
 } rsvd_profile;
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);

@@ -224,7 +224,8 @@ void rule_pass64(Job& J, std::function<const double*(int)> X, std::function<doub
 void pass64(Job& J, std::function<const double*(int)> X, std::function<double*(int)> Y, bool first);
 void build_fp64(Job& J);
 rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
-                       std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout);
+                       std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout,
+                       std::function<bool(int)> sel = nullptr);
 rsvd_status tc_pass(Job& J, int sa, int sx, int ncols_of_pass /*0: l, 1: lw*/);
 rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
                       std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout,

@@ -197,6 +197,174 @@ void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st) {
   note_launch();
 }
 
+// ------------------------------------------------------------ probe block
+// The probe block of the mixed path's error estimate (s <= 32 columns, far
+// narrower than the 128-wide tiles of the general products): C = Q^T Z
+// (l x s) and the residual R = Z - Q C in place of Z, FP32 FMA (ample for
+// an estimate).
+
+RSVD_DEV int probe_chan(const ProbeDesc* __restrict__ pd, int C, int b) {
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pd[mid].tile0 <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One block per (row split, 128-column chunk of Q): thread (i, jh) sums
+// Q[:, c0 + i] . Z[:, 16 jh + jj] over the split's rows, 32 rows at a time
+// staged in shared memory (Q by coalesced loads down its columns; Z's 32 x 32
+// block through L1), the 16 Z values of a row read as four 16-byte vectors;
+// the next 32 rows load into registers while the current ones are summed.
+__global__ void __launch_bounds__(256, 2) k_probe_tn(const ProbeDesc* __restrict__ pd, int C) {
+  __shared__ float Qs[32][129];
+  __shared__ __align__(16) float Zs[32][32];
+  const ProbeDesc* g = pd + probe_chan(pd, C, blockIdx.x);
+  const int local = blockIdx.x - g->tile0;
+  const int lch = (g->l + 127) >> 7;
+  const int split = local / lch, c0 = (local % lch) * 128;
+  const int n = g->n, l = g->l, s = g->s;
+  const int rb = split * g->split_rows, re = min(n, rb + g->split_rows);
+  const float* Q = g->Q;
+  const float* Z = g->Z;
+  const int64_t ldq = g->ldq, ldz = g->ldz;
+  const int tid = threadIdx.x, i = tid & 127, jh = tid >> 7;
+  float qn[16], zn[4];
+  auto fetch = [&](int r0) {
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      const int e = tid + 256 * p, rr = e & 31, cc = e >> 5;
+      const int gr = r0 + rr, gc = c0 + cc;
+      qn[p] = (gr < re && gc < l) ? __ldg(Q + gr + (int64_t)gc * ldq) : 0.0f;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int e = tid + 256 * p, jj = e & 31, rr = e >> 5;
+      const int gr = r0 + rr;
+      zn[p] = (gr < re && jj < s) ? __ldg(Z + gr + (int64_t)jj * ldz) : 0.0f;
+    }
+  };
+  float acc[16];
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.0f;
+  if (rb < re) fetch(rb);
+  for (int r0 = rb; r0 < re; r0 += 32) {
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      const int e = tid + 256 * p;
+      Qs[e & 31][e >> 5] = qn[p];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int e = tid + 256 * p;
+      Zs[e >> 5][e & 31] = zn[p];
+    }
+    __syncthreads();
+    if (r0 + 32 < re) fetch(r0 + 32);
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const float q = Qs[rr][i];
+      const float4* zr = reinterpret_cast<const float4*>(&Zs[rr][16 * jh]);
+#pragma unroll
+      for (int v4 = 0; v4 < 4; ++v4) {
+        const float4 z = zr[v4];
+        acc[4 * v4] = fmaf(q, z.x, acc[4 * v4]);
+        acc[4 * v4 + 1] = fmaf(q, z.y, acc[4 * v4 + 1]);
+        acc[4 * v4 + 2] = fmaf(q, z.z, acc[4 * v4 + 2]);
+        acc[4 * v4 + 3] = fmaf(q, z.w, acc[4 * v4 + 3]);
+      }
+    }
+    __syncthreads();
+  }
+  if (c0 + i < l) {
+    double* part = g->part + (int64_t)split * l * s;
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int j = 16 * jh + jj;
+      if (j < s) part[(c0 + i) + (int64_t)j * l] = f32_to_f64(acc[jj]);
+    }
+  }
+}
+
+// C = sum of the split partials (FP64, in split order), and its FP32
+// rounding padded to 32 columns per row of C (C32[k * 32 + j], zero for
+// j >= s) for the residual kernel.
+__global__ void k_probe_tn_reduce(const ProbeDesc* __restrict__ pd) {
+  const ProbeDesc* g = pd + blockIdx.y;
+  const int l = g->l, s = g->s, ls = l * s, splits = g->splits;
+  const double* part = g->part;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * 32; e += gridDim.x * blockDim.x) {
+    const int k = e >> 5, j = e & 31;
+    float c32 = 0.0f;
+    if (j < s) {
+      const int64_t o = k + (int64_t)j * l;
+      double v = 0.0;
+#pragma unroll 8
+      for (int p = 0; p < splits; ++p) v += __ldg(part + (int64_t)p * ls + o);
+      g->C[o] = v;
+      c32 = f64_to_f32_rn(v);
+    }
+    g->C32[e] = c32;
+  }
+}
+
+// A 128-row block, one row per thread, 16 columns at a time: R = Z - Q C
+// with C (rounded to FP32) in shared memory, read as 16-byte vectors, and Q
+// down its columns (coalesced), 16 k at a time so that 16 loads per thread
+// are in flight.
+__global__ void __launch_bounds__(128) k_probe_nn_sub(const ProbeDesc* __restrict__ pd, int C) {
+  __shared__ __align__(16) float Cs[256][32];
+  const ProbeDesc* g = pd + probe_chan(pd, C, blockIdx.x);
+  const int l = g->l, s = g->s, n = g->n;
+  {
+    const float4* src = reinterpret_cast<const float4*>(g->C32);
+    float4* dst = reinterpret_cast<float4*>(&Cs[0][0]);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < 256 * 8; e += blockDim.x)
+      dst[e] = e < l * 8 ? __ldg(src + e) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  __syncthreads();
+  const int r = (blockIdx.x - g->tile0) * 128 + threadIdx.x;
+  if (r >= n) return;
+  const float* q = g->Q + r;
+  const int64_t ldq = g->ldq;
+  for (int jb = 0; jb < s; jb += 16) {
+    float acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+    for (int k0 = 0; k0 < l; k0 += 16) {
+      float qk[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) qk[kk] = k0 + kk < l ? __ldg(q + (int64_t)(k0 + kk) * ldq) : 0.0f;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const float4* cr = reinterpret_cast<const float4*>(&Cs[k0 + kk][jb]);
+#pragma unroll
+        for (int v4 = 0; v4 < 4; ++v4) {
+          const float4 c = cr[v4];
+          acc[4 * v4] = fmaf(qk[kk], c.x, acc[4 * v4]);
+          acc[4 * v4 + 1] = fmaf(qk[kk], c.y, acc[4 * v4 + 1]);
+          acc[4 * v4 + 2] = fmaf(qk[kk], c.z, acc[4 * v4 + 2]);
+          acc[4 * v4 + 3] = fmaf(qk[kk], c.w, acc[4 * v4 + 3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (jb + j < s) g->Z[r + (int64_t)(jb + j) * g->ldz] -= acc[j];
+  }
+}
+
+void launch_probe_block(const ProbeDesc* d_tn, const ProbeDesc* d_nn, int C, int tn_blocks, int nn_blocks,
+                        cudaStream_t st) {
+  if (C <= 0) return;
+  k_probe_tn<<<tn_blocks, 256, 0, st>>>(d_tn, C);
+  k_probe_tn_reduce<<<dim3(16, C), 256, 0, st>>>(d_tn);
+  k_probe_nn_sub<<<nn_blocks, 128, 0, st>>>(d_nn, C);
+  note_launch(3);
+}
+
 // Zero column blocks of tall matrices (before k-split accumulation).
 __global__ void k_zero(const ZeroDesc* __restrict__ zd, const int* __restrict__ off, int C) {
   const int t = blockIdx.x;

@@ -45,13 +45,15 @@ constexpr int NT_SMEM = 2 * NT_IMG_BYTES + 1024 + NT_MISC;
 int nn_tc_img_bytes() { return NT_IMG_BYTES; }
 
 // ------------------------------------------------------------ B images
-// One CTA per channel: thread = output column j (a row of the B image),
-// half of the k range.  B' = B diag(colscale) rounded to FP32.
-__global__ void __launch_bounds__(256) k_nn_tc_prep(const NnTcDesc* __restrict__ nd) {
+// Grid (channel, 4): block y takes 32 output columns j (rows of the B
+// image); thread = column j, half h of the k range.  B' = B diag(colscale)
+// rounded to FP32.
+__global__ void __launch_bounds__(64) k_nn_tc_prep(const NnTcDesc* __restrict__ nd) {
   const NnTcDesc* g = nd + blockIdx.x;
   if (g->cond && !(*g->cond & FLAG_SHIFTED)) return;
-  __shared__ float smax[2][128];
-  const int tid = threadIdx.x, j = tid & 127, h = tid >> 7;
+  __shared__ float smax[2][32];
+  const int tid = threadIdx.x, jl = tid & 31, h = tid >> 5;
+  const int j = blockIdx.y * 32 + jl;
   const int K = g->K, N = g->N;
   float v[64];
   float mx = 0.0f;
@@ -77,9 +79,9 @@ __global__ void __launch_bounds__(256) k_nn_tc_prep(const NnTcDesc* __restrict__
 #pragma unroll
     for (int k = 0; k < 64; ++k) v[k] = 0.0f;
   }
-  smax[h][j] = mx;
+  smax[h][jl] = mx;
   __syncthreads();
-  const int f = slice_exp(fmaxf(smax[0][j], smax[1][j]));
+  const int f = slice_exp(fmaxf(smax[0][jl], smax[1][jl]));
   if (h == 0) g->fexp[j] = f;
   unsigned char* img = (unsigned char*)g->bimg;     // the shared-memory image, in global memory
   slice_row64<NT_SLICES>(v, pow2f_exp(-f), j, h, [&](int s, uint32_t off, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -309,7 +311,7 @@ k_nn_tc(const NnTcDesc* __restrict__ nd, int C, int tiles, int* __restrict__ err
 
 int launch_nn_tc(const NnTcDesc* d_nd, int C, int tiles, int* d_err, cudaStream_t st) {
   if (tiles <= 0 || C <= 0) return 0;
-  k_nn_tc_prep<<<C, 256, 0, st>>>(d_nd);
+  k_nn_tc_prep<<<dim3(C, 4), 64, 0, st>>>(d_nd);
   note_launch();
   const cudaError_t e = cudaFuncSetAttribute(k_nn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, NT_SMEM);
   if (e != cudaSuccess) return (int)e;

@@ -97,6 +97,25 @@ struct NnTcDesc {
 int launch_nn_tc(const NnTcDesc* d_nd, int C, int tiles, int* d_err, cudaStream_t st);
 int nn_tc_img_bytes();
 
+// Probe block of the mixed path (s <= 32, l <= 256): C = Q^T Z over row
+// splits (partials, then their sum, FP64 C, leading dim l), then Z -= Q C.
+// Two descriptor arrays with the same channels: in d_tn, tile0 is the
+// channel's first block of the C = Q^T Z launch (splits x ceil(l / 128)
+// blocks each), in d_nn its first block of the Z -= Q C launch
+// (ceil(n / 128) blocks each).
+struct ProbeDesc {
+  const float* Q; int64_t ldq;
+  float* Z; int64_t ldz;
+  int n, l, s;
+  int tile0;
+  int splits, split_rows;
+  double* part;
+  double* C;
+  float* C32;               // C rounded to FP32, l rows of 32 (16-byte aligned, l * 32 floats)
+};
+void launch_probe_block(const ProbeDesc* d_tn, const ProbeDesc* d_nn, int C, int tn_blocks, int nn_blocks,
+                        cudaStream_t st);
+
 // ------------------------------------------------------------ small kernels
 // ||A||_F^2 partials per 64-row block, non-finite detection (dense input).
 void launch_fro2(const Chan* d_ch, const int* d_off_rows64, int C, int tiles, cudaStream_t st);

@@ -8,7 +8,8 @@ namespace rsvd_api {
 
 // --------------------------------------------------------------- mixed path
 rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
-                       std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout) {
+                       std::function<const __nv_bfloat16*(int, int)> xword, std::function<float*(int)> yout,
+                       std::function<bool(int)> sel) {
   // one grouped tcgen05 launch: Y[:, 0:ncols) = sum words V_a X_b.
   // Default shape: all columns in one tile up to the kernel's register
   // accumulator width (TC_BN_NARROW), else balanced column tiles; k split only when
@@ -16,9 +17,15 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
   // shared memory holds; items longest channel first.  Autotuned: one or two
   // more column tiles, the split target (4 items per SM with shorter splits,
   // or none), a 4-stage pipeline, and the plain channel order.
+  // the channels of this launch (all of them, or those sel picks)
+  std::vector<int> chans;
+  for (int c = 0; c < J.C; ++c)
+    if (!sel || sel(c)) chans.push_back(c);
+  if (chans.empty()) return RSVD_OK;
+  const int CC = (int)chans.size();
   int maxnc = 16;
-  std::vector<int> nc_of(J.C);
-  for (int c = 0; c < J.C; ++c) {
+  std::vector<int> nc_of(J.C, 0);
+  for (int c : chans) {
     nc_of[c] = ncols_of(c);
     maxnc = std::max(maxnc, nc_of[c]);
   }
@@ -39,7 +46,7 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
   }
   auto ks_of = [&](const Cfg& g, int c) {
     int64_t items0 = 0;
-    for (int e = 0; e < J.C; ++e) items0 += (int64_t)cdiv(J.d[e].n, 128) * cdiv(nc_of[e], g.bn);
+    for (int e : chans) items0 += (int64_t)cdiv(J.d[e].n, 128) * cdiv(nc_of[e], g.bn);
     const int kt = cdiv(J.d[c].n, 64);
     const int ks = pick_splits(items0, kt, g.min_chunk, (int64_t)g.target * NSM);
     const int kps = cdiv(kt, ks);
@@ -51,7 +58,7 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
     std::vector<std::vector<int>> sigs;
     for (const Cfg& g : cands) {
       std::vector<int> sg = {g.bn, std::min(g.stages ? g.stages : 99, tc_stages(sa, sx, g.bn)), g.lpt};
-      for (int c = 0; c < J.C; ++c) sg.push_back(ks_of(g, c).first);
+      for (int c : chans) sg.push_back(ks_of(g, c).first);
       if (std::find(sigs.begin(), sigs.end(), sg) == sigs.end()) {
         sigs.push_back(sg);
         uniq.push_back(g);
@@ -60,23 +67,22 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
     cands.swap(uniq);
   }
   std::vector<int64_t> per;
-  for (int c = 0; c < J.C; ++c) { per.push_back(J.d[c].n); per.push_back(nc_of[c]); }
+  for (int c : chans) { per.push_back(J.d[c].n); per.push_back(nc_of[c]); }
   const std::string key = tune_key("tc", {sa, sx}, per);
   std::vector<std::function<rsvd_status()>> vars;
   std::vector<rsvd_tune_record> recs;
   for (int ci : tune_pick(J, key, cands.size())) {
     const Cfg g = cands[ci];
     const int bn = g.bn;
-    std::vector<TcChan> tcs(J.C);
+    std::vector<TcChan> tcs(CC);
     bool any_split = false;
     std::vector<ZeroDesc> zd(J.C);
     int item = 0;
     // items numbered longest first: the persistent CTAs take items
     // round-robin, so this order balances them (longest-processing-time-first)
-    std::vector<int> order(J.C);
-    for (int c = 0; c < J.C; ++c) order[c] = c;
+    std::vector<int> order(chans);
     if (g.lpt) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return J.d[a].n > J.d[b].n; });
-    for (int pos = 0; pos < J.C; ++pos) {
+    for (int pos = 0; pos < CC; ++pos) {
       const int c = order[pos];
       const ChanDims& d = J.d[c];
       const int nc = nc_of[c];
@@ -108,8 +114,9 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
     const int items = item;
     std::function<rsvd_status()> zero;
     if (any_split) {
-      const int* off = offsets(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
-      const int tiles64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
+      auto rows64 = [&](int c) { return (sel && !sel(c)) ? (int64_t)0 : (int64_t)cdiv(J.d[c].n, 64); };
+      const int* off = offsets(J, rows64);
+      const int tiles64 = total_of(J, rows64);
       const ZeroDesc* dzd = J.ar.put(zd.data(), zd.size());
       cudaStream_t st = J.P->st;
       const int C = J.C;
@@ -121,13 +128,13 @@ rsvd_status tc_pass_ex(Job& J, int sa, int sx, std::function<int(int)> ncols_of,
     const TcChan* dtc = J.ar.put(tcs.data(), tcs.size(), 128);
     cudaStream_t st = J.P->st;
     int* derr = J.P->d_err;
-    const int C = J.C;
+    const int C = CC;
     // algorithmic traffic: every V word, X word and Y element once; MMA flops
     double bytes = 0.0, flops = 0.0;
     int npairs = 0;
     for (int a = 0; a < sa; ++a)
       for (int x = 0; x < sx; ++x) npairs += (a + x < std::max(sa, sx));
-    for (int c = 0; c < J.C; ++c) {
+    for (int c : chans) {
       const double n = J.d[c].n, nc = nc_of[c];
       bytes += n * n * 2.0 * sa + n * nc * 2.0 * sx + n * nc * 4.0;
       flops += 2.0 * n * n * nc * npairs;
@@ -280,6 +287,104 @@ rsvd_status rule_pass(Job& J, int sx, std::function<int(int)> ncols_of,
 }
 
 // One pass over V (dense words) or over the generated rule entries.
+// The FP64-input passes (k_tc_f64), an alternative for the mixed path
+// without power iterations: two passes reading V in FP64 (16 bytes per
+// entry) instead of the conversion to words plus two passes over the words
+// (20).  On this part they lose: each pass must round V to FP32 on the
+// integer pipe again at ~2.7 values per clock per SM to keep up with HBM,
+// and with two 64 KiB stages beside the MMA operands the rounding, the MMAs
+// and the loads do not overlap enough (3.8-4.0 TB/s measured, against the
+// conversion kernel's 6.1 at 12 bytes per entry); so they are taken only on
+// request (RSVD_F64PASS=1).  A channel qualifies if its V is in device
+// memory with an even leading dimension and a 16-byte aligned base (the
+// TMA's row stride); the others keep the words.  The pass needs two words,
+// one column tile, and at least one 128-row tile per SM over its channels
+// (no k split).  Returns the per-channel choice (all zero: none).
+std::vector<char> f64pass_channels(const Job& J) {
+  std::vector<char> use(J.C, 0);
+  if (!J.mixed || J.rule || J.skip_convert || J.probe_job || J.q != 0 || J.nsl != 2) return use;
+  const char* e = getenv("RSVD_F64PASS");
+  if (!e || strcmp(e, "1") != 0) return use;
+  int64_t items = 0;
+  for (int c = 0; c < J.C; ++c) {
+    const rsvd_matrix& A = J.A[c];
+    if (J.d[c].lw > TC_BN_NARROW) return std::vector<char>(J.C, 0);
+    if (A.mem != RSVD_MEM_DEVICE || (A.ld & 1) || ((uintptr_t)A.data & 15)) continue;
+    use[c] = 1;
+    items += cdiv(J.d[c].n, 128);
+  }
+  if (items < NSM) use.assign(J.C, 0);
+  return use;
+}
+
+// One FP64-input pass Y[:, 0:ncols) = V X (sx X words); `stats` also writes
+// the channels' ||V||^2 and remainder partials and the Inf/NaN flag.
+rsvd_status f64_pass(Job& J, int sx, std::function<int(int)> ncols_of, bool stats, const std::vector<char>& use) {
+  std::vector<int> order;
+  int maxnc = 16;
+  for (int c = 0; c < J.C; ++c)
+    if (use[c]) {
+      order.push_back(c);
+      maxnc = std::max(maxnc, ncols_of(c));
+    }
+  const int CC = (int)order.size();
+  if (CC == 0) return RSVD_OK;
+  const int bn = (int)rup(maxnc, 16);
+  // longest channel first: the persistent CTAs take items round-robin
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return J.d[a].n > J.d[b].n; });
+  std::vector<TcChan> tcs(CC);
+  int item = 0;
+  double bytes = 0.0, flops = 0.0;
+  for (int pos = 0; pos < CC; ++pos) {
+    const int c = order[pos];
+    const ChanDims& d = J.d[c];
+    const int nc = ncols_of(c);
+    TcChan& t = tcs[pos];
+    memset(&t, 0, sizeof(t));
+    if (!J.measure) {
+      const void* X[2] = {J.ch[c].Xb[0], J.ch[c].Xb[1]};
+      const int e = f64pass_encode(&t, J.ch[c].A, J.ch[c].lda, d.n, X, sx, d.ldb, nc, bn);
+      if (e) return seterr(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", e);
+    }
+    t.Y = J.ch[c].Y32;
+    t.ldy = d.ldt;
+    t.n = d.n;
+    t.m = d.n;
+    t.ncols = nc;
+    t.mt = cdiv(d.n, 128);
+    t.nt = 1;
+    t.ks = 1;
+    t.kt_per_split = cdiv(d.n, 64);
+    t.item0 = item;
+    item += t.mt;
+    if (stats) {
+      t.fro_part = J.ch[c].fro_part;
+      t.wres_part = J.ch[c].wres_part;
+      t.flags = J.d_res ? (int*)((uintptr_t)(J.d_res + c) + offsetof(ChanResult, flags)) : nullptr;
+    }
+    bytes += (double)d.n * d.n * 8.0 + (double)d.n * nc * (2.0 * sx + 4.0);
+    flops += 2.0 * d.n * d.n * nc * (sx == 1 ? 2 : 3);
+  }
+  const int items = item;
+  const TcChan* dtc = J.ar.put(tcs.data(), tcs.size(), 128);
+  rsvd_plan_s* P = J.P;
+  cudaStream_t st = P->st;
+  int* derr = P->d_err;
+  const int C = CC;
+  J.steps.push_back([=]() {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (P->profiling) timed_begin(P, &ea, &eb);
+    const int e = f64pass_launch(dtc, C, items, sx, bn, stats, derr, st);
+    if (e) return seterr(RSVD_ERR_CUDA, "FP64-input tensor-core pass failed: %s", cudaGetErrorString((cudaError_t)e));
+    if (P->profiling) {
+      cudaEventRecord(eb, st);
+      P->pending.push_back({ea, eb, 6, bytes, flops});
+    }
+    return RSVD_OK;
+  });
+  return RSVD_OK;
+}
+
 rsvd_status pass_over(Job& J, int sa, int sx, int ncols_of_pass, bool first) {
   auto ncols = [&](int c) { return ncols_of_pass ? J.d[c].lw : J.d[c].l; };
   auto xw = [&](int c, int w) { return (const __nv_bfloat16*)J.ch[c].Xb[w]; };
@@ -624,11 +729,35 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
   const int t64 = total_of(J, [&](int c) { return (int64_t)cdiv(J.d[c].n, 64); });
   const uint64_t seed = J.P->o.seed;
   const uint64_t pseed = seed ^ 0x5DEECE66DULL;
+  const std::vector<char> f64use = J.rule ? std::vector<char>(C, 0) : f64pass_channels(J);
+  bool f64p = false, words = false;             // some channels read FP64 V, some read words
+  for (int c = 0; c < C; ++c) (f64use[c] ? f64p : words) = true;
+  auto wsel = [f64use](int c) { return f64use[c] == 0; };
   if (J.rule) {
     const std::vector<RuleDesc> rds = rule_descs(J);
     J.steps.push_back([=]() {
       for (const RuleDesc& r : rds) launch_rule_prep(r, st);
       launch_omega_bf16(dch, off64, C, t64, seed, 0, 0, 1 << 30, pseed, nsl, st);   // P and probes
+      return RSVD_OK;
+    });
+  } else if (f64p) {
+    // P and the probe block, and the words of the channels that keep them;
+    // the other channels' sketch pass reads V in FP64 and sums its energies
+    const int* offw = offsets(J, [&](int c) { return f64use[c] ? (int64_t)0 : (int64_t)cdiv(J.d[c].n, 8); });
+    const int tw = total_of(J, [&](int c) { return f64use[c] ? (int64_t)0 : (int64_t)cdiv(J.d[c].n, 8); });
+    double cbytes = 0.0;
+    for (int c = 0; c < C; ++c)
+      cbytes += (f64use[c] ? 0.0 : (double)J.d[c].n * J.d[c].n * (8.0 + 2.0 * nsl)) +
+                (double)J.d[c].n * J.d[c].lw * 2.0 * nsl;
+    rsvd_plan_s* P = J.P;
+    J.steps.push_back([=]() {
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (P->profiling) timed_begin(P, &ea, &eb);
+      launch_convert_omega(dch, offw, tw, off64, t64, C, nsl, seed, pseed, nsl, st);
+      if (P->profiling) {
+        cudaEventRecord(eb, st);
+        P->pending.push_back({ea, eb, 3, cbytes, 0.0});
+      }
       return RSVD_OK;
     });
   } else {
@@ -656,40 +785,95 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
     });
   }
   // sketch: only the l sketch columns (X word 0 = P exactly)
-  if (rsvd_status s = pass_over(J, nsl, 1, 0, true)) return s;
+  if (f64p) {
+    if (rsvd_status s = f64_pass(J, 1, [&](int c) { return J.d[c].l; }, true, f64use)) return s;
+    if (words)
+      if (rsvd_status s = tc_pass_ex(J, nsl, 1, [&](int c) { return J.d[c].l; },
+                                     [&](int c, int w) { return (const __nv_bfloat16*)J.ch[c].Xb[w]; },
+                                     [&](int c) { return J.ch[c].Y32; }, wsel))
+        return s;
+    J.steps.push_back([=]() {
+      launch_fro2_reduce_rows(dch, C, 8, st);
+      return RSVD_OK;
+    });
+  } else if (rsvd_status s = pass_over(J, nsl, 1, 0, true)) {
+    return s;
+  }
   cqr2_mixed(J, nsl);
   for (int r = 0; r < 2 * J.q; ++r) {
     if (rsvd_status s = pass_over(J, nsl, nsl, 0, false)) return s;
     cqr2_mixed(J, nsl);
   }
   // projection with the probe block: [W | V G] = V [Q | G]
-  if (rsvd_status s = pass_over(J, nsl, nsl, 1, false)) return s;
-  // C = Q^T (V G) (FP32 accumulate is ample for the error estimate)
-  add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
-         [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
-         [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
-  // probe residual R = V G - Q C in place of V G, then its column energies
-  {
+  if (f64p) {
+    if (rsvd_status s = f64_pass(J, nsl, [&](int c) { return J.d[c].lw; }, false, f64use)) return s;
+    if (words)
+      if (rsvd_status s = tc_pass_ex(J, nsl, nsl, [&](int c) { return J.d[c].lw; },
+                                     [&](int c, int w) { return (const __nv_bfloat16*)J.ch[c].Xb[w]; },
+                                     [&](int c) { return J.ch[c].Y32; }, wsel))
+        return s;
+  } else if (rsvd_status s = pass_over(J, nsl, nsl, 1, false)) {
+    return s;
+  }
+  // C = Q^T (V G) and the probe residual R = V G - Q C in place of V G
+  // (FP32 accumulate is ample for the error estimate), then R's column
+  // energies
+  bool narrow = true;                                     // the narrow probe kernels: s <= 32, 32 <= l <= 256
+  for (int c = 0; c < J.C; ++c)
+    narrow = narrow && J.d[c].s <= 32 && J.d[c].l >= 32 && J.d[c].l <= 256 && ch[c].Ri32;
+  std::vector<SumsqDesc> sd(J.C);
+  for (int c = 0; c < J.C; ++c)
+    sd[c] = SumsqDesc{ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt, J.d[c].ldt, J.d[c].n, J.d[c].s, 4, ch[c].est_part};
+  if (narrow) {
+    std::vector<ProbeDesc> tn(J.C), nn(J.C);
+    int tb = 0, nb = 0;
+    for (int c = 0; c < J.C; ++c) {
+      const ChanDims& d = J.d[c];
+      ProbeDesc p{};
+      p.Q = ch[c].Q32; p.ldq = d.ldt;
+      p.Z = ch[c].Y32 + (int64_t)d.l * d.ldt; p.ldz = d.ldt;
+      p.n = d.n; p.l = d.l; p.s = d.s;
+      p.split_rows = (int)rup(cdiv(d.n, d.gsplit), 32);    // the Gram's row splits
+      p.splits = cdiv(d.n, p.split_rows);
+      p.part = ch[c].gpart;
+      p.C = ch[c].C64;
+      p.C32 = ch[c].Ri32;                                   // l x l FP32 scratch, free here (l >= 32)
+      p.tile0 = tb;
+      tn[c] = p;
+      tb += p.splits * cdiv(d.l, 128);
+      p.tile0 = nb;
+      nn[c] = p;
+      nb += cdiv(d.n, 128);
+    }
+    const ProbeDesc* dtn = J.ar.put(tn.data(), tn.size());
+    const ProbeDesc* dnn = J.ar.put(nn.data(), nn.size());
+    J.steps.push_back([=]() {
+      launch_probe_block(dtn, dnn, C, tb, nb, st);
+      return RSVD_OK;
+    });
+  } else {
+    add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
+           [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
+           [&](int c) { return ch[c].C64; }, [&](int c) { return J.d[c].l; }, [&](int c) { return J.d[c].s; }, false);
     bool c32 = ri32_ok(J);                                  // C (l x s) must fit the l x l FP32 scratch
     for (int c = 0; c < J.C; ++c) c32 = c32 && J.d[c].s <= J.d[c].l;
     if (c32) add_cvt_f32(J, [&](int c) { return (const double*)ch[c].C64; },
                          [&](int c) { return (int64_t)J.d[c].l * J.d[c].s; });
     std::vector<MMDesc> md(J.C);
-    std::vector<SumsqDesc> sd(J.C);
     for (int c = 0; c < J.C; ++c) {
       const ChanDims& d = J.d[c];
-      float* VG = ch[c].Y32 + (int64_t)d.l * d.ldt;
       MMDesc m{};
       m.A = ch[c].Q32; m.lda = d.ldt;
       m.B = c32 ? (const void*)ch[c].Ri32 : (const void*)ch[c].C64; m.ldb = d.l;
-      m.Cm = VG; m.ldc = d.ldt;
+      m.Cm = ch[c].Y32 + (int64_t)d.l * d.ldt; m.ldc = d.ldt;
       m.m = d.n; m.n = d.s; m.k = d.l;
       m.ks = 1; m.kchunk = (int)rup(d.l, 16);
       m.mode = MM_SUB;
       md[c] = m;
-      sd[c] = SumsqDesc{VG, d.ldt, d.n, d.s, 4, ch[c].est_part};
     }
     add_mm(J, c32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
+  }
+  {
     const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
     const int s_max = NPROBE;
     J.steps.push_back([=]() {

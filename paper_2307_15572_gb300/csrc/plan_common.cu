@@ -88,6 +88,7 @@ void drain_profile(rsvd_plan_s* P) {
     if (t.kind == 0) { P->prof.tc_launches++; P->prof.tc_ms += ms; P->prof.tc_bytes += t.bytes; P->prof.tc_flops += t.flops; }
     else if (t.kind == 2) { P->prof.gen_launches++; P->prof.gen_ms += ms; P->prof.gen_flops += t.flops; P->prof.gen_mma_flops += t.bytes; }
     else if (t.kind == 3) { P->prof.cvt_launches++; P->prof.cvt_ms += ms; P->prof.cvt_bytes += t.bytes; }
+    else if (t.kind == 6) { P->prof.f64in_launches++; P->prof.f64in_ms += ms; P->prof.f64in_bytes += t.bytes; P->prof.f64in_flops += t.flops; }
     else if (t.kind == 5) { P->prof.nn_launches++; P->prof.nn_ms += ms; P->prof.nn_flops += t.flops; }
     else if (t.kind == 4) { P->prof.gram_launches++; P->prof.gram_ms += ms; P->prof.gram_flops += t.flops; P->prof.gram_mma_flops += t.bytes; }
     else { P->prof.f64_launches++; P->prof.f64_ms += ms; P->prof.f64_flops += t.flops; }

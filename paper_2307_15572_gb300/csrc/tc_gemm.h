@@ -37,7 +37,23 @@ struct alignas(64) TcChan {
   float eta_amp3;       // sqrt(3) * eta amplitude
   float hinv;           // 1 / hscale of the FP16 factor words: entry = acc * hinv * hinv
   double* part;
+  // FP64-input passes (k_tc_f64): tmA[0] maps the FP64 V (box 16 x 128);
+  // the first pass writes ||V||^2 and the word remainder energy per 8-row
+  // block and flags Inf/NaN
+  double* fro_part;
+  double* wres_part;
+  int* flags;
 };
+
+// FP64-input passes: maps of one channel (V FP64 with leading dim ldv, even,
+// 16-byte aligned; X words as in tc_encode); 0 on success, -2 for a V the
+// TMA cannot address.  Stages and launch (sx = 1 or 2 X words, bn <=
+// TC_BN_NARROW, one column tile per item, no k split); the launch returns a
+// cudaError_t value.
+int f64pass_encode(TcChan* h, const double* V, int64_t ldv, int n, const void* const* X, int sx, int64_t ldx,
+                   int ncols, int bn);
+int f64pass_stages(int sx, int bn);
+int f64pass_launch(const TcChan* d_ch, int C, int items, int sx, int bn, bool stats, int* d_err, cudaStream_t st);
 
 // Encode the maps of one channel (host).  Returns 0 on success.  f16: the
 // words are FP16 (the tile-rule factor), else BF16.

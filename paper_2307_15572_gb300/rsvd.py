@@ -66,7 +66,8 @@ class Profile(C.Structure):
                 ("cvt_launches", C.c_int64), ("cvt_ms", C.c_double), ("cvt_bytes", C.c_double),
                 ("gram_launches", C.c_int64), ("gram_ms", C.c_double), ("gram_flops", C.c_double),
                 ("gram_mma_flops", C.c_double), ("nn_launches", C.c_int64), ("nn_ms", C.c_double),
-                ("nn_flops", C.c_double)]
+                ("nn_flops", C.c_double), ("f64in_launches", C.c_int64), ("f64in_ms", C.c_double),
+                ("f64in_bytes", C.c_double), ("f64in_flops", C.c_double)]
 
 
 class TuneRecord(C.Structure):
