@@ -182,18 +182,51 @@ void launch_omega_bf16(const Chan* d_ch, const int* d_off, int C, int tiles, uin
 // vectors in M, C = Q^T V G), one warp per row i, lane j < s; the residual
 // energies est_part[0..s) come from the column sums of V G - Q C.
 __global__ void __launch_bounds__(256) k_probe_finish(const Chan* __restrict__ ch) {
+  // C (l x s, l <= 128) staged in shared memory with the probe index
+  // fastest (a warp reads one row of it, conflict-free); block y takes 32
+  // rows i of X, warp w rows i0 + 4w .. i0 + 4w + 3, lane = probe column j;
+  // four independent FMA chains per dot product
+  __shared__ double Cs[128][33];
   const Chan& h = ch[blockIdx.x];
   const int l = h.l, s = h.nprobe;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.y * 8 + warp;
-  if (i >= l || lane >= s) return;
-  double d = 0.0;
-  for (int a = 0; a < l; ++a) d = fma(h.M[a + (int64_t)i * l], h.C64[a + (int64_t)lane * l], d);
-  h.est_part[s + (int64_t)i * s + lane] = d * d;
+  if (l > 128) {                                   // wide factors: one dot product per thread
+    const int i = blockIdx.y * 32 + (threadIdx.x >> 5);
+    for (int ii = i; ii < min(l, blockIdx.y * 32 + 32); ii += 8) {
+      if (lane >= s) break;
+      double d = 0.0;
+      for (int a = 0; a < l; ++a) d = fma(h.M[a + (int64_t)ii * l], h.C64[a + (int64_t)lane * l], d);
+      h.est_part[s + (int64_t)ii * s + lane] = d * d;
+    }
+    return;
+  }
+  for (int e = threadIdx.x; e < l * 32; e += blockDim.x) {
+    const int a = e % l, j = e / l;
+    Cs[a][j] = j < s ? h.C64[a + (int64_t)j * l] : 0.0;
+  }
+  __syncthreads();
+  if (lane >= s) return;
+#pragma unroll 1
+  for (int r = 0; r < 4; ++r) {
+    const int i = blockIdx.y * 32 + 4 * warp + r;
+    if (i >= l) break;
+    const double* m = h.M + (int64_t)i * l;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    int a = 0;
+    for (; a + 4 <= l; a += 4) {
+      d0 = fma(__ldg(m + a), Cs[a][lane], d0);
+      d1 = fma(__ldg(m + a + 1), Cs[a + 1][lane], d1);
+      d2 = fma(__ldg(m + a + 2), Cs[a + 2][lane], d2);
+      d3 = fma(__ldg(m + a + 3), Cs[a + 3][lane], d3);
+    }
+    for (; a < l; ++a) d0 = fma(__ldg(m + a), Cs[a][lane], d0);
+    const double d = (d0 + d1) + (d2 + d3);
+    h.est_part[s + (int64_t)i * s + lane] = d * d;
+  }
 }
 
 void launch_probe_finish(const Chan* d_ch, int C, int max_l, cudaStream_t st) {
-  k_probe_finish<<<dim3(C, (max_l + 7) / 8), 256, 0, st>>>(d_ch);
+  k_probe_finish<<<dim3(C, (max_l + 31) / 32), 256, 0, st>>>(d_ch);
   note_launch();
 }
 

@@ -1018,15 +1018,24 @@ RSVD_DEV void probe_stats(double e, int s, double& mean, double& ucb) {
   ucb = mean + PROBE_Z * sqrt(var / s);
 }
 
-// One warp per channel.  Probe layout (mixed path): est_part[j] = ||R g_j||^2
-// with R = V G - Q C the probe residual, est_part[s + i s + j] = D_ij^2 for
-// D = X^T C; e_j(k) = est_part[j] + sum_{i >= k} est_part[s + i s + j].
-__global__ void k_select(const Chan* __restrict__ ch, int policy, double tol_plan, int use_probe) {
+// One 256-thread block per channel.  Probe layout (mixed path): est_part[j] =
+// ||R g_j||^2 with R = V G - Q C the probe residual, est_part[s + i s + j] =
+// D_ij^2 for D = X^T C; e_j(k) = est_part[j] + sum_{i >= k} est_part[s + i s + j].
+// For l <= 128 the lanes of warp 0 form e_j(k) for every k (the same
+// additions, in the same order, as a walk down from k0), the eight warps
+// evaluate the bound for all k at once, and thread 0 replays the walk on
+// the stored values; larger l walks on warp 0.  The chosen rank and
+// estimate are the same either way.
+__global__ void __launch_bounds__(256) k_select(const Chan* __restrict__ ch, int policy, double tol_plan,
+                                                int use_probe) {
+  __shared__ double E[129][33];
+  __shared__ double Ms[129], Us[129];
+  __shared__ int s_k;
   const Chan& h = ch[blockIdx.x];
   const double tol = h.tol > 0.0 ? h.tol : tol_plan;
   const int l = h.l;
   ChanResult* res = h.res;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double fro2 = res->fro2;
   const int kcap = min(h.k_cap, l);
   const double thr = tol * tol * fro2;
@@ -1038,69 +1047,116 @@ __global__ void k_select(const Chan* __restrict__ ch, int policy, double tol_pla
     const double* ep = h.est_part;
     const int kfix = min(h.k_fixed, kcap);
     const int k0 = policy == RSVD_RANK_FIXED ? kfix : kcap;
-    double e = 0.0;
-    if (lane < s) {
-      e = ep[lane];
-      for (int i = l - 1; i >= k0; --i) e += ep[s + (int64_t)i * s + lane];
-    }
     const double floor2 = precision_floor2(res->wres2, l, fro2);
-    double mean, ucb;
-    probe_stats(e, s, mean, ucb);
-    mean += floor2; ucb += floor2;
-    k = k0;
-    est2 = mean;
-    if (policy != RSVD_RANK_FIXED) {
-      if (ucb > thr) unmet = true;
-      else {
-        // walk k downward while the bound stays under the threshold
-        for (int kk = k0 - 1; kk >= 1; --kk) {
-          if (lane < s) e += ep[s + (int64_t)kk * s + lane];
-          probe_stats(e, s, mean, ucb);
-          mean += floor2; ucb += floor2;
-          if (ucb > thr) break;
-          k = kk;
-          est2 = mean;
+    if (l <= 128) {
+      const int kmin = policy == RSVD_RANK_FIXED ? k0 : 1;
+      // the D_ij^2 terms into shared memory (coalesced), then each lane's
+      // running sums replace them in place, walking down from l - 1
+      for (int e = tid; e < l * s; e += blockDim.x) E[e / s][e % s] = ep[s + e];
+      __syncthreads();
+      if (warp == 0) {
+        double e = 0.0;
+        if (lane < s) {
+          e = ep[lane];
+          for (int i = l - 1; i >= k0; --i) e += E[i][lane];
+          E[k0][lane] = e;
+          for (int kk = k0 - 1; kk >= kmin; --kk) {
+            e += E[kk][lane];
+            E[kk][lane] = e;
+          }
+        }
+      }
+      __syncthreads();
+      for (int kk = kmin + warp; kk <= k0; kk += 8) {
+        double mean, ucb;
+        probe_stats(lane < s ? E[kk][lane] : 0.0, s, mean, ucb);
+        if (lane == 0) {
+          Ms[kk] = mean + floor2;
+          Us[kk] = ucb + floor2;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        k = k0;
+        est2 = Ms[k0];
+        if (policy != RSVD_RANK_FIXED) {
+          if (Us[k0] > thr) unmet = true;
+          else
+            for (int kk = k0 - 1; kk >= 1; --kk) {
+              if (Us[kk] > thr) break;
+              k = kk;
+              est2 = Ms[kk];
+            }
+        }
+      }
+    } else if (warp == 0) {
+      double e = 0.0;
+      if (lane < s) {
+        e = ep[lane];
+        for (int i = l - 1; i >= k0; --i) e += ep[s + (int64_t)i * s + lane];
+      }
+      double mean, ucb;
+      probe_stats(e, s, mean, ucb);
+      mean += floor2; ucb += floor2;
+      k = k0;
+      est2 = mean;
+      if (policy != RSVD_RANK_FIXED) {
+        if (ucb > thr) unmet = true;
+        else {
+          // walk k downward while the bound stays under the threshold
+          for (int kk = k0 - 1; kk >= 1; --kk) {
+            if (lane < s) e += ep[s + (int64_t)kk * s + lane];
+            probe_stats(e, s, mean, ucb);
+            mean += floor2; ucb += floor2;
+            if (ucb > thr) break;
+            k = kk;
+            est2 = mean;
+          }
         }
       }
     }
   }
-  if (lane != 0) return;
-  int status = RSVD_OK;
-  if (res->flags & FLAG_NONFINITE) status = RSVD_ERR_NONFINITE;
-  else if (res->flags & FLAG_CHOL_FAIL) status = RSVD_ERR_NOT_CONVERGED;
-  if (!use_probe) {
-    if (policy == RSVD_RANK_FIXED) {
-      k = min(h.k_fixed, kcap);
-      double s2 = 0.0;
-      for (int i = 0; i < k; ++i) s2 += h.sig[i] * h.sig[i];
-      est2 = fmax(fro2 - s2, 0.0);
-    } else {
-      double s2 = 0.0;
-      for (int i = 0; i < kcap; ++i) {
-        s2 += h.sig[i] * h.sig[i];
-        if (fro2 - s2 <= thr) { k = i + 1; est2 = fmax(fro2 - s2, 0.0); break; }
+  if (tid == 0) {
+    int status = RSVD_OK;
+    if (res->flags & FLAG_NONFINITE) status = RSVD_ERR_NONFINITE;
+    else if (res->flags & FLAG_CHOL_FAIL) status = RSVD_ERR_NOT_CONVERGED;
+    if (!use_probe) {
+      if (policy == RSVD_RANK_FIXED) {
+        k = min(h.k_fixed, kcap);
+        double s2 = 0.0;
+        for (int i = 0; i < k; ++i) s2 += h.sig[i] * h.sig[i];
+        est2 = fmax(fro2 - s2, 0.0);
+      } else {
+        double s2 = 0.0;
+        for (int i = 0; i < kcap; ++i) {
+          s2 += h.sig[i] * h.sig[i];
+          if (fro2 - s2 <= thr) { k = i + 1; est2 = fmax(fro2 - s2, 0.0); break; }
+        }
+        if (k < 0) { k = kcap; est2 = fmax(fro2 - s2, 0.0); }
+        unmet = est2 > thr;
       }
-      if (k < 0) { k = kcap; est2 = fmax(fro2 - s2, 0.0); }
-      unmet = est2 > thr;
     }
+    if (policy != RSVD_RANK_FIXED && fro2 > 0.0 && unmet && status == RSVD_OK) status = RSVD_ERR_TOL_NOT_MET;
+    if (k < 0) k = 0;
+    s_k = k;
+    res->k_out = k;
+    res->l_used = l;
+    res->err_est = fro2 > 0.0 ? sqrt(est2 / fro2) : 0.0;
+    if (status == RSVD_OK && (res->flags & FLAG_JACOBI_CAP)) status = RSVD_ERR_NOT_CONVERGED;
+    if (status == RSVD_OK && (res->flags & FLAG_SHIFTED)) status = RSVD_WARN_SHIFTED_CQR;
+    res->status = status;
   }
-  if (policy != RSVD_RANK_FIXED && fro2 > 0.0 && unmet && status == RSVD_OK) status = RSVD_ERR_TOL_NOT_MET;
-  if (k < 0) k = 0;
-  for (int i = 0; i < k; ++i) {
+  __syncthreads();
+  const int kk = s_k;
+  for (int i = tid; i < kk; i += blockDim.x) {
     h.S[i] = h.sig[i];
     h.scr[i] = h.sig[i] > 0.0 ? 1.0 / h.sig[i] : 0.0;   // column scale of R_k = W X_k Sigma_k^{-1}
   }
-  res->k_out = k;
-  res->l_used = l;
-  res->err_est = fro2 > 0.0 ? sqrt(est2 / fro2) : 0.0;
-  if (status == RSVD_OK && (res->flags & FLAG_JACOBI_CAP)) status = RSVD_ERR_NOT_CONVERGED;
-  if (status == RSVD_OK && (res->flags & FLAG_SHIFTED)) status = RSVD_WARN_SHIFTED_CQR;
-  res->status = status;
 }
 
 void launch_select(const Chan* d_ch, int C, int policy, double tol, int use_probe,
                    cudaStream_t st) {
-  k_select<<<C, 32, 0, st>>>(d_ch, policy, tol, use_probe);
+  k_select<<<C, 256, 0, st>>>(d_ch, policy, tol, use_probe);
   note_launch();
 }
 
