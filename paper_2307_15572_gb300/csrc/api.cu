@@ -113,6 +113,12 @@ void rsvd_plan_destroy(rsvd_plan_t P) {
   if (P->ws) cudaFree(P->ws);
   if (P->hp) cudaFreeHost(P->hp);
   if (P->d_err) cudaFree(P->d_err);
+  if (P->side) {
+    cudaStreamSynchronize(P->side);
+    cudaStreamDestroy(P->side);
+  }
+  if (P->fork_ev) cudaEventDestroy(P->fork_ev);
+  if (P->join_ev) cudaEventDestroy(P->join_ev);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : P->tune_ev)
     if (e) cudaEventDestroy(e);

@@ -52,6 +52,10 @@ using namespace rsvd_api;
 struct rsvd_plan_s {
   rsvd_opts o;
   cudaStream_t st = nullptr;
+  // a second stream (and its fork/join events) for work that overlaps the
+  // per-channel kernels of the same decomposition; created on first use
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   char* ws = nullptr;
   size_t ws_cap = 0;
   char* hp = nullptr;      // pinned host staging

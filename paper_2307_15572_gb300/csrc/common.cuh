@@ -215,6 +215,7 @@ struct Chan {
   int lw;                   // columns of the last product (l + probes)
   int nprobe;
   double* C64;              // l x s  (Q^T A G)
+  float* C32;               // l x 32 FP32 copy of C for the probe kernels (mixed path)
   double* est_part;         // probe residual partials
   // outputs
   double* U; int64_t ldu;   // device (internal or user)

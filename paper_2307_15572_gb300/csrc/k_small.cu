@@ -564,6 +564,220 @@ __global__ void __launch_bounds__(256) k_chol_inv_reg(const Chan* __restrict__ c
   }
 }
 
+// The mixed path's factor in double-float arithmetic (pairs hi + lo of FP32
+// numbers, |lo| <= ulp(hi) / 2: about 48 significant bits; Dekker, 1971, and
+// the TwoSum of Knuth).  Same register layout, pivot order, shift and
+// retry as k_chol_inv_reg, with every FP64 operation of the column steps
+// replaced by FP32 instructions (this part issues FP64 arithmetic at a small
+// fraction of its FP32 rate).  The Gram is first scaled by an exact power of
+// two 2^(2k) that brings its largest diagonal entry into [1, 4), so that the
+// lo parts stay normal FP32 numbers; R = R' 2^-k and R^{-1} = R'^{-1} 2^k.
+// 48 bits match the accuracy of the tensor-core Gram it factors (six 8-bit
+// slices), and the factor feeds an FP32 product and an FP32 Jacobi; the FP64
+// path keeps k_chol_inv_reg<double>.  The inverse is the FP32 one of the
+// mixed path, from R' rounded to FP32.
+RSVD_DEV void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+RSVD_DEV void df_fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b| or a = 0
+  s = a + b;
+  e = b - (s - a);
+}
+// (xh, xl) (yh, yl), normalised
+RSVD_DEV void df_mul(float xh, float xl, float yh, float yl, float& rh, float& rl) {
+  const float pr = xh * yh;
+  float e = fmaf(xh, yh, -pr);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  df_fast_two_sum(pr, e, rh, rl);
+}
+// (ah, al) -= (xh, xl) (yh, yl)
+RSVD_DEV void df_fnms(float& ah, float& al, float xh, float xl, float yh, float yl) {
+  const float pr = xh * yh;
+  float e = fmaf(xh, yh, -pr);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  float sh, sl;
+  df_two_sum(ah, -pr, sh, sl);
+  sl += al - e;
+  df_fast_two_sum(sh, sl, ah, al);
+}
+RSVD_DEV void df_from_f64(double g, float& h, float& l) {
+  h = f64_to_f32_rn(g);
+  l = f64_to_f32_rn(g - f32_to_f64(h));
+}
+
+__global__ void __launch_bounds__(256, 1) k_chol_df(const Chan* __restrict__ ch, int conditional) {
+  const Chan& h = ch[blockIdx.x];
+  if (conditional && !(h.res->flags & FLAG_SHIFTED)) return;
+  const int l = h.l;
+  const double* G = h.G;
+  const int tid = threadIdx.x, ta = tid & 15, tb = tid >> 4;
+  __shared__ float rowh[128], rowl[128];
+  __shared__ float rih[128], ril[128];
+  __shared__ __align__(16) unsigned char ibuf[2 * 2 * 128 * sizeof(float) + 128 * sizeof(float)];
+  __shared__ int s_bad, fail, s_k;
+  __shared__ double s_shift;
+  if (tid < 32) {
+    double tr = 0.0, mx = 0.0;
+    for (int i = tid; i < l; i += 32) {
+      const double d = G[i + (int64_t)i * l];
+      tr += d;
+      mx = fmax(mx, d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (tid == 0) {
+      fail = 0;
+      // ilogb of the largest diagonal entry from its exponent field; zero,
+      // subnormal or non-finite maxima keep the scale 1 (the factor fails)
+      const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7FF);
+      const int k = (ex == 0 || ex == 0x7FF) ? 0 : -((ex - 1023) >> 1);
+      s_k = k;
+      s_shift = ldexp(11.0 * ((double)h.n * l + (double)l * (l + 1)) * 3.552713678800501e-15 * tr, 2 * k);
+    }
+  }
+  __syncthreads();
+  const int k2 = 2 * s_k;
+  float rh[36], rl[36];
+  int bad = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int p = 0; p <= q; ++p) {
+        const int a = ta + 16 * p, b = tb + 16 * q;
+        float vh = 0.0f, vl = 0.0f;
+        if (a <= b && b < l) {
+          double g = ldexp(G[a + (int64_t)b * l], k2);
+          if (attempt == 1 && a == b) g += s_shift;
+          df_from_f64(g, vh, vl);
+        }
+        rh[blk36(p, q)] = vh;
+        rl[blk36(p, q)] = vl;
+      }
+    bad = 0;
+#pragma unroll
+    for (int pj = 0; pj < 8; ++pj) {
+      if (16 * pj >= l || bad) continue;
+      for (int tj = 0; tj < 16; ++tj) {
+        const int j = 16 * pj + tj;
+        if (j >= l) break;
+        if (ta == tj && tb == tj) {            // the pivot, once: R_jj = sqrt(d), 1 / R_jj in double-float
+          const float dh = rh[blk36(pj, pj)], dl = rl[blk36(pj, pj)];
+          const int b0 = !(dh > 0.0f) || !isfinite(dh);
+          s_bad = b0;
+          if (!b0) {
+            const float sq = __fsqrt_rn(dh);   // one Newton step on sq^2 = d
+            const float pr = sq * sq;
+            const float pe = fmaf(sq, sq, -pr);
+            const float c = (((dh - pr) - pe) + dl) * (0.5f / sq);
+            float jh, jl;
+            df_fast_two_sum(sq, c, jh, jl);
+            const float iv = __frcp_rn(jh);    // one Newton step on R_jj x = 1
+            const float er = fmaf(-jh, iv, 1.0f) - jl * iv;
+            float ih, il;
+            df_fast_two_sum(iv, er * iv, ih, il);
+            rih[j] = ih;
+            ril[j] = il;
+            rh[blk36(pj, pj)] = jh;
+            rl[blk36(pj, pj)] = jl;
+          }
+        }
+        __syncthreads();
+        if (s_bad) { bad = 1; break; }         // uniform across the block
+        if (ta == tj) {                        // row j: scale, publish
+          const float ih = rih[j], il = ril[j];
+#pragma unroll
+          for (int q = pj; q < 8; ++q) {
+            const int b = tb + 16 * q;
+            if (b > j && b < l) {
+              float vh, vl;
+              df_mul(rh[blk36(pj, q)], rl[blk36(pj, q)], ih, il, vh, vl);
+              rh[blk36(pj, q)] = vh;
+              rl[blk36(pj, q)] = vl;
+              rowh[b] = vh;
+              rowl[b] = vl;
+            }
+          }
+        }
+        __syncthreads();
+        float rah[8], ral[8], rbh[8], rbl[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int a = ta + 16 * p, b = tb + 16 * p;
+          const bool ua = p >= pj && a > j && a < l, ub = p >= pj && b > j && b < l;
+          rah[p] = ua ? rowh[a] : 0.0f;
+          ral[p] = ua ? rowl[a] : 0.0f;
+          rbh[p] = ub ? rowh[b] : 0.0f;
+          rbl[p] = ub ? rowl[b] : 0.0f;
+        }
+#pragma unroll
+        for (int q = pj; q < 8; ++q)
+#pragma unroll
+          for (int p = pj; p <= q; ++p) {
+            const int a = ta + 16 * p, b = tb + 16 * q;
+            if (a > j && a <= b && b < l)
+              df_fnms(rh[blk36(p, q)], rl[blk36(p, q)], rah[p], ral[p], rbh[q], rbl[q]);
+          }
+      }
+    }
+    __syncthreads();
+    if (!bad) break;
+    if (tid == 0) {
+      if (attempt == 0) atomicOr(&h.res->flags, FLAG_SHIFTED);
+      else { fail = 1; atomicOr(&h.res->flags, FLAG_CHOL_FAIL); }
+    }
+    __syncthreads();
+    if (fail) return;
+  }
+  const int k = s_k;
+  // R = (hi + lo) 2^-k (upper, zero below) -> h.R
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int p = 0; p <= q; ++p) {
+      const int a = ta + 16 * p, b = tb + 16 * q;
+      if (a <= b && b < l)
+        h.R[a + (int64_t)b * l] = ldexp(f32_to_f64(rh[blk36(p, q)]) + f32_to_f64(rl[blk36(p, q)]), -k);
+    }
+  for (int b = tb; b < l; b += 16)
+    for (int a = ta; a < l; a += 16)
+      if (a > b) { h.R[a + (int64_t)b * l] = 0.0; h.Ri[a + (int64_t)b * l] = 0.0; }
+  // R^{-1} = R'^{-1} 2^k in FP32 from R' rounded to FP32 (its hi parts)
+  float* rinv = (float*)(ibuf + 2 * 2 * 128 * sizeof(float));
+  if (ta == tb) {
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (ta + 16 * p < l) rinv[ta + 16 * p] = 1.0f / rh[blk36(p, p)];
+  }
+  __syncthreads();
+  float (*rowx)[128] = (float (*)[128])ibuf;
+  float (*colr)[128] = (float (*)[128])(ibuf + 2 * 128 * sizeof(float));
+  reg_tri_inv<float>(rh, rinv, rowx, colr, l, ta, tb);
+  float* ri32 = h.Ri32;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int p = 0; p <= q; ++p) {
+      const int a = ta + 16 * p, b = tb + 16 * q;
+      if (a <= b && b < l) {
+        const float x = ldexpf(rh[blk36(p, q)], k);
+        h.Ri[a + (int64_t)b * l] = f32_to_f64(x);
+        if (ri32) ri32[a + (int64_t)b * l] = x;
+      }
+    }
+  if (ri32)
+    for (int b = tb; b < l; b += 16)
+      for (int a = ta; a < l; a += 16)
+        if (a > b) ri32[a + (int64_t)b * l] = 0.0f;
+}
+
 void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32_inverse,
                      cudaStream_t st, int f32_chol, int conditional) {
   // the factor (stride l+1) and the l reciprocals of its diagonal; the FP32
@@ -575,7 +789,8 @@ void launch_chol_inv(const Chan* d_ch, int C, int accumulate, int max_l, int f32
   const int use_smem = bytes <= 200 * 1024;
   if (max_l <= 128 && !accumulate) {
     if (f32_chol) k_chol_inv_reg<float><<<C, 256, 0, st>>>(d_ch, 1, conditional);
-    else k_chol_inv_reg<double><<<C, 256, 0, st>>>(d_ch, f32_inverse, conditional);
+    else if (f32_inverse) k_chol_df<<<C, 256, 0, st>>>(d_ch, conditional);     // the mixed path
+    else k_chol_inv_reg<double><<<C, 256, 0, st>>>(d_ch, 0, conditional);
     note_launch();
     return;
   }
@@ -791,7 +1006,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const Chan* __restrict__ ch, int
 // every pair of a round), and each lane keeps its NV float4 of both columns
 // in registers between the dot products and the rotation.  Same pair
 // schedule, summation order, rotation formulas and stopping rule as
-// k_jacobi<float, false>, so the same results.
+// k_jacobi<float, false>, so the same results (M is held scaled by an exact
+// power of two, which changes no rounding unless the unscaled squares would
+// overflow).
 template <int NV>
 __global__ void __launch_bounds__(512) k_jacobi_f32s(const Chan* __restrict__ ch, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char sraw[];
@@ -800,13 +1017,31 @@ __global__ void __launch_bounds__(512) k_jacobi_f32s(const Chan* __restrict__ ch
   const int l = h.l;
   const int m = l + (l & 1);
   float* Mw = (float*)sraw;
+  __shared__ float smx[16];
+  float mx = 0.0f;
   for (int e = threadIdx.x; e < lp * l; e += blockDim.x) {
     const int i = e % lp, j = e / lp;
-    Mw[e] = (i < l) ? (float)h.R[j + (int64_t)i * l] : 0.0f;      // M = R^T
+    const float v = (i < l) ? (float)h.R[j + (int64_t)i * l] : 0.0f;      // M = R^T
+    Mw[e] = v;
+    mx = fmaxf(mx, fabsf(v));
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) smx[warp] = mx;
+  __syncthreads();
+  mx = 0.0f;
+#pragma unroll
+  for (int w = 0; w < 16; ++w) mx = fmaxf(mx, smx[w]);
+  // M 2^-e with its largest entry in [1/2, 1), so that the squared norms and
+  // their products below cannot overflow (scale 1 for a zero or non-finite
+  // M); an exact power of two, undone before the finish
+  const int ex = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+  const int es = (ex == 0 || ex == 0xFF) ? 0 : ex - 126;
+  if (es != 0)
+    for (int e = threadIdx.x; e < lp * l; e += blockDim.x) Mw[e] = ldexpf(Mw[e], -es);
   __syncthreads();
   const float thr = (float)l * 5.9604645e-8f;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane >> 3, gl = lane & 7;
   const int pi = warp * 4 + grp;                   // this group's pair slot
   const int npairs = m / 2;
@@ -867,6 +1102,10 @@ __global__ void __launch_bounds__(512) k_jacobi_f32s(const Chan* __restrict__ ch
       if (r < m - 2) __syncthreads();
     }
     if (!__syncthreads_or(rotated)) break;         // also the barrier after the last round
+  }
+  if (es != 0) {
+    for (int e = threadIdx.x; e < lp * l; e += blockDim.x) Mw[e] = ldexpf(Mw[e], es);
+    __syncthreads();
   }
   jacobi_finish<float, false, true>(h, Mw, (const float*)nullptr, lp, l, sweep, max_sweeps);
 }
@@ -971,7 +1210,14 @@ void launch_jacobi(const Chan* d_ch, int C, int fp32, int max_l, cudaStream_t st
   const int sweeps = jacobi_max_sweeps();
   if (fp32 && max_l <= 128) {
     const int nv = (max_l + 31) / 32;
-    const int b2 = max_l * 32 * nv * (int)sizeof(float);
+    int b2 = max_l * 32 * nv * (int)sizeof(float);
+    // one wave of channels: take most of the shared memory, so that no other
+    // kernel's block (the probe block runs beside this one on a second
+    // stream) shares the SM with this latency-bound one
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        C <= nsm && b2 < 200 * 1024)
+      b2 = 200 * 1024;
     void (*kf)(const Chan*, int) = nv == 1 ? k_jacobi_f32s<1> : nv == 2 ? k_jacobi_f32s<2>
                                  : nv == 3 ? k_jacobi_f32s<3> : k_jacobi_f32s<4>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, b2);

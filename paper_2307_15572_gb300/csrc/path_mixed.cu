@@ -820,10 +820,13 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
   // energies
   bool narrow = true;                                     // the narrow probe kernels: s <= 32, 32 <= l <= 256
   for (int c = 0; c < J.C; ++c)
-    narrow = narrow && J.d[c].s <= 32 && J.d[c].l >= 32 && J.d[c].l <= 256 && ch[c].Ri32;
+    narrow = narrow && J.d[c].s <= 32 && J.d[c].l >= 32 && J.d[c].l <= 256 && ch[c].C32;
   std::vector<SumsqDesc> sd(J.C);
   for (int c = 0; c < J.C; ++c)
     sd[c] = SumsqDesc{ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt, J.d[c].ldt, J.d[c].n, J.d[c].s, 4, ch[c].est_part};
+  const ProbeDesc* dtn = nullptr;
+  const ProbeDesc* dnn = nullptr;
+  int ptb = 0, pnb = 0;
   if (narrow) {
     std::vector<ProbeDesc> tn(J.C), nn(J.C);
     int tb = 0, nb = 0;
@@ -837,7 +840,7 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
       p.splits = cdiv(d.n, p.split_rows);
       p.part = ch[c].gpart;
       p.C = ch[c].C64;
-      p.C32 = ch[c].Ri32;                                   // l x l FP32 scratch, free here (l >= 32)
+      p.C32 = ch[c].C32;
       p.tile0 = tb;
       tn[c] = p;
       tb += p.splits * cdiv(d.l, 128);
@@ -845,12 +848,10 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
       nn[c] = p;
       nb += cdiv(d.n, 128);
     }
-    const ProbeDesc* dtn = J.ar.put(tn.data(), tn.size());
-    const ProbeDesc* dnn = J.ar.put(nn.data(), nn.size());
-    J.steps.push_back([=]() {
-      launch_probe_block(dtn, dnn, C, tb, nb, st);
-      return RSVD_OK;
-    });
+    dtn = J.ar.put(tn.data(), tn.size());
+    dnn = J.ar.put(nn.data(), nn.size());
+    ptb = tb;
+    pnb = nb;
   } else {
     add_tn(J, MMK_GRAM_F32, [&](int c) { return (const void*)ch[c].Q32; },
            [&](int c) { return (const void*)(ch[c].Y32 + (int64_t)J.d[c].l * J.d[c].ldt); },
@@ -873,17 +874,48 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
     }
     add_mm(J, c32 ? MMK_NN_F32 : MMK_NN_F32_F64B, md);
   }
-  {
-    const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
-    const int s_max = NPROBE;
+  const SumsqDesc* dsd = J.ar.put(sd.data(), sd.size());
+  const int s_max = NPROBE;
+  if (!narrow)
     J.steps.push_back([=]() {
       launch_colsumsq(dsd, C, s_max, st);
       return RSVD_OK;
     });
-  }
   const int maxl = J.max_l;
   // W^T W = R^T R
   add_gram32(J, [&](int c) { return (const float*)ch[c].Y32; }, false);
+  // The narrow probe block runs on a second stream beside the Cholesky and
+  // the Jacobi of W (one CTA per channel each): it reads Q and the probe
+  // columns of Y32, writes C, its FP32 copy, the Gram partials (consumed by
+  // now) and the probe columns, none of which those two read or write; the
+  // main stream waits for it before the next use of the partials.
+  // Only with l <= 128 (the one-CTA shared-memory Cholesky and Jacobi; the
+  // cooperative forms for large l need every CTA resident at once).
+  rsvd_plan_s* P = J.P;
+  const bool overlap = narrow && maxl <= 128;
+  if (narrow && !overlap)
+    J.steps.push_back([=]() {
+      launch_probe_block(dtn, dnn, C, ptb, pnb, st);
+      launch_colsumsq(dsd, C, s_max, st);
+      return RSVD_OK;
+    });
+  if (overlap) {
+    if (!P->side) {
+      CK(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming));
+    }
+    cudaStream_t side = P->side;
+    cudaEvent_t fork_ev = P->fork_ev, join_ev = P->join_ev;
+    J.steps.push_back([=]() {
+      CK(cudaEventRecord(fork_ev, st));
+      CK(cudaStreamWaitEvent(side, fork_ev, 0));
+      launch_probe_block(dtn, dnn, C, ptb, pnb, side);
+      launch_colsumsq(dsd, C, s_max, side);
+      CK(cudaEventRecord(join_ev, side));
+      return RSVD_OK;
+    });
+  }
   add_chol(J, 0);
   const int policy = J.policy;
   const double tol = J.tol;
@@ -895,6 +927,13 @@ rsvd_status build_mixed(Job& J, bool skip_convert) {
     run_jacobi(dch, ls, 1, maxl, coop, derr_w, st);
     return RSVD_OK;
   });
+  if (overlap) {                                 // join before the re-orthonormalisation (its Gram uses the partials)
+    cudaEvent_t join_ev = P->join_ev;
+    J.steps.push_back([=]() {
+      CK(cudaStreamWaitEvent(st, join_ev, 0));
+      return RSVD_OK;
+    });
+  }
   const Chan* dsw = reorth_x(J);                 // X~ in J
   J.steps.push_back([=]() {
     launch_probe_finish(dsw, C, maxl, st);

@@ -497,6 +497,7 @@ void layout(Job& J, Bump& b) {
         h.nn_fexp = b.take<int>(128);
       }
       h.C64 = b.take<double>((size_t)d.l * std::max(d.s, 1));
+      h.C32 = b.take<float>((size_t)d.l * 32);
       h.est_part = b.take<double>((size_t)std::max(d.s, 1) * (1 + d.l));
     }
     if (F.mem == RSVD_MEM_HOST) {

@@ -56,3 +56,32 @@ def test_seed_spread_within_hmt_bound(lib, prec):
     print(f"{prec}: mean {errs.mean():.4f} sd {errs.std():.4f} bound {bound:.4f} tail {tail:.4f}")
     assert errs.mean() - 3 * errs.std() / np.sqrt(len(errs)) <= bound
     assert errs.min() >= np.sqrt(np.sum(sig[k + p:] ** 2)) * (1 - 1e-6)
+
+
+def test_mixed_power_of_two_scale_invariance(lib):
+    """V and 2^(+-36) V on the mixed path: the steps of the method commute
+    with an exact power of two up to FP32 rounding (the word splitting, the
+    sliced Grams and products take per-row/column exponents, the
+    double-float Cholesky and the FP32 Jacobi rescale their input), so the
+    rank and the scaled singular values agree, and the relative errors to
+    1e-4 of their value (measured: 2.6e-5 at 2^36).  Without
+    the Jacobi's rescaling, the products of squared column norms of 2^36 V
+    (about 2^144) overflow FP32 and those of 2^-36 V underflow."""
+    import torch
+    mats = [synth.batch_channel(c, n) for c, n in enumerate([3000, 2200])]
+    out = {}
+    for e in (0, 36, -36):
+        plan = lib.Plan(3000, k=118, p=10, q=0, seed=4, tol=1e-4, policy="tol", precision="bf16x", slices=2)
+        try:
+            ts = [torch.as_tensor(np.ldexp(A, e), device="cuda") for A in mats]
+            st, res = plan.decompose_batched(ts, 128)
+            assert st >= 0, lib.last_error()
+            out[e] = [(r["k"], np.ldexp(r["S"].cpu().numpy(), -e), plan.reconstruct_error(t, r))
+                      for t, r in zip(ts, res)]
+        finally:
+            plan.close()
+    for e in (36, -36):
+        for (k0, s0, e0), (k1, s1, e1) in zip(out[0], out[e]):
+            assert k1 == k0, (e, k0, k1)
+            assert np.max(np.abs(s1[:k0] - s0[:k0])) <= 1e-6 * s0[0], e
+            assert e1 <= 1e-4 and abs(e1 - e0) <= 1e-4 * e0, (e, e0, e1)
