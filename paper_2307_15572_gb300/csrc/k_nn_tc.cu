@@ -269,7 +269,9 @@ k_nn_tc(const NnTcDesc* __restrict__ nd, int C, int tiles, int* __restrict__ err
       mma_commit(bar_m);          // also after a failed wait: completes when prior MMAs do
     }
 
-    // ---- epilogue
+    // ---- epilogue (the error word is read before the wait, so that its
+    // load overlaps the products)
+    const int errv = *(volatile int*)err;
     int ok = 1;
     if (lane == 0) ok = mbar_wait(bar_m, (uint32_t)(it & 1)) ? 1 : 0;
     ++it;
@@ -278,7 +280,7 @@ k_nn_tc(const NnTcDesc* __restrict__ nd, int C, int tiles, int* __restrict__ err
       if (lane == 0) set_err(err, DERR_TIMEOUT_EPI);
       healthy = false;
     }
-    if (healthy) healthy = (*(volatile int*)err == 0);
+    if (healthy) healthy = errv == 0;
     tc_fence_after();
     if (healthy) {
       const int i = qd * 32 + lane;                   // tile row

@@ -565,8 +565,9 @@ __global__ void __launch_bounds__(256) k_chol_inv_reg(const Chan* __restrict__ c
 }
 
 // The mixed path's factor in double-float arithmetic (pairs hi + lo of FP32
-// numbers, |lo| <= ulp(hi) / 2: about 48 significant bits; Dekker, 1971, and
-// the TwoSum of Knuth).  Same register layout, pivot order, shift and
+// numbers, about 48 significant bits; Dekker, 1971, and the TwoSum of Knuth;
+// the trailing update keeps each pair in the unnormalised Sum2 form below
+// until its row is the pivot row).  Same register layout, pivot order, shift and
 // retry as k_chol_inv_reg, with every FP64 operation of the column steps
 // replaced by FP32 instructions (this part issues FP64 arithmetic at a small
 // fraction of its FP32 rate).  The Gram is first scaled by an exact power of
@@ -593,16 +594,19 @@ RSVD_DEV void df_mul(float xh, float xl, float yh, float yl, float& rh, float& r
   e = fmaf(xl, yh, e);
   df_fast_two_sum(pr, e, rh, rl);
 }
-// (ah, al) -= (xh, xl) (yh, yl)
-RSVD_DEV void df_fnms(float& ah, float& al, float xh, float xl, float yh, float yl) {
+// (ah, al) -= (xh, xl) (yh, yl), leaving the pair unnormalised: ah is the
+// running FP32 sum and al collects every rounding error (the TwoSum error
+// and the product's error terms), as in Sum2 / Dot2 of Ogita, Rump & Oishi
+// (2005); the pair is renormalised once, when its row becomes the pivot row.
+RSVD_DEV void df_fnms_lazy(float& ah, float& al, float xh, float xl, float yh, float yl) {
   const float pr = xh * yh;
   float e = fmaf(xh, yh, -pr);
   e = fmaf(xh, yl, e);
   e = fmaf(xl, yh, e);
   float sh, sl;
   df_two_sum(ah, -pr, sh, sl);
-  sl += al - e;
-  df_fast_two_sum(sh, sl, ah, al);
+  ah = sh;
+  al += sl - e;
 }
 RSVD_DEV void df_from_f64(double g, float& h, float& l) {
   h = f64_to_f32_rn(g);
@@ -669,7 +673,8 @@ __global__ void __launch_bounds__(256, 1) k_chol_df(const Chan* __restrict__ ch,
         const int j = 16 * pj + tj;
         if (j >= l) break;
         if (ta == tj && tb == tj) {            // the pivot, once: R_jj = sqrt(d), 1 / R_jj in double-float
-          const float dh = rh[blk36(pj, pj)], dl = rl[blk36(pj, pj)];
+          float dh, dl;
+          df_two_sum(rh[blk36(pj, pj)], rl[blk36(pj, pj)], dh, dl);
           const int b0 = !(dh > 0.0f) || !isfinite(dh);
           s_bad = b0;
           if (!b0) {
@@ -697,8 +702,9 @@ __global__ void __launch_bounds__(256, 1) k_chol_df(const Chan* __restrict__ ch,
           for (int q = pj; q < 8; ++q) {
             const int b = tb + 16 * q;
             if (b > j && b < l) {
-              float vh, vl;
-              df_mul(rh[blk36(pj, q)], rl[blk36(pj, q)], ih, il, vh, vl);
+              float uh, ul, vh, vl;
+              df_two_sum(rh[blk36(pj, q)], rl[blk36(pj, q)], uh, ul);
+              df_mul(uh, ul, ih, il, vh, vl);
               rh[blk36(pj, q)] = vh;
               rl[blk36(pj, q)] = vl;
               rowh[b] = vh;
@@ -723,7 +729,7 @@ __global__ void __launch_bounds__(256, 1) k_chol_df(const Chan* __restrict__ ch,
           for (int p = pj; p <= q; ++p) {
             const int a = ta + 16 * p, b = tb + 16 * q;
             if (a > j && a <= b && b < l)
-              df_fnms(rh[blk36(p, q)], rl[blk36(p, q)], rah[p], ral[p], rbh[q], rbl[q]);
+              df_fnms_lazy(rh[blk36(p, q)], rl[blk36(p, q)], rah[p], ral[p], rbh[q], rbl[q]);
           }
       }
     }
