@@ -526,7 +526,7 @@ def run_gpu(args):
                           "channels": args.channels, "sum_n2_per_gpu": entries, "tol": TOL, "l": L_COLS,
                           "q": 0, "words": 2, "policy": "tol",
                           "precision": "V and X as 2 BF16 words, FP32 accumulate; FP64-grade Grams (exact BF16 "
-                                       "slices on the tensor cores), FP64 Cholesky",
+                                       "slices on the tensor cores), double-float (FP64-grade) Cholesky",
                           "l2": "inputs larger than L2 (no flush)", "max_rel_err": max_err,
                           "verified_tol": bool(max_err <= TOL), "ranks": [min(ks), max(ks)],
                           "parallelism": ("fixed set split by LPT over %d GPUs" % ws if args.split == "fixed"
