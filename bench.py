@@ -133,23 +133,32 @@ def bf16_peak(sustained=False):
     return (1700.0 if sustained else 1900.0), "fallback"
 
 
-def tc_traffic_record():
-    """ncu DRAM bytes of the tensor-core pass, per algorithmic byte, from the
-    committed profile summary -- only if the kernel source is unchanged."""
-    p = os.path.join(ROOT, "profiles", "tc_gemm_batch40.md")
-    src = os.path.join(ROOT, "paper_2307_15572_gb300", "csrc", "k_tc.cu")
-    if not os.path.exists(p):
+def traffic_record(summary, source):
+    """ncu DRAM bytes of a kernel per algorithmic byte, from a committed profile
+    summary -- only if the kernel's source file is unchanged since the capture
+    (the summary records its SHA-256 prefix)."""
+    p = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2307_15572_gb300", "csrc", source)
+    if not os.path.exists(p) or not os.path.exists(src):
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     rec = {}
     for line in open(p):
         if line.startswith("traffic_per_algorithmic_byte:"):
             rec["ratio"] = float(line.split(":")[1])
-        if line.startswith("k_tc_source_sha256_16:"):
+        if line.startswith("source_sha256_16:"):
             rec["sha"] = line.split(":")[1].strip()
     if rec.get("sha") != h or "ratio" not in rec:
         return None
     return rec["ratio"]
+
+
+def tc_traffic_record():
+    return traffic_record("tc_gemm_batch40.md", "k_tc.cu")
+
+
+def cvt_traffic_record():
+    return traffic_record("convert_omega_batch8.md", "k_mixed.cu")
 
 
 class Clocks:
@@ -322,13 +331,15 @@ def run_gpu(args):
     plan.close()
     hbm_peak, peak_kind = peaks()
     ratio = tc_traffic_record()
+    cvt_ratio = cvt_traffic_record()
     kern = []
     if prof["cvt_launches"]:
         c_ms = prof["cvt_ms"] / prof["cvt_launches"]
         c_bytes = prof["cvt_bytes"] / prof["cvt_launches"]
         c_ach = c_bytes / (c_ms / 1e3) / 1e9
         kern.append({"bound": "hbm", "achieved": c_ach, "peak": hbm_peak, "unit": "GB/s", "frac": c_ach / hbm_peak,
-                     "traffic": None, "kernel": "k_convert_omega (FP64 V -> BF16 words, ||V||^2, P)",
+                     "traffic": (cvt_ratio * c_bytes) if cvt_ratio else None,
+                     "kernel": "k_convert_omega (FP64 V -> BF16 words, ||V||^2, P)",
                      "peak_source": peak_kind, "launches": prof["cvt_launches"], "avg_launch_ms": c_ms,
                      "algorithmic_bytes_per_launch": c_bytes,
                      "bytes_per_unit": "8 B read + 2 B per word written per V entry, + P words",
